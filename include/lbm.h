@@ -1,0 +1,197 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) reactive multi-component lattice Boltzmann step.
+ *
+ * The library advances the coupled CooLBM models (Alamian, Nayak, Shadloo, arXiv 2502.12955)
+ * on one GPU: a D2Q9 / D3Q19 flow lattice per fluid component with the Shan-Chen
+ * pseudopotential force (Sec. 2.1.1, Eq. 1.11-1.16), Guo or Shan-Chen velocity-shift forcing
+ * (Sec. 2.1.2-2.1.3, Eq. 1.17-1.21), D2Q5 / D3Q7 advection-diffusion lattices for solute and
+ * temperature (Sec. 2.1.5, Eq. therpop_species, therpopeq_species), halfway bounce-back, the
+ * Kang wet-node reactive boundary (Eq. wetnode9), and the geometry update driven by reaction
+ * (solid consumption, Sec. 2.1.5) or deposition (Sec. 3.3, Eq. surface_deposition).
+ *
+ * Conventions shared by every call:
+ *  - Node index n = x + nx*(y + ny*z), x fastest; 2D domains use nz == 1.
+ *  - Flags: 0 fluid, 1 inert solid, 2 reactive solid.
+ *  - The library owns all device memory.  Host pointers belong to the caller and are only
+ *    read or written during the call.  Fields cross the boundary in FP64.
+ *  - Every call returns an lbm_status; no call aborts the process.  On error,
+ *    lbm_last_error() holds a one-line message.
+ *  - Work is enqueued on params.stream (a cudaStream_t, NULL for the legacy default stream).
+ *    lbm_step returns after enqueueing.  Calls that return data synchronise that stream.
+ *  - One context is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+  LBM_OK = 0,
+  LBM_ERR_INVALID_ARG = -1,  /* argument out of range; nothing was changed */
+  LBM_ERR_OOM = -2,          /* device or host allocation failed */
+  LBM_ERR_CUDA = -3,         /* a CUDA runtime call failed (message in lbm_last_error) */
+  LBM_ERR_NONFINITE = -4,    /* a monitor evaluation found non-finite populations */
+  LBM_ERR_TIMEOUT = -5,      /* a bounded device wait ran out */
+  LBM_ERR_STATE = -6,        /* call out of order (e.g. step before fields were set) */
+  LBM_ERR_CAPACITY = -7      /* a device work list overflowed; results after it are invalid */
+} lbm_status;
+
+typedef enum lbm_lattice {
+  LBM_D2Q9_D2Q5 = 2,   /* D2Q9 flow (Table D2Q9, axis weights 1/9) + D2Q5 scalars (Table D2Q5) */
+  LBM_D3Q19_D3Q7 = 3   /* D3Q19 flow (Table D3Q19) + D3Q7 scalars */
+} lbm_lattice;
+
+typedef enum lbm_precision {
+  LBM_FP64 = 0,          /* populations and arithmetic in FP64 */
+  LBM_FP32 = 1,          /* populations and arithmetic in FP32 */
+  LBM_FP16_SHIFTED = 2,  /* stored as FP16 deviation from w_i * reference, FP32 arithmetic */
+  LBM_BF16_SHIFTED = 3   /* stored as BF16 deviation from w_i * reference, FP32 arithmetic */
+} lbm_precision;
+
+enum { LBM_FORCING_GUO = 0, LBM_FORCING_SC_SHIFT = 1 };
+enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_MRT = 1 };
+enum { LBM_PSI_EXP = 0, LBM_PSI_IDENTITY = 1 };
+enum { LBM_GEO_NONE = 0, LBM_GEO_DISSOLVE = 1, LBM_GEO_DEPOSIT = 2 };
+
+/* Case parameters (the paper's problem statement: lattice, relaxation times, forces,
+   reaction constants, boundary values).  Fill with lbm_params_default() first. */
+typedef struct lbm_params {
+  int32_t precision;          /* lbm_precision */
+  int32_t n_comp;             /* fluid components sigma: 1 or 2 */
+  double tau[2];              /* relaxation time per component, > 0.5 (Eq. 1.16) */
+  double G[2][2];             /* cohesion G_{sigma,sigma~} (Eq. 1.12-1.14); all zero disables it */
+  double G_ads[2];            /* adhesion G_ads,sigma (Eq. 1.15) */
+  double rho_solid;           /* density whose psi solid neighbours carry (Eq. 1.13) */
+  int32_t psi_kind;           /* LBM_PSI_EXP (Eq. 1.11, rho0) or LBM_PSI_IDENTITY (psi = rho) */
+  double rho0;                /* reference density of Eq. 1.11 */
+  int32_t forcing;            /* LBM_FORCING_GUO (Eq. 1.19-1.21) or LBM_FORCING_SC_SHIFT (1.17-1.18) */
+  double g[3];                /* body acceleration: F_body^sigma = rho^sigma g */
+  int32_t collision;          /* LBM_COLLISION_BGK or LBM_COLLISION_MRT (single component, Guo) */
+  double s_e, s_eps, s_q, s_pi, s_m;  /* MRT rates of the energy, energy-square, heat-flux,
+                                          ghost-stress and cubic moment groups; stress uses 1/tau */
+  int32_t n_scal;             /* advection-diffusion lattices: 0, 1 or 2; scalar 0 reacts */
+  double tau_c[2];            /* scalar relaxation times, > 0.5 (Eq. therpop_species) */
+  double J0;                  /* rest weight of D2Q5 / D3Q7, in [0, 1) */
+  double k_react;             /* first-order surface rate k of scalar 0 at reactive links */
+  int32_t ade_open_x;         /* 1: scalar inlet at x = 0 (value C_in) and zero-gradient outlet
+                                 at x = nx-1; the flow lattice keeps its own periodicity */
+  double C_in[2];
+  int32_t periodic[3];        /* flow-lattice periodicity per axis; a closed axis has walls */
+  int32_t geo_mode;           /* LBM_GEO_NONE / DISSOLVE / DEPOSIT */
+  double V_m;                 /* solid mass per unit reacted (dissolution) */
+  double m_s0;                /* solid mass of a reactive node (dissolution threshold) */
+  double DP;                  /* deposition probability (Eq. surface_deposition) */
+  int32_t deposit_conservative; /* 1: deposited particle mass leaves the populations */
+  int32_t N_geo;              /* geometry flips every N_geo steps (>= 1) */
+  int32_t N_mon;              /* automatic monitor + residual every N_mon steps (0: never) */
+  double rho_ref[2];          /* storage shift references for 16-bit modes (flow) */
+  double C_ref[2];            /* storage shift references for 16-bit modes (scalars) */
+  void* stream;               /* cudaStream_t for all work of this context */
+  int32_t block_x;            /* threads per block along x for the step kernel: 0 (automatic)
+                                 or a multiple of 32 up to 256 */
+  int32_t device;             /* CUDA device ordinal */
+} lbm_params;
+
+/* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */
+typedef struct lbm_monitors {
+  double step;                /* completed steps */
+  double mass[2];             /* sum of stored populations per component over fluid nodes */
+  double momentum[3];         /* sum_sigma sum_i c_i f_i over fluid nodes */
+  double species[2];          /* sum of stored scalar populations over fluid nodes */
+  double reacted;             /* cumulative reaction k C_b over reactive links (scalar 0) */
+  double inflow[2];           /* cumulative scalar entering through the inlet */
+  double outflow[2];          /* cumulative scalar leaving through the outlet */
+  double injected_mass[2];    /* added by dissolution flips */
+  double injected_species[2];
+  double removed_mass[2];     /* removed by deposition flips */
+  double removed_species[2];
+  double deposited;           /* cumulative deposited particle mass */
+  double n_solid;
+  double n_fluid;
+  double nonfinite;           /* fluid nodes holding a non-finite population */
+  double wall_exchange;       /* cumulative scalar-0 population loss through reactive links */
+  double residual;            /* last automatic residual (-1 if none yet) */
+} lbm_monitors;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *p with defaults: FP32, one component, tau 1, no forces, BGK, Guo, no scalars,
+   periodic box, no geometry update, N_geo 1, N_mon 0, device 0. */
+lbm_status lbm_params_default(lbm_params* p);
+
+/* Allocate a context for an nx x ny x nz domain (Sec. 2.1.4 lattices).  Validates every
+   parameter (tau > 0.5, n_comp, n_scal, J0, MRT only with one component and Guo forcing,
+   nz == 1 for 2D, nx >= 2 with ade_open_x).  Device memory: populations in SoA planes
+   pop[q][n], one in-place copy per lattice, plus flags, link masks and FP64 bookkeeping.
+   *out is NULL on error; lbm_last_error(NULL) then holds the reason. */
+lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz,
+                      const lbm_params* params, lbm_ctx** out);
+
+/* Copy the geometry (flags[n], n = nx*ny*nz bytes, host) and rebuild the link masks.  Resets
+   the per-node bookkeeping (consumed / deposited amounts) to zero.  Values above 2 are
+   rejected.  Call lbm_set_fields afterwards. */
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, size_t n);
+
+/* Initialise populations at equilibrium (Eq. 6, Eq. therpopeq_species) from host FP64 fields:
+   rho [n_comp][N], u [3][N] (2D: the z row is ignored), C [n_scal][N] (NULL when n_scal == 0).
+   Solid nodes are ignored.  Resets the step counter and all monitors. */
+lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* C,
+                          size_t n);
+
+/* Enqueue nsteps time steps (Sec. 2.1: collide-stream of every lattice, reactive closure,
+   geometry update every N_geo steps, monitors every N_mon steps). */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Wait for the context's stream; report device-side errors (LBM_ERR_CAPACITY,
+   LBM_ERR_NONFINITE from the automatic monitor). */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Copy macroscopic fields at the current time into caller buffers (any may be NULL):
+   rho [n_comp][N]; u [3][N], the physical velocity sum_sigma (j^sigma + F^sigma/2) / rho
+   (Eq. 1.19); C [n_scal][N] with the wet-node closure applied; flags [N]; acc [N], the
+   per-node consumed amount (reactive solids) or deposited fraction (deposition). */
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, double* C, uint8_t* flags,
+                          double* acc);
+
+/* Pre-collision populations at the current time, FP64, [n_comp][Qf][N] and [n_scal][Qc][N]
+   (either may be NULL).  Reactive-link scalar slots hold the stored bounce-back value. */
+lbm_status lbm_get_pops(lbm_ctx* ctx, double* f, double* h);
+lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f, const double* h);
+
+/* Evaluate the monitors now (FP64 reductions on the device) and copy them to *out. */
+lbm_status lbm_get_monitors(lbm_ctx* ctx, lbm_monitors* out);
+
+/* Relative L2 change of u and C (max of the two) over fluid nodes since the previous call;
+   -1 on the first call.  Replaces the stored snapshot. */
+lbm_status lbm_residual(lbm_ctx* ctx, double* r);
+
+/* Checkpoint: raw populations in storage precision, flags, bookkeeping, step counter (which
+   fixes the in-place layout parity) and cumulative monitors.  With host == NULL, *nbytes
+   receives the required size.  lbm_set_state restores a checkpoint of the same shape and
+   parameters bit for bit. */
+lbm_status lbm_get_state(lbm_ctx* ctx, void* host, size_t* nbytes);
+lbm_status lbm_set_state(lbm_ctx* ctx, const void* host, size_t nbytes);
+
+/* Device time of the fused step kernel: when enabled, lbm_step brackets every launch of it
+   with CUDA events on the context's stream.  lbm_profile_read synchronises and returns the
+   summed milliseconds and the number of launches since the last read. */
+lbm_status lbm_profile_enable(lbm_ctx* ctx, int32_t on);
+lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches);
+
+/* Kernel launches enqueued by this context since creation (all kernels of the library). */
+lbm_status lbm_launch_count(lbm_ctx* ctx, int64_t* launches);
+
+/* Message of the last failed call on ctx; with ctx == NULL, of the last failed lbm_create on
+   the calling thread. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,11 @@
+// inst_d3_bf16.cu -- kernels for lattice D3 with __nv_bfloat16 population storage.
+#include <type_traits>
+
+#include "launch.cuh"
+
+namespace lbm {
+const KernelSet& kernels_d3_bf16() {
+  static const KernelSet k = Launchers<D3, __nv_bfloat16>::make();
+  return k;
+}
+}  // namespace lbm

@@ -1,0 +1,1142 @@
+// kernels.cuh -- sm_103a kernels of the reactive multi-component LBM step.
+//
+// Storage: structure of arrays, one plane per direction, pop[i * pitch + n], n = x + nx*(y + ny*z).
+// Every lattice keeps ONE copy of its populations and streams in place with the A-A pattern:
+//   even steps (parity 0) read f_i(n) from slot (n, i) and write the post-collision f*_i to
+//   slot (n, opp i); odd steps (parity 1) read f_i(n) from (n - c_i, opp i) and write f*_i to
+//   (n + c_i, i).  A population that meets a wall is written to (n, opp i) at either parity
+//   (halfway bounce-back), and read back from (n, i).  Each slot is read and then written by
+//   the same thread within a step, so one pass reads and writes every population exactly once.
+// After an even number of steps the layout is natural (f_i(n) at (n, i)); after an odd number
+// it is swapped.  Every reader of the state (moments, monitors, flips, checkpoints) follows
+// the same rule.
+//
+// The reactive wet-node closure of scalar 0 (Eq. wetnode9) is applied when a node gathers its
+// populations: the stored value of a reactive link is the bounce-back value, and the closure
+// computes the unknown population from the gathered one moving toward the wall.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+// ------------------------------------------------------------------ storage
+
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+  using T = double;
+  static constexpr bool kShift = false;
+  __device__ static T ld(const double* p) { return __ldg(p); }
+  __device__ static T ldv(const double* p) { return *p; }
+  __device__ static void st(double* p, T v) { *p = v; }
+};
+template <>
+struct Store<float> {
+  using T = float;
+  static constexpr bool kShift = false;
+  __device__ static T ld(const float* p) { return __ldg(p); }
+  __device__ static T ldv(const float* p) { return *p; }
+  __device__ static void st(float* p, T v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+  using T = float;
+  static constexpr bool kShift = true;
+  __device__ static T ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static T ldv(const __half* p) { return __half2float(*p); }
+  __device__ static void st(__half* p, T v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  using T = float;
+  static constexpr bool kShift = true;
+  __device__ static T ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  __device__ static T ldv(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static void st(__nv_bfloat16* p, T v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------------------- arguments
+
+enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_CAS = 4 };
+enum : int { GEO_NONE = 0, GEO_DISSOLVE = 1, GEO_DEPOSIT = 2 };
+enum : uint8_t { FL_FLUID = 0, FL_SOLID = 1, FL_REACTIVE = 2, FL_FLIPPING = 3 };
+
+// Everything a kernel needs, in double; kernels convert to their compute type.
+struct Args {
+  void* f[2];
+  void* h[2];
+  void* psi[2];              // compute-type psi per component (Shan-Chen only)
+  uint8_t* flags;
+  uint32_t* mask;
+  double* acc;               // consumed (reactive solid) / deposited (fluid) per node
+  uint32_t* flip_list;
+  unsigned int* flip_count;
+  unsigned int flip_cap;
+  double* flip_scratch;      // [flip_cap][4]
+  double* flip_mon;          // [8] inj_mass[2], inj_spec[2], rem_mass[2], rem_spec[2]
+  int* err;
+  double* wallx_row;         // [rows]
+  double* inflow_row;        // [2][rows]
+  double* outflow_row;       // [2][rows]
+  double* partials;          // monitor partial sums [blocks][NMON]
+  double* mon_out;           // [NMON]
+  double* d_rho;             // FP64 staging [n_comp][N]
+  double* d_u;               // [3][N]
+  double* d_C;               // [n_scal][N]
+  double* snap_u;            // [3][N]
+  double* snap_C;            // [N]
+  long long pitch;           // elements per population plane (>= N, multiple of 32)
+  long long N;
+  int nx, ny, nz;
+  int n_comp, n_scal;
+  int per[3];                // flow periodicity
+  int open_x;                // scalar inlet / outlet on the x faces
+  int sc_on, ads_on, shift_forcing, psi_identity;
+  int geo_mode, deposit_conservative;
+  double tau[2], G[2][2], G_ads[2], psi_wall, rho0, g[3];
+  double s_grp[5];           // MRT rates: e, eps, q, pi, m
+  double tau_c[2], J0, k_react, C_in[2];
+  double V_m, m_s0, DP;
+  double rho_ref[2], C_ref[2];
+  int bx, by;                // step-kernel block shape
+};
+
+constexpr int NMON = 18;
+// partial-sum slots
+enum : int {
+  M_MASS = 0, M_MOM = 2, M_SPEC = 5, M_REACT = 7, M_DEPO = 8, M_IN = 9, M_OUT = 11,
+  M_WALLX = 13, M_NSOLID = 14, M_NFLUID = 15, M_NONFIN = 16, M_SPARE = 17
+};
+
+// ------------------------------------------------------------- indexing
+
+struct Nbr {
+  int x, y, z;
+  int xm, xp, ym, yp, zm, zp;
+  int nx, ny;
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    const int X = dx < 0 ? xm : (dx > 0 ? xp : x);
+    const int Y = dy < 0 ? ym : (dy > 0 ? yp : y);
+    const int Z = dz < 0 ? zm : (dz > 0 ? zp : z);
+    return X + nx * (Y + ny * Z);
+  }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Args& a, int x, int y, int z) {
+  Nbr b;
+  b.x = x; b.y = y; b.z = z;
+  b.nx = a.nx; b.ny = a.ny;
+  // always wrap: walls on closed axes are excluded by the link masks before any access
+  b.xm = x == 0 ? a.nx - 1 : x - 1;
+  b.xp = x == a.nx - 1 ? 0 : x + 1;
+  b.ym = y == 0 ? a.ny - 1 : y - 1;
+  b.yp = y == a.ny - 1 ? 0 : y + 1;
+  b.zm = z == 0 ? a.nz - 1 : z - 1;
+  b.zp = z == a.nz - 1 ? 0 : z + 1;
+  return b;
+}
+
+template <class L>
+__device__ __forceinline__ bool flow_wall(uint32_t m, int i) { return (m >> i) & 1u; }
+
+// ------------------------------------------------------------- gathers
+
+// Pre-collision flow populations of node n (as stored; shift added for 16-bit storage).
+template <class L, class S>
+__device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long pitch, int n,
+                                            uint32_t m, const Nbr& nb, int parity, double ref,
+                                            typename Store<S>::T* out) {
+  using T = typename Store<S>::T;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const S* p;
+    if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i))) {
+      p = f + (long long)i * pitch + n;
+    } else {
+      p = f + (long long)L::opp(i) * pitch + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+    }
+    T v = Store<S>::ld(p);
+    if (Store<S>::kShift) v += T(L::w(i)) * T(ref);
+    out[i] = v;
+  }
+}
+
+template <class L>
+__device__ __forceinline__ double scal_w(int j, double J0) {
+  return j == 0 ? J0 : (1.0 - J0) / double(L::QC - 1);
+}
+
+template <class L, class S>
+__device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long pitch, int n,
+                                            uint32_t m, const Nbr& nb, int parity, double ref,
+                                            double J0, typename Store<S>::T* out) {
+  using T = typename Store<S>::T;
+#pragma unroll
+  for (int j = 0; j < L::QC; ++j) {
+    const S* p;
+    if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0) {
+      p = h + (long long)j * pitch + n;
+    } else {
+      p = h + (long long)L::opp(j) * pitch + nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+    }
+    T v = Store<S>::ld(p);
+    if (Store<S>::kShift) v += T(scal_w<L>(j, J0) * ref);
+    out[j] = v;
+  }
+}
+
+// Wet-node closure (Eq. wetnode9 per link).  For direction j whose source n - c_j is a
+// reactive solid: C_b = 2 hb / (2 w + K), h_j = 2 w C_b - hb, hb = gathered h_{opp j}.
+// All closures use the values before closure.  Returns, through the callbacks' arguments,
+// the reaction rate k C_b per link and the stored-minus-closed exchange.
+template <class L, class T, class OnLink>
+__device__ __forceinline__ void close_scalar(T* h, uint32_t m, T wax, T Kr, OnLink on_link) {
+  T old[L::QC];
+#pragma unroll
+  for (int j = 0; j < L::QC; ++j) old[j] = h[j];
+#pragma unroll
+  for (int j = 1; j < L::QC; ++j) {
+    if (MaskBits<L>::code(m, L::opp(j)) == 2u) {
+      const T hb = old[L::opp(j)];
+      const T Cb = T(2) * hb / (T(2) * wax + Kr);
+      const T hn = T(2) * wax * Cb - hb;
+      h[j] = hn;
+      on_link(j, Cb, old[j] - hn);
+    }
+  }
+}
+
+// ---------------------------------------------------------- equilibria
+
+template <class L, class T>
+__device__ __forceinline__ T feq(int i, T rho, T ux, T uy, T uz) {
+  const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+  const T uu = ux * ux + uy * uy + uz * uz;
+  return T(L::w(i)) * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+}
+
+// Guo forcing term (Eq. 1.21) with c_s^2 = 1/3
+template <class L, class T>
+__device__ __forceinline__ T guo(int i, T ux, T uy, T uz, T Fx, T Fy, T Fz) {
+  const T cx = T(L::cx(i)), cy = T(L::cy(i)), cz = T(L::cz(i));
+  const T cu = cx * ux + cy * uy + cz * uz;
+  const T cF = cx * Fx + cy * Fy + cz * Fz;
+  const T uF = ux * Fx + uy * Fy + uz * Fz;
+  return T(L::w(i)) * (T(3) * (cF - uF) + T(9) * cu * cF);
+}
+
+// -------------------------------------------------------- flip list append
+
+__device__ __forceinline__ void push_flip(const Args& a, int n) {
+  const unsigned int k = atomicAdd(a.flip_count, 1u);
+  if (k < a.flip_cap)
+    a.flip_list[k] = (uint32_t)n;
+  else
+    atomicOr(a.err, ERR_CAPACITY);
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ================================================================ step
+
+// One fused time step for every fluid node: gather (A-A parity), wet-node closure and its
+// bookkeeping, deposition, moments, forces, velocity, flow collision (BGK / MRT, Guo or
+// velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
+template <class L, class S, int NC, int NS, int COLL>
+__global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool inside = (x < a.nx) && (y < a.ny);
+  const int n = inside ? x + a.nx * (y + a.ny * z) : 0;
+  const uint32_t m = inside ? a.mask[n] : 0u;
+  const bool active = (m & 1u) != 0u;
+  T wallx = T(0);
+  if (active) {
+    const Nbr nb = make_nbr(a, x, y, z);
+    const long long P = a.pitch;
+    const int row = y + a.ny * z;
+    // ---- gather
+    T f[NC][Q];
+#pragma unroll
+    for (int s = 0; s < NC; ++s)
+      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), P, n, m, nb, parity, a.rho_ref[s], f[s]);
+    T h[NS > 0 ? NS : 1][QC];
+    const T J0 = T(a.J0);
+    const T wax = T((1.0 - a.J0) / double(QC - 1));
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), P, n, m, nb, parity, a.C_ref[s], a.J0, h[s]);
+    // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
+    if (NS > 0) {
+      const T Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
+      const double kr = a.k_react;
+      const double Vm = a.V_m, ms0 = a.m_s0;
+      const bool dissolve = a.geo_mode == GEO_DISSOLVE;
+      close_scalar<L, T>(h[0], m, wax, Kr, [&](int j, T Cb, T exch) {
+        const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+        const double r = kr * double(Cb);
+        const double old = atomicAdd(a.acc + src, r);
+        if (dissolve && Vm * old < ms0 && Vm * (old + r) >= ms0) push_flip(a, src);
+        wallx += exch;
+      });
+      // ---- deposition at near-substrate nodes (Eq. surface_deposition)
+      if (a.geo_mode == GEO_DEPOSIT) {
+        bool near = false;
+#pragma unroll
+        for (int j = 1; j < QC; ++j) {
+          const uint32_t c = MaskBits<L>::code(m, j);
+          near |= (c == 1u || c == 2u);
+        }
+        if (near) {
+          T sum = T(0);
+#pragma unroll
+          for (int j = 0; j < QC; ++j) sum += h[0][j];
+          const double dep = a.DP * double(sum);
+          const double old = a.acc[n];
+          a.acc[n] = old + dep;
+          if (old <= 1.0 && old + dep > 1.0) push_flip(a, n);
+          if (a.deposit_conservative) {
+            const T keep = T(1.0 - a.DP);
+#pragma unroll
+            for (int j = 0; j < QC; ++j) h[0][j] *= keep;
+          }
+        }
+      }
+    }
+    // ---- moments (Eq. 1.7, 1.8)
+    T rho[NC], jx[NC], jy[NC], jz[NC];
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      T r = T(0), ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        r += f[s][i];
+        if (L::cx(i)) ax += T(L::cx(i)) * f[s][i];
+        if (L::cy(i)) ay += T(L::cy(i)) * f[s][i];
+        if (L::cz(i)) az += T(L::cz(i)) * f[s][i];
+      }
+      rho[s] = r; jx[s] = ax; jy[s] = ay; jz[s] = az;
+    }
+    // ---- forces: Shan-Chen cohesion / solid psi (Eq. 1.13, 1.14), adhesion (1.15), body
+    T Fx[NC], Fy[NC], Fz[NC];
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      Fx[s] = rho[s] * T(a.g[0]);
+      Fy[s] = rho[s] * T(a.g[1]);
+      Fz[s] = rho[s] * T(a.g[2]);
+    }
+    if (a.sc_on) {
+      T sx[NC], sy[NC], sz[NC];
+#pragma unroll
+      for (int s2 = 0; s2 < NC; ++s2) {
+        const T* ps = reinterpret_cast<const T*>(a.psi[s2]);
+        T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const T pv = flow_wall<L>(m, i) ? T(a.psi_wall) : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
+          const T wp = T(L::w(i)) * pv;
+          if (L::cx(i)) ax += T(L::cx(i)) * wp;
+          if (L::cy(i)) ay += T(L::cy(i)) * wp;
+          if (L::cz(i)) az += T(L::cz(i)) * wp;
+        }
+        sx[s2] = ax; sy[s2] = ay; sz[s2] = az;
+      }
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const T pself = reinterpret_cast<const T*>(a.psi[s])[n];
+#pragma unroll
+        for (int s2 = 0; s2 < NC; ++s2) {
+          const T Gss = T(a.G[s][s2]);
+          Fx[s] -= pself * Gss * sx[s2];
+          Fy[s] -= pself * Gss * sy[s2];
+          Fz[s] -= pself * Gss * sz[s2];
+        }
+      }
+    }
+    if (a.ads_on) {
+      T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (flow_wall<L>(m, i)) {
+          ax += T(L::w(i)) * T(L::cx(i));
+          ay += T(L::w(i)) * T(L::cy(i));
+          az += T(L::w(i)) * T(L::cz(i));
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const T ga = T(a.G_ads[s]) * rho[s];
+        Fx[s] -= ga * ax; Fy[s] -= ga * ay; Fz[s] -= ga * az;
+      }
+    }
+    // ---- physical / barycentric velocity (Eq. 1.19, 1.20)
+    T rt = T(0), mx = T(0), my = T(0), mz = T(0);
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      rt += rho[s];
+      mx += jx[s] + T(0.5) * Fx[s];
+      my += jy[s] + T(0.5) * Fy[s];
+      mz += jz[s] + T(0.5) * Fz[s];
+    }
+    const T irt = T(1) / rt;
+    const T ux = mx * irt, uy = my * irt, uz = mz * irt;
+    // ---- flow collision
+    if (a.shift_forcing) {
+      // Shan-Chen velocity shift (Eq. 1.17, 1.18), BGK, F_i = 0
+      T nxs = T(0), nys = T(0), nzs = T(0), den = T(0);
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const T it = T(1.0 / a.tau[s]);
+        nxs += jx[s] * it; nys += jy[s] * it; nzs += jz[s] * it;
+        den += rho[s] * it;
+      }
+      const T iden = T(1) / den;
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const T ts = T(a.tau[s]);
+        const T ir = T(1) / rho[s];
+        const T ex = nxs * iden + ts * Fx[s] * ir;
+        const T ey = nys * iden + ts * Fy[s] * ir;
+        const T ez = nzs * iden + ts * Fz[s] * ir;
+        const T om = T(1.0 / a.tau[s]);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[s][i] -= om * (f[s][i] - feq<L, T>(i, rho[s], ex, ey, ez));
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const T om = T(1.0 / a.tau[s]);
+        if (COLL == 0) {
+          // Eq. 1.16 with Guo forcing: f* = f + F_i - omega (f - f_eq + F_i / 2)
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const T Fi = guo<L, T>(i, ux, uy, uz, Fx[s], Fy[s], Fz[s]);
+            const T nq = f[s][i] - feq<L, T>(i, rho[s], ux, uy, uz) + T(0.5) * Fi;
+            f[s][i] = f[s][i] + Fi - om * nq;
+          }
+        } else {
+          // MRT: f* = f + F_i - M^-1 S M (f - f_eq + F_i / 2), written as BGK with rate
+          // 1/tau plus projections on the non-hydrodynamic groups with rate (s_g - 1/tau).
+          T nq[Q];
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const T Fi = guo<L, T>(i, ux, uy, uz, Fx[s], Fy[s], Fz[s]);
+            nq[i] = f[s][i] - feq<L, T>(i, rho[s], ux, uy, uz) + T(0.5) * Fi;
+            f[s][i] = f[s][i] + Fi - om * nq[i];
+          }
+          T coef[L::NMRT];
+#pragma unroll
+          for (int k = 0; k < L::NMRT; ++k) {
+            T mk = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              const double r = Mrt<L>::row(k, i);
+              if (r != 0.0) mk += T(r) * nq[i];
+            }
+            coef[k] = (T(a.s_grp[Mrt<L>::group(k)]) - om) * mk * T(1.0 / mrt_norm2<L>(k));
+          }
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            T c = T(0);
+#pragma unroll
+            for (int k = 0; k < L::NMRT; ++k) {
+              const double r = Mrt<L>::row(k, i);
+              if (r != 0.0) c += T(r) * coef[k];
+            }
+            f[s][i] -= c;
+          }
+        }
+      }
+    }
+    // ---- scalar collision (Eq. therpop_species, therpopeq_species), u = physical velocity
+    const T cs2c = T(2.0 * (1.0 - a.J0) / double(QC - 1));
+    const T ics2 = T(1) / cs2c;
+    T hpost[NS > 0 ? NS : 1][QC];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      T C = T(0);
+#pragma unroll
+      for (int j = 0; j < QC; ++j) C += h[s][j];
+      const T om = T(1.0 / a.tau_c[s]);
+#pragma unroll
+      for (int j = 0; j < QC; ++j) {
+        const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
+        const T wj = j == 0 ? J0 : wax;
+        const T he = wj * C * (T(1) + cu * ics2);
+        hpost[s][j] = h[s][j] - om * (h[s][j] - he);
+      }
+    }
+    // ---- scatter flow
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      S* fs = reinterpret_cast<S*>(a.f[s]);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        T v = f[s][i];
+        if (Store<S>::kShift) v -= T(L::w(i)) * T(a.rho_ref[s]);
+        S* p;
+        if (parity == 0 || i == 0 || flow_wall<L>(m, i))
+          p = fs + (long long)L::opp(i) * P + n;
+        else
+          p = fs + (long long)i * P + nb.at(L::cx(i), L::cy(i), L::cz(i));
+        Store<S>::st(p, v);
+      }
+    }
+    // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      S* hs = reinterpret_cast<S*>(a.h[s]);
+      const T sref = T(a.C_ref[s]);
+#pragma unroll
+      for (int j = 0; j < QC; ++j) {
+        const uint32_t code = j == 0 ? 0u : MaskBits<L>::code(m, j);
+        T v = hpost[s][j];
+        S* p;
+        if (code == 3u) {
+          // open face: the population arriving from outside replaces the one leaving
+          const int jb = L::opp(j);
+          T b;
+          if (L::cx(j) < 0) {
+            const T cu = T(L::cx(jb)) * ux + T(L::cy(jb)) * uy + T(L::cz(jb)) * uz;
+            b = wax * T(a.C_in[s]) * (T(1) + cu * ics2);
+            a.inflow_row[s * (a.ny * a.nz) + row] += double(b) - double(v);
+          } else {
+            b = hpost[s][jb];
+            a.outflow_row[s * (a.ny * a.nz) + row] += double(v) - double(b);
+          }
+          v = b;
+          p = hs + (long long)jb * P + n;
+        } else if (parity == 0 || j == 0 || code != 0u) {
+          p = hs + (long long)L::opp(j) * P + n;
+        } else {
+          p = hs + (long long)j * P + nb.at(L::cx(j), L::cy(j), L::cz(j));
+        }
+        if (Store<S>::kShift) v -= T(scal_w<L>(j, a.J0)) * sref;
+        Store<S>::st(p, v);
+      }
+    }
+    (void)row;
+  }
+  // ---- wall-exchange monitor: one atomic per warp that saw a reactive link
+  if (NS > 0) {
+    const unsigned int any = __ballot_sync(0xffffffffu, wallx != T(0));
+    if (any) {
+      // warps run along x inside one (y, z) row (block x extent is a multiple of 32)
+      const double w = warp_sum(double(wallx));
+      if ((threadIdx.x & 31) == 0 && y < a.ny) atomicAdd(a.wallx_row + (y + a.ny * z), w);
+    }
+  }
+}
+
+// ================================================================ psi
+
+template <class L, class S, int NC>
+__global__ void __launch_bounds__(256) k_psi(const Args a, const int parity) {
+  using T = typename Store<S>::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const int n = x + a.nx * (y + a.ny * z);
+  const uint32_t m = a.mask[n];
+  if (!(m & 1u)) return;
+  const Nbr nb = make_nbr(a, x, y, z);
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    T f[L::Q];
+    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, a.rho_ref[s], f);
+    T r = T(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) r += f[i];
+    T p;
+    if (a.psi_identity) p = r;
+    else p = T(a.rho0) * (T(1) - exp(-r / T(a.rho0)));   // Eq. 1.11
+    reinterpret_cast<T*>(a.psi[s])[n] = p;
+  }
+}
+
+// ================================================================ moments
+
+// Macroscopic fields into FP64 staging: rho^sigma, physical velocity, closed scalars.
+template <class L, class S, int NC, int NS>
+__global__ void __launch_bounds__(256) k_moments(const Args a, const int parity) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const int n = x + a.nx * (y + a.ny * z);
+  const long long N = a.N;
+  const uint32_t m = a.mask[n];
+  if (!(m & 1u)) {
+    for (int s = 0; s < NC; ++s) a.d_rho[s * N + n] = 0.0;
+    for (int c = 0; c < 3; ++c) a.d_u[c * N + n] = 0.0;
+    for (int s = 0; s < NS; ++s) a.d_C[s * N + n] = 0.0;
+    return;
+  }
+  const Nbr nb = make_nbr(a, x, y, z);
+  T rho[NC], jx[NC], jy[NC], jz[NC], Fx[NC], Fy[NC], Fz[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    T f[Q];
+    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, a.rho_ref[s], f);
+    T r = T(0), ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      r += f[i];
+      ax += T(L::cx(i)) * f[i];
+      ay += T(L::cy(i)) * f[i];
+      az += T(L::cz(i)) * f[i];
+    }
+    rho[s] = r; jx[s] = ax; jy[s] = ay; jz[s] = az;
+    Fx[s] = r * T(a.g[0]); Fy[s] = r * T(a.g[1]); Fz[s] = r * T(a.g[2]);
+  }
+  if (a.sc_on) {
+    for (int s = 0; s < NC; ++s) {
+      const T pself = reinterpret_cast<const T*>(a.psi[s])[n];
+      for (int s2 = 0; s2 < NC; ++s2) {
+        const T* ps = reinterpret_cast<const T*>(a.psi[s2]);
+        T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const T pv = flow_wall<L>(m, i) ? T(a.psi_wall) : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
+          ax += T(L::w(i)) * pv * T(L::cx(i));
+          ay += T(L::w(i)) * pv * T(L::cy(i));
+          az += T(L::w(i)) * pv * T(L::cz(i));
+        }
+        const T Gss = T(a.G[s][s2]);
+        Fx[s] -= pself * Gss * ax; Fy[s] -= pself * Gss * ay; Fz[s] -= pself * Gss * az;
+      }
+    }
+  }
+  if (a.ads_on) {
+    T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (flow_wall<L>(m, i)) {
+        ax += T(L::w(i)) * T(L::cx(i));
+        ay += T(L::w(i)) * T(L::cy(i));
+        az += T(L::w(i)) * T(L::cz(i));
+      }
+    for (int s = 0; s < NC; ++s) {
+      const T ga = T(a.G_ads[s]) * rho[s];
+      Fx[s] -= ga * ax; Fy[s] -= ga * ay; Fz[s] -= ga * az;
+    }
+  }
+  T rt = T(0), mx = T(0), my = T(0), mz = T(0);
+  for (int s = 0; s < NC; ++s) {
+    rt += rho[s];
+    mx += jx[s] + T(0.5) * Fx[s];
+    my += jy[s] + T(0.5) * Fy[s];
+    mz += jz[s] + T(0.5) * Fz[s];
+  }
+  for (int s = 0; s < NC; ++s) a.d_rho[s * N + n] = double(rho[s]);
+  a.d_u[0 * N + n] = double(mx / rt);
+  a.d_u[1 * N + n] = double(my / rt);
+  a.d_u[2 * N + n] = double(mz / rt);
+  const T wax = T((1.0 - a.J0) / double(QC - 1));
+  const T Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T h[QC];
+    gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, a.C_ref[s], a.J0, h);
+    if (s == 0) close_scalar<L, T>(h, m, wax, Kr, [](int, T, T) {});
+    T C = T(0);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) C += h[j];
+    a.d_C[s * N + n] = double(C);
+  }
+}
+
+// ================================================================ monitors
+
+template <int K>
+__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* out) {
+  __shared__ double sh[32][K];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[wid][k] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = lane < nw ? sh[lane][k] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) out[k] = s;
+    }
+  }
+}
+
+template <class L, class S, int NC, int NS>
+__global__ void __launch_bounds__(256) k_monitor(const Args a, const int parity) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  double v[NMON];
+#pragma unroll
+  for (int k = 0; k < NMON; ++k) v[k] = 0.0;
+  if (x < a.nx && y < a.ny) {
+    const int n = x + a.nx * (y + a.ny * z);
+    const uint32_t m = a.mask[n];
+    const uint8_t fl = a.flags[n];
+    const double acc = a.acc[n];
+    if (a.geo_mode == GEO_DEPOSIT) {
+      if (fl == FL_REACTIVE) v[M_REACT] += acc; else v[M_DEPO] += acc;
+    } else {
+      v[M_REACT] += acc;
+    }
+    if (x == 0) {
+      const int row = y + a.ny * z;
+      const int rows = a.ny * a.nz;
+      v[M_WALLX] += a.wallx_row[row];
+      for (int s = 0; s < NS; ++s) {
+        v[M_IN + s] += a.inflow_row[s * rows + row];
+        v[M_OUT + s] += a.outflow_row[s * rows + row];
+      }
+    }
+    if (!(m & 1u)) {
+      v[M_NSOLID] += 1.0;
+    } else {
+      v[M_NFLUID] += 1.0;
+      const Nbr nb = make_nbr(a, x, y, z);
+      bool bad = false;
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        T f[Q];
+        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, a.rho_ref[s], f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const double fi = double(f[i]);
+          v[M_MASS + s] += fi;
+          v[M_MOM + 0] += L::cx(i) * fi;
+          v[M_MOM + 1] += L::cy(i) * fi;
+          v[M_MOM + 2] += L::cz(i) * fi;
+          bad |= !isfinite(fi);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        T h[QC];
+        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, a.C_ref[s], a.J0, h);
+#pragma unroll
+        for (int j = 0; j < QC; ++j) {
+          v[M_SPEC + s] += double(h[j]);
+          bad |= !isfinite(double(h[j]));
+        }
+      }
+      if (bad) v[M_NONFIN] += 1.0;
+    }
+  }
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  block_reduce_store<NMON>(v, a.partials + (long long)bid * NMON);
+}
+
+// ================================================================ init / pop I/O
+
+// Equilibrium populations from FP64 staging fields (Eq. 6, Eq. therpopeq_species), natural layout.
+template <class L, class S, int NC, int NS>
+__global__ void __launch_bounds__(256) k_init(const Args a) {
+  using T = typename Store<S>::T;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const bool fluid = a.flags[n] == FL_FLUID;
+  const double ux = a.d_u[n], uy = a.d_u[a.N + n], uz = (L::D == 3) ? a.d_u[2 * a.N + n] : 0.0;
+  for (int s = 0; s < NC; ++s) {
+    S* fs = reinterpret_cast<S*>(a.f[s]);
+    const double r = a.d_rho[s * a.N + n];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      double v = fluid ? double(feq<L, double>(i, r, ux, uy, uz)) : 0.0;
+      if (Store<S>::kShift) v -= L::w(i) * a.rho_ref[s];
+      Store<S>::st(fs + (long long)i * a.pitch + n, T(v));
+    }
+  }
+  const double cs2c = 2.0 * (1.0 - a.J0) / double(L::QC - 1);
+  for (int s = 0; s < NS; ++s) {
+    S* hs = reinterpret_cast<S*>(a.h[s]);
+    const double C = a.d_C[s * a.N + n];
+#pragma unroll
+    for (int j = 0; j < L::QC; ++j) {
+      const double cu = L::cx(j) * ux + L::cy(j) * uy + L::cz(j) * uz;
+      const double wj = scal_w<L>(j, a.J0);
+      double v = fluid ? wj * C * (1.0 + cu / cs2c) : 0.0;
+      if (Store<S>::kShift) v -= wj * a.C_ref[s];
+      Store<S>::st(hs + (long long)j * a.pitch + n, T(v));
+    }
+  }
+}
+
+// Natural-order FP64 copy of the pre-collision populations (dir = 0: device state -> out,
+// dir = 1: in -> device state at the current layout parity).  Solid nodes read as 0.
+template <class L, class S, int NC, int NS>
+__global__ void __launch_bounds__(256) k_pops_io(const Args a, const int parity, const int dir,
+                                                 double* fio, double* hio) {
+  using T = typename Store<S>::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const int n = x + a.nx * (y + a.ny * z);
+  const uint32_t m = a.mask[n];
+  const bool fluid = (m & 1u) != 0u;
+  const Nbr nb = make_nbr(a, x, y, z);
+  const long long N = a.N, P = a.pitch;
+  if (fio) {
+    for (int s = 0; s < NC; ++s) {
+      S* fs = reinterpret_cast<S*>(a.f[s]);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        double* io = fio + ((long long)s * L::Q + i) * N + n;
+        if (!fluid) {
+          if (dir == 0) *io = 0.0;
+          continue;
+        }
+        S* p;
+        if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
+          p = fs + (long long)i * P + n;
+        else
+          p = fs + (long long)L::opp(i) * P + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+        const double sh = Store<S>::kShift ? L::w(i) * a.rho_ref[s] : 0.0;
+        if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
+        else Store<S>::st(p, T(*io - sh));
+      }
+    }
+  }
+  if (hio) {
+    for (int s = 0; s < NS; ++s) {
+      S* hs = reinterpret_cast<S*>(a.h[s]);
+#pragma unroll
+      for (int j = 0; j < L::QC; ++j) {
+        double* io = hio + ((long long)s * L::QC + j) * N + n;
+        if (!fluid) {
+          if (dir == 0) *io = 0.0;
+          continue;
+        }
+        S* p;
+        if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0u)
+          p = hs + (long long)j * P + n;
+        else
+          p = hs + (long long)L::opp(j) * P + nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+        const double sh = Store<S>::kShift ? scal_w<L>(j, a.J0) * a.C_ref[s] : 0.0;
+        if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
+        else Store<S>::st(p, T(*io - sh));
+      }
+    }
+  }
+}
+
+// ================================================================ link masks
+
+// Neighbour of (x, y, z) in direction (dx, dy, dz) under per-axis periodicity: -1 if outside.
+// *axis_out receives the first axis that left the box (0, 1, 2) or -1.
+__device__ __forceinline__ long long nbr_checked(const Args& a, int x, int y, int z, int dx, int dy,
+                                                 int dz, const int* per, int* axis_out) {
+  int v[3] = {x + dx, y + dy, z + dz};
+  const int n3[3] = {a.nx, a.ny, a.nz};
+  *axis_out = -1;
+  for (int c = 0; c < 3; ++c) {
+    if (v[c] < 0 || v[c] >= n3[c]) {
+      if (!per[c]) {
+        *axis_out = c;
+        return -1;
+      }
+      v[c] = v[c] < 0 ? v[c] + n3[c] : v[c] - n3[c];
+    }
+  }
+  return v[0] + (long long)a.nx * (v[1] + (long long)a.ny * v[2]);
+}
+
+template <class L>
+__device__ uint32_t compute_mask(const Args& a, int x, int y, int z) {
+  const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
+  if (a.flags[n] != FL_FLUID) return 0u;
+  uint32_t m = 1u;
+  int ax;
+  for (int i = 1; i < L::Q; ++i) {
+    const long long q = nbr_checked(a, x, y, z, L::cx(i), L::cy(i), L::cz(i), a.per, &ax);
+    if (q < 0 || a.flags[q] != FL_FLUID) m |= 1u << i;
+  }
+  const int perc[3] = {a.open_x ? 0 : a.per[0], a.per[1], a.per[2]};
+  for (int j = 1; j < L::QC; ++j) {
+    const long long q = nbr_checked(a, x, y, z, L::cx(j), L::cy(j), L::cz(j), perc, &ax);
+    uint32_t code;
+    if (q < 0) code = (ax == 0 && a.open_x) ? 3u : 1u;
+    else {
+      const uint8_t fl = a.flags[q];
+      code = fl == FL_FLUID ? 0u : (fl == FL_REACTIVE ? 2u : 1u);
+    }
+    m |= code << (MaskBits<L>::SC_BASE + 2 * (j - 1));
+  }
+  return m;
+}
+
+template <class L>
+__global__ void __launch_bounds__(256) k_masks(const Args a) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const int x = int(n % a.nx);
+  const int y = int((n / a.nx) % a.ny);
+  const int z = int(n / ((long long)a.nx * a.ny));
+  a.mask[n] = compute_mask<L>(a, x, y, z);
+}
+
+// ================================================================ geometry flips
+
+__device__ __forceinline__ bool cas_flag(uint8_t* flags, long long n, uint8_t expect, uint8_t desired,
+                                         int* err) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(flags + (n & ~3ll));
+  const int sh = int(n & 3) * 8;
+  unsigned int old = atomicAdd(w, 0u);
+  for (int it = 0; it < 64; ++it) {
+    if (((old >> sh) & 0xffu) != expect) return false;
+    const unsigned int nw = (old & ~(0xffu << sh)) | (unsigned(desired) << sh);
+    const unsigned int prev = atomicCAS(w, old, nw);
+    if (prev == old) return true;
+    old = prev;
+  }
+  atomicOr(err, ERR_CAS);
+  return false;
+}
+
+// FLIPPING (0b11) -> v in {FLUID 0b00, SOLID 0b01, REACTIVE 0b10} with one atomic operation,
+// so a concurrent reader never sees an intermediate value.
+__device__ __forceinline__ void leave_flipping(uint8_t* flags, long long n, uint8_t v) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(flags + (n & ~3ll));
+  const int sh = int(n & 3) * 8;
+  atomicAnd(w, ~((3u ^ unsigned(v)) << sh));
+}
+
+__device__ __forceinline__ void coords_of(const Args& a, long long n, int* x, int* y, int* z) {
+  *x = int(n % a.nx);
+  *y = int((n / a.nx) % a.ny);
+  *z = int(n / ((long long)a.nx * a.ny));
+}
+
+// One block processes the whole flip list in phases separated by __syncthreads:
+//   0 claim entries (validate, mark FLIPPING, drop duplicates)
+//   1 dissolution: neighbour means (flags before the flip);  deposition: removed sums
+//   2 write populations of the new fluid nodes / hand populations to remaining neighbours
+//   3 final flags;  4 link masks of every node around a flipped one;  5 clear the list
+// parity_next is the layout parity of the state the flips act on (steps completed & 1).
+template <class L, class S, int NC, int NS>
+__global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_next) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC;
+  const unsigned int cnt_raw = *a.flip_count;
+  const unsigned int cnt = cnt_raw < a.flip_cap ? cnt_raw : a.flip_cap;
+  if (cnt == 0) return;
+  const int percf[3] = {a.per[0], a.per[1], a.per[2]};
+  const int percs[3] = {a.open_x ? 0 : a.per[0], a.per[1], a.per[2]};
+  const long long P = a.pitch;
+  const bool dissolve = a.geo_mode == GEO_DISSOLVE;
+  __shared__ double sred[8];
+  if (threadIdx.x < 8) sred[threadIdx.x] = 0.0;
+  // ---- phase 0: claim
+  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const long long s = a.flip_list[k];
+    bool ok;
+    if (dissolve)
+      ok = a.flags[s] == FL_REACTIVE && a.V_m * a.acc[s] >= a.m_s0 &&
+           cas_flag(a.flags, s, FL_REACTIVE, FL_FLIPPING, a.err);
+    else
+      ok = a.flags[s] == FL_FLUID && a.acc[s] > 1.0 && cas_flag(a.flags, s, FL_FLUID, FL_FLIPPING, a.err);
+    if (!ok) a.flip_list[k] = 0xffffffffu;
+  }
+  __syncthreads();
+  // ---- phase 1
+  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    if (a.flip_list[k] == 0xffffffffu) continue;
+    const long long s = a.flip_list[k];
+    int x, y, z;
+    coords_of(a, s, &x, &y, &z);
+    if (dissolve) {
+      double sr[2] = {0.0, 0.0}, sc[2] = {0.0, 0.0};
+      int count = 0;
+      int ax;
+      for (int i = 1; i < Q; ++i) {
+        const long long q = nbr_checked(a, x, y, z, L::cx(i), L::cy(i), L::cz(i), percf, &ax);
+        if (q < 0 || a.flags[q] != FL_FLUID) continue;
+        ++count;
+        int qx, qy, qz;
+        coords_of(a, q, &qx, &qy, &qz);
+        const Nbr nq = make_nbr(a, qx, qy, qz);
+        const uint32_t mq = a.mask[q];
+        for (int c = 0; c < NC; ++c) {
+          T f[Q];
+          gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(q), mq, nq, parity_next, a.rho_ref[c], f);
+          double r = 0.0;
+          for (int j = 0; j < Q; ++j) r += double(f[j]);
+          sr[c] += r;
+        }
+        const T wax = T((1.0 - a.J0) / double(QC - 1));
+        const T Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
+        for (int c = 0; c < NS; ++c) {
+          T h[QC];
+          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(q), mq, nq, parity_next, a.C_ref[c], a.J0, h);
+          if (c == 0) close_scalar<L, T>(h, mq, wax, Kr, [](int, T, T) {});
+          double C = 0.0;
+          for (int j = 0; j < QC; ++j) C += double(h[j]);
+          sc[c] += C;
+        }
+      }
+      double* sc4 = a.flip_scratch + 4ll * k;
+      if (count == 0) {
+        leave_flipping(a.flags, s, FL_REACTIVE);   // nothing to average: stays solid
+        a.flip_list[k] = 0xffffffffu;
+        continue;
+      }
+      for (int c = 0; c < 2; ++c) {
+        sc4[c] = sr[c] / count;
+        sc4[2 + c] = sc[c] / count;
+      }
+    } else {
+      const Nbr ns = make_nbr(a, x, y, z);
+      const uint32_t ms = a.mask[s];
+      for (int c = 0; c < NC; ++c) {
+        T f[Q];
+        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(s), ms, ns, parity_next, a.rho_ref[c], f);
+        double r = 0.0;
+        for (int j = 0; j < Q; ++j) r += double(f[j]);
+        atomicAdd(&sred[4 + c], r);
+      }
+      for (int c = 0; c < NS; ++c) {
+        T h[QC];
+        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(s), ms, ns, parity_next, a.C_ref[c], a.J0, h);
+        double C = 0.0;
+        for (int j = 0; j < QC; ++j) C += double(h[j]);
+        atomicAdd(&sred[6 + c], C);
+      }
+    }
+  }
+  __syncthreads();
+  // ---- phase 2
+  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    if (a.flip_list[k] == 0xffffffffu) continue;
+    const long long s = a.flip_list[k];
+    int x, y, z;
+    coords_of(a, s, &x, &y, &z);
+    int ax;
+    if (dissolve) {
+      const double* sc4 = a.flip_scratch + 4ll * k;
+      for (int c = 0; c < NC; ++c) {
+        S* fs = reinterpret_cast<S*>(a.f[c]);
+        const double r = sc4[c];
+        atomicAdd(&sred[c], r);
+        for (int j = 0; j < Q; ++j) {
+          double v = L::w(j) * r;                      // f_eq(rho_bar, u = 0)
+          if (Store<S>::kShift) v -= L::w(j) * a.rho_ref[c];
+          const T tv = T(v);
+          if (parity_next == 0 || j == 0) {
+            Store<S>::st(fs + (long long)j * P + s, tv);
+            continue;
+          }
+          const long long src = nbr_checked(a, x, y, z, -L::cx(j), -L::cy(j), -L::cz(j), percf, &ax);
+          const uint8_t fl = src < 0 ? FL_SOLID : a.flags[src];
+          if (fl == FL_FLUID) {
+            S* from = fs + (long long)L::opp(j) * P + src;
+            *(fs + (long long)j * P + s) = *from;      // neighbour's bounced value moves
+            Store<S>::st(from, tv);
+          } else if (fl == FL_FLIPPING) {
+            Store<S>::st(fs + (long long)L::opp(j) * P + src, tv);
+          } else {
+            Store<S>::st(fs + (long long)j * P + s, tv);
+          }
+        }
+      }
+      for (int c = 0; c < NS; ++c) {
+        S* hs = reinterpret_cast<S*>(a.h[c]);
+        const double C = sc4[2 + c];
+        atomicAdd(&sred[2 + c], C);
+        for (int j = 0; j < QC; ++j) {
+          const double wj = scal_w<L>(j, a.J0);
+          double v = wj * C;
+          if (Store<S>::kShift) v -= wj * a.C_ref[c];
+          const T tv = T(v);
+          if (parity_next == 0 || j == 0) {
+            Store<S>::st(hs + (long long)j * P + s, tv);
+            continue;
+          }
+          const long long src = nbr_checked(a, x, y, z, -L::cx(j), -L::cy(j), -L::cz(j), percs, &ax);
+          const uint8_t fl = src < 0 ? FL_SOLID : a.flags[src];
+          if (fl == FL_FLUID) {
+            S* from = hs + (long long)L::opp(j) * P + src;
+            *(hs + (long long)j * P + s) = *from;
+            Store<S>::st(from, tv);
+          } else if (fl == FL_FLIPPING) {
+            Store<S>::st(hs + (long long)L::opp(j) * P + src, tv);
+          } else {
+            Store<S>::st(hs + (long long)j * P + s, tv);
+          }
+        }
+      }
+    } else if (parity_next == 1) {
+      // deposition in the swapped layout: a remaining fluid neighbour y = s + c_d now reads its
+      // population from the new wall at (y, d); give it what s streamed toward it, (s, opp d)
+      for (int c = 0; c < NC; ++c) {
+        S* fs = reinterpret_cast<S*>(a.f[c]);
+        for (int d = 1; d < Q; ++d) {
+          const long long yn = nbr_checked(a, x, y, z, L::cx(d), L::cy(d), L::cz(d), percf, &ax);
+          if (yn < 0 || a.flags[yn] != FL_FLUID) continue;
+          *(fs + (long long)d * P + yn) = *(fs + (long long)L::opp(d) * P + s);
+        }
+      }
+      for (int c = 0; c < NS; ++c) {
+        S* hs = reinterpret_cast<S*>(a.h[c]);
+        for (int d = 1; d < QC; ++d) {
+          const long long yn = nbr_checked(a, x, y, z, L::cx(d), L::cy(d), L::cz(d), percs, &ax);
+          if (yn < 0 || a.flags[yn] != FL_FLUID) continue;
+          *(hs + (long long)d * P + yn) = *(hs + (long long)L::opp(d) * P + s);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // ---- phase 3: final flags
+  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    if (a.flip_list[k] == 0xffffffffu) continue;
+    leave_flipping(a.flags, a.flip_list[k], dissolve ? FL_FLUID : FL_SOLID);
+  }
+  __syncthreads();
+  // ---- phase 4: masks around every flipped node
+  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    if (a.flip_list[k] == 0xffffffffu) continue;
+    const long long s = a.flip_list[k];
+    int x, y, z, ax;
+    coords_of(a, s, &x, &y, &z);
+    a.mask[s] = compute_mask<L>(a, x, y, z);
+    for (int i = 1; i < Q; ++i) {
+      const long long q = nbr_checked(a, x, y, z, L::cx(i), L::cy(i), L::cz(i), percf, &ax);
+      if (q < 0) continue;
+      int qx, qy, qz;
+      coords_of(a, q, &qx, &qy, &qz);
+      a.mask[q] = compute_mask<L>(a, qx, qy, qz);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && sred[threadIdx.x] != 0.0) atomicAdd(a.flip_mon + threadIdx.x, sred[threadIdx.x]);
+  if (threadIdx.x == 0) *a.flip_count = 0u;
+}
+
+}  // namespace lbm

@@ -1,0 +1,731 @@
+// runtime.cu -- context, device memory, step sequencing and the C ABI of include/lbm.h.
+//
+// One lbm_ctx owns every device buffer of one domain on one GPU.  lbm_step enqueues, per time
+// step: the psi pass (Shan-Chen runs only), the fused step kernel, the geometry-flip kernel
+// every N_geo steps, and the monitor / residual kernels every N_mon steps.  Nothing here falls
+// back to host arithmetic: every step of the update runs in the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "launch.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+  int lattice = 0;
+  int nx = 0, ny = 0, nz = 0;
+  long long N = 0, pitch = 0;
+  int Qf = 0, Qc = 0;
+  lbm_params p{};
+  cudaStream_t stream = nullptr;
+  const KernelSet* ks = nullptr;
+  size_t elem = 0;                 // bytes per stored population
+  Args a{};
+  long long step = 0;
+  bool fields_set = false;
+  bool have_snap = false;
+  int res_evals = 0;               // residual evaluations since the fields were set
+  long long launches = 0;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
+  std::string err;
+  std::vector<void*> allocs;
+  double* mon_host = nullptr;      // pinned [NMON + 8]
+};
+
+namespace {
+
+thread_local std::string g_create_err;   // message of the last failed lbm_create on this thread
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+  } while (0)
+
+#define LAUNCH(call)                                           \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    c->launches += 1;                                          \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+  } while (0)
+
+lbm_status dalloc(lbm_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LBM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return LBM_OK;
+}
+
+const KernelSet* pick(int lattice, int precision) {
+  if (lattice == LBM_D2Q9_D2Q5) {
+    switch (precision) {
+      case LBM_FP64: return &kernels_d2_f64();
+      case LBM_FP32: return &kernels_d2_f32();
+      case LBM_FP16_SHIFTED: return &kernels_d2_f16();
+      case LBM_BF16_SHIFTED: return &kernels_d2_bf16();
+    }
+  } else {
+    switch (precision) {
+      case LBM_FP64: return &kernels_d3_f64();
+      case LBM_FP32: return &kernels_d3_f32();
+      case LBM_FP16_SHIFTED: return &kernels_d3_f16();
+      case LBM_BF16_SHIFTED: return &kernels_d3_bf16();
+    }
+  }
+  return nullptr;
+}
+
+double psi_of(const lbm_params& p, double rho) {
+  return p.psi_kind == LBM_PSI_IDENTITY ? rho : p.rho0 * (1.0 - std::exp(-rho / p.rho0));
+}
+
+lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_params* p) {
+  if (!p) return fail(c, LBM_ERR_INVALID_ARG, "params is NULL");
+  if (lattice != LBM_D2Q9_D2Q5 && lattice != LBM_D3Q19_D3Q7) return fail(c, LBM_ERR_INVALID_ARG, "unknown lattice %d", lattice);
+  if (nx < 1 || ny < 1 || nz < 1) return fail(c, LBM_ERR_INVALID_ARG, "domain %dx%dx%d", nx, ny, nz);
+  if (lattice == LBM_D2Q9_D2Q5 && nz != 1) return fail(c, LBM_ERR_INVALID_ARG, "2D lattice needs nz == 1");
+  if ((long long)nx * ny * nz >= (1ll << 31)) return fail(c, LBM_ERR_INVALID_ARG, "more than 2^31 nodes");
+  if (ny > 65535 || nz > 65535) return fail(c, LBM_ERR_INVALID_ARG, "ny and nz must not exceed 65535");
+  if (p->precision < 0 || p->precision > 3) return fail(c, LBM_ERR_INVALID_ARG, "precision %d", p->precision);
+  if (p->n_comp < 1 || p->n_comp > 2) return fail(c, LBM_ERR_INVALID_ARG, "n_comp %d", p->n_comp);
+  for (int s = 0; s < p->n_comp; ++s)
+    if (!(p->tau[s] > 0.5)) return fail(c, LBM_ERR_INVALID_ARG, "tau[%d] = %g must exceed 0.5", s, p->tau[s]);
+  if (p->n_scal < 0 || p->n_scal > 2) return fail(c, LBM_ERR_INVALID_ARG, "n_scal %d", p->n_scal);
+  for (int s = 0; s < p->n_scal; ++s)
+    if (!(p->tau_c[s] > 0.5)) return fail(c, LBM_ERR_INVALID_ARG, "tau_c[%d] = %g must exceed 0.5", s, p->tau_c[s]);
+  if (p->n_scal > 0 && !(p->J0 >= 0.0 && p->J0 < 1.0)) return fail(c, LBM_ERR_INVALID_ARG, "J0 %g", p->J0);
+  if (p->forcing != LBM_FORCING_GUO && p->forcing != LBM_FORCING_SC_SHIFT) return fail(c, LBM_ERR_INVALID_ARG, "forcing");
+  if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_MRT) return fail(c, LBM_ERR_INVALID_ARG, "collision");
+  if (p->collision == LBM_COLLISION_MRT && (p->n_comp != 1 || p->forcing != LBM_FORCING_GUO))
+    return fail(c, LBM_ERR_INVALID_ARG, "MRT needs one component and Guo forcing");
+  if (p->psi_kind != LBM_PSI_EXP && p->psi_kind != LBM_PSI_IDENTITY) return fail(c, LBM_ERR_INVALID_ARG, "psi_kind");
+  if (p->psi_kind == LBM_PSI_EXP && !(p->rho0 > 0.0)) return fail(c, LBM_ERR_INVALID_ARG, "rho0");
+  if (p->geo_mode < 0 || p->geo_mode > 2) return fail(c, LBM_ERR_INVALID_ARG, "geo_mode");
+  if (p->geo_mode != LBM_GEO_NONE && p->n_scal < 1) return fail(c, LBM_ERR_INVALID_ARG, "geometry update needs a scalar");
+  if (p->N_geo < 1) return fail(c, LBM_ERR_INVALID_ARG, "N_geo must be >= 1");
+  if (p->N_mon < 0) return fail(c, LBM_ERR_INVALID_ARG, "N_mon must be >= 0");
+  if (p->ade_open_x && nx < 2) return fail(c, LBM_ERR_INVALID_ARG, "inlet/outlet needs nx >= 2");
+  if (p->block_x < 0 || p->block_x > 256 || (p->block_x % 32) != 0)
+    return fail(c, LBM_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [0, 256]");
+  return LBM_OK;
+}
+
+void fill_args(lbm_ctx* c) {
+  Args& a = c->a;
+  const lbm_params& p = c->p;
+  a.pitch = c->pitch;
+  a.N = c->N;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+  a.n_comp = p.n_comp; a.n_scal = p.n_scal;
+  for (int k = 0; k < 3; ++k) a.per[k] = p.periodic[k] ? 1 : 0;
+  a.open_x = p.ade_open_x ? 1 : 0;
+  bool sc = false;
+  for (int s = 0; s < 2; ++s)
+    for (int t = 0; t < 2; ++t) {
+      a.G[s][t] = (s < p.n_comp && t < p.n_comp) ? p.G[s][t] : 0.0;
+      sc |= a.G[s][t] != 0.0;
+    }
+  a.sc_on = sc ? 1 : 0;
+  a.ads_on = 0;
+  for (int s = 0; s < p.n_comp; ++s) {
+    a.G_ads[s] = p.G_ads[s];
+    a.ads_on |= p.G_ads[s] != 0.0;
+  }
+  a.shift_forcing = p.forcing == LBM_FORCING_SC_SHIFT;
+  a.psi_identity = p.psi_kind == LBM_PSI_IDENTITY;
+  a.psi_wall = psi_of(p, p.rho_solid);
+  a.rho0 = p.rho0;
+  for (int s = 0; s < 2; ++s) {
+    a.tau[s] = p.tau[s] > 0.5 ? p.tau[s] : 1.0;
+    a.tau_c[s] = p.tau_c[s] > 0.5 ? p.tau_c[s] : 1.0;
+    a.C_in[s] = p.C_in[s];
+    a.rho_ref[s] = p.rho_ref[s];
+    a.C_ref[s] = p.C_ref[s];
+  }
+  for (int k = 0; k < 3; ++k) a.g[k] = (k < 2 || c->lattice == LBM_D3Q19_D3Q7) ? p.g[k] : 0.0;
+  a.s_grp[0] = p.s_e; a.s_grp[1] = p.s_eps; a.s_grp[2] = p.s_q; a.s_grp[3] = p.s_pi; a.s_grp[4] = p.s_m;
+  a.J0 = p.J0;
+  a.k_react = p.k_react;
+  a.geo_mode = p.geo_mode;
+  a.deposit_conservative = p.deposit_conservative ? 1 : 0;
+  a.V_m = p.V_m; a.m_s0 = p.m_s0; a.DP = p.DP;
+  int bx = p.block_x;
+  if (bx == 0) bx = c->nx >= 256 ? 256 : (c->nx >= 128 ? 128 : (c->nx > 32 ? 64 : 32));
+  a.bx = bx;
+  a.by = 1;
+}
+
+int parity_of(long long step) { return int(step & 1); }
+
+lbm_status run_monitor(lbm_ctx* c) {
+  long long nb = 0;
+  LAUNCH(c->ks->monitor(c->a, parity_of(c->step), c->stream, &nb));
+  LAUNCH(launch_reduce(c->a.partials, nb, NMON, c->a.mon_out, c->a.err, M_NONFIN, c->stream));
+  return LBM_OK;
+}
+
+lbm_status run_moments(lbm_ctx* c) {
+  if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, parity_of(c->step), c->stream));
+  LAUNCH(c->ks->moments(c->a, parity_of(c->step), c->stream));
+  return LBM_OK;
+}
+
+// residual partials land in partials[0 .. 4*nb); summed into mon_out[NMON .. NMON+4)
+lbm_status run_residual(lbm_ctx* c) {
+  lbm_status st = run_moments(c);
+  if (st != LBM_OK) return st;
+  long long nb = 0;
+  LAUNCH(launch_residual(c->a, c->p.n_scal > 0 ? 1 : 0, c->stream, &nb));
+  LAUNCH(launch_reduce(c->a.partials, nb, 4, c->a.mon_out + NMON, c->a.err, -1, c->stream));
+  return LBM_OK;
+}
+
+double residual_from(const double* r4) {
+  double r = r4[1] > 0.0 ? std::sqrt(r4[0] / r4[1]) : 0.0;
+  if (r4[3] > 0.0) {
+    const double rc = std::sqrt(r4[2] / r4[3]);
+    if (rc > r) r = rc;
+  }
+  return r;
+}
+
+lbm_status check_err(lbm_ctx* c) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, c->a.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (e & ERR_CAPACITY) return fail(c, LBM_ERR_CAPACITY, "geometry flip list overflowed");
+  if (e & ERR_CAS) return fail(c, LBM_ERR_TIMEOUT, "flag update retry limit reached");
+  if (e & ERR_NONFINITE) return fail(c, LBM_ERR_NONFINITE, "non-finite populations detected");
+  return LBM_OK;
+}
+
+}  // namespace
+
+namespace lbm {
+
+// Fixed-order sum of the per-block partials (deterministic).
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restrict__ partials,
+                                                          long long nblocks, int K,
+                                                          double* __restrict__ out, int* err,
+                                                          int nonfin_slot) {
+  __shared__ double sh[1024];
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[b * K + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = sh[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && nonfin_slot >= 0 && out[nonfin_slot] > 0.0) atomicOr(err, ERR_NONFINITE);
+}
+
+// Residual partials: sum (u - u_snap)^2, sum u^2, sum (C - C_snap)^2, sum C^2; snapshot update.
+__global__ void __launch_bounds__(256) k_residual(const Args a, int has_c) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (n < a.N && (a.mask[n] & 1u)) {
+    for (int c = 0; c < 3; ++c) {
+      const double u = a.d_u[c * a.N + n];
+      const double d = u - a.snap_u[c * a.N + n];
+      v[0] += d * d;
+      v[1] += u * u;
+      a.snap_u[c * a.N + n] = u;
+    }
+    if (has_c) {
+      const double C = a.d_C[n];
+      const double d = C - a.snap_C[n];
+      v[2] += d * d;
+      v[3] += C * C;
+      a.snap_C[n] = C;
+    }
+  }
+  block_reduce_store<4>(v, a.partials + (long long)blockIdx.x * 4);
+}
+
+cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
+                          int nonfin_slot, cudaStream_t st) {
+  k_reduce_partials<<<1, 1024, 0, st>>>(partials, nblocks, K, out, err, nonfin_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Args& a, int has_c, cudaStream_t st, long long* nblocks) {
+  const long long nb = (a.N + 255) / 256;
+  *nblocks = nb;
+  k_residual<<<(unsigned int)nb, 256, 0, st>>>(a, has_c);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+lbm_status lbm_params_default(lbm_params* p) {
+  if (!p) return LBM_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->precision = LBM_FP32;
+  p->n_comp = 1;
+  p->tau[0] = p->tau[1] = 1.0;
+  p->rho0 = 1.0;
+  p->forcing = LBM_FORCING_GUO;
+  p->collision = LBM_COLLISION_BGK;
+  p->s_e = 1.19; p->s_eps = 1.4; p->s_q = 1.2; p->s_pi = 1.0; p->s_m = 1.98;
+  p->tau_c[0] = p->tau_c[1] = 1.0;
+  p->J0 = 0.25;
+  p->periodic[0] = p->periodic[1] = p->periodic[2] = 1;
+  p->V_m = 1.0; p->m_s0 = 1.0;
+  p->deposit_conservative = 1;
+  p->N_geo = 1;
+  p->rho_ref[0] = p->rho_ref[1] = 1.0;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, const lbm_params* params,
+                      lbm_ctx** out) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  lbm_ctx tmp;
+  lbm_status st = validate(&tmp, lattice, nx, ny, nz, params);
+  if (st != LBM_OK) {
+    g_create_err = tmp.err;
+    return st;
+  }
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  c->lattice = lattice;
+  c->nx = nx; c->ny = ny; c->nz = nz;
+  c->N = (long long)nx * ny * nz;
+  c->pitch = (c->N + 31) / 32 * 32;
+  c->p = *params;
+  c->Qf = lattice == LBM_D3Q19_D3Q7 ? 19 : 9;
+  c->Qc = lattice == LBM_D3Q19_D3Q7 ? 7 : 5;
+  c->stream = reinterpret_cast<cudaStream_t>(params->stream);
+  c->ks = pick(lattice, params->precision);
+  c->elem = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32 ? 4 : 2);
+  auto bail = [&](lbm_status s) {
+    g_create_err = c->err;    // reachable through lbm_last_error(NULL)
+    lbm_destroy(c);
+    return s;
+  };
+  cudaError_t e = cudaSetDevice(params->device);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaSetDevice"));
+  fill_args(c);
+  Args& a = c->a;
+  const long long N = c->N, P = c->pitch;
+  const long long rows = (long long)ny * nz;
+  void* v;
+#define DA(ptr, bytes)                                      \
+  do {                                                      \
+    st = dalloc(c, &v, (size_t)(bytes));                    \
+    if (st != LBM_OK) return bail(st);                      \
+    ptr = reinterpret_cast<decltype(ptr)>(v);               \
+  } while (0)
+  for (int s = 0; s < params->n_comp; ++s) DA(a.f[s], P * c->Qf * c->elem);
+  for (int s = 0; s < params->n_scal; ++s) DA(a.h[s], P * c->Qc * c->elem);
+  if (a.sc_on)
+    for (int s = 0; s < params->n_comp; ++s) DA(a.psi[s], P * c->ks->psi_bytes);
+  DA(a.flags, (N + 3) / 4 * 4);
+  DA(a.mask, N * 4);
+  DA(a.acc, N * 8);
+  unsigned int cap = (unsigned int)std::min<long long>(std::max<long long>(4096, N / 16), 1ll << 22);
+  a.flip_cap = cap;
+  DA(a.flip_list, (size_t)cap * 4);
+  DA(a.flip_count, 16);
+  DA(a.flip_scratch, (size_t)cap * 4 * 8);
+  DA(a.flip_mon, 8 * 8);
+  DA(a.err, 16);
+  DA(a.wallx_row, rows * 8);
+  DA(a.inflow_row, 2 * rows * 8);
+  DA(a.outflow_row, 2 * rows * 8);
+  // monitor partials: the monitor grid uses 128-thread blocks over x; the residual 256 over N
+  const long long mon_blocks = ((nx + 127) / 128) * rows;
+  const long long res_blocks = (N + 255) / 256;
+  DA(a.partials, std::max(mon_blocks * NMON, res_blocks * 4) * 8);
+  DA(a.mon_out, (NMON + 8) * 8);
+  DA(a.d_rho, 2 * N * 8);
+  DA(a.d_u, 3 * N * 8);
+  DA(a.d_C, std::max<long long>(1, params->n_scal) * N * 8);
+  DA(a.snap_u, 3 * N * 8);
+  DA(a.snap_C, N * 8);
+#undef DA
+  e = cudaMallocHost(reinterpret_cast<void**>(&c->mon_host), (NMON + 8) * sizeof(double));
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
+  // zero everything the kernels accumulate into
+  e = cudaMemsetAsync(a.flags, 0, (N + 3) / 4 * 4, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.mask, 0, N * 4, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.acc, 0, N * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_count, 0, 16, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 16, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_row, 0, rows * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.inflow_row, 0, 2 * rows * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 2 * rows * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.mon_out, 0, (NMON + 8) * 8, c->stream);
+  for (int s = 0; s < params->n_comp && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.f[s], 0, P * c->Qf * c->elem, c->stream);
+  for (int s = 0; s < params->n_scal && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "initial memset"));
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, size_t n) {
+  if (!c || !flags) return LBM_ERR_INVALID_ARG;
+  if ((long long)n != c->N) return fail(c, LBM_ERR_INVALID_ARG, "geometry has %zu entries, domain %lld", n, c->N);
+  for (size_t k = 0; k < n; ++k)
+    if (flags[k] > 2) return fail(c, LBM_ERR_INVALID_ARG, "flag %u at node %zu", flags[k], k);
+  CK(cudaMemcpyAsync(c->a.flags, flags, n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
+  LAUNCH(c->ks->masks(c->a, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->fields_set = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const double* C, size_t n) {
+  if (!c || !rho || !u) return LBM_ERR_INVALID_ARG;
+  if ((long long)n != c->N) return fail(c, LBM_ERR_INVALID_ARG, "fields have %zu nodes, domain %lld", n, c->N);
+  if (c->p.n_scal > 0 && !C) return fail(c, LBM_ERR_INVALID_ARG, "C is NULL with n_scal > 0");
+  const size_t N = (size_t)c->N;
+  CK(cudaMemcpyAsync(c->a.d_rho, rho, c->p.n_comp * N * 8, cudaMemcpyHostToDevice, c->stream));
+  const int ud = c->lattice == LBM_D3Q19_D3Q7 ? 3 : 2;
+  CK(cudaMemcpyAsync(c->a.d_u, u, ud * N * 8, cudaMemcpyHostToDevice, c->stream));
+  if (ud == 2) CK(cudaMemsetAsync(c->a.d_u + 2 * N, 0, N * 8, c->stream));
+  if (c->p.n_scal > 0) CK(cudaMemcpyAsync(c->a.d_C, C, c->p.n_scal * N * 8, cudaMemcpyHostToDevice, c->stream));
+  LAUNCH(c->ks->init(c->a, c->stream));
+  const long long rows = (long long)c->ny * c->nz;
+  CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
+  CK(cudaMemsetAsync(c->a.flip_mon, 0, 64, c->stream));
+  CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
+  CK(cudaMemsetAsync(c->a.wallx_row, 0, rows * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.inflow_row, 0, 2 * rows * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.outflow_row, 0, 2 * rows * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->step = 0;
+  c->fields_set = true;
+  c->have_snap = false;
+  c->res_evals = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
+  if (!c->fields_set) return fail(c, LBM_ERR_STATE, "lbm_set_fields must precede lbm_step");
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const int par = parity_of(c->step);
+    if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, par, c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+      if (c->ev_free.size() < 2) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+      } else {
+        e0 = c->ev_free.back(); c->ev_free.pop_back();
+        e1 = c->ev_free.back(); c->ev_free.pop_back();
+      }
+      CK(cudaEventRecord(e0, c->stream));
+    }
+    LAUNCH(c->ks->step(c->a, par, c->p.collision, c->stream));
+    if (c->profile) {
+      CK(cudaEventRecord(e1, c->stream));
+      c->ev_used.push_back({e0, e1});
+    }
+    c->step += 1;
+    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0)
+      LAUNCH(c->ks->flip(c->a, parity_of(c->step), c->stream));
+    if (c->p.N_mon > 0 && (c->step % c->p.N_mon) == 0) {
+      lbm_status st = run_monitor(c);
+      if (st != LBM_OK) return st;
+      st = run_residual(c);
+      if (st != LBM_OK) return st;
+      c->have_snap = true;
+      c->res_evals += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  return check_err(c);
+}
+
+lbm_status lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* C, uint8_t* flags, double* acc) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (!c->fields_set) return fail(c, LBM_ERR_STATE, "fields were never set");
+  lbm_status st = run_moments(c);
+  if (st != LBM_OK) return st;
+  const size_t N = (size_t)c->N;
+  if (rho) CK(cudaMemcpyAsync(rho, c->a.d_rho, c->p.n_comp * N * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (u) CK(cudaMemcpyAsync(u, c->a.d_u, 3 * N * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (C && c->p.n_scal > 0) CK(cudaMemcpyAsync(C, c->a.d_C, c->p.n_scal * N * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (flags) CK(cudaMemcpyAsync(flags, c->a.flags, N, cudaMemcpyDeviceToHost, c->stream));
+  if (acc) CK(cudaMemcpyAsync(acc, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_pops(lbm_ctx* c, double* f, double* h) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const size_t N = (size_t)c->N;
+  double* df = nullptr;
+  double* dh = nullptr;
+  if (f) CK(cudaMalloc(&df, c->p.n_comp * c->Qf * N * 8));
+  if (h && c->p.n_scal > 0) CK(cudaMalloc(&dh, c->p.n_scal * c->Qc * N * 8));
+  cudaError_t e = c->ks->pops_io(c->a, parity_of(c->step), 0, df, dh, c->stream);
+  c->launches += 1;
+  if (e == cudaSuccess && df) e = cudaMemcpyAsync(f, df, c->p.n_comp * c->Qf * N * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && dh) e = cudaMemcpyAsync(h, dh, c->p.n_scal * c->Qc * N * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(df);
+  cudaFree(dh);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_pops");
+  return LBM_OK;
+}
+
+lbm_status lbm_set_pops(lbm_ctx* c, const double* f, const double* h) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const size_t N = (size_t)c->N;
+  double* df = nullptr;
+  double* dh = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (f) e = cudaMalloc(&df, c->p.n_comp * c->Qf * N * 8);
+  if (e == cudaSuccess && h && c->p.n_scal > 0) e = cudaMalloc(&dh, c->p.n_scal * c->Qc * N * 8);
+  if (e == cudaSuccess && df) e = cudaMemcpyAsync(df, f, c->p.n_comp * c->Qf * N * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && dh) e = cudaMemcpyAsync(dh, h, c->p.n_scal * c->Qc * N * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    e = c->ks->pops_io(c->a, parity_of(c->step), 1, df, dh, c->stream);
+    c->launches += 1;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(df);
+  cudaFree(dh);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_pops");
+  c->fields_set = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_monitors(lbm_ctx* c, lbm_monitors* out) {
+  if (!c || !out) return LBM_ERR_INVALID_ARG;
+  if (!c->fields_set) return fail(c, LBM_ERR_STATE, "fields were never set");
+  lbm_status st = run_monitor(c);
+  if (st != LBM_OK) return st;
+  double* hm = c->mon_host;
+  CK(cudaMemcpyAsync(hm, c->a.mon_out, NMON * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hm + NMON, c->a.flip_mon, 8 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof(*out));
+  out->step = double(c->step);
+  out->mass[0] = hm[M_MASS]; out->mass[1] = hm[M_MASS + 1];
+  for (int k = 0; k < 3; ++k) out->momentum[k] = hm[M_MOM + k];
+  out->species[0] = hm[M_SPEC]; out->species[1] = hm[M_SPEC + 1];
+  out->reacted = hm[M_REACT];
+  out->deposited = hm[M_DEPO];
+  for (int s = 0; s < 2; ++s) {
+    out->inflow[s] = hm[M_IN + s];
+    out->outflow[s] = hm[M_OUT + s];
+    out->injected_mass[s] = hm[NMON + s];
+    out->injected_species[s] = hm[NMON + 2 + s];
+    out->removed_mass[s] = hm[NMON + 4 + s];
+    out->removed_species[s] = hm[NMON + 6 + s];
+  }
+  out->wall_exchange = hm[M_WALLX];
+  out->n_solid = hm[M_NSOLID];
+  out->n_fluid = hm[M_NFLUID];
+  out->nonfinite = hm[M_NONFIN];
+  // latest residual evaluation (automatic every N_mon steps, or lbm_residual)
+  out->residual = -1.0;
+  if (c->res_evals >= 2) {
+    double r4[4];
+    CK(cudaMemcpyAsync(r4, c->a.mon_out + NMON, 32, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out->residual = residual_from(r4);
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_ctx* c, double* r) {
+  if (!c || !r) return LBM_ERR_INVALID_ARG;
+  if (!c->fields_set) return fail(c, LBM_ERR_STATE, "fields were never set");
+  lbm_status st = run_residual(c);
+  if (st != LBM_OK) return st;
+  double r4[4];
+  CK(cudaMemcpyAsync(r4, c->a.mon_out + NMON, 32, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *r = c->have_snap ? residual_from(r4) : -1.0;
+  c->have_snap = true;
+  c->res_evals += 1;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, lattice, precision, n_comp, n_scal, nx, ny, nz;
+  int64_t step;
+};
+size_t state_bytes(const lbm_ctx* c) {
+  const size_t N = (size_t)c->N, P = (size_t)c->pitch, rows = (size_t)c->ny * c->nz;
+  return sizeof(StateHeader) + (c->p.n_comp * c->Qf + c->p.n_scal * c->Qc) * P * c->elem +
+         (N + 3) / 4 * 4 + N * 8 + 5 * rows * 8 + 8 * 8;
+}
+}  // namespace
+
+lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
+  if (!c || !nbytes) return LBM_ERR_INVALID_ARG;
+  const size_t need = state_bytes(c);
+  if (!host) {
+    *nbytes = need;
+    return LBM_OK;
+  }
+  if (*nbytes < need) return fail(c, LBM_ERR_INVALID_ARG, "state buffer %zu < %zu bytes", *nbytes, need);
+  uint8_t* o = static_cast<uint8_t*>(host);
+  StateHeader hd{};
+  std::memcpy(hd.magic, "LBMSTAT1", 8);
+  hd.version = 1; hd.lattice = c->lattice; hd.precision = c->p.precision;
+  hd.n_comp = c->p.n_comp; hd.n_scal = c->p.n_scal; hd.nx = c->nx; hd.ny = c->ny; hd.nz = c->nz;
+  hd.step = c->step;
+  std::memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
+  for (int s = 0; s < c->p.n_comp; ++s) {
+    CK(cudaMemcpyAsync(o, c->a.f[s], c->Qf * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    o += c->Qf * P * c->elem;
+  }
+  for (int s = 0; s < c->p.n_scal; ++s) {
+    CK(cudaMemcpyAsync(o, c->a.h[s], c->Qc * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    o += c->Qc * P * c->elem;
+  }
+  CK(cudaMemcpyAsync(o, c->a.flags, (N + 3) / 4 * 4, cudaMemcpyDeviceToHost, c->stream)); o += (N + 3) / 4 * 4;
+  CK(cudaMemcpyAsync(o, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream)); o += N * 8;
+  CK(cudaMemcpyAsync(o, c->a.wallx_row, rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += rows * 8;
+  CK(cudaMemcpyAsync(o, c->a.inflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
+  CK(cudaMemcpyAsync(o, c->a.outflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
+  CK(cudaMemcpyAsync(o, c->a.flip_mon, 64, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *nbytes = need;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
+  if (!c || !host) return LBM_ERR_INVALID_ARG;
+  const size_t need = state_bytes(c);
+  if (nbytes != need) return fail(c, LBM_ERR_INVALID_ARG, "state has %zu bytes, expected %zu", nbytes, need);
+  const uint8_t* o = static_cast<const uint8_t*>(host);
+  StateHeader hd;
+  std::memcpy(&hd, o, sizeof hd);
+  if (std::memcmp(hd.magic, "LBMSTAT1", 8) != 0 || hd.lattice != c->lattice || hd.precision != c->p.precision ||
+      hd.n_comp != c->p.n_comp || hd.n_scal != c->p.n_scal || hd.nx != c->nx || hd.ny != c->ny || hd.nz != c->nz)
+    return fail(c, LBM_ERR_INVALID_ARG, "checkpoint does not match this context");
+  o += sizeof hd;
+  const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
+  for (int s = 0; s < c->p.n_comp; ++s) {
+    CK(cudaMemcpyAsync(c->a.f[s], o, c->Qf * P * c->elem, cudaMemcpyHostToDevice, c->stream));
+    o += c->Qf * P * c->elem;
+  }
+  for (int s = 0; s < c->p.n_scal; ++s) {
+    CK(cudaMemcpyAsync(c->a.h[s], o, c->Qc * P * c->elem, cudaMemcpyHostToDevice, c->stream));
+    o += c->Qc * P * c->elem;
+  }
+  CK(cudaMemcpyAsync(c->a.flags, o, (N + 3) / 4 * 4, cudaMemcpyHostToDevice, c->stream)); o += (N + 3) / 4 * 4;
+  CK(cudaMemcpyAsync(c->a.acc, o, N * 8, cudaMemcpyHostToDevice, c->stream)); o += N * 8;
+  CK(cudaMemcpyAsync(c->a.wallx_row, o, rows * 8, cudaMemcpyHostToDevice, c->stream)); o += rows * 8;
+  CK(cudaMemcpyAsync(c->a.inflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
+  CK(cudaMemcpyAsync(c->a.outflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
+  CK(cudaMemcpyAsync(c->a.flip_mon, o, 64, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
+  CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
+  LAUNCH(c->ks->masks(c->a, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->step = hd.step;
+  c->fields_set = true;
+  c->have_snap = false;
+  c->res_evals = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_enable(lbm_ctx* c, int32_t on) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  c->profile = on != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return LBM_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  double total = 0.0;
+  for (auto& pr : c->ev_used) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+    total += t;
+    c->ev_free.push_back(pr.first);
+    c->ev_free.push_back(pr.second);
+  }
+  *launches = (int64_t)c->ev_used.size();
+  c->ev_used.clear();
+  *ms = total;
+  return LBM_OK;
+}
+
+lbm_status lbm_launch_count(lbm_ctx* c, int64_t* launches) {
+  if (!c || !launches) return LBM_ERR_INVALID_ARG;
+  *launches = c->launches;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  for (auto& pr : c->ev_used) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
+  if (c->mon_host) cudaFreeHost(c->mon_host);
+  delete c;
+}
+
+}  // extern "C"

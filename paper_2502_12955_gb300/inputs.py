@@ -48,8 +48,9 @@ def sphere_packing_3d(n: int, r_min: float = 6.0, r_max: float = 12.0, solid_fra
     nz, ny, nx = shape if shape is not None else (n, n, n)
     solid = np.zeros((nz, ny, nx), dtype=bool)
     total = solid.size
+    n_solid = 0
     count = 0
-    while solid.sum() < solid_fraction * total and count < max_spheres:
+    while n_solid < solid_fraction * total and count < max_spheres:
         r = float(rng.uniform(r_min, r_max))
         c = rng.uniform(0, 1, size=3) * np.array([nz, ny, nx])
         R = int(np.ceil(r))
@@ -60,7 +61,9 @@ def sphere_packing_3d(n: int, r_min: float = 6.0, r_max: float = 12.0, solid_fra
         ix = np.floor(c[2]).astype(int) + dx
         d2 = (iz + 0.5 - c[0]) ** 2 + (iy + 0.5 - c[1]) ** 2 + (ix + 0.5 - c[2]) ** 2
         m = d2 <= r * r
-        solid[iz[m] % nz, iy[m] % ny, ix[m] % nx] = True
+        idx = (iz[m] % nz, iy[m] % ny, ix[m] % nx)
+        n_solid += int(np.count_nonzero(~solid[idx]))
+        solid[idx] = True
         count += 1
     g = np.zeros((nz, ny, nx), dtype=np.uint8)
     g[solid] = flag

@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every entry point
+include/lbm.h declares, the ctypes mirrors match the C layouts, and invalid arguments are
+rejected before any CUDA call."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2502_12955_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "include", "lbm.h")
+
+
+def declared_functions():
+    text = open(HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load()
+    names = declared_functions()
+    assert set(names) == set(lbm.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+    nm = subprocess.run(["nm", "-D", "--defined-only", lbm.library_path()], capture_output=True,
+                        text=True).stdout
+    for name in names:
+        assert re.search(rf"\bT {name}$", nm, re.M), f"{name} not exported"
+
+
+def _c_layout(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "lbm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, stream),
+         offsetof(lbm_params, N_mon), offsetof(lbm_params, C_ref), sizeof(lbm_monitors),
+         offsetof(lbm_monitors, wall_exchange), offsetof(lbm_monitors, residual));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HDR), str(src), "-o", str(exe)], check=True)
+    return [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+
+
+def test_ctypes_layout_matches_c(tmp_path):
+    c = _c_layout(tmp_path)
+    P, M = lbm.LbmParams, lbm.LbmMonitors
+    assert c == [C.sizeof(P), P.stream.offset, P.N_mon.offset, P.C_ref.offset, C.sizeof(M),
+                 M.wall_exchange.offset, M.residual.offset]
+
+
+def test_params_default():
+    lib = lbm.load()
+    p = lbm.LbmParams()
+    assert lib.lbm_params_default(C.byref(p)) == 0
+    assert p.precision == 1 and p.n_comp == 1 and p.tau[0] == 1.0 and p.N_geo == 1
+    assert list(p.periodic) == [1, 1, 1] and p.deposit_conservative == 1
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau=[0.5]), dict(n_comp=3), dict(n_scal=3), dict(collision="mrt", n_comp=2, tau=[1, 1]),
+    dict(collision="mrt", forcing="sc_shift"), dict(N_geo=0), dict(block_x=48),
+    dict(n_scal=1, tau_c=[0.4]), dict(geo_mode="dissolve", n_scal=0), dict(J0=1.0, n_scal=1),
+])
+def test_create_rejects_invalid_parameters(bad):
+    lib = lbm.load()
+    cfg = dict(dim=2, nx=8, ny=8, precision="fp64")
+    cfg.update(bad)
+    p = lbm.make_params(cfg, lib)
+    h = C.c_void_p()
+    st = lib.lbm_create(lbm.LBM_D2Q9_D2Q5, 8, 8, 1, C.byref(p), C.byref(h))
+    assert st == -1 and not h.value
+    assert lib.lbm_last_error(None)
+
+
+def test_create_rejects_bad_shapes():
+    lib = lbm.load()
+    p = lbm.make_params(dict(dim=2, nx=8, ny=8), lib)
+    h = C.c_void_p()
+    assert lib.lbm_create(lbm.LBM_D2Q9_D2Q5, 8, 8, 2, C.byref(p), C.byref(h)) == -1
+    assert lib.lbm_create(lbm.LBM_D3Q19_D3Q7, 0, 8, 8, C.byref(p), C.byref(h)) == -1
+    assert lib.lbm_create(7, 8, 8, 1, C.byref(p), C.byref(h)) == -1
+
+
+def test_null_context_calls_fail_cleanly():
+    lib = lbm.load()
+    assert lib.lbm_step(None, 1) == -1
+    assert lib.lbm_sync(None) == -1
+    m = lbm.LbmMonitors()
+    assert lib.lbm_get_monitors(None, C.byref(m)) == -1
+    lib.lbm_destroy(None)

@@ -1,0 +1,203 @@
+"""GPU (CUDA path through the C ABI) against the FP64 oracle, element by element.
+
+FP64 mode must match within 1e-10 relative L2 on every field, population array and monitor,
+with integer flags bit-exact, after the stated number of steps.  Cases cover both in-place
+layout parities (odd and even step counts), ragged sizes, walls on closed axes, inlet /
+outlet, the wet-node closure, dissolution and deposition flips, MRT, Shan-Chen multi-
+component and single-component forces, adhesion and the velocity-shift scheme.
+"""
+import numpy as np
+import pytest
+
+from paper_2502_12955_gb300 import inputs
+from tests.gpu_common import FP64_TOL, compare, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def test_reactive_channel_2d_full_workload():
+    """128x64 D2Q9 BGK + D2Q5 reactive channel, 2000 steps (checked at 1, 2 and 2000)."""
+    cfg, geom, fields = inputs.reactive_channel_2d()
+    o, g = make_pair(cfg, geom, fields)
+    done = 0
+    for target in (1, 2, 2000):
+        o.step(target - done)
+        g.step(target - done)
+        done = target
+        compare(o, g, what=f"channel step {target}")
+
+
+@pytest.mark.parametrize("steps", [7, 40])
+def test_2d_all_scalar_features(steps):
+    """Ragged 37x23, inert + reactive solids, two scalars, inlet / outlet, body force."""
+    shape = (1, 23, 37)
+    geom = inputs.random_solids(shape, 0.2, seed=21)
+    geom[0, :, 0] = 0
+    geom[0, :, -1] = 0
+    cfg = dict(dim=2, nx=37, ny=23, tau=[0.8], g=[3e-5, -1e-5, 0], n_scal=2, tau_c=[0.7, 1.1],
+               J0=0.4, k_react=0.05, ade_open_x=True, C_in=[1.0, 0.3], periodic=[1, 1, 1])
+    fields = inputs.perturbed_fields(shape, 1, 2, seed=22, amp_rho=0.01, amp_u=0.01)
+    o, g = make_pair(cfg, geom, fields)
+    o.step(steps)
+    g.step(steps)
+    compare(o, g, what=f"2d scalars {steps}")
+
+
+@pytest.mark.parametrize("periodic", [[1, 1, 1], [1, 0, 1], [0, 0, 0]])
+def test_3d_bgk_walls_and_scalars(periodic):
+    shape = (9, 13, 18)
+    geom = inputs.random_solids(shape, 0.15, seed=23)
+    cfg = dict(dim=3, nx=18, ny=13, nz=9, tau=[0.9], g=[1e-5, 2e-6, -3e-6], n_scal=2,
+               tau_c=[0.8, 0.6], J0=0.25, k_react=0.02, periodic=periodic)
+    fields = inputs.perturbed_fields(shape, 1, 2, seed=24, amp_rho=0.01, amp_u=0.01)
+    o, g = make_pair(cfg, geom, fields)
+    o.step(31)
+    g.step(31)
+    compare(o, g, what=f"3d bgk {periodic}")
+
+
+@pytest.mark.parametrize("steps", [60, 61])
+def test_3d_mrt_dissolution_with_flips(steps):
+    """D3Q19 MRT + D3Q7, ragged 20x14x11 packing, fast consumption so solids dissolve."""
+    cfg, geom, fields = inputs.dissolution_3d(shape=(11, 14, 20), g=5e-5)
+    cfg.update(k_react=0.05, V_m=25.0)
+    o, g = make_pair(cfg, geom, fields)
+    o.step(steps)
+    g.step(steps)
+    m = o.monitors()
+    assert m["inj_mass0"] > 0, "the case should dissolve some solids"
+    compare(o, g, what=f"mrt dissolution {steps}")
+
+
+def test_dissolution_every_n_geo():
+    cfg, geom, fields = inputs.dissolution_3d(shape=(8, 12, 16), g=5e-5)
+    cfg.update(k_react=0.05, V_m=25.0, N_geo=3, collision="bgk")
+    o, g = make_pair(cfg, geom, fields)
+    o.step(47)
+    g.step(47)
+    assert o.monitors()["inj_mass0"] > 0
+    compare(o, g, what="n_geo 3")
+
+
+@pytest.mark.parametrize("conservative,steps", [(True, 150), (True, 151), (False, 120)])
+def test_2d_deposition_with_flips(conservative, steps):
+    cfg, geom, fields = inputs.reactive_channel_2d(nx=48, ny=24, seed=3)
+    geom[geom != 0] = 1
+    cfg.update(k_react=0.0, geo_mode="deposit", DP=0.2, deposit_conservative=conservative,
+               ade_open_x=False, g=[5e-5, 0, 0])
+    fields[2][:] = 2.0
+    o, g = make_pair(cfg, geom, fields)
+    o.step(steps)
+    g.step(steps)
+    assert o.monitors()["rem_mass0"] > 0, "the case should grow deposits"
+    compare(o, g, what=f"deposition {conservative} {steps}")
+
+
+def test_3d_deposition_inlet():
+    cfg, geom, fields = inputs.dissolution_3d(shape=(10, 12, 22), g=5e-5)
+    geom[geom != 0] = 1
+    cfg.update(geo_mode="deposit", DP=0.3, k_react=0.0, C_in=[3.0])
+    o, g = make_pair(cfg, geom, fields)
+    o.step(45)
+    g.step(45)
+    compare(o, g, what="3d deposition")
+
+
+def test_two_component_droplet_3d():
+    cfg, geom, fields = inputs.droplet_3d(n=24, radius=7.0, precision="fp64")
+    o, g = make_pair(cfg, geom, fields)
+    o.step(101)
+    g.step(101)
+    compare(o, g, what="droplet 3d")
+
+
+@pytest.mark.parametrize("forcing", ["guo", "sc_shift"])
+def test_two_component_2d_forcing_schemes(forcing):
+    shape = (1, 30, 34)
+    cfg = dict(dim=2, nx=34, ny=30, n_comp=2, tau=[1.0, 0.8], G=[[0, 2.5], [2.5, 0]],
+               psi_kind="identity", forcing=forcing, g=[0, -1e-5, 0], periodic=[1, 1, 1])
+    rho, u = inputs.droplet_fields(shape, 9.0)
+    o, g = make_pair(cfg, np.zeros(shape, np.uint8), (rho, u, None))
+    o.step(150)
+    g.step(150)
+    compare(o, g, what=f"two component {forcing}")
+
+
+def test_single_component_sc_with_walls_adhesion():
+    """Eq. 1.13 / 1.15: exp pseudopotential, G = -5, solid psi and adhesion on closed walls."""
+    shape = (1, 28, 40)
+    geom = np.zeros(shape, np.uint8)
+    geom[0, 10:14, 15:22] = 1
+    cfg = dict(dim=2, nx=40, ny=28, n_comp=1, tau=[1.0], G=[[-5.0, 0], [0, 0]], psi_kind="exp",
+               G_ads=[-0.3, 0], rho_solid=0.4, periodic=[1, 0, 1])
+    rng = np.random.default_rng(25)
+    rho = (0.7 * (1 + 0.05 * rng.uniform(-1, 1, size=shape)))[None]
+    u = np.zeros((3,) + shape)
+    o, g = make_pair(cfg, geom, (rho, u, None))
+    o.step(120)
+    g.step(120)
+    compare(o, g, what="sc single")
+
+
+def test_two_component_3d_with_solid_and_adhesion():
+    shape = (10, 12, 14)
+    geom = inputs.random_solids(shape, 0.1, seed=26, reactive_fraction=0.0)
+    cfg = dict(dim=3, nx=14, ny=12, nz=10, n_comp=2, tau=[1.0, 1.0], G=[[0, 2.2], [2.2, 0]],
+               psi_kind="identity", G_ads=[0.1, -0.1], rho_solid=0.5, periodic=[1, 1, 0])
+    rng = np.random.default_rng(27)
+    rho = np.stack([0.5 + 0.1 * rng.uniform(size=shape), 0.5 + 0.1 * rng.uniform(size=shape)])
+    u = np.zeros((3,) + shape)
+    o, g = make_pair(cfg, geom, (rho, u, None))
+    o.step(33)
+    g.step(33)
+    compare(o, g, what="sc 3d walls")
+
+
+def test_pops_roundtrip_and_odd_layout():
+    cfg, geom, fields = inputs.dissolution_3d(shape=(6, 7, 9), g=1e-5)
+    _, g = make_pair(cfg, geom, fields)
+    g.step(3)
+    f, h = g.pops()
+    g.set_pops(f, h)
+    f2, h2 = g.pops()
+    assert np.array_equal(f, f2) and np.array_equal(h, h2)
+
+
+def test_checkpoint_resume_is_bitwise():
+    cfg, geom, fields = inputs.dissolution_3d(shape=(10, 12, 16), g=5e-5)
+    cfg.update(geo_mode="none", precision="fp32")
+    _, g = make_pair(cfg, geom, fields, precision="fp32")
+    g.step(31)
+    blob = g.get_state()
+    g.step(20)
+    fa, ha = g.pops()
+    g.set_state(blob)
+    g.step(20)
+    fb, hb = g.pops()
+    assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp16", 3e-3), ("bf16", 2e-2)])
+def test_reduced_precision_against_fp64_oracle(precision, tol):
+    cfg, geom, fields = inputs.dissolution_3d(shape=(12, 14, 18), g=2e-5)
+    cfg.update(geo_mode="none")
+    o, g = make_pair(cfg, geom, fields, precision=precision)
+    o.step(80)
+    g.step(80)
+    fo, fg = o.fields(), g.fields()
+    u_scale = np.linalg.norm(fo["u"])
+    errs = {"rho": rel_l2(fo["rho"], fg["rho"]), "C": rel_l2(fo["C"], fg["C"]),
+            "u": np.linalg.norm(fo["u"] - fg["u"]) / u_scale}
+    for k, e in errs.items():
+        assert e < tol, f"{precision} {k}: {e:.3e}"
+
+
+def test_state_errors():
+    from paper_2502_12955_gb300.lbm import LbmError, Solver
+    s = Solver(dict(dim=2, nx=8, ny=8, precision="fp64"))
+    with pytest.raises(LbmError) as e:
+        s.step(1)
+    assert e.value.status == -6
+    with pytest.raises(LbmError) as e:
+        s.set_geometry(np.full((1, 8, 8), 3, np.uint8))
+    assert e.value.status == -1
