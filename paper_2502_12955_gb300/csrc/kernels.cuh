@@ -14,6 +14,11 @@
 // The reactive wet-node closure of scalar 0 (Eq. wetnode9) is applied when a node gathers its
 // populations: the stored value of a reactive link is the bounce-back value, and the closure
 // computes the unknown population from the gathered one moving toward the wall.
+//
+// Populations are stored as deviations from w_i * ref (ref = 0 in FP64 mode, the configured
+// reference density / concentration otherwise), and the collision works on deviations, so
+// the large w_i * ref part never enters a difference in reduced precision.  All parameter
+// arithmetic is done on the host (Coef<T>): the kernels see only compute-type constants.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -31,7 +36,6 @@ struct Store;
 template <>
 struct Store<double> {
   using T = double;
-  static constexpr bool kShift = false;
   __device__ static T ld(const double* p) { return __ldg(p); }
   __device__ static T ldv(const double* p) { return *p; }
   __device__ static void st(double* p, T v) { *p = v; }
@@ -39,7 +43,6 @@ struct Store<double> {
 template <>
 struct Store<float> {
   using T = float;
-  static constexpr bool kShift = false;
   __device__ static T ld(const float* p) { return __ldg(p); }
   __device__ static T ldv(const float* p) { return *p; }
   __device__ static void st(float* p, T v) { *p = v; }
@@ -47,7 +50,6 @@ struct Store<float> {
 template <>
 struct Store<__half> {
   using T = float;
-  static constexpr bool kShift = true;
   __device__ static T ld(const __half* p) { return __half2float(__ldg(p)); }
   __device__ static T ldv(const __half* p) { return __half2float(*p); }
   __device__ static void st(__half* p, T v) { *p = __float2half_rn(v); }
@@ -55,7 +57,6 @@ struct Store<__half> {
 template <>
 struct Store<__nv_bfloat16> {
   using T = float;
-  static constexpr bool kShift = true;
   __device__ static T ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   __device__ static T ldv(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static void st(__nv_bfloat16* p, T v) { *p = __float2bfloat16_rn(v); }
@@ -107,6 +108,25 @@ struct Args {
   int bx, by;                // step-kernel block shape
 };
 
+// Compute-type constants derived on the host from Args (see make_coef).
+template <class T>
+struct Coef {
+  T om[2];          // 1 / tau
+  T tau[2];
+  T G[2][2], G_ads[2], psi_wall, rho0, g[3];
+  T s_grp[5];       // MRT group rates
+  T inv_norm[10];   // 1 / |R_k|^2 of the MRT rows
+  T omc[2];         // 1 / tau_c
+  T wc0, wca;       // scalar weights: rest, axis
+  T ics2c;          // 1 / c_s^2 of the scalar lattice
+  T Kr;             // k tau_c / (tau_c - 1/2)
+  T kr;             // k
+  T C_in[2];
+  T DP, keep;       // deposition probability, 1 - DP
+  T rref[2], cref[2];   // storage references (0 in FP64 mode)
+  double thr;       // dissolution threshold on acc: m_s0 / V_m (+inf if V_m == 0)
+};
+
 constexpr int NMON = 18;
 // partial-sum slots
 enum : int {
@@ -148,11 +168,11 @@ __device__ __forceinline__ bool flow_wall(uint32_t m, int i) { return (m >> i) &
 // ------------------------------------------------------------- gathers
 
 // Pre-collision flow populations of node n (as stored; shift added for 16-bit storage).
+// Stored (deviation) values of the pre-collision flow populations of node n.
 template <class L, class S>
 __device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long pitch, int n,
-                                            uint32_t m, const Nbr& nb, int parity, double ref,
+                                            uint32_t m, const Nbr& nb, int parity,
                                             typename Store<S>::T* out) {
-  using T = typename Store<S>::T;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const S* p;
@@ -161,22 +181,17 @@ __device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long p
     } else {
       p = f + (long long)L::opp(i) * pitch + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
     }
-    T v = Store<S>::ld(p);
-    if (Store<S>::kShift) v += T(L::w(i)) * T(ref);
-    out[i] = v;
+    out[i] = Store<S>::ld(p);
   }
 }
 
-template <class L>
-__device__ __forceinline__ double scal_w(int j, double J0) {
-  return j == 0 ? J0 : (1.0 - J0) / double(L::QC - 1);
-}
+template <class T>
+__device__ __forceinline__ T scal_w(int j, const Coef<T>& k) { return j == 0 ? k.wc0 : k.wca; }
 
 template <class L, class S>
 __device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long pitch, int n,
-                                            uint32_t m, const Nbr& nb, int parity, double ref,
-                                            double J0, typename Store<S>::T* out) {
-  using T = typename Store<S>::T;
+                                            uint32_t m, const Nbr& nb, int parity,
+                                            typename Store<S>::T* out) {
 #pragma unroll
   for (int j = 0; j < L::QC; ++j) {
     const S* p;
@@ -185,9 +200,7 @@ __device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long p
     } else {
       p = h + (long long)L::opp(j) * pitch + nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
     }
-    T v = Store<S>::ld(p);
-    if (Store<S>::kShift) v += T(scal_w<L>(j, J0) * ref);
-    out[j] = v;
+    out[j] = Store<S>::ld(p);
   }
 }
 
@@ -195,17 +208,19 @@ __device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long p
 // reactive solid: C_b = 2 hb / (2 w + K), h_j = 2 w C_b - hb, hb = gathered h_{opp j}.
 // All closures use the values before closure.  Returns, through the callbacks' arguments,
 // the reaction rate k C_b per link and the stored-minus-closed exchange.
+// h holds deviations from w_j * cref; the closure works on full values at reactive links.
 template <class L, class T, class OnLink>
-__device__ __forceinline__ void close_scalar(T* h, uint32_t m, T wax, T Kr, OnLink on_link) {
+__device__ __forceinline__ void close_scalar(T* h, uint32_t m, const Coef<T>& k, OnLink on_link) {
   T old[L::QC];
 #pragma unroll
   for (int j = 0; j < L::QC; ++j) old[j] = h[j];
+  const T sh = k.wca * k.cref[0];
 #pragma unroll
   for (int j = 1; j < L::QC; ++j) {
     if (MaskBits<L>::code(m, L::opp(j)) == 2u) {
-      const T hb = old[L::opp(j)];
-      const T Cb = T(2) * hb / (T(2) * wax + Kr);
-      const T hn = T(2) * wax * Cb - hb;
+      const T hb = old[L::opp(j)] + sh;
+      const T Cb = T(2) * hb / (T(2) * k.wca + k.Kr);
+      const T hn = T(2) * k.wca * Cb - hb - sh;
       h[j] = hn;
       on_link(j, Cb, old[j] - hn);
     }
@@ -219,6 +234,14 @@ __device__ __forceinline__ T feq(int i, T rho, T ux, T uy, T uz) {
   const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
   const T uu = ux * ux + uy * uy + uz * uz;
   return T(L::w(i)) * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+}
+
+// f_i^eq - w_i rref, given drho = rho - rref (Eq. 6 written as a deviation)
+template <class L, class T>
+__device__ __forceinline__ T feq_dev(int i, T rho, T drho, T ux, T uy, T uz) {
+  const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+  const T uu = ux * ux + uy * uy + uz * uz;
+  return T(L::w(i)) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
 }
 
 // Guo forcing term (Eq. 1.21) with c_s^2 = 1/3
@@ -253,8 +276,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 // One fused time step for every fluid node: gather (A-A parity), wet-node closure and its
 // bookkeeping, deposition, moments, forces, velocity, flow collision (BGK / MRT, Guo or
 // velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
+// Registers hold deviations from w_i * ref throughout.
 template <class L, class S, int NC, int NS, int COLL>
-__global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
+__global__ void __launch_bounds__(256) k_step(const Args a, const Coef<typename Store<S>::T> k,
+                                              const int parity) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,24 +298,19 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
     T f[NC][Q];
 #pragma unroll
     for (int s = 0; s < NC; ++s)
-      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), P, n, m, nb, parity, a.rho_ref[s], f[s]);
+      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), P, n, m, nb, parity, f[s]);
     T h[NS > 0 ? NS : 1][QC];
-    const T J0 = T(a.J0);
-    const T wax = T((1.0 - a.J0) / double(QC - 1));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), P, n, m, nb, parity, a.C_ref[s], a.J0, h[s]);
+      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), P, n, m, nb, parity, h[s]);
     // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
     if (NS > 0) {
-      const T Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
-      const double kr = a.k_react;
-      const double Vm = a.V_m, ms0 = a.m_s0;
       const bool dissolve = a.geo_mode == GEO_DISSOLVE;
-      close_scalar<L, T>(h[0], m, wax, Kr, [&](int j, T Cb, T exch) {
+      close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
         const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
-        const double r = kr * double(Cb);
+        const double r = double(k.kr * Cb);
         const double old = atomicAdd(a.acc + src, r);
-        if (dissolve && Vm * old < ms0 && Vm * (old + r) >= ms0) push_flip(a, src);
+        if (dissolve && old < k.thr && old + r >= k.thr) push_flip(a, src);
         wallx += exch;
       });
       // ---- deposition at near-substrate nodes (Eq. surface_deposition)
@@ -302,23 +322,22 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
           near |= (c == 1u || c == 2u);
         }
         if (near) {
-          T sum = T(0);
+          T sum = k.cref[0];
 #pragma unroll
           for (int j = 0; j < QC; ++j) sum += h[0][j];
-          const double dep = a.DP * double(sum);
+          const double dep = double(k.DP * sum);
           const double old = a.acc[n];
           a.acc[n] = old + dep;
           if (old <= 1.0 && old + dep > 1.0) push_flip(a, n);
           if (a.deposit_conservative) {
-            const T keep = T(1.0 - a.DP);
 #pragma unroll
-            for (int j = 0; j < QC; ++j) h[0][j] *= keep;
+            for (int j = 0; j < QC; ++j) h[0][j] = h[0][j] * k.keep - scal_w<T>(j, k) * k.cref[0] * k.DP;
           }
         }
       }
     }
-    // ---- moments (Eq. 1.7, 1.8)
-    T rho[NC], jx[NC], jy[NC], jz[NC];
+    // ---- moments (Eq. 1.7, 1.8): rho = rref + sum of deviations
+    T drho[NC], rho[NC], jx[NC], jy[NC], jz[NC];
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T r = T(0), ax = T(0), ay = T(0), az = T(0);
@@ -329,15 +348,17 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
         if (L::cy(i)) ay += T(L::cy(i)) * f[s][i];
         if (L::cz(i)) az += T(L::cz(i)) * f[s][i];
       }
-      rho[s] = r; jx[s] = ax; jy[s] = ay; jz[s] = az;
+      drho[s] = r;
+      rho[s] = k.rref[s] + r;
+      jx[s] = ax; jy[s] = ay; jz[s] = az;
     }
     // ---- forces: Shan-Chen cohesion / solid psi (Eq. 1.13, 1.14), adhesion (1.15), body
     T Fx[NC], Fy[NC], Fz[NC];
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
-      Fx[s] = rho[s] * T(a.g[0]);
-      Fy[s] = rho[s] * T(a.g[1]);
-      Fz[s] = rho[s] * T(a.g[2]);
+      Fx[s] = rho[s] * k.g[0];
+      Fy[s] = rho[s] * k.g[1];
+      Fz[s] = rho[s] * k.g[2];
     }
     if (a.sc_on) {
       T sx[NC], sy[NC], sz[NC];
@@ -347,7 +368,7 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
         T ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-          const T pv = flow_wall<L>(m, i) ? T(a.psi_wall) : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
+          const T pv = flow_wall<L>(m, i) ? k.psi_wall : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
           const T wp = T(L::w(i)) * pv;
           if (L::cx(i)) ax += T(L::cx(i)) * wp;
           if (L::cy(i)) ay += T(L::cy(i)) * wp;
@@ -360,7 +381,7 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
         const T pself = reinterpret_cast<const T*>(a.psi[s])[n];
 #pragma unroll
         for (int s2 = 0; s2 < NC; ++s2) {
-          const T Gss = T(a.G[s][s2]);
+          const T Gss = k.G[s][s2];
           Fx[s] -= pself * Gss * sx[s2];
           Fy[s] -= pself * Gss * sy[s2];
           Fz[s] -= pself * Gss * sz[s2];
@@ -379,7 +400,7 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
       }
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
-        const T ga = T(a.G_ads[s]) * rho[s];
+        const T ga = k.G_ads[s] * rho[s];
         Fx[s] -= ga * ax; Fy[s] -= ga * ay; Fz[s] -= ga * az;
       }
     }
@@ -400,32 +421,30 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
       T nxs = T(0), nys = T(0), nzs = T(0), den = T(0);
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
-        const T it = T(1.0 / a.tau[s]);
-        nxs += jx[s] * it; nys += jy[s] * it; nzs += jz[s] * it;
-        den += rho[s] * it;
+        nxs += jx[s] * k.om[s]; nys += jy[s] * k.om[s]; nzs += jz[s] * k.om[s];
+        den += rho[s] * k.om[s];
       }
       const T iden = T(1) / den;
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
-        const T ts = T(a.tau[s]);
         const T ir = T(1) / rho[s];
-        const T ex = nxs * iden + ts * Fx[s] * ir;
-        const T ey = nys * iden + ts * Fy[s] * ir;
-        const T ez = nzs * iden + ts * Fz[s] * ir;
-        const T om = T(1.0 / a.tau[s]);
+        const T ex = nxs * iden + k.tau[s] * Fx[s] * ir;
+        const T ey = nys * iden + k.tau[s] * Fy[s] * ir;
+        const T ez = nzs * iden + k.tau[s] * Fz[s] * ir;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[s][i] -= om * (f[s][i] - feq<L, T>(i, rho[s], ex, ey, ez));
+        for (int i = 0; i < Q; ++i)
+          f[s][i] -= k.om[s] * (f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ex, ey, ez));
       }
     } else {
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
-        const T om = T(1.0 / a.tau[s]);
+        const T om = k.om[s];
         if (COLL == 0) {
           // Eq. 1.16 with Guo forcing: f* = f + F_i - omega (f - f_eq + F_i / 2)
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const T Fi = guo<L, T>(i, ux, uy, uz, Fx[s], Fy[s], Fz[s]);
-            const T nq = f[s][i] - feq<L, T>(i, rho[s], ux, uy, uz) + T(0.5) * Fi;
+            const T nq = f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ux, uy, uz) + T(0.5) * Fi;
             f[s][i] = f[s][i] + Fi - om * nq;
           }
         } else {
@@ -435,27 +454,27 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const T Fi = guo<L, T>(i, ux, uy, uz, Fx[s], Fy[s], Fz[s]);
-            nq[i] = f[s][i] - feq<L, T>(i, rho[s], ux, uy, uz) + T(0.5) * Fi;
+            nq[i] = f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ux, uy, uz) + T(0.5) * Fi;
             f[s][i] = f[s][i] + Fi - om * nq[i];
           }
           T coef[L::NMRT];
 #pragma unroll
-          for (int k = 0; k < L::NMRT; ++k) {
+          for (int kk = 0; kk < L::NMRT; ++kk) {
             T mk = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-              const double r = Mrt<L>::row(k, i);
-              if (r != 0.0) mk += T(r) * nq[i];
+              const int r = Mrt<L>::row(kk, i);
+              if (r != 0) mk += T(r) * nq[i];
             }
-            coef[k] = (T(a.s_grp[Mrt<L>::group(k)]) - om) * mk * T(1.0 / mrt_norm2<L>(k));
+            coef[kk] = (k.s_grp[Mrt<L>::group(kk)] - om) * mk * k.inv_norm[kk];
           }
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             T c = T(0);
 #pragma unroll
-            for (int k = 0; k < L::NMRT; ++k) {
-              const double r = Mrt<L>::row(k, i);
-              if (r != 0.0) c += T(r) * coef[k];
+            for (int kk = 0; kk < L::NMRT; ++kk) {
+              const int r = Mrt<L>::row(kk, i);
+              if (r != 0) c += T(r) * coef[kk];
             }
             f[s][i] -= c;
           }
@@ -463,21 +482,17 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
       }
     }
     // ---- scalar collision (Eq. therpop_species, therpopeq_species), u = physical velocity
-    const T cs2c = T(2.0 * (1.0 - a.J0) / double(QC - 1));
-    const T ics2 = T(1) / cs2c;
-    T hpost[NS > 0 ? NS : 1][QC];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      T C = T(0);
+      T dC = T(0);
 #pragma unroll
-      for (int j = 0; j < QC; ++j) C += h[s][j];
-      const T om = T(1.0 / a.tau_c[s]);
+      for (int j = 0; j < QC; ++j) dC += h[s][j];
+      const T C = k.cref[s] + dC;
 #pragma unroll
       for (int j = 0; j < QC; ++j) {
         const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
-        const T wj = j == 0 ? J0 : wax;
-        const T he = wj * C * (T(1) + cu * ics2);
-        hpost[s][j] = h[s][j] - om * (h[s][j] - he);
+        const T he = scal_w<T>(j, k) * (dC + C * cu * k.ics2c);
+        h[s][j] -= k.omc[s] * (h[s][j] - he);
       }
     }
     // ---- scatter flow
@@ -486,36 +501,34 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
       S* fs = reinterpret_cast<S*>(a.f[s]);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        T v = f[s][i];
-        if (Store<S>::kShift) v -= T(L::w(i)) * T(a.rho_ref[s]);
         S* p;
         if (parity == 0 || i == 0 || flow_wall<L>(m, i))
           p = fs + (long long)L::opp(i) * P + n;
         else
           p = fs + (long long)i * P + nb.at(L::cx(i), L::cy(i), L::cz(i));
-        Store<S>::st(p, v);
+        Store<S>::st(p, f[s][i]);
       }
     }
     // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       S* hs = reinterpret_cast<S*>(a.h[s]);
-      const T sref = T(a.C_ref[s]);
 #pragma unroll
       for (int j = 0; j < QC; ++j) {
         const uint32_t code = j == 0 ? 0u : MaskBits<L>::code(m, j);
-        T v = hpost[s][j];
+        T v = h[s][j];
         S* p;
         if (code == 3u) {
           // open face: the population arriving from outside replaces the one leaving
           const int jb = L::opp(j);
           T b;
+          const T sh = k.wca * k.cref[s];
           if (L::cx(j) < 0) {
             const T cu = T(L::cx(jb)) * ux + T(L::cy(jb)) * uy + T(L::cz(jb)) * uz;
-            b = wax * T(a.C_in[s]) * (T(1) + cu * ics2);
+            b = k.wca * k.C_in[s] * (T(1) + cu * k.ics2c) - sh;
             a.inflow_row[s * (a.ny * a.nz) + row] += double(b) - double(v);
           } else {
-            b = hpost[s][jb];
+            b = h[s][jb];
             a.outflow_row[s * (a.ny * a.nz) + row] += double(v) - double(b);
           }
           v = b;
@@ -525,11 +538,9 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
         } else {
           p = hs + (long long)j * P + nb.at(L::cx(j), L::cy(j), L::cz(j));
         }
-        if (Store<S>::kShift) v -= T(scal_w<L>(j, a.J0)) * sref;
         Store<S>::st(p, v);
       }
     }
-    (void)row;
   }
   // ---- wall-exchange monitor: one atomic per warp that saw a reactive link
   if (NS > 0) {
@@ -545,7 +556,8 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const int parity) {
 // ================================================================ psi
 
 template <class L, class S, int NC>
-__global__ void __launch_bounds__(256) k_psi(const Args a, const int parity) {
+__global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename Store<S>::T> k,
+                                             const int parity) {
   using T = typename Store<S>::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -558,13 +570,13 @@ __global__ void __launch_bounds__(256) k_psi(const Args a, const int parity) {
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     T f[L::Q];
-    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, a.rho_ref[s], f);
-    T r = T(0);
+    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
+    T r = k.rref[s];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) r += f[i];
     T p;
     if (a.psi_identity) p = r;
-    else p = T(a.rho0) * (T(1) - exp(-r / T(a.rho0)));   // Eq. 1.11
+    else p = k.rho0 * (T(1) - exp(-r / k.rho0));   // Eq. 1.11
     reinterpret_cast<T*>(a.psi[s])[n] = p;
   }
 }
@@ -573,7 +585,8 @@ __global__ void __launch_bounds__(256) k_psi(const Args a, const int parity) {
 
 // Macroscopic fields into FP64 staging: rho^sigma, physical velocity, closed scalars.
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(256) k_moments(const Args a, const int parity) {
+__global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typename Store<S>::T> k,
+                                                 const int parity) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -594,7 +607,7 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const int parity)
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     T f[Q];
-    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, a.rho_ref[s], f);
+    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
     T r = T(0), ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -603,8 +616,9 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const int parity)
       ay += T(L::cy(i)) * f[i];
       az += T(L::cz(i)) * f[i];
     }
+    r += k.rref[s];
     rho[s] = r; jx[s] = ax; jy[s] = ay; jz[s] = az;
-    Fx[s] = r * T(a.g[0]); Fy[s] = r * T(a.g[1]); Fz[s] = r * T(a.g[2]);
+    Fx[s] = r * k.g[0]; Fy[s] = r * k.g[1]; Fz[s] = r * k.g[2];
   }
   if (a.sc_on) {
     for (int s = 0; s < NC; ++s) {
@@ -614,12 +628,12 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const int parity)
         T ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-          const T pv = flow_wall<L>(m, i) ? T(a.psi_wall) : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
+          const T pv = flow_wall<L>(m, i) ? k.psi_wall : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
           ax += T(L::w(i)) * pv * T(L::cx(i));
           ay += T(L::w(i)) * pv * T(L::cy(i));
           az += T(L::w(i)) * pv * T(L::cz(i));
         }
-        const T Gss = T(a.G[s][s2]);
+        const T Gss = k.G[s][s2];
         Fx[s] -= pself * Gss * ax; Fy[s] -= pself * Gss * ay; Fz[s] -= pself * Gss * az;
       }
     }
@@ -634,7 +648,7 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const int parity)
         az += T(L::w(i)) * T(L::cz(i));
       }
     for (int s = 0; s < NC; ++s) {
-      const T ga = T(a.G_ads[s]) * rho[s];
+      const T ga = k.G_ads[s] * rho[s];
       Fx[s] -= ga * ax; Fy[s] -= ga * ay; Fz[s] -= ga * az;
     }
   }
@@ -649,14 +663,12 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const int parity)
   a.d_u[0 * N + n] = double(mx / rt);
   a.d_u[1 * N + n] = double(my / rt);
   a.d_u[2 * N + n] = double(mz / rt);
-  const T wax = T((1.0 - a.J0) / double(QC - 1));
-  const T Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T h[QC];
-    gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, a.C_ref[s], a.J0, h);
-    if (s == 0) close_scalar<L, T>(h, m, wax, Kr, [](int, T, T) {});
-    T C = T(0);
+    gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, h);
+    if (s == 0) close_scalar<L, T>(h, m, k, [](int, T, T) {});
+    T C = k.cref[s];
 #pragma unroll
     for (int j = 0; j < QC; ++j) C += h[j];
     a.d_C[s * N + n] = double(C);
@@ -688,7 +700,8 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[K], double* out) 
 }
 
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(256) k_monitor(const Args a, const int parity) {
+__global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typename Store<S>::T> k,
+                                                 const int parity) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const int parity)
   const int z = blockIdx.z;
   double v[NMON];
 #pragma unroll
-  for (int k = 0; k < NMON; ++k) v[k] = 0.0;
+  for (int q = 0; q < NMON; ++q) v[q] = 0.0;
   if (x < a.nx && y < a.ny) {
     const int n = x + a.nx * (y + a.ny * z);
     const uint32_t m = a.mask[n];
@@ -725,26 +738,30 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const int parity)
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
         T f[Q];
-        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, a.rho_ref[s], f);
+        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
+        double r = double(k.rref[s]);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const double fi = double(f[i]);
-          v[M_MASS + s] += fi;
+          r += fi;
           v[M_MOM + 0] += L::cx(i) * fi;
           v[M_MOM + 1] += L::cy(i) * fi;
           v[M_MOM + 2] += L::cz(i) * fi;
           bad |= !isfinite(fi);
         }
+        v[M_MASS + s] += r;
       }
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         T h[QC];
-        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, a.C_ref[s], a.J0, h);
+        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, h);
+        double C = double(k.cref[s]);
 #pragma unroll
         for (int j = 0; j < QC; ++j) {
-          v[M_SPEC + s] += double(h[j]);
+          C += double(h[j]);
           bad |= !isfinite(double(h[j]));
         }
+        v[M_SPEC + s] += C;
       }
       if (bad) v[M_NONFIN] += 1.0;
     }
@@ -757,7 +774,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const int parity)
 
 // Equilibrium populations from FP64 staging fields (Eq. 6, Eq. therpopeq_species), natural layout.
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(256) k_init(const Args a) {
+__global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= a.N) return;
@@ -766,33 +783,35 @@ __global__ void __launch_bounds__(256) k_init(const Args a) {
   for (int s = 0; s < NC; ++s) {
     S* fs = reinterpret_cast<S*>(a.f[s]);
     const double r = a.d_rho[s * a.N + n];
+    const double rr = double(k.rref[s]);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      double v = fluid ? double(feq<L, double>(i, r, ux, uy, uz)) : 0.0;
-      if (Store<S>::kShift) v -= L::w(i) * a.rho_ref[s];
+      const double v = fluid ? feq_dev<L, double>(i, r, r - rr, ux, uy, uz) : 0.0;
       Store<S>::st(fs + (long long)i * a.pitch + n, T(v));
     }
   }
-  const double cs2c = 2.0 * (1.0 - a.J0) / double(L::QC - 1);
+  const double ics2 = double(k.ics2c);
   for (int s = 0; s < NS; ++s) {
     S* hs = reinterpret_cast<S*>(a.h[s]);
     const double C = a.d_C[s * a.N + n];
+    const double cr = double(k.cref[s]);
 #pragma unroll
     for (int j = 0; j < L::QC; ++j) {
       const double cu = L::cx(j) * ux + L::cy(j) * uy + L::cz(j) * uz;
-      const double wj = scal_w<L>(j, a.J0);
-      double v = fluid ? wj * C * (1.0 + cu / cs2c) : 0.0;
-      if (Store<S>::kShift) v -= wj * a.C_ref[s];
+      const double wj = double(scal_w<T>(j, k));
+      const double v = fluid ? wj * (C - cr) + wj * C * cu * ics2 : 0.0;
       Store<S>::st(hs + (long long)j * a.pitch + n, T(v));
     }
   }
 }
 
 // Natural-order FP64 copy of the pre-collision populations (dir = 0: device state -> out,
-// dir = 1: in -> device state at the current layout parity).  Solid nodes read as 0.
+// dir = 1: in -> device state at the current layout parity).  Full values (reference added
+// back).  Solid nodes read as 0.
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(256) k_pops_io(const Args a, const int parity, const int dir,
-                                                 double* fio, double* hio) {
+__global__ void __launch_bounds__(256) k_pops_io(const Args a, const Coef<typename Store<S>::T> k,
+                                                 const int parity, const int dir, double* fio,
+                                                 double* hio) {
   using T = typename Store<S>::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -818,7 +837,7 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const int parity,
           p = fs + (long long)i * P + n;
         else
           p = fs + (long long)L::opp(i) * P + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
-        const double sh = Store<S>::kShift ? L::w(i) * a.rho_ref[s] : 0.0;
+        const double sh = L::w(i) * double(k.rref[s]);
         if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
         else Store<S>::st(p, T(*io - sh));
       }
@@ -839,7 +858,7 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const int parity,
           p = hs + (long long)j * P + n;
         else
           p = hs + (long long)L::opp(j) * P + nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
-        const double sh = Store<S>::kShift ? scal_w<L>(j, a.J0) * a.C_ref[s] : 0.0;
+        const double sh = double(scal_w<T>(j, k)) * double(k.cref[s]);
         if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
         else Store<S>::st(p, T(*io - sh));
       }
@@ -941,7 +960,8 @@ __device__ __forceinline__ void coords_of(const Args& a, long long n, int* x, in
 //   3 final flags;  4 link masks of every node around a flipped one;  5 clear the list
 // parity_next is the layout parity of the state the flips act on (steps completed & 1).
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_next) {
+__global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename Store<S>::T> k,
+                                               const int parity_next) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const unsigned int cnt_raw = *a.flip_count;
@@ -954,21 +974,21 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_ne
   __shared__ double sred[8];
   if (threadIdx.x < 8) sred[threadIdx.x] = 0.0;
   // ---- phase 0: claim
-  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    const long long s = a.flip_list[k];
+  for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const long long s = a.flip_list[e];
     bool ok;
     if (dissolve)
-      ok = a.flags[s] == FL_REACTIVE && a.V_m * a.acc[s] >= a.m_s0 &&
+      ok = a.flags[s] == FL_REACTIVE && a.acc[s] >= k.thr &&
            cas_flag(a.flags, s, FL_REACTIVE, FL_FLIPPING, a.err);
     else
       ok = a.flags[s] == FL_FLUID && a.acc[s] > 1.0 && cas_flag(a.flags, s, FL_FLUID, FL_FLIPPING, a.err);
-    if (!ok) a.flip_list[k] = 0xffffffffu;
+    if (!ok) a.flip_list[e] = 0xffffffffu;
   }
   __syncthreads();
   // ---- phase 1
-  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    if (a.flip_list[k] == 0xffffffffu) continue;
-    const long long s = a.flip_list[k];
+  for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    if (a.flip_list[e] == 0xffffffffu) continue;
+    const long long s = a.flip_list[e];
     int x, y, z;
     coords_of(a, s, &x, &y, &z);
     if (dissolve) {
@@ -985,26 +1005,24 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_ne
         const uint32_t mq = a.mask[q];
         for (int c = 0; c < NC; ++c) {
           T f[Q];
-          gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(q), mq, nq, parity_next, a.rho_ref[c], f);
-          double r = 0.0;
+          gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(q), mq, nq, parity_next, f);
+          double r = double(k.rref[c]);
           for (int j = 0; j < Q; ++j) r += double(f[j]);
           sr[c] += r;
         }
-        const T wax = T((1.0 - a.J0) / double(QC - 1));
-        const T Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
         for (int c = 0; c < NS; ++c) {
           T h[QC];
-          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(q), mq, nq, parity_next, a.C_ref[c], a.J0, h);
-          if (c == 0) close_scalar<L, T>(h, mq, wax, Kr, [](int, T, T) {});
-          double C = 0.0;
+          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(q), mq, nq, parity_next, h);
+          if (c == 0) close_scalar<L, T>(h, mq, k, [](int, T, T) {});
+          double C = double(k.cref[c]);
           for (int j = 0; j < QC; ++j) C += double(h[j]);
           sc[c] += C;
         }
       }
-      double* sc4 = a.flip_scratch + 4ll * k;
+      double* sc4 = a.flip_scratch + 4ll * e;
       if (count == 0) {
         leave_flipping(a.flags, s, FL_REACTIVE);   // nothing to average: stays solid
-        a.flip_list[k] = 0xffffffffu;
+        a.flip_list[e] = 0xffffffffu;
         continue;
       }
       for (int c = 0; c < 2; ++c) {
@@ -1016,15 +1034,15 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_ne
       const uint32_t ms = a.mask[s];
       for (int c = 0; c < NC; ++c) {
         T f[Q];
-        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(s), ms, ns, parity_next, a.rho_ref[c], f);
-        double r = 0.0;
+        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(s), ms, ns, parity_next, f);
+        double r = double(k.rref[c]);
         for (int j = 0; j < Q; ++j) r += double(f[j]);
         atomicAdd(&sred[4 + c], r);
       }
       for (int c = 0; c < NS; ++c) {
         T h[QC];
-        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(s), ms, ns, parity_next, a.C_ref[c], a.J0, h);
-        double C = 0.0;
+        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(s), ms, ns, parity_next, h);
+        double C = double(k.cref[c]);
         for (int j = 0; j < QC; ++j) C += double(h[j]);
         atomicAdd(&sred[6 + c], C);
       }
@@ -1032,22 +1050,20 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_ne
   }
   __syncthreads();
   // ---- phase 2
-  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    if (a.flip_list[k] == 0xffffffffu) continue;
-    const long long s = a.flip_list[k];
+  for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    if (a.flip_list[e] == 0xffffffffu) continue;
+    const long long s = a.flip_list[e];
     int x, y, z;
     coords_of(a, s, &x, &y, &z);
     int ax;
     if (dissolve) {
-      const double* sc4 = a.flip_scratch + 4ll * k;
+      const double* sc4 = a.flip_scratch + 4ll * e;
       for (int c = 0; c < NC; ++c) {
         S* fs = reinterpret_cast<S*>(a.f[c]);
         const double r = sc4[c];
         atomicAdd(&sred[c], r);
         for (int j = 0; j < Q; ++j) {
-          double v = L::w(j) * r;                      // f_eq(rho_bar, u = 0)
-          if (Store<S>::kShift) v -= L::w(j) * a.rho_ref[c];
-          const T tv = T(v);
+          const T tv = T(L::w(j) * (r - double(k.rref[c])));   // f_eq(rho_bar, u = 0) - w rref
           if (parity_next == 0 || j == 0) {
             Store<S>::st(fs + (long long)j * P + s, tv);
             continue;
@@ -1070,10 +1086,8 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_ne
         const double C = sc4[2 + c];
         atomicAdd(&sred[2 + c], C);
         for (int j = 0; j < QC; ++j) {
-          const double wj = scal_w<L>(j, a.J0);
-          double v = wj * C;
-          if (Store<S>::kShift) v -= wj * a.C_ref[c];
-          const T tv = T(v);
+          const double wj = double(scal_w<T>(j, k));
+          const T tv = T(wj * (C - double(k.cref[c])));       // h_eq(C_bar, u = 0) - w cref
           if (parity_next == 0 || j == 0) {
             Store<S>::st(hs + (long long)j * P + s, tv);
             continue;
@@ -1114,15 +1128,15 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const int parity_ne
   }
   __syncthreads();
   // ---- phase 3: final flags
-  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    if (a.flip_list[k] == 0xffffffffu) continue;
-    leave_flipping(a.flags, a.flip_list[k], dissolve ? FL_FLUID : FL_SOLID);
+  for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    if (a.flip_list[e] == 0xffffffffu) continue;
+    leave_flipping(a.flags, a.flip_list[e], dissolve ? FL_FLUID : FL_SOLID);
   }
   __syncthreads();
   // ---- phase 4: masks around every flipped node
-  for (unsigned int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    if (a.flip_list[k] == 0xffffffffu) continue;
-    const long long s = a.flip_list[k];
+  for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    if (a.flip_list[e] == 0xffffffffu) continue;
+    const long long s = a.flip_list[e];
     int x, y, z, ax;
     coords_of(a, s, &x, &y, &z);
     a.mask[s] = compute_mask<L>(a, x, y, z);

@@ -60,7 +60,7 @@ struct D3 {
   static constexpr int NMRT = 10;
 };
 
-// MRT correction rows R_k(c) and their group: 0 e, 1 eps, 2 q, 3 pi, 4 m.
+// MRT correction rows R_k(c) (integer valued) and their group: 0 e, 1 eps, 2 q, 3 pi, 4 m.
 template <class L>
 struct Mrt;
 
@@ -69,20 +69,20 @@ struct Mrt<D3> {
   __host__ __device__ static constexpr int group(int k) {
     return k == 0 ? 0 : (k == 1 ? 1 : (k <= 4 ? 2 : (k <= 6 ? 3 : 4)));
   }
-  __host__ __device__ static constexpr double row(int k, int i) {
-    const double x = D3::cx(i), y = D3::cy(i), z = D3::cz(i);
-    const double c2 = x * x + y * y + z * z;
+  __host__ __device__ static constexpr int row(int k, int i) {
+    const int x = D3::cx(i), y = D3::cy(i), z = D3::cz(i);
+    const int c2 = x * x + y * y + z * z;
     switch (k) {
-      case 0: return 19.0 * c2 - 30.0;                                  // e
-      case 1: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;          // eps
-      case 2: return (5.0 * c2 - 9.0) * x;                               // q_x
-      case 3: return (5.0 * c2 - 9.0) * y;                               // q_y
-      case 4: return (5.0 * c2 - 9.0) * z;                               // q_z
-      case 5: return (3.0 * c2 - 5.0) * (3.0 * x * x - c2);              // 3 pi_xx
-      case 6: return (3.0 * c2 - 5.0) * (y * y - z * z);                 // pi_ww
-      case 7: return x * (y * y - z * z);                                // m_x
-      case 8: return y * (z * z - x * x);                                // m_y
-      default: return z * (x * x - y * y);                               // m_z
+      case 0: return 19 * c2 - 30;                                  // e
+      case 1: return (21 * c2 * c2 - 53 * c2 + 24) / 2;             // eps
+      case 2: return (5 * c2 - 9) * x;                              // q_x
+      case 3: return (5 * c2 - 9) * y;                              // q_y
+      case 4: return (5 * c2 - 9) * z;                              // q_z
+      case 5: return (3 * c2 - 5) * (3 * x * x - c2);               // 3 pi_xx
+      case 6: return (3 * c2 - 5) * (y * y - z * z);                // pi_ww
+      case 7: return x * (y * y - z * z);                           // m_x
+      case 8: return y * (z * z - x * x);                           // m_y
+      default: return z * (x * x - y * y);                          // m_z
     }
   }
 };
@@ -90,21 +90,21 @@ struct Mrt<D3> {
 template <>
 struct Mrt<D2> {
   __host__ __device__ static constexpr int group(int k) { return k == 0 ? 0 : (k == 1 ? 1 : 2); }
-  __host__ __device__ static constexpr double row(int k, int i) {
-    const double x = D2::cx(i), y = D2::cy(i);
-    const double c2 = x * x + y * y;
+  __host__ __device__ static constexpr int row(int k, int i) {
+    const int x = D2::cx(i), y = D2::cy(i);
+    const int c2 = x * x + y * y;
     switch (k) {
-      case 0: return 3.0 * c2 - 4.0;                                     // e
-      case 1: return 4.0 - 10.5 * c2 + 4.5 * c2 * c2;                    // eps
-      case 2: return (3.0 * c2 - 5.0) * x;                               // q_x
-      default: return (3.0 * c2 - 5.0) * y;                             // q_y
+      case 0: return 3 * c2 - 4;                                    // e
+      case 1: return (8 - 21 * c2 + 9 * c2 * c2) / 2;               // eps
+      case 2: return (3 * c2 - 5) * x;                              // q_x
+      default: return (3 * c2 - 5) * y;                             // q_y
     }
   }
 };
 
 template <class L>
-__host__ __device__ constexpr double mrt_norm2(int k) {
-  double s = 0.0;
+__host__ __device__ constexpr int mrt_norm2(int k) {
+  int s = 0;
   for (int i = 0; i < L::Q; ++i) s += Mrt<L>::row(k, i) * Mrt<L>::row(k, i);
   return s;
 }

@@ -27,12 +27,46 @@ inline dim3 node_grid(const Args& a, dim3 blk) {
 
 inline dim3 step_block(const Args& a) { return dim3(a.bx, a.by, 1); }
 
+// Host-side derivation of every constant the kernels use, in their compute type.
+template <class L, class T>
+Coef<T> make_coef(const Args& a, bool shifted) {
+  Coef<T> k{};
+  for (int s = 0; s < 2; ++s) {
+    k.om[s] = T(1.0 / a.tau[s]);
+    k.tau[s] = T(a.tau[s]);
+    k.G_ads[s] = T(a.G_ads[s]);
+    for (int t = 0; t < 2; ++t) k.G[s][t] = T(a.G[s][t]);
+    k.omc[s] = T(1.0 / a.tau_c[s]);
+    k.C_in[s] = T(a.C_in[s]);
+    k.rref[s] = shifted ? T(a.rho_ref[s]) : T(0);
+    k.cref[s] = shifted ? T(a.C_ref[s]) : T(0);
+  }
+  k.psi_wall = T(a.psi_wall);
+  k.rho0 = T(a.rho0);
+  for (int c = 0; c < 3; ++c) k.g[c] = T(a.g[c]);
+  for (int q = 0; q < 5; ++q) k.s_grp[q] = T(a.s_grp[q]);
+  for (int q = 0; q < 10; ++q) k.inv_norm[q] = q < L::NMRT ? T(1.0 / double(mrt_norm2<L>(q))) : T(0);
+  k.wc0 = T(a.J0);
+  k.wca = T((1.0 - a.J0) / double(L::QC - 1));
+  k.ics2c = T(double(L::QC - 1) / (2.0 * (1.0 - a.J0)));
+  k.Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
+  k.kr = T(a.k_react);
+  k.DP = T(a.DP);
+  k.keep = T(1.0 - a.DP);
+  k.thr = a.V_m > 0.0 ? a.m_s0 / a.V_m : __builtin_huge_val();
+  return k;
+}
+
 template <class L, class S>
 struct Launchers {
+  using T = typename Store<S>::T;
+  static constexpr bool kShifted = !std::is_same<S, double>::value;
+  static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
+
   template <int NC, int NS, int COLL>
   static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
     const dim3 blk = step_block(a);
-    k_step<L, S, NC, NS, COLL><<<node_grid(a, blk), blk, 0, st>>>(a, parity);
+    k_step<L, S, NC, NS, COLL><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
     return cudaGetLastError();
   }
   template <int NC, int NS>
@@ -57,8 +91,8 @@ struct Launchers {
 
   static cudaError_t psi(const Args& a, int parity, cudaStream_t st) {
     const dim3 blk(128, 1, 1);
-    if (a.n_comp == 1) k_psi<L, S, 1><<<node_grid(a, blk), blk, 0, st>>>(a, parity);
-    else k_psi<L, S, 2><<<node_grid(a, blk), blk, 0, st>>>(a, parity);
+    if (a.n_comp == 1) k_psi<L, S, 1><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
+    else k_psi<L, S, 2><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
     return cudaGetLastError();
   }
 
@@ -79,7 +113,7 @@ struct Launchers {
   static cudaError_t moments(const Args& a, int parity, cudaStream_t st) {
     const dim3 blk(128, 1, 1);
     by_nc_ns(a, [&](auto nc, auto ns) {
-      k_moments<L, S, decltype(nc)::value, decltype(ns)::value><<<node_grid(a, blk), blk, 0, st>>>(a, parity);
+      k_moments<L, S, decltype(nc)::value, decltype(ns)::value><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
     });
     return cudaGetLastError();
   }
@@ -89,7 +123,7 @@ struct Launchers {
     const dim3 grd = node_grid(a, blk);
     *nblocks = (long long)grd.x * grd.y * grd.z;
     by_nc_ns(a, [&](auto nc, auto ns) {
-      k_monitor<L, S, decltype(nc)::value, decltype(ns)::value><<<grd, blk, 0, st>>>(a, parity);
+      k_monitor<L, S, decltype(nc)::value, decltype(ns)::value><<<grd, blk, 0, st>>>(a, coef(a), parity);
     });
     return cudaGetLastError();
   }
@@ -97,7 +131,7 @@ struct Launchers {
   static cudaError_t init(const Args& a, cudaStream_t st) {
     const unsigned int nb = (unsigned int)((a.N + 255) / 256);
     by_nc_ns(a, [&](auto nc, auto ns) {
-      k_init<L, S, decltype(nc)::value, decltype(ns)::value><<<nb, 256, 0, st>>>(a);
+      k_init<L, S, decltype(nc)::value, decltype(ns)::value><<<nb, 256, 0, st>>>(a, coef(a));
     });
     return cudaGetLastError();
   }
@@ -106,14 +140,14 @@ struct Launchers {
     const dim3 blk(128, 1, 1);
     by_nc_ns(a, [&](auto nc, auto ns) {
       k_pops_io<L, S, decltype(nc)::value, decltype(ns)::value>
-          <<<node_grid(a, blk), blk, 0, st>>>(a, parity, dir, f, h);
+          <<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity, dir, f, h);
     });
     return cudaGetLastError();
   }
 
   static cudaError_t flip(const Args& a, int parity_next, cudaStream_t st) {
     by_nc_ns(a, [&](auto nc, auto ns) {
-      k_flip<L, S, decltype(nc)::value, decltype(ns)::value><<<1, 1024, 0, st>>>(a, parity_next);
+      k_flip<L, S, decltype(nc)::value, decltype(ns)::value><<<1, 1024, 0, st>>>(a, coef(a), parity_next);
     });
     return cudaGetLastError();
   }

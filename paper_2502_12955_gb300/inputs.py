@@ -162,16 +162,17 @@ def droplet_3d(n=128, radius=16.0, precision="fp32", G=2.7):
 DISSOLUTION_G = 2.2e-4
 
 
-def dissolution_3d(n=256, seed=0, precision="fp32", shape=None, g=None):
+def dissolution_3d(n=256, seed=0, precision="fp32", shape=None, g=None, radius=(6.0, 12.0)):
     """3D reactive dissolution in a random-sphere packing: D3Q19 MRT (tau 1) flow by
     body force + D3Q7 solute, first-order reaction at reactive links consuming solid mass,
-    inlet C = 1 at x = 0, zero-gradient outlet, periodic flow."""
+    inlet C = 1 at x = 0, zero-gradient outlet, periodic flow.  Small test domains pass a
+    proportionally smaller sphere radius range."""
     shp = shape if shape is not None else (n, n, n)
     cfg = dict(dim=3, nx=shp[2], ny=shp[1], nz=shp[0], n_comp=1, tau=[1.0],
                g=[DISSOLUTION_G if g is None else g, 0.0, 0.0], collision="mrt", forcing="guo",
                n_scal=1, tau_c=[0.5667], J0=0.25, k_react=1.85e-4, ade_open_x=True,
                C_in=[1.0], periodic=[1, 1, 1], geo_mode="dissolve", V_m=1.0, m_s0=1.0,
-               precision=precision)
-    geom = sphere_packing_3d(n, 6.0, 12.0, 0.6, seed, REACTIVE, shape=shp)
+               C_ref=[1.0], precision=precision)
+    geom = sphere_packing_3d(n, radius[0], radius[1], 0.6, seed, REACTIVE, shape=shp)
     rho, u, C = uniform_fields(shp, 1, 1, rho=1.0, C=1.0)
     return cfg, geom, (rho, u, C)

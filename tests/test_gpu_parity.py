@@ -59,7 +59,7 @@ def test_3d_bgk_walls_and_scalars(periodic):
 @pytest.mark.parametrize("steps", [60, 61])
 def test_3d_mrt_dissolution_with_flips(steps):
     """D3Q19 MRT + D3Q7, ragged 20x14x11 packing, fast consumption so solids dissolve."""
-    cfg, geom, fields = inputs.dissolution_3d(shape=(11, 14, 20), g=5e-5)
+    cfg, geom, fields = inputs.dissolution_3d(shape=(11, 14, 20), g=5e-4, radius=(2.0, 4.0))
     cfg.update(k_react=0.05, V_m=25.0)
     o, g = make_pair(cfg, geom, fields)
     o.step(steps)
@@ -70,7 +70,7 @@ def test_3d_mrt_dissolution_with_flips(steps):
 
 
 def test_dissolution_every_n_geo():
-    cfg, geom, fields = inputs.dissolution_3d(shape=(8, 12, 16), g=5e-5)
+    cfg, geom, fields = inputs.dissolution_3d(shape=(8, 12, 16), g=5e-4, radius=(2.0, 4.0))
     cfg.update(k_react=0.05, V_m=25.0, N_geo=3, collision="bgk")
     o, g = make_pair(cfg, geom, fields)
     o.step(47)
@@ -94,7 +94,7 @@ def test_2d_deposition_with_flips(conservative, steps):
 
 
 def test_3d_deposition_inlet():
-    cfg, geom, fields = inputs.dissolution_3d(shape=(10, 12, 22), g=5e-5)
+    cfg, geom, fields = inputs.dissolution_3d(shape=(10, 12, 22), g=5e-4, radius=(2.0, 4.0))
     geom[geom != 0] = 1
     cfg.update(geo_mode="deposit", DP=0.3, k_react=0.0, C_in=[3.0])
     o, g = make_pair(cfg, geom, fields)
@@ -154,7 +154,7 @@ def test_two_component_3d_with_solid_and_adhesion():
 
 
 def test_pops_roundtrip_and_odd_layout():
-    cfg, geom, fields = inputs.dissolution_3d(shape=(6, 7, 9), g=1e-5)
+    cfg, geom, fields = inputs.dissolution_3d(shape=(6, 7, 9), g=1e-4, radius=(1.5, 2.5))
     _, g = make_pair(cfg, geom, fields)
     g.step(3)
     f, h = g.pops()
@@ -164,7 +164,7 @@ def test_pops_roundtrip_and_odd_layout():
 
 
 def test_checkpoint_resume_is_bitwise():
-    cfg, geom, fields = inputs.dissolution_3d(shape=(10, 12, 16), g=5e-5)
+    cfg, geom, fields = inputs.dissolution_3d(shape=(10, 12, 16), g=5e-4, radius=(2.0, 4.0))
     cfg.update(geo_mode="none", precision="fp32")
     _, g = make_pair(cfg, geom, fields, precision="fp32")
     g.step(31)
@@ -177,19 +177,25 @@ def test_checkpoint_resume_is_bitwise():
     assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp16", 3e-3), ("bf16", 2e-2)])
-def test_reduced_precision_against_fp64_oracle(precision, tol):
-    cfg, geom, fields = inputs.dissolution_3d(shape=(12, 14, 18), g=2e-5)
+# Relative L2 tolerances per field of the reduced-precision modes against the FP64 oracle on
+# the dissolution workload's transport parameters (velocity ~ 1e-2), 200 steps.
+REDUCED_TOL = {"fp32": {"rho": 1e-6, "u": 1e-4, "C": 1e-5},
+               "fp16": {"rho": 1e-4, "u": 1e-2, "C": 2e-3},
+               "bf16": {"rho": 1e-3, "u": 5e-2, "C": 1e-2}}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_reduced_precision_against_fp64_oracle(precision):
+    cfg, geom, fields = inputs.dissolution_3d(shape=(16, 18, 24), radius=(2.0, 4.0), g=2e-3)
     cfg.update(geo_mode="none")
     o, g = make_pair(cfg, geom, fields, precision=precision)
-    o.step(80)
-    g.step(80)
+    o.step(200)
+    g.step(200)
     fo, fg = o.fields(), g.fields()
-    u_scale = np.linalg.norm(fo["u"])
-    errs = {"rho": rel_l2(fo["rho"], fg["rho"]), "C": rel_l2(fo["C"], fg["C"]),
-            "u": np.linalg.norm(fo["u"] - fg["u"]) / u_scale}
+    errs = {k: rel_l2(fo[k], fg[k]) for k in ("rho", "u", "C")}
+    print(precision, {k: f"{e:.2e}" for k, e in errs.items()})
     for k, e in errs.items():
-        assert e < tol, f"{precision} {k}: {e:.3e}"
+        assert e < REDUCED_TOL[precision][k], f"{precision} {k}: {e:.3e}"
 
 
 def test_state_errors():
