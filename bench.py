@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the reactive lattice Boltzmann step on one GB300 (or N independent replicas).
+
+Default workload: 3D reactive dissolution, 256^3 seeded random-sphere packing (porosity 0.4),
+D3Q19 MRT flow + D3Q7 solute, wet-node reaction, solid consumption with geometry flips, FP32.
+A "step" is one time step of the whole path (fused collide-stream, interface detection and
+flips, monitors every N_mon steps).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload dissolution|droplet|channel] [--precision fp32|fp16|bf16|fp64]
+                  [--size S] [--no-e2e] [--no-cpu]
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2502_12955_gb300 import inputs  # noqa: E402
+
+PEAK_FALLBACK_GBS = 6800.0
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+# ------------------------------------------------------------------ workloads
+
+def workload(name, size, precision):
+    """(cfg, geom, fields, label) of a bench workload."""
+    if name == "dissolution":
+        n = size or 256
+        cfg, geom, fields = inputs.dissolution_3d(n=n, precision=precision)
+        label = f"dissolution3d_{n}^3_d3q19mrt_d3q7_{precision}"
+    elif name == "droplet":
+        n = size or 128
+        cfg, geom, fields = inputs.droplet_3d(n=n, radius=n / 8.0, precision=precision)
+        label = f"droplet3d_{n}^3_2x_d3q19_shanchen_{precision}"
+    elif name == "channel":
+        cfg, geom, fields = inputs.reactive_channel_2d(precision=precision)
+        label = f"channel2d_128x64_d2q9_d2q5_{precision}"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    cfg = dict(cfg, precision=precision, N_mon=100)
+    return cfg, geom, fields, label
+
+
+def bytes_per_fluid_node(cfg):
+    """Algorithmic HBM bytes per fluid node and step: one read and one write of every
+    population of every lattice."""
+    q = 19 if cfg["dim"] == 3 else 9
+    qc = 7 if cfg["dim"] == 3 else 5
+    elem = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[cfg["precision"]]
+    return 2 * elem * (q * cfg.get("n_comp", 1) + qc * cfg.get("n_scal", 0))
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2502_12955_gb300", "csrc", "*.cu*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(label):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    path = os.path.join(PROFILES, f"k_step_{label.split('_')[0]}_{label.split('_')[-1]}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(name, precision, seconds=10.0, sample_n=64, steps=None, warmup=2):
+    """Time the FP64 oracle (single thread) on a bounded sample of the workload."""
+    from oracle.oracle import Oracle
+
+    if name == "dissolution":
+        cfg, geom, fields = inputs.dissolution_3d(n=sample_n, precision="fp64")
+        sample = f"dissolution 3D {sample_n}^3 seeded packing (same recipe), MRT + D3Q7, FP64 oracle"
+    elif name == "droplet":
+        cfg, geom, fields = inputs.droplet_3d(n=sample_n, radius=sample_n / 8.0, precision="fp64")
+        sample = f"droplet 3D {sample_n}^3, two components, FP64 oracle"
+    else:
+        cfg, geom, fields = inputs.reactive_channel_2d(precision="fp64")
+        sample = "channel 2D 128x64, FP64 oracle"
+    o = Oracle(cfg)
+    o.set_geometry(geom)
+    rho, u, C = fields
+    o.set_fields(rho, u, C if o.p.n_scal else None)
+    o.step(warmup)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if steps is not None and n >= steps:
+            break
+        if steps is None and el >= seconds and n >= 3:
+            break
+    nodes = geom.size
+    return {"value": nodes * n / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, {n} steps after {warmup} warm-up, {el:.1f} s",
+            "steps": n, "seconds": el}
+
+
+# ------------------------------------------------------------------ main
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="dissolution", choices=["dissolution", "droplet", "channel"])
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--size", type=int, default=0)
+    ap.add_argument("--block-x", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
+    cfg, geom, fields, label = workload(args.workload, args.size, precision)
+    # each timed step is one oracle step on a bounded sample of the workload (48^3 in 3D)
+    res = oracle_sample(args.workload, precision, steps=args.steps, sample_n=48, warmup=args.warmup)
+    value = res["value"]
+    ms = res["seconds"] * 1e3 / res["steps"]
+    line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": label, "reference": "FP64 CPU oracle (oracle/lbm_oracle.c)",
+                       "sample": res["sample"]},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = dist_mod
+
+    from paper_2502_12955_gb300.lbm import Solver
+
+    precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
+    cfg, geom, fields, label = workload(args.workload, args.size, precision)
+    cfg = dict(cfg, device=local, block_x=args.block_x)
+    stream = torch.cuda.Stream(device=local)
+    s = Solver(cfg, stream=stream.cuda_stream)
+    s.set_geometry(geom)
+    rho, u, C = fields
+    s.set_fields(rho, u, C if s.n_scal else None)
+    N = geom.size
+    Nf = int((geom == 0).sum())
+    s.step(args.warmup)
+    s.sync()
+
+    # ---------------- timed region: K steps, inputs resident in HBM
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    s.profile(True)
+    s.profile_read()
+    launches0 = s.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = s.launch_count() - launches0
+    kern_ms, kern_n = s.profile_read()
+    s.profile(False)
+    s.sync()
+    if dist:
+        t = torch.tensor([ms_total], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    mlups = ws * N * args.steps / (ms_total * 1e-3) / 1e6
+    mflups = ws * Nf * args.steps / (ms_total * 1e-3) / 1e6
+    mon = s.monitors()
+
+    # roofline of the fused step kernel (per launch, CUDA events on the launching stream)
+    bpn = bytes_per_fluid_node(cfg)
+    algo_bytes = Nf * bpn
+    kavg_ms = kern_ms / max(1, kern_n)
+    achieved = algo_bytes / (kavg_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profile_traffic(label),
+                "peak_source": peak_src, "kernel": "k_step", "kernel_ms": kavg_ms,
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "bytes_per_fluid_node": bpn}
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ke = max(10, min(args.steps, 100))
+        flags_h = torch.from_numpy(np.ascontiguousarray(geom, dtype=np.uint8)).pin_memory().numpy()
+        rho_h = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory().numpy()
+        u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()
+        C_h = torch.from_numpy(np.ascontiguousarray(C)).pin_memory().numpy() if s.n_scal else None
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_geometry(flags_h)
+        s.set_fields(rho_h, u_h, C_h)
+        for _ in range(ke):
+            s.step(1)
+            s.sync()          # per-step read of the device status word (4 bytes)
+        out = s.fields()
+        torch.cuda.synchronize()
+        barrier()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = geom.nbytes + rho.nbytes + u[: (3 if cfg["dim"] == 3 else 2)].nbytes + (C.nbytes if s.n_scal else 0)
+        d2h = 4 * ke + sum(v.nbytes for v in out.values())
+        e2e = {"value": ws * N * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / ke,
+               "d2h_bytes_per_step": d2h / ke, "steps": ke,
+               "includes": "set_geometry + set_fields from pinned host memory, per-step lbm_step + "
+                           "lbm_sync (4-byte status read), final lbm_get_fields to host"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = oracle_sample(args.workload, precision, seconds=12.0)
+
+    q = 19 if cfg["dim"] == 3 else 9
+    qc = 7 if cfg["dim"] == 3 else 5
+    state_gb = N * (q * cfg.get("n_comp", 1) + qc * cfg.get("n_scal", 0)) * (bpn // (2 * (q * cfg.get("n_comp", 1) + qc * cfg.get("n_scal", 0)))) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math",
+                      "bf16": "bf16 storage, f32 math"}[precision],
+            "data": "synthetic (seeded geometry, inputs/ recipe)",
+            "config": {"workload": label, "nodes": N, "fluid_nodes": Nf,
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": f"population state {state_gb:.2f} GB > 0.13 GB L2: no flush needed",
+                       "mflups": mflups, "achieved_gbs_step": Nf * bpn / (ms_step * 1e-3) / 1e9,
+                       "mass": mon["mass0"], "n_solid": mon["nsolid"], "nonfinite": mon["nonfinite"]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

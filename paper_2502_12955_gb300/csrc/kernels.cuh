@@ -76,6 +76,9 @@ struct Args {
   uint8_t* flags;
   uint32_t* mask;
   double* acc;               // consumed (reactive solid) / deposited (fluid) per node
+  uint32_t* iface_list;       // reactive solids with a fluid scalar-lattice neighbour
+  unsigned int* iface_count;
+  uint8_t* listed;           // 1 once a node is in iface_list
   uint32_t* flip_list;
   unsigned int* flip_count;
   unsigned int flip_cap;
@@ -305,12 +308,11 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const Coef<typename 
       gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), P, n, m, nb, parity, h[s]);
     // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
     if (NS > 0) {
-      const bool dissolve = a.geo_mode == GEO_DISSOLVE;
+      // the consumed totals are reductions (no value returned): the threshold test runs in
+      // k_detect over the interface list before the geometry update
       close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
         const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
-        const double r = double(k.kr * Cb);
-        const double old = atomicAdd(a.acc + src, r);
-        if (dissolve && old < k.thr && old + r >= k.thr) push_flip(a, src);
+        atomicAdd(a.acc + src, double(k.kr * Cb));
         wallx += exch;
       });
       // ---- deposition at near-substrate nodes (Eq. surface_deposition)
@@ -921,6 +923,38 @@ __global__ void __launch_bounds__(256) k_masks(const Args a) {
   a.mask[n] = compute_mask<L>(a, x, y, z);
 }
 
+// ================================================================ interface list
+
+template <class L>
+__device__ __forceinline__ bool has_fluid_scalar_neighbour(const Args& a, int x, int y, int z) {
+  const int perc[3] = {a.open_x ? 0 : a.per[0], a.per[1], a.per[2]};
+  int ax;
+  for (int j = 1; j < L::QC; ++j) {
+    const long long q = nbr_checked(a, x, y, z, L::cx(j), L::cy(j), L::cz(j), perc, &ax);
+    if (q >= 0 && a.flags[q] == FL_FLUID) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void push_iface(const Args& a, long long n) {
+  const unsigned int e = atomicAdd(a.iface_count, 1u);
+  if (e < a.N) a.iface_list[e] = (uint32_t)n;
+  else atomicOr(a.err, ERR_CAPACITY);
+}
+
+// Reactive solids touching the fluid through a scalar link; listed[] must be zero on entry.
+template <class L>
+__global__ void __launch_bounds__(256) k_iface_build(const Args a) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N || a.flags[n] != FL_REACTIVE) return;
+  const int x = int(n % a.nx);
+  const int y = int((n / a.nx) % a.ny);
+  const int z = int(n / ((long long)a.nx * a.ny));
+  if (!has_fluid_scalar_neighbour<L>(a, x, y, z)) return;
+  a.listed[n] = 1;
+  push_iface(a, n);
+}
+
 // ================================================================ geometry flips
 
 __device__ __forceinline__ bool cas_flag(uint8_t* flags, long long n, uint8_t expect, uint8_t desired,
@@ -1146,6 +1180,13 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
       int qx, qy, qz;
       coords_of(a, q, &qx, &qy, &qz);
       a.mask[q] = compute_mask<L>(a, qx, qy, qz);
+    }
+    if (dissolve) {
+      // reactive solids that now touch the new fluid node join the interface list
+      for (int j = 1; j < QC; ++j) {
+        const long long q = nbr_checked(a, x, y, z, L::cx(j), L::cy(j), L::cz(j), percs, &ax);
+        if (q >= 0 && a.flags[q] == FL_REACTIVE && cas_flag(a.listed, q, 0, 1, a.err)) push_iface(a, q);
+      }
     }
   }
   __syncthreads();

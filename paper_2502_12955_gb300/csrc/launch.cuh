@@ -18,6 +18,7 @@ struct KernelSet {
   cudaError_t (*pops_io)(const Args&, int parity, int dir, double* f, double* h, cudaStream_t);
   cudaError_t (*flip)(const Args&, int parity_next, cudaStream_t);
   cudaError_t (*masks)(const Args&, cudaStream_t);
+  cudaError_t (*iface)(const Args&, cudaStream_t);
   int psi_bytes;   // bytes per psi element (compute type)
 };
 
@@ -158,6 +159,12 @@ struct Launchers {
     return cudaGetLastError();
   }
 
+  static cudaError_t iface(const Args& a, cudaStream_t st) {
+    const unsigned int nb = (unsigned int)((a.N + 255) / 256);
+    k_iface_build<L><<<nb, 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+
   static KernelSet make() {
     KernelSet k;
     k.step = &step;
@@ -168,6 +175,7 @@ struct Launchers {
     k.pops_io = &pops_io;
     k.flip = &flip;
     k.masks = &masks;
+    k.iface = &iface;
     k.psi_bytes = (int)sizeof(typename Store<S>::T);
     return k;
   }
@@ -187,5 +195,6 @@ const KernelSet& kernels_d3_bf16();
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
                           int nonfin_slot, cudaStream_t st);
 cudaError_t launch_residual(const Args& a, int has_c, cudaStream_t st, long long* nblocks);
+cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st);
 
 }  // namespace lbm

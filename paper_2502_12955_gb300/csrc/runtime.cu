@@ -188,6 +188,18 @@ void fill_args(lbm_ctx* c) {
 
 int parity_of(long long step) { return int(step & 1); }
 
+lbm_status rebuild_geometry(lbm_ctx* c) {
+  LAUNCH(c->ks->masks(c->a, c->stream));
+  CK(cudaMemsetAsync(c->a.iface_count, 0, 16, c->stream));
+  CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
+  LAUNCH(c->ks->iface(c->a, c->stream));
+  return LBM_OK;
+}
+
+double dissolve_threshold(const lbm_params& p) {
+  return p.V_m > 0.0 ? p.m_s0 / p.V_m : HUGE_VAL;
+}
+
 lbm_status run_monitor(lbm_ctx* c) {
   long long nb = 0;
   LAUNCH(c->ks->monitor(c->a, parity_of(c->step), c->stream, &nb));
@@ -284,6 +296,23 @@ cudaError_t launch_reduce(const double* partials, long long nblocks, int K, doub
   return cudaGetLastError();
 }
 
+// Dissolution threshold test (acc >= m_s0 / V_m) over the interface list.
+__global__ void __launch_bounds__(256) k_detect(const Args a, const double thr) {
+  const unsigned int cnt = *a.iface_count;
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const long long n = a.iface_list[e];
+    if (a.flags[n] == FL_REACTIVE && a.acc[n] >= thr) push_flip(a, int(n));
+  }
+}
+
+cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st) {
+  long long nb = (a.N / 8 + 255) / 256;
+  if (nb < 1) nb = 1;
+  if (nb > 152 * 16) nb = 152 * 16;
+  k_detect<<<(unsigned int)nb, 256, 0, st>>>(a, thr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const Args& a, int has_c, cudaStream_t st, long long* nblocks) {
   const long long nb = (a.N + 255) / 256;
   *nblocks = nb;
@@ -366,6 +395,9 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   DA(a.acc, N * 8);
   unsigned int cap = (unsigned int)std::min<long long>(std::max<long long>(4096, N / 16), 1ll << 22);
   a.flip_cap = cap;
+  DA(a.iface_list, N * 4);
+  DA(a.iface_count, 16);
+  DA(a.listed, (N + 3) / 4 * 4);
   DA(a.flip_list, (size_t)cap * 4);
   DA(a.flip_count, 16);
   DA(a.flip_scratch, (size_t)cap * 4 * 8);
@@ -392,6 +424,8 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.mask, 0, N * 4, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.acc, 0, N * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_count, 0, 16, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.iface_count, 0, 16, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.listed, 0, (N + 3) / 4 * 4, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_row, 0, rows * 8, c->stream);
@@ -413,7 +447,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, size_t n) {
     if (flags[k] > 2) return fail(c, LBM_ERR_INVALID_ARG, "flag %u at node %zu", flags[k], k);
   CK(cudaMemcpyAsync(c->a.flags, flags, n, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
-  LAUNCH(c->ks->masks(c->a, c->stream));
+  lbm_status st = rebuild_geometry(c);
+  if (st != LBM_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
   c->fields_set = false;
   return LBM_OK;
@@ -469,8 +504,11 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
       c->ev_used.push_back({e0, e1});
     }
     c->step += 1;
-    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0)
+    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0) {
+      if (c->p.geo_mode == LBM_GEO_DISSOLVE)
+        LAUNCH(launch_detect(c->a, dissolve_threshold(c->p), c->stream));
       LAUNCH(c->ks->flip(c->a, parity_of(c->step), c->stream));
+    }
     if (c->p.N_mon > 0 && (c->step % c->p.N_mon) == 0) {
       lbm_status st = run_monitor(c);
       if (st != LBM_OK) return st;
@@ -675,7 +713,8 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   CK(cudaMemcpyAsync(c->a.flip_mon, o, 64, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
-  LAUNCH(c->ks->masks(c->a, c->stream));
+  lbm_status st = rebuild_geometry(c);
+  if (st != LBM_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
   c->step = hd.step;
   c->fields_set = true;
