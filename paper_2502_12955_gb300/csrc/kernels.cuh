@@ -76,6 +76,10 @@ struct Args {
   uint8_t* flags;
   uint32_t* mask;
   double* acc;               // consumed (reactive solid) / deposited (fluid) per node
+  uint32_t* fluid_list;       // fluid node indices (sorted at each rebuild, appended by flips)
+  unsigned int* fluid_count;
+  unsigned int* block_counts; // ordered-compaction scratch [N / 1024 + 1]
+  double* wallx_slot;        // [WALLX_SLOTS] wall-exchange accumulators
   uint32_t* iface_list;       // reactive solids with a fluid scalar-lattice neighbour
   unsigned int* iface_count;
   uint8_t* listed;           // 1 once a node is in iface_list
@@ -85,7 +89,6 @@ struct Args {
   double* flip_scratch;      // [flip_cap][4]
   double* flip_mon;          // [8] inj_mass[2], inj_spec[2], rem_mass[2], rem_spec[2]
   int* err;
-  double* wallx_row;         // [rows]
   double* inflow_row;        // [2][rows]
   double* outflow_row;       // [2][rows]
   double* partials;          // monitor partial sums [blocks][NMON]
@@ -131,6 +134,7 @@ struct Coef {
 };
 
 constexpr int NMON = 18;
+constexpr int WALLX_SLOTS = 4096;
 // partial-sum slots
 enum : int {
   M_MASS = 0, M_MOM = 2, M_SPEC = 5, M_REACT = 7, M_DEPO = 8, M_IN = 9, M_OUT = 11,
@@ -281,19 +285,22 @@ __device__ __forceinline__ T warp_sum(T v) {
 // velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
 // Registers hold deviations from w_i * ref throughout.
 template <class L, class S, int NC, int NS, int COLL>
-__global__ void __launch_bounds__(256) k_step(const Args a, const Coef<typename Store<S>::T> k,
+__global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k,
                                               const int parity) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  const bool inside = (x < a.nx) && (y < a.ny);
-  const int n = inside ? x + a.nx * (y + a.ny * z) : 0;
-  const uint32_t m = inside ? a.mask[n] : 0u;
-  const bool active = (m & 1u) != 0u;
   T wallx = T(0);
-  if (active) {
+  const unsigned int count = *a.fluid_count;
+  // threads walk the fluid-node list, so every lane of a warp updates a fluid node
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+  const int n = int(a.fluid_list[e]);
+  const uint32_t m = a.mask[n];
+  if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
+  const int x = n % a.nx;
+  const int yz = n / a.nx;
+  const int y = yz % a.ny;
+  const int z = yz / a.ny;
+  {
     const Nbr nb = make_nbr(a, x, y, z);
     const long long P = a.pitch;
     const int row = y + a.ny * z;
@@ -544,13 +551,15 @@ __global__ void __launch_bounds__(256) k_step(const Args a, const Coef<typename 
       }
     }
   }
-  // ---- wall-exchange monitor: one atomic per warp that saw a reactive link
+  }
+  // ---- wall-exchange monitor: one reduction per warp that saw a reactive link
   if (NS > 0) {
     const unsigned int any = __ballot_sync(0xffffffffu, wallx != T(0));
     if (any) {
-      // warps run along x inside one (y, z) row (block x extent is a multiple of 32)
-      const double w = warp_sum(double(wallx));
-      if ((threadIdx.x & 31) == 0 && y < a.ny) atomicAdd(a.wallx_row + (y + a.ny * z), w);
+      const T w = warp_sum(wallx);
+      if ((threadIdx.x & 31) == 0)
+        atomicAdd(a.wallx_slot + ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
+                  double(w));
     }
   }
 }
@@ -722,10 +731,13 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
     } else {
       v[M_REACT] += acc;
     }
+    {
+      const int nid = x + a.nx * (y + a.ny * z);
+      if (nid < WALLX_SLOTS) v[M_WALLX] += a.wallx_slot[nid];
+    }
     if (x == 0) {
       const int row = y + a.ny * z;
       const int rows = a.ny * a.nz;
-      v[M_WALLX] += a.wallx_row[row];
       for (int s = 0; s < NS; ++s) {
         v[M_IN + s] += a.inflow_row[s * rows + row];
         v[M_OUT + s] += a.outflow_row[s * rows + row];
@@ -921,6 +933,78 @@ __global__ void __launch_bounds__(256) k_masks(const Args a) {
   const int y = int((n / a.nx) % a.ny);
   const int z = int(n / ((long long)a.nx * a.ny));
   a.mask[n] = compute_mask<L>(a, x, y, z);
+}
+
+// ================================================================ fluid list
+
+// Ordered stream compaction of the fluid nodes in chunks of 1024 nodes: count, scan, write.
+__device__ __forceinline__ bool is_fluid_flag(const Args& a, long long n) { return a.flags[n] == FL_FLUID; }
+
+template <int DUMMY = 0>
+__global__ void __launch_bounds__(1024) k_fluid_count(const Args a) {
+  __shared__ unsigned int wsum[32];
+  const long long n = blockIdx.x * 1024ll + threadIdx.x;
+  const bool f = n < a.N && is_fluid_flag(a, n);
+  const unsigned int b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned int v = wsum[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) a.block_counts[blockIdx.x] = v;
+  }
+}
+
+// exclusive scan of the chunk counts by one block; total into fluid_count
+template <int DUMMY = 0>
+__global__ void __launch_bounds__(1024) k_fluid_scan(const Args a, unsigned int nchunks) {
+  __shared__ unsigned int part[1024];
+  __shared__ unsigned int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (unsigned int base = 0; base < nchunks; base += 1024) {
+    const unsigned int i = base + threadIdx.x;
+    const unsigned int v = i < nchunks ? a.block_counts[i] : 0u;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (unsigned int o = 1; o < 1024; o <<= 1) {
+      const unsigned int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+      __syncthreads();
+      part[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nchunks) a.block_counts[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.fluid_count = carry;
+}
+
+template <int DUMMY = 0>
+__global__ void __launch_bounds__(1024) k_fluid_write(const Args a) {
+  __shared__ unsigned int wsum[32];
+  const long long n = blockIdx.x * 1024ll + threadIdx.x;
+  const bool f = n < a.N && is_fluid_flag(a, n);
+  const unsigned int b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wsum[wid] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned int v = wsum[threadIdx.x], incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (threadIdx.x >= o) incl += t;
+    }
+    wsum[threadIdx.x] = incl - v;
+  }
+  __syncthreads();
+  if (f) {
+    const unsigned int pos = a.block_counts[blockIdx.x] + wsum[wid] + __popc(b & ((1u << lane) - 1u));
+    a.fluid_list[pos] = (uint32_t)n;
+  }
 }
 
 // ================================================================ interface list
@@ -1161,10 +1245,16 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
     }
   }
   __syncthreads();
-  // ---- phase 3: final flags
+  // ---- phase 3: final flags; new fluid nodes join the fluid list (removed ones are skipped by
+  // their mask until the next rebuild)
   for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
     if (a.flip_list[e] == 0xffffffffu) continue;
     leave_flipping(a.flags, a.flip_list[e], dissolve ? FL_FLUID : FL_SOLID);
+    if (dissolve) {
+      const unsigned int pos = atomicAdd(a.fluid_count, 1u);
+      if (pos < a.N) a.fluid_list[pos] = a.flip_list[e];
+      else atomicOr(a.err, ERR_CAPACITY);
+    }
   }
   __syncthreads();
   // ---- phase 4: masks around every flipped node

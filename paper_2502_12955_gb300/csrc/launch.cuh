@@ -64,10 +64,22 @@ struct Launchers {
   static constexpr bool kShifted = !std::is_same<S, double>::value;
   static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
 
+  // one resident wave of blocks; the kernel walks the fluid list with a grid-stride loop
   template <int NC, int NS, int COLL>
   static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
-    const dim3 blk = step_block(a);
-    k_step<L, S, NC, NS, COLL><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
+    const int threads = a.bx;
+    static int cached_threads = -1, cached_blocks = 0;
+    if (cached_threads != threads) {
+      int dev = 0, sms = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL>, threads, 0);
+      cached_blocks = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
+      cached_threads = threads;
+    }
+    long long need = (a.N + threads - 1) / threads;
+    const unsigned int blocks = (unsigned int)(need < cached_blocks ? need : cached_blocks);
+    k_step<L, S, NC, NS, COLL><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a), parity);
     return cudaGetLastError();
   }
   template <int NC, int NS>
@@ -196,5 +208,6 @@ cudaError_t launch_reduce(const double* partials, long long nblocks, int K, doub
                           int nonfin_slot, cudaStream_t st);
 cudaError_t launch_residual(const Args& a, int has_c, cudaStream_t st, long long* nblocks);
 cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st);
+cudaError_t launch_fluid_list(const Args& a, cudaStream_t st);
 
 }  // namespace lbm

@@ -188,8 +188,11 @@ void fill_args(lbm_ctx* c) {
 
 int parity_of(long long step) { return int(step & 1); }
 
+constexpr long long kListRebuild = 1024;   // steps between sorted rebuilds of the fluid list
+
 lbm_status rebuild_geometry(lbm_ctx* c) {
   LAUNCH(c->ks->masks(c->a, c->stream));
+  LAUNCH(launch_fluid_list(c->a, c->stream));
   CK(cudaMemsetAsync(c->a.iface_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
   LAUNCH(c->ks->iface(c->a, c->stream));
@@ -305,6 +308,14 @@ __global__ void __launch_bounds__(256) k_detect(const Args a, const double thr) 
   }
 }
 
+cudaError_t launch_fluid_list(const Args& a, cudaStream_t st) {
+  const unsigned int chunks = (unsigned int)((a.N + 1023) / 1024);
+  k_fluid_count<<<chunks, 1024, 0, st>>>(a);
+  k_fluid_scan<<<1, 1024, 0, st>>>(a, chunks);
+  k_fluid_write<<<chunks, 1024, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st) {
   long long nb = (a.N / 8 + 255) / 256;
   if (nb < 1) nb = 1;
@@ -395,6 +406,10 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   DA(a.acc, N * 8);
   unsigned int cap = (unsigned int)std::min<long long>(std::max<long long>(4096, N / 16), 1ll << 22);
   a.flip_cap = cap;
+  DA(a.fluid_list, N * 4);
+  DA(a.fluid_count, 16);
+  DA(a.block_counts, ((N + 1023) / 1024 + 1) * 4);
+  DA(a.wallx_slot, WALLX_SLOTS * 8);
   DA(a.iface_list, N * 4);
   DA(a.iface_count, 16);
   DA(a.listed, (N + 3) / 4 * 4);
@@ -403,7 +418,6 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   DA(a.flip_scratch, (size_t)cap * 4 * 8);
   DA(a.flip_mon, 8 * 8);
   DA(a.err, 16);
-  DA(a.wallx_row, rows * 8);
   DA(a.inflow_row, 2 * rows * 8);
   DA(a.outflow_row, 2 * rows * 8);
   // monitor partials: the monitor grid uses 128-thread blocks over x; the residual 256 over N
@@ -428,7 +442,8 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.listed, 0, (N + 3) / 4 * 4, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 16, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_row, 0, rows * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, WALLX_SLOTS * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.fluid_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.inflow_row, 0, 2 * rows * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 2 * rows * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.mon_out, 0, (NMON + 8) * 8, c->stream);
@@ -469,7 +484,7 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.flip_mon, 0, 64, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
-  CK(cudaMemsetAsync(c->a.wallx_row, 0, rows * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.wallx_slot, 0, WALLX_SLOTS * 8, c->stream));
   CK(cudaMemsetAsync(c->a.inflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.outflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
@@ -504,6 +519,9 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
       c->ev_used.push_back({e0, e1});
     }
     c->step += 1;
+    // geometry updates append new fluid nodes to the list; restore its sorted order now and then
+    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % kListRebuild) == 0)
+      LAUNCH(launch_fluid_list(c->a, c->stream));
     if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0) {
       if (c->p.geo_mode == LBM_GEO_DISSOLVE)
         LAUNCH(launch_detect(c->a, dissolve_threshold(c->p), c->stream));
@@ -645,7 +663,7 @@ struct StateHeader {
 size_t state_bytes(const lbm_ctx* c) {
   const size_t N = (size_t)c->N, P = (size_t)c->pitch, rows = (size_t)c->ny * c->nz;
   return sizeof(StateHeader) + (c->p.n_comp * c->Qf + c->p.n_scal * c->Qc) * P * c->elem +
-         (N + 3) / 4 * 4 + N * 8 + 5 * rows * 8 + 8 * 8;
+         (N + 3) / 4 * 4 + N * 8 + WALLX_SLOTS * 8 + 4 * rows * 8 + 8 * 8;
 }
 }  // namespace
 
@@ -676,7 +694,7 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   }
   CK(cudaMemcpyAsync(o, c->a.flags, (N + 3) / 4 * 4, cudaMemcpyDeviceToHost, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(o, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream)); o += N * 8;
-  CK(cudaMemcpyAsync(o, c->a.wallx_row, rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += rows * 8;
+  CK(cudaMemcpyAsync(o, c->a.wallx_slot, WALLX_SLOTS * 8, cudaMemcpyDeviceToHost, c->stream)); o += WALLX_SLOTS * 8;
   CK(cudaMemcpyAsync(o, c->a.inflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(o, c->a.outflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(o, c->a.flip_mon, 64, cudaMemcpyDeviceToHost, c->stream));
@@ -707,7 +725,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   }
   CK(cudaMemcpyAsync(c->a.flags, o, (N + 3) / 4 * 4, cudaMemcpyHostToDevice, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(c->a.acc, o, N * 8, cudaMemcpyHostToDevice, c->stream)); o += N * 8;
-  CK(cudaMemcpyAsync(c->a.wallx_row, o, rows * 8, cudaMemcpyHostToDevice, c->stream)); o += rows * 8;
+  CK(cudaMemcpyAsync(c->a.wallx_slot, o, WALLX_SLOTS * 8, cudaMemcpyHostToDevice, c->stream)); o += WALLX_SLOTS * 8;
   CK(cudaMemcpyAsync(c->a.inflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(c->a.outflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(c->a.flip_mon, o, 64, cudaMemcpyHostToDevice, c->stream));
