@@ -96,8 +96,7 @@ struct Args {
   double* d_rho;             // FP64 staging [n_comp][N]
   double* d_u;               // [3][N]
   double* d_C;               // [n_scal][N]
-  double* snap_u;            // [3][N]
-  double* snap_C;            // [N]
+  void* snap;                // compute-type residual snapshots [4][N]: u_x, u_y, u_z, C
   long long pitch;           // elements per population plane (>= N, multiple of 32)
   long long N;
   int nx, ny, nz;
@@ -592,28 +591,124 @@ __global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename S
   }
 }
 
-// ================================================================ moments
+// ================================================================ monitors
 
-// Macroscopic fields into FP64 staging: rho^sigma, physical velocity, closed scalars.
+template <int K>
+__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* out) {
+  __shared__ double sh[32][K];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) sh[wid][q] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double s = lane < nw ? sh[lane][q] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) out[q] = s;
+    }
+  }
+}
+
+// Monitors, one wave of blocks: population sums over the fluid list in the compute type
+// (deviations from the reference, so the sums stay accurate), bookkeeping sums over all nodes
+// in FP64, per-block partials in FP64 (summed in fixed order by k_reduce_partials).
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typename Store<S>::T> k,
+__global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typename Store<S>::T> k,
                                                  const int parity) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= a.nx || y >= a.ny) return;
-  const int n = x + a.nx * (y + a.ny * z);
-  const long long N = a.N;
-  const uint32_t m = a.mask[n];
-  if (!(m & 1u)) {
-    for (int s = 0; s < NC; ++s) a.d_rho[s * N + n] = 0.0;
-    for (int c = 0; c < 3; ++c) a.d_u[c * N + n] = 0.0;
-    for (int s = 0; s < NS; ++s) a.d_C[s * N + n] = 0.0;
-    return;
+  const unsigned int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned int nthr = gridDim.x * blockDim.x;
+  T dm[NC > 0 ? NC : 1], mom[3] = {T(0), T(0), T(0)}, dsp[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) dm[s] = T(0);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) dsp[s] = T(0);
+  unsigned int nfluid = 0, nonfin = 0;
+  const unsigned int count = *a.fluid_count;
+  for (unsigned int e = tid; e < count; e += nthr) {
+    const int n = int(a.fluid_list[e]);
+    const uint32_t m = a.mask[n];
+    if (!(m & 1u)) continue;
+    ++nfluid;
+    const Nbr nb = make_nbr(a, n % a.nx, (n / a.nx) % a.ny, n / a.nx / a.ny);
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      T f[Q];
+      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
+      T r = T(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        r += f[i];
+        if (L::cx(i)) mom[0] += T(L::cx(i)) * f[i];
+        if (L::cy(i)) mom[1] += T(L::cy(i)) * f[i];
+        if (L::cz(i)) mom[2] += T(L::cz(i)) * f[i];
+      }
+      bad |= !isfinite(r);
+      dm[s] += r;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      T h[QC];
+      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, h);
+      T c = T(0);
+#pragma unroll
+      for (int j = 0; j < QC; ++j) c += h[j];
+      bad |= !isfinite(c);
+      dsp[s] += c;
+    }
+    nonfin += bad ? 1u : 0u;
   }
-  const Nbr nb = make_nbr(a, x, y, z);
+  double v[NMON];
+#pragma unroll
+  for (int q = 0; q < NMON; ++q) v[q] = 0.0;
+  for (int s = 0; s < NC; ++s) v[M_MASS + s] = double(dm[s]) + double(k.rref[s]) * double(nfluid);
+  for (int c = 0; c < 3; ++c) v[M_MOM + c] = double(mom[c]);
+  for (int s = 0; s < NS; ++s) v[M_SPEC + s] = double(dsp[s]) + double(k.cref[s]) * double(nfluid);
+  v[M_NFLUID] = double(nfluid);
+  v[M_NONFIN] = double(nonfin);
+  // bookkeeping over every node
+  const bool dep = a.geo_mode == GEO_DEPOSIT;
+  double react = 0.0, depo = 0.0, nsolid = 0.0;
+  for (long long n = tid; n < a.N; n += nthr) {
+    const uint8_t fl = a.flags[n];
+    nsolid += fl != FL_FLUID ? 1.0 : 0.0;
+    const double acc = a.acc[n];
+    if (acc != 0.0) {
+      if (dep && fl != FL_REACTIVE) depo += acc; else react += acc;
+    }
+  }
+  v[M_REACT] = react;
+  v[M_DEPO] = depo;
+  v[M_NSOLID] = nsolid;
+  const int rows = a.ny * a.nz;
+  for (int r = tid; r < rows; r += nthr)
+    for (int s = 0; s < NS; ++s) {
+      v[M_IN + s] += a.inflow_row[s * rows + r];
+      v[M_OUT + s] += a.outflow_row[s * rows + r];
+    }
+  for (int q = tid; q < WALLX_SLOTS; q += nthr) v[M_WALLX] += a.wallx_slot[q];
+  block_reduce_store<NMON>(v, a.partials + (long long)blockIdx.x * NMON);
+}
+
+// ================================================================ node macroscopics
+
+// rho^sigma, physical velocity (Eq. 1.19) and closed scalars of fluid node n; psi arrays must be
+// current when Shan-Chen forces are on.
+template <class L, class S, int NC, int NS>
+__device__ __forceinline__ void node_macros(const Args& a, const Coef<typename Store<S>::T>& k, int n,
+                                            uint32_t m, int parity, typename Store<S>::T* rho_out,
+                                            typename Store<S>::T* u_out, typename Store<S>::T* C_out) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC;
+  const Nbr nb = make_nbr(a, n % a.nx, (n / a.nx) % a.ny, n / a.nx / a.ny);
   T rho[NC], jx[NC], jy[NC], jz[NC], Fx[NC], Fy[NC], Fz[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
@@ -670,10 +765,10 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typena
     my += jy[s] + T(0.5) * Fy[s];
     mz += jz[s] + T(0.5) * Fz[s];
   }
-  for (int s = 0; s < NC; ++s) a.d_rho[s * N + n] = double(rho[s]);
-  a.d_u[0 * N + n] = double(mx / rt);
-  a.d_u[1 * N + n] = double(my / rt);
-  a.d_u[2 * N + n] = double(mz / rt);
+  for (int s = 0; s < NC; ++s) rho_out[s] = rho[s];
+  u_out[0] = mx / rt;
+  u_out[1] = my / rt;
+  u_out[2] = mz / rt;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T h[QC];
@@ -682,139 +777,96 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typena
     T C = k.cref[s];
 #pragma unroll
     for (int j = 0; j < QC; ++j) C += h[j];
-    a.d_C[s * N + n] = double(C);
+    C_out[s] = C;
   }
 }
 
-// ================================================================ monitors
-
-template <int K>
-__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* out) {
-  __shared__ double sh[32][K];
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int lane = tid & 31, wid = tid >> 5;
-  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) sh[wid][k] = s;
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = lane < nw ? sh[lane][k] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0) out[k] = s;
-    }
-  }
-}
-
+// Macroscopic fields of every node into FP64 staging (solid nodes read 0).
 template <class L, class S, int NC, int NS>
-__global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typename Store<S>::T> k,
+__global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typename Store<S>::T> k,
                                                  const int parity) {
   using T = typename Store<S>::T;
-  constexpr int Q = L::Q, QC = L::QC;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  double v[NMON];
-#pragma unroll
-  for (int q = 0; q < NMON; ++q) v[q] = 0.0;
-  if (x < a.nx && y < a.ny) {
-    const int n = x + a.nx * (y + a.ny * z);
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const long long N = a.N;
+  const uint32_t m = a.mask[n];
+  T rho[NC], u[3], C[NS > 0 ? NS : 1];
+  if (m & 1u) {
+    node_macros<L, S, NC, NS>(a, k, int(n), m, parity, rho, u, C);
+  } else {
+    for (int s = 0; s < NC; ++s) rho[s] = T(0);
+    u[0] = u[1] = u[2] = T(0);
+    for (int s = 0; s < NS; ++s) C[s] = T(0);
+  }
+  for (int s = 0; s < NC; ++s) a.d_rho[s * N + n] = double(rho[s]);
+  for (int c = 0; c < 3; ++c) a.d_u[c * N + n] = double(u[c]);
+  for (int s = 0; s < NS; ++s) a.d_C[s * N + n] = double(C[s]);
+}
+
+// Residual partials over the fluid list against compute-type snapshots [4][N] (u, C), which
+// are replaced: sum (u - u_s)^2, sum u^2, sum (C - C_s)^2, sum C^2.
+template <class L, class S, int NC, int NS>
+__global__ void __launch_bounds__(256) k_resid(const Args a, const Coef<typename Store<S>::T> k,
+                                               const int parity) {
+  using T = typename Store<S>::T;
+  T* snap = reinterpret_cast<T*>(a.snap);
+  const long long N = a.N;
+  T du = T(0), uu = T(0), dc = T(0), cc = T(0);
+  const unsigned int count = *a.fluid_count;
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    const int n = int(a.fluid_list[e]);
     const uint32_t m = a.mask[n];
-    const uint8_t fl = a.flags[n];
-    const double acc = a.acc[n];
-    if (a.geo_mode == GEO_DEPOSIT) {
-      if (fl == FL_REACTIVE) v[M_REACT] += acc; else v[M_DEPO] += acc;
-    } else {
-      v[M_REACT] += acc;
+    if (!(m & 1u)) continue;
+    T rho[NC], u[3], C[NS > 0 ? NS : 1];
+    node_macros<L, S, NC, NS>(a, k, n, m, parity, rho, u, C);
+    for (int c = 0; c < 3; ++c) {
+      const T d = u[c] - snap[c * N + n];
+      du += d * d;
+      uu += u[c] * u[c];
+      snap[c * N + n] = u[c];
     }
-    {
-      const int nid = x + a.nx * (y + a.ny * z);
-      if (nid < WALLX_SLOTS) v[M_WALLX] += a.wallx_slot[nid];
-    }
-    if (x == 0) {
-      const int row = y + a.ny * z;
-      const int rows = a.ny * a.nz;
-      for (int s = 0; s < NS; ++s) {
-        v[M_IN + s] += a.inflow_row[s * rows + row];
-        v[M_OUT + s] += a.outflow_row[s * rows + row];
-      }
-    }
-    if (!(m & 1u)) {
-      v[M_NSOLID] += 1.0;
-    } else {
-      v[M_NFLUID] += 1.0;
-      const Nbr nb = make_nbr(a, x, y, z);
-      bool bad = false;
-#pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        T f[Q];
-        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
-        double r = double(k.rref[s]);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const double fi = double(f[i]);
-          r += fi;
-          v[M_MOM + 0] += L::cx(i) * fi;
-          v[M_MOM + 1] += L::cy(i) * fi;
-          v[M_MOM + 2] += L::cz(i) * fi;
-          bad |= !isfinite(fi);
-        }
-        v[M_MASS + s] += r;
-      }
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        T h[QC];
-        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, h);
-        double C = double(k.cref[s]);
-#pragma unroll
-        for (int j = 0; j < QC; ++j) {
-          C += double(h[j]);
-          bad |= !isfinite(double(h[j]));
-        }
-        v[M_SPEC + s] += C;
-      }
-      if (bad) v[M_NONFIN] += 1.0;
+    if (NS > 0) {
+      const T d = C[0] - snap[3 * N + n];
+      dc += d * d;
+      cc += C[0] * C[0];
+      snap[3 * N + n] = C[0];
     }
   }
-  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_reduce_store<NMON>(v, a.partials + (long long)bid * NMON);
+  double v[4] = {double(du), double(uu), double(dc), double(cc)};
+  block_reduce_store<4>(v, a.partials + (long long)blockIdx.x * 4);
 }
 
 // ================================================================ init / pop I/O
 
-// Equilibrium populations from FP64 staging fields (Eq. 6, Eq. therpopeq_species), natural layout.
+// Equilibrium populations from FP64 staging fields (Eq. 6, Eq. therpopeq_species), natural
+// layout, computed in the compute type.
 template <class L, class S, int NC, int NS>
 __global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= a.N) return;
   const bool fluid = a.flags[n] == FL_FLUID;
-  const double ux = a.d_u[n], uy = a.d_u[a.N + n], uz = (L::D == 3) ? a.d_u[2 * a.N + n] : 0.0;
+  const T ux = T(a.d_u[n]), uy = T(a.d_u[a.N + n]), uz = (L::D == 3) ? T(a.d_u[2 * a.N + n]) : T(0);
   for (int s = 0; s < NC; ++s) {
     S* fs = reinterpret_cast<S*>(a.f[s]);
-    const double r = a.d_rho[s * a.N + n];
-    const double rr = double(k.rref[s]);
+    const T r = T(a.d_rho[s * a.N + n]);
+    const T dr = T(a.d_rho[s * a.N + n] - double(k.rref[s]));
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      const double v = fluid ? feq_dev<L, double>(i, r, r - rr, ux, uy, uz) : 0.0;
-      Store<S>::st(fs + (long long)i * a.pitch + n, T(v));
+      const T v = fluid ? feq_dev<L, T>(i, r, dr, ux, uy, uz) : T(0);
+      Store<S>::st(fs + (long long)i * a.pitch + n, v);
     }
   }
-  const double ics2 = double(k.ics2c);
   for (int s = 0; s < NS; ++s) {
     S* hs = reinterpret_cast<S*>(a.h[s]);
-    const double C = a.d_C[s * a.N + n];
-    const double cr = double(k.cref[s]);
+    const T C = T(a.d_C[s * a.N + n]);
+    const T dC = T(a.d_C[s * a.N + n] - double(k.cref[s]));
 #pragma unroll
     for (int j = 0; j < L::QC; ++j) {
-      const double cu = L::cx(j) * ux + L::cy(j) * uy + L::cz(j) * uz;
-      const double wj = double(scal_w<T>(j, k));
-      const double v = fluid ? wj * (C - cr) + wj * C * cu * ics2 : 0.0;
-      Store<S>::st(hs + (long long)j * a.pitch + n, T(v));
+      const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
+      const T wj = scal_w<T>(j, k);
+      const T v = fluid ? wj * (dC + C * cu * k.ics2c) : T(0);
+      Store<S>::st(hs + (long long)j * a.pitch + n, v);
     }
   }
 }
@@ -935,16 +987,29 @@ __global__ void __launch_bounds__(256) k_masks(const Args a) {
   a.mask[n] = compute_mask<L>(a, x, y, z);
 }
 
-// ================================================================ fluid list
+// ================================================================ node lists
 
-// Ordered stream compaction of the fluid nodes in chunks of 1024 nodes: count, scan, write.
-__device__ __forceinline__ bool is_fluid_flag(const Args& a, long long n) { return a.flags[n] == FL_FLUID; }
+// Ordered stream compaction of the nodes that satisfy a predicate, in chunks of 1024 nodes:
+// count, scan, write.  PRED 0: fluid nodes (the step kernel's work list).  PRED 1: reactive
+// solids touching the fluid through a scalar link (the dissolution interface list; also marks
+// listed[]).
+template <class L>
+__device__ __forceinline__ bool has_fluid_scalar_neighbour(const Args& a, int x, int y, int z);
 
-template <int DUMMY = 0>
-__global__ void __launch_bounds__(1024) k_fluid_count(const Args a) {
+template <class L, int PRED>
+__device__ __forceinline__ bool list_pred(const Args& a, long long n) {
+  if (n >= a.N) return false;
+  if (PRED == 0) return a.flags[n] == FL_FLUID;
+  if (a.flags[n] != FL_REACTIVE) return false;
+  return has_fluid_scalar_neighbour<L>(a, int(n % a.nx), int((n / a.nx) % a.ny),
+                                       int(n / ((long long)a.nx * a.ny)));
+}
+
+template <class L, int PRED>
+__global__ void __launch_bounds__(1024) k_list_count(const Args a) {
   __shared__ unsigned int wsum[32];
   const long long n = blockIdx.x * 1024ll + threadIdx.x;
-  const bool f = n < a.N && is_fluid_flag(a, n);
+  const bool f = list_pred<L, PRED>(a, n);
   const unsigned int b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
   __syncthreads();
@@ -956,9 +1021,10 @@ __global__ void __launch_bounds__(1024) k_fluid_count(const Args a) {
   }
 }
 
-// exclusive scan of the chunk counts by one block; total into fluid_count
+// exclusive scan of the chunk counts by one block; the total goes to *count
 template <int DUMMY = 0>
-__global__ void __launch_bounds__(1024) k_fluid_scan(const Args a, unsigned int nchunks) {
+__global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int nchunks,
+                                                    unsigned int* count) {
   __shared__ unsigned int part[1024];
   __shared__ unsigned int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -979,14 +1045,14 @@ __global__ void __launch_bounds__(1024) k_fluid_scan(const Args a, unsigned int 
     if (threadIdx.x == 1023) carry += part[1023];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *a.fluid_count = carry;
+  if (threadIdx.x == 0) *count = carry;
 }
 
-template <int DUMMY = 0>
-__global__ void __launch_bounds__(1024) k_fluid_write(const Args a) {
+template <class L, int PRED>
+__global__ void __launch_bounds__(1024) k_list_write(const Args a, uint32_t* list) {
   __shared__ unsigned int wsum[32];
   const long long n = blockIdx.x * 1024ll + threadIdx.x;
-  const bool f = n < a.N && is_fluid_flag(a, n);
+  const bool f = list_pred<L, PRED>(a, n);
   const unsigned int b = __ballot_sync(0xffffffffu, f);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) wsum[wid] = __popc(b);
@@ -1003,7 +1069,8 @@ __global__ void __launch_bounds__(1024) k_fluid_write(const Args a) {
   __syncthreads();
   if (f) {
     const unsigned int pos = a.block_counts[blockIdx.x] + wsum[wid] + __popc(b & ((1u << lane) - 1u));
-    a.fluid_list[pos] = (uint32_t)n;
+    list[pos] = (uint32_t)n;
+    if (PRED == 1) a.listed[n] = 1;
   }
 }
 
@@ -1024,19 +1091,6 @@ __device__ __forceinline__ void push_iface(const Args& a, long long n) {
   const unsigned int e = atomicAdd(a.iface_count, 1u);
   if (e < a.N) a.iface_list[e] = (uint32_t)n;
   else atomicOr(a.err, ERR_CAPACITY);
-}
-
-// Reactive solids touching the fluid through a scalar link; listed[] must be zero on entry.
-template <class L>
-__global__ void __launch_bounds__(256) k_iface_build(const Args a) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= a.N || a.flags[n] != FL_REACTIVE) return;
-  const int x = int(n % a.nx);
-  const int y = int((n / a.nx) % a.ny);
-  const int z = int(n / ((long long)a.nx * a.ny));
-  if (!has_fluid_scalar_neighbour<L>(a, x, y, z)) return;
-  a.listed[n] = 1;
-  push_iface(a, n);
 }
 
 // ================================================================ geometry flips

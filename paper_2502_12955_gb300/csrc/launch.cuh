@@ -18,7 +18,8 @@ struct KernelSet {
   cudaError_t (*pops_io)(const Args&, int parity, int dir, double* f, double* h, cudaStream_t);
   cudaError_t (*flip)(const Args&, int parity_next, cudaStream_t);
   cudaError_t (*masks)(const Args&, cudaStream_t);
-  cudaError_t (*iface)(const Args&, cudaStream_t);
+  cudaError_t (*lists)(const Args&, int which, cudaStream_t);   // which: 1 fluid, 2 interface, 3 both
+  cudaError_t (*resid)(const Args&, int parity, cudaStream_t, long long* nblocks);
   int psi_bytes;   // bytes per psi element (compute type)
 };
 
@@ -27,6 +28,18 @@ inline dim3 node_grid(const Args& a, dim3 blk) {
 }
 
 inline dim3 step_block(const Args& a) { return dim3(a.bx, a.by, 1); }
+
+// blocks of 256 threads for one resident wave (4 per SM) of the reduction kernels
+inline unsigned int wave_blocks() {
+  static unsigned int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached = (unsigned int)((sms > 0 ? sms : 1) * 4);
+  }
+  return cached;
+}
 
 // Host-side derivation of every constant the kernels use, in their compute type.
 template <class L, class T>
@@ -124,19 +137,27 @@ struct Launchers {
   }
 
   static cudaError_t moments(const Args& a, int parity, cudaStream_t st) {
-    const dim3 blk(128, 1, 1);
+    const unsigned int nb = (unsigned int)((a.N + 255) / 256);
     by_nc_ns(a, [&](auto nc, auto ns) {
-      k_moments<L, S, decltype(nc)::value, decltype(ns)::value><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
+      k_moments<L, S, decltype(nc)::value, decltype(ns)::value><<<nb, 256, 0, st>>>(a, coef(a), parity);
     });
     return cudaGetLastError();
   }
 
   static cudaError_t monitor(const Args& a, int parity, cudaStream_t st, long long* nblocks) {
-    const dim3 blk(128, 1, 1);
-    const dim3 grd = node_grid(a, blk);
-    *nblocks = (long long)grd.x * grd.y * grd.z;
+    const unsigned int grd = wave_blocks();
+    *nblocks = grd;
     by_nc_ns(a, [&](auto nc, auto ns) {
-      k_monitor<L, S, decltype(nc)::value, decltype(ns)::value><<<grd, blk, 0, st>>>(a, coef(a), parity);
+      k_monitor<L, S, decltype(nc)::value, decltype(ns)::value><<<grd, 256, 0, st>>>(a, coef(a), parity);
+    });
+    return cudaGetLastError();
+  }
+
+  static cudaError_t resid(const Args& a, int parity, cudaStream_t st, long long* nblocks) {
+    const unsigned int grd = wave_blocks();
+    *nblocks = grd;
+    by_nc_ns(a, [&](auto nc, auto ns) {
+      k_resid<L, S, decltype(nc)::value, decltype(ns)::value><<<grd, 256, 0, st>>>(a, coef(a), parity);
     });
     return cudaGetLastError();
   }
@@ -171,9 +192,19 @@ struct Launchers {
     return cudaGetLastError();
   }
 
-  static cudaError_t iface(const Args& a, cudaStream_t st) {
-    const unsigned int nb = (unsigned int)((a.N + 255) / 256);
-    k_iface_build<L><<<nb, 256, 0, st>>>(a);
+  // ordered rebuild of the fluid list (which & 1) and the interface list (which & 2)
+  static cudaError_t lists(const Args& a, int which, cudaStream_t st) {
+    const unsigned int chunks = (unsigned int)((a.N + 1023) / 1024);
+    if (which & 1) {
+      k_list_count<L, 0><<<chunks, 1024, 0, st>>>(a);
+      k_list_scan<<<1, 1024, 0, st>>>(a, chunks, a.fluid_count);
+      k_list_write<L, 0><<<chunks, 1024, 0, st>>>(a, a.fluid_list);
+    }
+    if (which & 2) {
+      k_list_count<L, 1><<<chunks, 1024, 0, st>>>(a);
+      k_list_scan<<<1, 1024, 0, st>>>(a, chunks, a.iface_count);
+      k_list_write<L, 1><<<chunks, 1024, 0, st>>>(a, a.iface_list);
+    }
     return cudaGetLastError();
   }
 
@@ -187,7 +218,8 @@ struct Launchers {
     k.pops_io = &pops_io;
     k.flip = &flip;
     k.masks = &masks;
-    k.iface = &iface;
+    k.lists = &lists;
+    k.resid = &resid;
     k.psi_bytes = (int)sizeof(typename Store<S>::T);
     return k;
   }
@@ -206,8 +238,6 @@ const KernelSet& kernels_d3_bf16();
 // Storage-independent kernels (runtime.cu)
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
                           int nonfin_slot, cudaStream_t st);
-cudaError_t launch_residual(const Args& a, int has_c, cudaStream_t st, long long* nblocks);
 cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st);
-cudaError_t launch_fluid_list(const Args& a, cudaStream_t st);
 
 }  // namespace lbm

@@ -192,10 +192,8 @@ constexpr long long kListRebuild = 1024;   // steps between sorted rebuilds of t
 
 lbm_status rebuild_geometry(lbm_ctx* c) {
   LAUNCH(c->ks->masks(c->a, c->stream));
-  LAUNCH(launch_fluid_list(c->a, c->stream));
-  CK(cudaMemsetAsync(c->a.iface_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
-  LAUNCH(c->ks->iface(c->a, c->stream));
+  LAUNCH(c->ks->lists(c->a, 3, c->stream));
   return LBM_OK;
 }
 
@@ -218,10 +216,9 @@ lbm_status run_moments(lbm_ctx* c) {
 
 // residual partials land in partials[0 .. 4*nb); summed into mon_out[NMON .. NMON+4)
 lbm_status run_residual(lbm_ctx* c) {
-  lbm_status st = run_moments(c);
-  if (st != LBM_OK) return st;
+  if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, parity_of(c->step), c->stream));
   long long nb = 0;
-  LAUNCH(launch_residual(c->a, c->p.n_scal > 0 ? 1 : 0, c->stream, &nb));
+  LAUNCH(c->ks->resid(c->a, parity_of(c->step), c->stream, &nb));
   LAUNCH(launch_reduce(c->a.partials, nb, 4, c->a.mon_out + NMON, c->a.err, -1, c->stream));
   return LBM_OK;
 }
@@ -270,29 +267,6 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restri
   if (threadIdx.x == 0 && nonfin_slot >= 0 && out[nonfin_slot] > 0.0) atomicOr(err, ERR_NONFINITE);
 }
 
-// Residual partials: sum (u - u_snap)^2, sum u^2, sum (C - C_snap)^2, sum C^2; snapshot update.
-__global__ void __launch_bounds__(256) k_residual(const Args a, int has_c) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  if (n < a.N && (a.mask[n] & 1u)) {
-    for (int c = 0; c < 3; ++c) {
-      const double u = a.d_u[c * a.N + n];
-      const double d = u - a.snap_u[c * a.N + n];
-      v[0] += d * d;
-      v[1] += u * u;
-      a.snap_u[c * a.N + n] = u;
-    }
-    if (has_c) {
-      const double C = a.d_C[n];
-      const double d = C - a.snap_C[n];
-      v[2] += d * d;
-      v[3] += C * C;
-      a.snap_C[n] = C;
-    }
-  }
-  block_reduce_store<4>(v, a.partials + (long long)blockIdx.x * 4);
-}
-
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
                           int nonfin_slot, cudaStream_t st) {
   k_reduce_partials<<<1, 1024, 0, st>>>(partials, nblocks, K, out, err, nonfin_slot);
@@ -308,26 +282,11 @@ __global__ void __launch_bounds__(256) k_detect(const Args a, const double thr) 
   }
 }
 
-cudaError_t launch_fluid_list(const Args& a, cudaStream_t st) {
-  const unsigned int chunks = (unsigned int)((a.N + 1023) / 1024);
-  k_fluid_count<<<chunks, 1024, 0, st>>>(a);
-  k_fluid_scan<<<1, 1024, 0, st>>>(a, chunks);
-  k_fluid_write<<<chunks, 1024, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st) {
   long long nb = (a.N / 8 + 255) / 256;
   if (nb < 1) nb = 1;
   if (nb > 152 * 16) nb = 152 * 16;
   k_detect<<<(unsigned int)nb, 256, 0, st>>>(a, thr);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_residual(const Args& a, int has_c, cudaStream_t st, long long* nblocks) {
-  const long long nb = (a.N + 255) / 256;
-  *nblocks = nb;
-  k_residual<<<(unsigned int)nb, 256, 0, st>>>(a, has_c);
   return cudaGetLastError();
 }
 
@@ -421,15 +380,12 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   DA(a.inflow_row, 2 * rows * 8);
   DA(a.outflow_row, 2 * rows * 8);
   // monitor partials: the monitor grid uses 128-thread blocks over x; the residual 256 over N
-  const long long mon_blocks = ((nx + 127) / 128) * rows;
-  const long long res_blocks = (N + 255) / 256;
-  DA(a.partials, std::max(mon_blocks * NMON, res_blocks * 4) * 8);
+  DA(a.partials, (long long)wave_blocks() * NMON * 8);
   DA(a.mon_out, (NMON + 8) * 8);
   DA(a.d_rho, 2 * N * 8);
   DA(a.d_u, 3 * N * 8);
   DA(a.d_C, std::max<long long>(1, params->n_scal) * N * 8);
-  DA(a.snap_u, 3 * N * 8);
-  DA(a.snap_C, N * 8);
+  DA(a.snap, 4 * N * c->ks->psi_bytes);
 #undef DA
   e = cudaMallocHost(reinterpret_cast<void**>(&c->mon_host), (NMON + 8) * sizeof(double));
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
@@ -488,6 +444,7 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
   CK(cudaMemsetAsync(c->a.inflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.outflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.snap, 0, 4 * c->N * c->ks->psi_bytes, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->step = 0;
   c->fields_set = true;
@@ -520,8 +477,10 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
     }
     c->step += 1;
     // geometry updates append new fluid nodes to the list; restore its sorted order now and then
-    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % kListRebuild) == 0)
-      LAUNCH(launch_fluid_list(c->a, c->stream));
+    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % kListRebuild) == 0) {
+      CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
+      LAUNCH(c->ks->lists(c->a, 3, c->stream));
+    }
     if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0) {
       if (c->p.geo_mode == LBM_GEO_DISSOLVE)
         LAUNCH(launch_detect(c->a, dissolve_threshold(c->p), c->stream));
