@@ -290,10 +290,19 @@ __global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, c
   constexpr int Q = L::Q, QC = L::QC;
   T wallx = T(0);
   const unsigned int count = *a.fluid_count;
-  // threads walk the fluid-node list, so every lane of a warp updates a fluid node
-  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
-  const int n = int(a.fluid_list[e]);
-  const uint32_t m = a.mask[n];
+  const unsigned int stride = gridDim.x * blockDim.x;
+  // threads walk the fluid-node list, so every lane of a warp updates a fluid node; the list
+  // entry is fetched two iterations and the link mask one iteration ahead
+  unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int n_next = e < count ? int(a.fluid_list[e]) : 0;
+  int n_next2 = e + stride < count ? int(a.fluid_list[e + stride]) : 0;
+  uint32_t m_next = e < count ? a.mask[n_next] : 0u;
+  for (; e < count; e += stride) {
+  const int n = n_next;
+  const uint32_t m = m_next;
+  n_next = n_next2;
+  if (e + stride < count) m_next = a.mask[n_next];
+  if (e + 2 * stride < count) n_next2 = int(a.fluid_list[e + 2 * stride]);
   if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
   const int x = n % a.nx;
   const int yz = n / a.nx;
