@@ -283,9 +283,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // bookkeeping, deposition, moments, forces, velocity, flow collision (BGK / MRT, Guo or
 // velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
 // Registers hold deviations from w_i * ref throughout.
-template <class L, class S, int NC, int NS, int COLL>
-__global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k,
-                                              const int parity) {
+template <class L, class S, int NC, int NS, int COLL, int parity>
+__global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   T wallx = T(0);
@@ -453,47 +452,85 @@ __global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, c
           f[s][i] -= k.om[s] * (f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ex, ey, ez));
       }
     } else {
+      // Eq. 1.16 with Guo forcing (Eq. 1.21): f* = f + F_i - omega (f - f_eq + F_i / 2), for BGK;
+      // MRT adds the projections of n = f - f_eq + F_i / 2 on the non-hydrodynamic groups with
+      // rate (s_g - 1/tau).  Opposite directions are handled as pairs: the equilibrium and the
+      // Guo term split into even and odd parts, even MRT rows see n_i + n_opp(i), odd rows see
+      // n_i - n_opp(i).
+      const T uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
       for (int s = 0; s < NC; ++s) {
         const T om = k.om[s];
-        if (COLL == 0) {
-          // Eq. 1.16 with Guo forcing: f* = f + F_i - omega (f - f_eq + F_i / 2)
+        const T uF = ux * Fx[s] + uy * Fy[s] + uz * Fz[s];
+        T sp[Q], dp[Q];   // pair sums / differences of n (MRT only), index of the first member
+        {
+          // rest population
+          const T w0 = T(L::w(0));
+          const T fe = w0 * (drho[s] - rho[s] * T(1.5) * uu);
+          const T Fi = w0 * (T(-3) * uF);
+          const T nq = f[s][0] - fe + T(0.5) * Fi;
+          if (COLL == 1) sp[0] = nq;
+          f[s][0] = f[s][0] + Fi - om * nq;
+        }
 #pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const T Fi = guo<L, T>(i, ux, uy, uz, Fx[s], Fy[s], Fz[s]);
-            const T nq = f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ux, uy, uz) + T(0.5) * Fi;
-            f[s][i] = f[s][i] + Fi - om * nq;
+        for (int i = 1; i < Q; ++i) {
+          if (i > L::opp(i)) continue;
+          const int o = L::opp(i);
+          const T w = T(L::w(i));
+          const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+          const T cF = T(L::cx(i)) * Fx[s] + T(L::cy(i)) * Fy[s] + T(L::cz(i)) * Fz[s];
+          const T fe_e = w * (drho[s] + rho[s] * (T(4.5) * cu * cu - T(1.5) * uu));
+          const T fe_o = w * (T(3) * rho[s] * cu);
+          const T Fi_e = w * (T(9) * cu * cF - T(3) * uF);
+          const T Fi_o = w * (T(3) * cF);
+          const T nq_i = f[s][i] - (fe_e + fe_o) + T(0.5) * (Fi_e + Fi_o);
+          const T nq_o = f[s][o] - (fe_e - fe_o) + T(0.5) * (Fi_e - Fi_o);
+          if (COLL == 1) {
+            sp[i] = nq_i + nq_o;
+            dp[i] = nq_i - nq_o;
           }
-        } else {
-          // MRT: f* = f + F_i - M^-1 S M (f - f_eq + F_i / 2), written as BGK with rate
-          // 1/tau plus projections on the non-hydrodynamic groups with rate (s_g - 1/tau).
-          T nq[Q];
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const T Fi = guo<L, T>(i, ux, uy, uz, Fx[s], Fy[s], Fz[s]);
-            nq[i] = f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ux, uy, uz) + T(0.5) * Fi;
-            f[s][i] = f[s][i] + Fi - om * nq[i];
-          }
+          f[s][i] = f[s][i] + (Fi_e + Fi_o) - om * nq_i;
+          f[s][o] = f[s][o] + (Fi_e - Fi_o) - om * nq_o;
+        }
+        if (COLL == 1) {
           T coef[L::NMRT];
 #pragma unroll
           for (int kk = 0; kk < L::NMRT; ++kk) {
             T mk = T(0);
+            if (!mrt_odd<L>(kk)) {
+              const int r0 = Mrt<L>::row(kk, 0);
+              if (r0 != 0) mk += T(r0) * sp[0];
+            }
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
+            for (int i = 1; i < Q; ++i) {
+              if (i > L::opp(i)) continue;
               const int r = Mrt<L>::row(kk, i);
-              if (r != 0) mk += T(r) * nq[i];
+              if (r != 0) mk += T(r) * (mrt_odd<L>(kk) ? dp[i] : sp[i]);
             }
             coef[kk] = (k.s_grp[Mrt<L>::group(kk)] - om) * mk * k.inv_norm[kk];
           }
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
+          {
             T c = T(0);
 #pragma unroll
             for (int kk = 0; kk < L::NMRT; ++kk) {
-              const int r = Mrt<L>::row(kk, i);
-              if (r != 0) c += T(r) * coef[kk];
+              const int r = Mrt<L>::row(kk, 0);
+              if (r != 0 && !mrt_odd<L>(kk)) c += T(r) * coef[kk];
             }
-            f[s][i] -= c;
+            f[s][0] -= c;
+          }
+#pragma unroll
+          for (int i = 1; i < Q; ++i) {
+            if (i > L::opp(i)) continue;
+            T ce = T(0), co = T(0);
+#pragma unroll
+            for (int kk = 0; kk < L::NMRT; ++kk) {
+              const int r = Mrt<L>::row(kk, i);
+              if (r == 0) continue;
+              if (mrt_odd<L>(kk)) co += T(r) * coef[kk];
+              else ce += T(r) * coef[kk];
+            }
+            f[s][i] -= ce + co;
+            f[s][L::opp(i)] -= ce - co;
           }
         }
       }

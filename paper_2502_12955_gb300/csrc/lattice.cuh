@@ -102,6 +102,12 @@ struct Mrt<D2> {
   }
 };
 
+// odd rows (heat flux q, cubic m) change sign under c -> -c; the others are even
+template <class L>
+__host__ __device__ constexpr bool mrt_odd(int k) {
+  return Mrt<L>::group(k) == 2 || Mrt<L>::group(k) == 4;
+}
+
 template <class L>
 __host__ __device__ constexpr int mrt_norm2(int k) {
   int s = 0;

@@ -78,22 +78,26 @@ struct Launchers {
   static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
 
   // one resident wave of blocks; the kernel walks the fluid list with a grid-stride loop
-  template <int NC, int NS, int COLL>
-  static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
+  template <int NC, int NS, int COLL, int PAR>
+  static cudaError_t step_p(const Args& a, cudaStream_t st) {
     const int threads = a.bx;
     static int cached_threads = -1, cached_blocks = 0;
     if (cached_threads != threads) {
       int dev = 0, sms = 0, occ = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL>, threads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL, PAR>, threads, 0);
       cached_blocks = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
       cached_threads = threads;
     }
     long long need = (a.N + threads - 1) / threads;
     const unsigned int blocks = (unsigned int)(need < cached_blocks ? need : cached_blocks);
-    k_step<L, S, NC, NS, COLL><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a), parity);
+    k_step<L, S, NC, NS, COLL, PAR><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a));
     return cudaGetLastError();
+  }
+  template <int NC, int NS, int COLL>
+  static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
+    return parity ? step_p<NC, NS, COLL, 1>(a, st) : step_p<NC, NS, COLL, 0>(a, st);
   }
   template <int NC, int NS>
   static cudaError_t step_c(const Args& a, int parity, int coll, cudaStream_t st) {

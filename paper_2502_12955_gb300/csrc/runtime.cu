@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_detect(const Args a, const double thr) 
   const unsigned int cnt = *a.iface_count;
   for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
     const long long n = a.iface_list[e];
-    if (a.flags[n] == FL_REACTIVE && a.acc[n] >= thr) push_flip(a, int(n));
+    if (a.acc[n] >= thr && a.flags[n] == FL_REACTIVE) push_flip(a, int(n));
   }
 }
 
