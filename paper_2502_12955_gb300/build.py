@@ -45,8 +45,12 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every CUDA translation unit and link liblbm.so; returns its path."""
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          csrc: str | None = None, out_dir: str | None = None, extra_flags=()) -> str:
+    """Compile every CUDA translation unit and link liblbm.so; returns its path.  csrc /
+    out_dir / extra_flags build a variant of the sources into another directory."""
+    if csrc or out_dir or extra_flags:
+        return _build_variant(csrc or CSRC, out_dir or BUILD, list(extra_flags), jobs)
     os.makedirs(BUILD, exist_ok=True)
     if not force and not _stale(LIB, _deps()):
         return LIB
@@ -80,6 +84,24 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def _build_variant(csrc, out_dir, extra, jobs):
+    os.makedirs(out_dir, exist_ok=True)
+    nvcc = _nvcc()
+    srcs = sorted(glob.glob(os.path.join(csrc, "*.cu")))
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    cmds = [[nvcc, *ARCH, *NVFLAGS, *extra, "-c", s, "-o", o] for s, o in zip(srcs, objs)]
+    with cf.ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:
+        for r in ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), cmds):
+            if r.returncode != 0:
+                raise RuntimeError(r.stderr[-4000:])
+    lib = os.path.join(out_dir, "liblbm.so")
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", lib, *objs],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-4000:])
+    return lib
 
 
 if __name__ == "__main__":

@@ -72,6 +72,8 @@ enum : uint8_t { FL_FLUID = 0, FL_SOLID = 1, FL_REACTIVE = 2, FL_FLIPPING = 3 };
 struct Args {
   void* f[2];
   void* h[2];
+  void* fplane[2][19];       // base pointer of every population plane (host-computed)
+  void* hplane[2][7];
   void* psi[2];              // compute-type psi per component (Shan-Chen only)
   uint8_t* flags;
   uint32_t* mask;
@@ -191,6 +193,38 @@ __device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long p
   }
 }
 
+// Same as gather_flow, addressing through per-plane base pointers with 64-bit node offsets
+// (no multiply by the plane pitch in the kernel).
+template <class L, class S>
+__device__ __forceinline__ void gather_flow_pl(void* const* planes, int n, uint32_t m, const Nbr& nb,
+                                               int parity, typename Store<S>::T* out) {
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const S* p;
+    if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
+      p = reinterpret_cast<const S*>(planes[i]) + (long long)n;
+    else
+      p = reinterpret_cast<const S*>(planes[L::opp(i)]) +
+          (long long)nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+    out[i] = Store<S>::ld(p);
+  }
+}
+
+template <class L, class S>
+__device__ __forceinline__ void gather_scal_pl(void* const* planes, int n, uint32_t m, const Nbr& nb,
+                                               int parity, typename Store<S>::T* out) {
+#pragma unroll
+  for (int j = 0; j < L::QC; ++j) {
+    const S* p;
+    if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
+      p = reinterpret_cast<const S*>(planes[j]) + (long long)n;
+    else
+      p = reinterpret_cast<const S*>(planes[L::opp(j)]) +
+          (long long)nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+    out[j] = Store<S>::ld(p);
+  }
+}
+
 template <class T>
 __device__ __forceinline__ T scal_w(int j, const Coef<T>& k) { return j == 0 ? k.wc0 : k.wca; }
 
@@ -283,8 +317,11 @@ __device__ __forceinline__ T warp_sum(T v) {
 // bookkeeping, deposition, moments, forces, velocity, flow collision (BGK / MRT, Guo or
 // velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
 // Registers hold deviations from w_i * ref throughout.
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 3   // resident 256-thread blocks per SM for one component (80 registers)
+#endif
 template <class L, class S, int NC, int NS, int COLL, int parity>
-__global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
+__global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   T wallx = T(0);
@@ -314,12 +351,10 @@ __global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, c
     // ---- gather
     T f[NC][Q];
 #pragma unroll
-    for (int s = 0; s < NC; ++s)
-      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), P, n, m, nb, parity, f[s]);
+    for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], n, m, nb, parity, f[s]);
     T h[NS > 0 ? NS : 1][QC];
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), P, n, m, nb, parity, h[s]);
+    for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], n, m, nb, parity, h[s]);
     // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
     if (NS > 0) {
       // the consumed totals are reductions (no value returned): the threshold test runs in
@@ -552,21 +587,19 @@ __global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, c
     // ---- scatter flow
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
-      S* fs = reinterpret_cast<S*>(a.f[s]);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         S* p;
         if (parity == 0 || i == 0 || flow_wall<L>(m, i))
-          p = fs + (long long)L::opp(i) * P + n;
+          p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + (long long)n;
         else
-          p = fs + (long long)i * P + nb.at(L::cx(i), L::cy(i), L::cz(i));
+          p = reinterpret_cast<S*>(a.fplane[s][i]) + (long long)nb.at(L::cx(i), L::cy(i), L::cz(i));
         Store<S>::st(p, f[s][i]);
       }
     }
     // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      S* hs = reinterpret_cast<S*>(a.h[s]);
 #pragma unroll
       for (int j = 0; j < QC; ++j) {
         const uint32_t code = j == 0 ? 0u : MaskBits<L>::code(m, j);
@@ -586,11 +619,11 @@ __global__ void __launch_bounds__(256, (NC == 1 ? 3 : 2)) k_step(const Args a, c
             a.outflow_row[s * (a.ny * a.nz) + row] += double(v) - double(b);
           }
           v = b;
-          p = hs + (long long)jb * P + n;
+          p = reinterpret_cast<S*>(a.hplane[s][jb]) + (long long)n;
         } else if (parity == 0 || j == 0 || code != 0u) {
-          p = hs + (long long)L::opp(j) * P + n;
+          p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + (long long)n;
         } else {
-          p = hs + (long long)j * P + nb.at(L::cx(j), L::cy(j), L::cz(j));
+          p = reinterpret_cast<S*>(a.hplane[s][j]) + (long long)nb.at(L::cx(j), L::cy(j), L::cz(j));
         }
         Store<S>::st(p, v);
       }

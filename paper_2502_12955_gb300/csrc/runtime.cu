@@ -358,6 +358,10 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   } while (0)
   for (int s = 0; s < params->n_comp; ++s) DA(a.f[s], P * c->Qf * c->elem);
   for (int s = 0; s < params->n_scal; ++s) DA(a.h[s], P * c->Qc * c->elem);
+  for (int s = 0; s < params->n_comp; ++s)
+    for (int i = 0; i < c->Qf; ++i) a.fplane[s][i] = static_cast<char*>(a.f[s]) + (size_t)i * P * c->elem;
+  for (int s = 0; s < params->n_scal; ++s)
+    for (int j = 0; j < c->Qc; ++j) a.hplane[s][j] = static_cast<char*>(a.h[s]) + (size_t)j * P * c->elem;
   if (a.sc_on)
     for (int s = 0; s < params->n_comp; ++s) DA(a.psi[s], P * c->ks->psi_bytes);
   DA(a.flags, (N + 3) / 4 * 4);

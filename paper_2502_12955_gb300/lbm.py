@@ -74,13 +74,14 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load liblbm.so (building it first when absent or stale and nvcc is available)."""
+    """Load liblbm.so (building it first when absent or stale and nvcc is available).
+    The environment variable LBM_LIBRARY selects another build of the same ABI."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing:
+        path = os.environ.get("LBM_LIBRARY") or _build.LIB
+        if build_if_missing and not os.environ.get("LBM_LIBRARY"):
             path = _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"liblbm.so not found at {path}; build it with "
