@@ -206,6 +206,7 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--size", type=int, default=0)
     ap.add_argument("--block-x", type=int, default=0)
+    ap.add_argument("--l2-fetch", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -259,7 +260,7 @@ def main():
 
     precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
     cfg, geom, fields, label = workload(args.workload, args.size, precision)
-    cfg = dict(cfg, device=local, block_x=args.block_x)
+    cfg = dict(cfg, device=local, block_x=args.block_x, l2_fetch_bytes=args.l2_fetch)
     stream = torch.cuda.Stream(device=local)
     s = Solver(cfg, stream=stream.cuda_stream)
     s.set_geometry(geom)

@@ -136,6 +136,8 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
   if (p->N_geo < 1) return fail(c, LBM_ERR_INVALID_ARG, "N_geo must be >= 1");
   if (p->N_mon < 0) return fail(c, LBM_ERR_INVALID_ARG, "N_mon must be >= 0");
   if (p->ade_open_x && nx < 2) return fail(c, LBM_ERR_INVALID_ARG, "inlet/outlet needs nx >= 2");
+  if (p->l2_fetch_bytes != 0 && p->l2_fetch_bytes != 32 && p->l2_fetch_bytes != 64 && p->l2_fetch_bytes != 128)
+    return fail(c, LBM_ERR_INVALID_ARG, "l2_fetch_bytes must be 0, 32, 64 or 128");
   if (p->block_x < 0 || p->block_x > 256 || (p->block_x % 32) != 0)
     return fail(c, LBM_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [0, 256]");
   return LBM_OK;
@@ -313,6 +315,7 @@ lbm_status lbm_params_default(lbm_params* p) {
   p->deposit_conservative = 1;
   p->N_geo = 1;
   p->rho_ref[0] = p->rho_ref[1] = 1.0;
+  p->l2_fetch_bytes = 32;
   return LBM_OK;
 }
 
@@ -345,6 +348,10 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   };
   cudaError_t e = cudaSetDevice(params->device);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaSetDevice"));
+  if (params->l2_fetch_bytes > 0) {
+    e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)params->l2_fetch_bytes);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaDeviceSetLimit(MaxL2FetchGranularity)"));
+  }
   fill_args(c);
   Args& a = c->a;
   const long long N = c->N, P = c->pitch;

@@ -47,7 +47,7 @@ class LbmParams(C.Structure):
         ("m_s0", C.c_double), ("DP", C.c_double), ("deposit_conservative", C.c_int32),
         ("N_geo", C.c_int32), ("N_mon", C.c_int32), ("rho_ref", C.c_double * 2),
         ("C_ref", C.c_double * 2), ("stream", C.c_void_p), ("block_x", C.c_int32),
-        ("device", C.c_int32),
+        ("device", C.c_int32), ("l2_fetch_bytes", C.c_int32),
     ]
 
 
@@ -175,6 +175,7 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     p.C_ref[0], p.C_ref[1] = float(cr[0]), float(cr[1] if len(cr) > 1 else cr[0])
     p.block_x = int(d.get("block_x", 0))
     p.device = int(d.get("device", 0))
+    p.l2_fetch_bytes = int(d.get("l2_fetch_bytes", 32))
     return p
 
 
