@@ -206,7 +206,7 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--size", type=int, default=0)
     ap.add_argument("--block-x", type=int, default=0)
-    ap.add_argument("--l2-fetch", type=int, default=32)
+    ap.add_argument("--l2-fetch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()

@@ -96,9 +96,9 @@ typedef struct lbm_params {
                                  or a multiple of 32 up to 256 */
   int32_t device;             /* CUDA device ordinal */
   int32_t l2_fetch_bytes;     /* L2 fetch granularity hint for this process's context
-                                 (cudaLimitMaxL2FetchGranularity: 32, 64 or 128; 0 leaves the
-                                 context's current value).  Short fluid runs in porous media
-                                 waste most of a 128-byte fetch, so the default is 32. */
+                                 (cudaLimitMaxL2FetchGranularity: 32, 64 or 128; 0, the default,
+                                 leaves the context's current value).  Smaller fetches move fewer
+                                 bytes on porous geometries but expose more latency. */
 } lbm_params;
 
 /* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */
@@ -125,7 +125,7 @@ typedef struct lbm_monitors {
 typedef struct lbm_ctx lbm_ctx;
 
 /* Fill *p with defaults: FP32, one component, tau 1, no forces, BGK, Guo, no scalars,
-   periodic box, no geometry update, N_geo 1, N_mon 0, device 0, l2_fetch_bytes 32. */
+   periodic box, no geometry update, N_geo 1, N_mon 0, device 0, l2_fetch_bytes 0. */
 lbm_status lbm_params_default(lbm_params* p);
 
 /* Allocate a context for an nx x ny x nz domain (Sec. 2.1.4 lattices).  Validates every

@@ -315,7 +315,7 @@ lbm_status lbm_params_default(lbm_params* p) {
   p->deposit_conservative = 1;
   p->N_geo = 1;
   p->rho_ref[0] = p->rho_ref[1] = 1.0;
-  p->l2_fetch_bytes = 32;
+  p->l2_fetch_bytes = 0;
   return LBM_OK;
 }
 

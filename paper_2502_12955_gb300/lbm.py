@@ -175,7 +175,7 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     p.C_ref[0], p.C_ref[1] = float(cr[0]), float(cr[1] if len(cr) > 1 else cr[0])
     p.block_x = int(d.get("block_x", 0))
     p.device = int(d.get("device", 0))
-    p.l2_fetch_bytes = int(d.get("l2_fetch_bytes", 32))
+    p.l2_fetch_bytes = int(d.get("l2_fetch_bytes", 0))
     return p
 
 
