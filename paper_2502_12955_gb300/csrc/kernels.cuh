@@ -24,7 +24,6 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
-#include <cstring>
 
 #include "lattice.cuh"
 
@@ -229,97 +228,6 @@ __device__ __forceinline__ void gather_scal_pl(void* const* planes, int n, uint3
 template <class T>
 __device__ __forceinline__ T scal_w(int j, const Coef<T>& k) { return j == 0 ? k.wc0 : k.wca; }
 
-// ------------------------------------------------------------- staged gathers
-
-// The step kernel stages the next node's populations into shared memory with cp.async while
-// it collides the current one.  A slot holds one population; 16-bit populations are staged
-// as the aligned 32-bit word that contains them plus a bit that selects the half.
-template <class S>
-struct StageSlot {
-  using W = uint32_t;
-  static constexpr int kBytes = 4;
-};
-template <>
-struct StageSlot<double> {
-  using W = unsigned long long;
-  static constexpr int kBytes = 8;
-};
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async_slot(void* smem, const void* gmem) {
-  const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Issue the copies of one population into this thread's slot; returns the half-select bit.
-template <class S>
-__device__ __forceinline__ unsigned long long stage_one(typename StageSlot<S>::W* slot, const S* p) {
-  if (sizeof(S) == 2) {
-    const uintptr_t ad = reinterpret_cast<uintptr_t>(p);
-    cp_async_slot<4>(slot, reinterpret_cast<const void*>(ad & ~uintptr_t(3)));
-    return (unsigned long long)((ad >> 1) & 1u);
-  }
-  cp_async_slot<StageSlot<S>::kBytes>(slot, p);
-  return 0ull;
-}
-
-template <class S>
-__device__ __forceinline__ typename Store<S>::T read_slot(const typename StageSlot<S>::W* slot,
-                                                         unsigned long long hi) {
-  using T = typename Store<S>::T;
-  if (sizeof(S) == 2) {
-    const uint32_t w = *slot;
-    const unsigned short b = static_cast<unsigned short>(hi ? (w >> 16) : (w & 0xffffu));
-    S v;
-    memcpy(&v, &b, 2);
-    return Store<S>::ldv(&v);
-  }
-  S v;
-  memcpy(&v, slot, sizeof(S));
-  return T(v);
-}
-
-// Stage every pre-collision population of node n (same addressing as gather_flow_pl /
-// gather_scal_pl).  Slot q of this thread lives at base[q * pitch_slots].
-template <class L, class S, int NC, int NS>
-__device__ __forceinline__ unsigned long long stage_node(const Args& a, int n, uint32_t m, const Nbr& nb,
-                                                         int parity, typename StageSlot<S>::W* base,
-                                                         int pitch_slots) {
-  unsigned long long hbits = 0ull;
-#pragma unroll
-  for (int s = 0; s < NC; ++s)
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      const S* p;
-      if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
-        p = reinterpret_cast<const S*>(a.fplane[s][i]) + (long long)n;
-      else
-        p = reinterpret_cast<const S*>(a.fplane[s][L::opp(i)]) +
-            (long long)nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
-      const int q = s * L::Q + i;
-      hbits |= stage_one<S>(base + q * pitch_slots, p) << q;
-    }
-#pragma unroll
-  for (int s = 0; s < NS; ++s)
-#pragma unroll
-    for (int j = 0; j < L::QC; ++j) {
-      const S* p;
-      if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
-        p = reinterpret_cast<const S*>(a.hplane[s][j]) + (long long)n;
-      else
-        p = reinterpret_cast<const S*>(a.hplane[s][L::opp(j)]) +
-            (long long)nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
-      const int q = NC * L::Q + s * L::QC + j;
-      hbits |= stage_one<S>(base + q * pitch_slots, p) << q;
-    }
-  return hbits;
-}
-
-
-
 template <class L, class S>
 __device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long pitch, int n,
                                             uint32_t m, const Nbr& nb, int parity,
@@ -415,76 +323,38 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <class L, class S, int NC, int NS, int COLL, int parity>
 __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
-  using W = typename StageSlot<S>::W;
   constexpr int Q = L::Q, QC = L::QC;
-  constexpr int NP = NC * Q + NS * QC;
-  static_assert(NP <= 64, "half-select bits fit one 64-bit word");
-  extern __shared__ unsigned char stage_mem[];
-  W* const stage_base = reinterpret_cast<W*>(stage_mem) + threadIdx.x;
-  const int slot_pitch = blockDim.x;                   // slots of one population are contiguous
-  const int stage_slots = NP * blockDim.x;
   T wallx = T(0);
   const unsigned int count = *a.fluid_count;
   const unsigned int stride = gridDim.x * blockDim.x;
-  // Threads walk the fluid-node list, so every lane of a warp updates a fluid node.  The
-  // populations of the next node are staged into shared memory (cp.async) while the current
-  // node is collided; the list entry is fetched three and the link mask two iterations ahead.
+  // threads walk the fluid-node list, so every lane of a warp updates a fluid node; the list
+  // entry is fetched two iterations and the link mask one iteration ahead
   unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
-  int n_cur = e < count ? int(a.fluid_list[e]) : 0;
-  uint32_t m_cur = e < count ? a.mask[n_cur] : 0u;
-  int n_nx = e + stride < count ? int(a.fluid_list[e + stride]) : 0;
-  int n_nx2 = e + 2 * stride < count ? int(a.fluid_list[e + 2 * stride]) : 0;
-  uint32_t m_nx = e + stride < count ? a.mask[n_nx] : 0u;
-  int stage = 0;
-  unsigned long long hb_cur = 0ull;
-  if (e < count && (m_cur & 1u)) {
-    const Nbr nb0 = make_nbr(a, n_cur % a.nx, (n_cur / a.nx) % a.ny, n_cur / a.nx / a.ny);
-    hb_cur = stage_node<L, S, NC, NS>(a, n_cur, m_cur, nb0, parity, stage_base, slot_pitch);
-  }
-  cp_async_commit();
+  int n_next = e < count ? int(a.fluid_list[e]) : 0;
+  int n_next2 = e + stride < count ? int(a.fluid_list[e + stride]) : 0;
+  uint32_t m_next = e < count ? a.mask[n_next] : 0u;
   for (; e < count; e += stride) {
-  const int n = n_cur;
-  const uint32_t m = m_cur;
-  const unsigned long long hbits = hb_cur;
-  W* const cur = stage_base + stage * stage_slots;
-  // stage the next node, then advance the list / mask prefetch
-  unsigned long long hb_next = 0ull;
-  if (e + stride < count && (m_nx & 1u)) {
-    const Nbr nbn = make_nbr(a, n_nx % a.nx, (n_nx / a.nx) % a.ny, n_nx / a.nx / a.ny);
-    hb_next = stage_node<L, S, NC, NS>(a, n_nx, m_nx, nbn, parity, stage_base + (stage ^ 1) * stage_slots,
-                                       slot_pitch);
-  }
-  cp_async_commit();
-  n_cur = n_nx;
-  m_cur = m_nx;
-  hb_cur = hb_next;
-  n_nx = n_nx2;
-  if (e + 2 * stride < count) m_nx = a.mask[n_nx];
-  if (e + 3 * stride < count) n_nx2 = int(a.fluid_list[e + 3 * stride]);
-  stage ^= 1;
-  cp_async_wait<1>();           // this thread's copies of the current node are complete
-  if (!(m & 1u)) continue;      // a node removed by deposition since the last list rebuild
+  const int n = n_next;
+  const uint32_t m = m_next;
+  n_next = n_next2;
+  if (e + stride < count) m_next = a.mask[n_next];
+  if (e + 2 * stride < count) n_next2 = int(a.fluid_list[e + 2 * stride]);
+  if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
   const int x = n % a.nx;
   const int yz = n / a.nx;
   const int y = yz % a.ny;
   const int z = yz / a.ny;
   {
     const Nbr nb = make_nbr(a, x, y, z);
+    const long long P = a.pitch;
     const int row = y + a.ny * z;
-    // ---- gather (from the staged copies)
+    // ---- gather
     T f[NC][Q];
 #pragma unroll
-    for (int s = 0; s < NC; ++s)
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[s][i] = read_slot<S>(cur + (s * Q + i) * slot_pitch, (hbits >> (s * Q + i)) & 1ull);
+    for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], n, m, nb, parity, f[s]);
     T h[NS > 0 ? NS : 1][QC];
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-      for (int j = 0; j < QC; ++j) {
-        const int q = NC * Q + s * QC + j;
-        h[s][j] = read_slot<S>(cur + q * slot_pitch, (hbits >> q) & 1ull);
-      }
+    for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], n, m, nb, parity, h[s]);
     // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
     if (NS > 0) {
       // the consumed totals are reductions (no value returned): the threshold test runs in
@@ -760,7 +630,6 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
     }
   }
   }
-  cp_async_wait<0>();
   // ---- wall-exchange monitor: one reduction per warp that saw a reactive link
   if (NS > 0) {
     const unsigned int any = __ballot_sync(0xffffffffu, wallx != T(0));

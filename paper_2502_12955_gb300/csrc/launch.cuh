@@ -78,38 +78,21 @@ struct Launchers {
   static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
 
   // one resident wave of blocks; the kernel walks the fluid list with a grid-stride loop
-  // Dynamic shared memory of the step kernel: two stages of NP slots per thread.
-  template <int NC, int NS>
-  static size_t stage_bytes(int threads) {
-    constexpr int NP = NC * L::Q + NS * L::QC;
-    return 2ull * NP * (size_t)threads * sizeof(typename StageSlot<S>::W);
-  }
-
   template <int NC, int NS, int COLL, int PAR>
   static cudaError_t step_p(const Args& a, cudaStream_t st) {
-    static int cached_req = -1, cached_threads = 0, cached_blocks = 0;
-    static size_t cached_smem = 0;
-    if (cached_req != a.bx) {
-      int dev = 0, sms = 0, occ = 0, smem_optin = 0;
+    const int threads = a.bx;
+    static int cached_threads = -1, cached_blocks = 0;
+    if (cached_threads != threads) {
+      int dev = 0, sms = 0, occ = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      int threads = a.bx;
-      while (threads > 32 && stage_bytes<NC, NS>(threads) > (size_t)smem_optin) threads -= 32;
-      const size_t smem = stage_bytes<NC, NS>(threads);
-      cudaError_t e = cudaFuncSetAttribute(k_step<L, S, NC, NS, COLL, PAR>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL, PAR>, threads, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL, PAR>, threads, 0);
       cached_blocks = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
       cached_threads = threads;
-      cached_smem = smem;
-      cached_req = a.bx;
     }
-    const int threads = cached_threads;
     long long need = (a.N + threads - 1) / threads;
     const unsigned int blocks = (unsigned int)(need < cached_blocks ? need : cached_blocks);
-    k_step<L, S, NC, NS, COLL, PAR><<<blocks > 0 ? blocks : 1, threads, cached_smem, st>>>(a, coef(a));
+    k_step<L, S, NC, NS, COLL, PAR><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a));
     return cudaGetLastError();
   }
   template <int NC, int NS, int COLL>
