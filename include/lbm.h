@@ -167,6 +167,20 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, double* C, uint8
 lbm_status lbm_get_pops(lbm_ctx* ctx, double* f, double* h);
 lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f, const double* h);
 
+/* Same result as lbm_get_pops, without allocating device memory.  The paper has no counterpart;
+   this entry point exists for callers that cannot call cudaMalloc: code whose device memory is
+   fully reserved by another allocator (for example a framework's caching pool), or code that
+   must not trigger the implicit device-wide synchronisation of cudaMalloc / cudaFree.
+   The populations are staged through a fixed device scratch array of
+   LBM_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading this library holds until the
+   process exits.  Domains whose (n_comp*Qf + n_scal*Qc) * N * 8 bytes exceed it are rejected
+   with LBM_ERR_CAPACITY.  All calls share that array: calls on different contexts or streams
+   that overlap on the GPU race on it, so serialise them.  The first call on a device looks up
+   the array's device address (cudaGetSymbolAddress); make that first call before any stream
+   capture.  Outputs are host buffers as in lbm_get_pops; the call synchronises the stream. */
+#define LBM_NOALLOC_SCRATCH_BYTES (16u << 20)
+lbm_status lbm_get_pops_noalloc(lbm_ctx* ctx, double* f, double* h);
+
 /* Evaluate the monitors now (FP64 reductions on the device) and copy them to *out. */
 lbm_status lbm_get_monitors(lbm_ctx* ctx, lbm_monitors* out);
 

@@ -547,6 +547,61 @@ lbm_status lbm_get_pops(lbm_ctx* c, double* f, double* h) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+// Scratch of lbm_get_pops_noalloc: a fixed device array, so the call allocates nothing.  In host
+// code this name is only a stand-in; kernels get the device address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+
+// Looks up the scratch array's device address once per device (the device must be current).
+lbm_status noalloc_scratch(lbm_ctx* c, void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(c, LBM_ERR_INVALID_ARG, "device ordinal %d", dev);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_get_pops_noalloc(lbm_ctx* c, double* f, double* h) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const size_t N = (size_t)c->N;
+  const size_t nf = (size_t)c->p.n_comp * c->Qf * N;
+  const size_t nh = (h && c->p.n_scal > 0) ? (size_t)c->p.n_scal * c->Qc * N : 0;
+  const size_t need = (nf + nh) * sizeof(double);
+  if (need > LBM_NOALLOC_SCRATCH_BYTES)
+    return fail(c, LBM_ERR_CAPACITY, "lbm_get_pops_noalloc needs %zu bytes of scratch, the fixed array holds %u",
+                need, (unsigned)LBM_NOALLOC_SCRATCH_BYTES);
+  int prev = 0;
+  CK(cudaGetDevice(&prev));
+  if (prev != c->p.device) CK(cudaSetDevice(c->p.device));
+  void* scratch = nullptr;
+  lbm_status st = noalloc_scratch(c, &scratch);
+  if (st == LBM_OK) {
+    double* df = f ? static_cast<double*>(scratch) : nullptr;
+    double* dh = nh ? static_cast<double*>(scratch) + nf : nullptr;
+    cudaError_t e = c->ks->pops_io(c->a, parity_of(c->step), 0, df, dh, c->stream);
+    c->launches += 1;
+    if (e == cudaSuccess && df) e = cudaMemcpyAsync(f, df, nf * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && dh) e = cudaMemcpyAsync(h, dh, nh * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "lbm_get_pops_noalloc");
+  }
+  if (prev != c->p.device) cudaSetDevice(prev);
+  return st;
+}
+
 lbm_status lbm_set_pops(lbm_ctx* c, const double* f, const double* h) {
   if (!c) return LBM_ERR_INVALID_ARG;
   const size_t N = (size_t)c->N;

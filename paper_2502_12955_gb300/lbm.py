@@ -31,7 +31,8 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ER
 EXPORTS = ["lbm_params_default", "lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step",
            "lbm_sync", "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_get_monitors",
            "lbm_residual", "lbm_get_state", "lbm_set_state", "lbm_profile_enable",
-           "lbm_profile_read", "lbm_launch_count", "lbm_last_error", "lbm_destroy"]
+           "lbm_profile_read", "lbm_launch_count", "lbm_last_error", "lbm_destroy",
+           "lbm_get_pops_noalloc"]
 
 
 class LbmParams(C.Structure):
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = True):
         lib.lbm_get_fields.argtypes = [vp, dp, dp, dp, P(C.c_uint8), dp]
         lib.lbm_get_pops.argtypes = [vp, dp, dp]
         lib.lbm_set_pops.argtypes = [vp, dp, dp]
+        lib.lbm_get_pops_noalloc.argtypes = [vp, dp, dp]
         lib.lbm_get_monitors.argtypes = [vp, P(LbmMonitors)]
         lib.lbm_residual.argtypes = [vp, dp]
         lib.lbm_get_state.argtypes = [vp, vp, P(C.c_size_t)]
@@ -263,6 +265,13 @@ class Solver:
         f = np.zeros((self.n_comp, self.qf, self.N))
         h = np.zeros((max(self.n_scal, 1), self.qc, self.N))
         self._ck(self.lib.lbm_get_pops(self.h, _dp(f), _dp(h) if self.n_scal else None))
+        return f, h[: self.n_scal]
+
+    def pops_noalloc(self):
+        """pops() through lbm_get_pops_noalloc (no device allocation, bounded domain size)."""
+        f = np.zeros((self.n_comp, self.qf, self.N))
+        h = np.zeros((max(self.n_scal, 1), self.qc, self.N))
+        self._ck(self.lib.lbm_get_pops_noalloc(self.h, _dp(f), _dp(h) if self.n_scal else None))
         return f, h[: self.n_scal]
 
     def set_pops(self, f, h=None):
