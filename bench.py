@@ -212,6 +212,19 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_over_ranks(dist, device, seconds, units):
+    """Whole-job figures of a replica run: the slowest rank's time and the units all ranks
+    processed (each rank steps its own independent problem; no data-path collective)."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -296,13 +309,13 @@ def main():
     kern_ms, kern_n = s.profile_read()
     s.profile(False)
     s.sync()
-    if dist:
-        t = torch.tensor([ms_total], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    dev = f"cuda:{local}"
+    sec, nodes_all = reduce_over_ranks(dist, dev, ms_total * 1e-3, N * args.steps)
+    _, fluid_all = reduce_over_ranks(dist, dev, 0.0, Nf * args.steps)
+    ms_total = sec * 1e3
     ms_step = ms_total / args.steps
-    mlups = ws * N * args.steps / (ms_total * 1e-3) / 1e6
-    mflups = ws * Nf * args.steps / (ms_total * 1e-3) / 1e6
+    mlups = nodes_all / sec / 1e6
+    mflups = fluid_all / sec / 1e6
     mon = s.monitors()
 
     # roofline of the fused step kernel (per launch, CUDA events on the launching stream)
@@ -336,14 +349,10 @@ def main():
         out = s.fields()
         torch.cuda.synchronize()
         barrier()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el, e2e_nodes = reduce_over_ranks(dist, dev, time.perf_counter() - t0, N * ke)
         h2d = geom.nbytes + rho.nbytes + u[: (3 if cfg["dim"] == 3 else 2)].nbytes + (C.nbytes if s.n_scal else 0)
         d2h = 4 * ke + sum(v.nbytes for v in out.values())
-        e2e = {"value": ws * N * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / ke,
+        e2e = {"value": e2e_nodes / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / ke,
                "d2h_bytes_per_step": d2h / ke, "steps": ke,
                "includes": "set_geometry + set_fields from pinned host memory, per-step lbm_step + "
                            "lbm_sync (4-byte status read), final lbm_get_fields to host"}

@@ -1,0 +1,74 @@
+"""Full-size parity: the 256^3 D3Q19 MRT + D3Q7 dissolution workload the benchmark times,
+CUDA path (FP64 and the benchmark's FP32 launch configuration) against the FP64 oracle on
+the whole domain after one and two steps (both in-place layout parities).
+
+The oracle needs about 11 GB of host memory and ~15 s per step at this size, so the case
+stops at two steps; the small parity cases cover long runs and the geometry flips.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2502_12955_gb300 import inputs
+from paper_2502_12955_gb300.lbm import Solver
+from tests.gpu_common import FP64_TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# FP32 storage and arithmetic after <= 2 steps: a handful of roundings of O(1) values, so
+# relative L2 errors of a few 1e-8 are expected; the bounds leave a 10-100x margin while
+# staying far below anything a wrong term (O(1e-3) and up at these velocities) would give.
+FP32_TOL = {"rho": 1e-6, "u": 1e-5, "C": 1e-6, "acc": 1e-5}
+FP32_POP_ABS = 2e-6   # max |f_gpu - f_oracle| over every population of every node
+
+
+@pytest.fixture(scope="module")
+def full_case():
+    cfg, geom, fields = inputs.dissolution_3d(256, precision="fp64")
+    cfg = dict(cfg, N_mon=100)
+    o = Oracle(cfg)
+    o.set_geometry(geom)
+    o.set_fields(*fields)
+    return cfg, geom, fields, o
+
+
+def _solver(cfg, geom, fields, precision):
+    s = Solver(dict(cfg, precision=precision))
+    s.set_geometry(geom)
+    s.set_fields(*fields)
+    return s
+
+
+def test_full_size_fp64_and_fp32_two_steps(full_case):
+    cfg, geom, fields, o = full_case
+    assert geom.shape == (256, 256, 256)
+    g64 = _solver(cfg, geom, fields, "fp64")
+    g32 = _solver(cfg, geom, fields, "fp32")
+    for step in (1, 2):
+        o.step(1)
+        g64.step(1)
+        g32.step(1)
+        fo = o.fields()
+        for name, g, tol in (("fp64", g64, None), ("fp32", g32, FP32_TOL)):
+            fg = g.fields()
+            assert np.array_equal(fo["flags"], fg["flags"]), f"{name} step {step}: flags"
+            for k in ("rho", "u", "C", "acc"):
+                e = rel_l2(fo[k], fg[k])
+                bound = FP64_TOL if tol is None else tol[k]
+                assert e <= bound, f"{name} step {step}: {k} rel L2 {e:.3e} > {bound:.1e}"
+        f_o, h_o = o.pops()
+        for name, g in (("fp64", g64), ("fp32", g32)):
+            f_g, h_g = g.pops()
+            if name == "fp64":
+                assert rel_l2(f_o, f_g) <= FP64_TOL and rel_l2(h_o, h_g) <= FP64_TOL
+            else:
+                df = float(np.max(np.abs(f_o - f_g)))
+                dh = float(np.max(np.abs(h_o - h_g)))
+                assert df <= FP32_POP_ABS and dh <= FP32_POP_ABS, (step, df, dh)
+            del f_g, h_g
+        del f_o, h_o
+        mo, m64 = o.monitors(), g64.monitors()
+        for k, v in mo.items():
+            assert abs(m64[k] - v) <= 1e-9 * max(abs(v), abs(mo["mass0"])), (k, m64[k], v)
+    g64.close()
+    g32.close()
