@@ -20,6 +20,10 @@ pytestmark = pytest.mark.gpu
 # staying far below anything a wrong term (O(1e-3) and up at these velocities) would give.
 FP32_TOL = {"rho": 1e-6, "u": 1e-5, "C": 1e-6, "acc": 1e-5}
 FP32_POP_ABS = 2e-6   # max |f_gpu - f_oracle| over every population of every node
+# The FP64 monitors are sums over up to 26 N populations.  The oracle adds them one at a time
+# (error bound n u sum|x| for n terms, u = 2^-53), the CUDA path by a tree, so at 256^3 they may
+# differ by up to ~1e-7 of the summed magnitude (measured: 1.0e-9 on the flow mass).
+MON_TOL = 2 * 26 * 256 ** 3 * 2.0 ** -53
 
 
 @pytest.fixture(scope="module")
@@ -69,6 +73,6 @@ def test_full_size_fp64_and_fp32_two_steps(full_case):
         del f_o, h_o
         mo, m64 = o.monitors(), g64.monitors()
         for k, v in mo.items():
-            assert abs(m64[k] - v) <= 1e-9 * max(abs(v), abs(mo["mass0"])), (k, m64[k], v)
+            assert abs(m64[k] - v) <= MON_TOL * max(abs(v), abs(mo["mass0"])), (k, m64[k], v)
     g64.close()
     g32.close()
