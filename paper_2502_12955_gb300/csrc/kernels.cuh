@@ -1,6 +1,9 @@
 // kernels.cuh -- sm_103a kernels of the reactive multi-component LBM step.
 //
-// Storage: structure of arrays, one plane per direction, pop[i * pitch + n], n = x + nx*(y + ny*z).
+// Storage: structure of arrays, one plane per direction, pop[i * pitch + slot[n]], node
+// n = x + nx*(y + ny*z).  The slot map puts the fluid nodes first, in list order, so a warp's
+// lanes touch consecutive slots in every plane and no cache line carries solid-node bytes; the
+// cells named (n, i) below are pop[i * pitch + slot[n]].
 // Every lattice keeps ONE copy of its populations and streams in place with the A-A pattern:
 //   even steps (parity 0) read f_i(n) from slot (n, i) and write the post-collision f*_i to
 //   slot (n, opp i); odd steps (parity 1) read f_i(n) from (n - c_i, opp i) and write f*_i to
@@ -79,7 +82,12 @@ struct Args {
   uint32_t* mask;
   double* acc;               // consumed (reactive solid) / deposited (fluid) per node
   uint32_t* fluid_list;       // fluid node indices (sorted at each rebuild, appended by flips)
-  unsigned int* fluid_count;
+  unsigned int* fluid_count;  // [0] list length, [1] length at the last rebuild (see slot)
+  // Storage slot of every node: populations of node n live at plane * pitch + slot[n].  Each
+  // rebuild renumbers the fluid nodes to slots 0 .. F-1 in list order (so list entry e < F has
+  // slot e) and the solid nodes to F .. N-1; nodes that become fluid later keep their slot.
+  uint32_t* slot;
+  uint32_t* slot_new;         // rebuild scratch
   unsigned int* block_counts; // ordered-compaction scratch [N / 1024 + 1]
   double* wallx_slot;        // [WALLX_SLOTS] wall-exchange accumulators
   uint32_t* iface_list;       // reactive solids with a fluid scalar-lattice neighbour
@@ -177,17 +185,18 @@ __device__ __forceinline__ bool flow_wall(uint32_t m, int i) { return (m >> i) &
 
 // Pre-collision flow populations of node n (as stored; shift added for 16-bit storage).
 // Stored (deviation) values of the pre-collision flow populations of node n.
+// sn is the node's storage slot; neighbour slots come from the slot map.
 template <class L, class S>
-__device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long pitch, int n,
-                                            uint32_t m, const Nbr& nb, int parity,
-                                            typename Store<S>::T* out) {
+__device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long pitch, long long sn,
+                                            const uint32_t* __restrict__ slot, uint32_t m,
+                                            const Nbr& nb, int parity, typename Store<S>::T* out) {
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const S* p;
     if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i))) {
-      p = f + (long long)i * pitch + n;
+      p = f + (long long)i * pitch + sn;
     } else {
-      p = f + (long long)L::opp(i) * pitch + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+      p = f + (long long)L::opp(i) * pitch + __ldg(slot + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)));
     }
     out[i] = Store<S>::ld(p);
   }
@@ -196,31 +205,33 @@ __device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long p
 // Same as gather_flow, addressing through per-plane base pointers with 64-bit node offsets
 // (no multiply by the plane pitch in the kernel).
 template <class L, class S>
-__device__ __forceinline__ void gather_flow_pl(void* const* planes, int n, uint32_t m, const Nbr& nb,
-                                               int parity, typename Store<S>::T* out) {
+__device__ __forceinline__ void gather_flow_pl(void* const* planes, long long sn,
+                                               const uint32_t* __restrict__ slot, uint32_t m,
+                                               const Nbr& nb, int parity, typename Store<S>::T* out) {
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const S* p;
     if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
-      p = reinterpret_cast<const S*>(planes[i]) + (long long)n;
+      p = reinterpret_cast<const S*>(planes[i]) + sn;
     else
       p = reinterpret_cast<const S*>(planes[L::opp(i)]) +
-          (long long)nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+          (long long)__ldg(slot + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)));
     out[i] = Store<S>::ld(p);
   }
 }
 
 template <class L, class S>
-__device__ __forceinline__ void gather_scal_pl(void* const* planes, int n, uint32_t m, const Nbr& nb,
-                                               int parity, typename Store<S>::T* out) {
+__device__ __forceinline__ void gather_scal_pl(void* const* planes, long long sn,
+                                               const uint32_t* __restrict__ slot, uint32_t m,
+                                               const Nbr& nb, int parity, typename Store<S>::T* out) {
 #pragma unroll
   for (int j = 0; j < L::QC; ++j) {
     const S* p;
     if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
-      p = reinterpret_cast<const S*>(planes[j]) + (long long)n;
+      p = reinterpret_cast<const S*>(planes[j]) + sn;
     else
       p = reinterpret_cast<const S*>(planes[L::opp(j)]) +
-          (long long)nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+          (long long)__ldg(slot + nb.at(-L::cx(j), -L::cy(j), -L::cz(j)));
     out[j] = Store<S>::ld(p);
   }
 }
@@ -229,16 +240,16 @@ template <class T>
 __device__ __forceinline__ T scal_w(int j, const Coef<T>& k) { return j == 0 ? k.wc0 : k.wca; }
 
 template <class L, class S>
-__device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long pitch, int n,
-                                            uint32_t m, const Nbr& nb, int parity,
-                                            typename Store<S>::T* out) {
+__device__ __forceinline__ void gather_scal(const S* __restrict__ h, long long pitch, long long sn,
+                                            const uint32_t* __restrict__ slot, uint32_t m,
+                                            const Nbr& nb, int parity, typename Store<S>::T* out) {
 #pragma unroll
   for (int j = 0; j < L::QC; ++j) {
     const S* p;
     if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0) {
-      p = h + (long long)j * pitch + n;
+      p = h + (long long)j * pitch + sn;
     } else {
-      p = h + (long long)L::opp(j) * pitch + nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+      p = h + (long long)L::opp(j) * pitch + __ldg(slot + nb.at(-L::cx(j), -L::cy(j), -L::cz(j)));
     }
     out[j] = Store<S>::ld(p);
   }
@@ -325,7 +336,8 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   T wallx = T(0);
-  const unsigned int count = *a.fluid_count;
+  const unsigned int count = a.fluid_count[0];
+  const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
   const unsigned int stride = gridDim.x * blockDim.x;
   // threads walk the fluid-node list, so every lane of a warp updates a fluid node; the list
   // entry is fetched two iterations and the link mask one iteration ahead
@@ -340,6 +352,7 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
   if (e + stride < count) m_next = a.mask[n_next];
   if (e + 2 * stride < count) n_next2 = int(a.fluid_list[e + 2 * stride]);
   if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
+  const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
   const int x = n % a.nx;
   const int yz = n / a.nx;
   const int y = yz % a.ny;
@@ -351,10 +364,10 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
     // ---- gather
     T f[NC][Q];
 #pragma unroll
-    for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], n, m, nb, parity, f[s]);
+    for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f[s]);
     T h[NS > 0 ? NS : 1][QC];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], n, m, nb, parity, h[s]);
+    for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s]);
     // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
     if (NS > 0) {
       // the consumed totals are reductions (no value returned): the threshold test runs in
@@ -591,9 +604,10 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
       for (int i = 0; i < Q; ++i) {
         S* p;
         if (parity == 0 || i == 0 || flow_wall<L>(m, i))
-          p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + (long long)n;
+          p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + sn;
         else
-          p = reinterpret_cast<S*>(a.fplane[s][i]) + (long long)nb.at(L::cx(i), L::cy(i), L::cz(i));
+          p = reinterpret_cast<S*>(a.fplane[s][i]) +
+              (long long)__ldg(a.slot + nb.at(L::cx(i), L::cy(i), L::cz(i)));
         Store<S>::st(p, f[s][i]);
       }
     }
@@ -619,11 +633,12 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
             a.outflow_row[s * (a.ny * a.nz) + row] += double(v) - double(b);
           }
           v = b;
-          p = reinterpret_cast<S*>(a.hplane[s][jb]) + (long long)n;
+          p = reinterpret_cast<S*>(a.hplane[s][jb]) + sn;
         } else if (parity == 0 || j == 0 || code != 0u) {
-          p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + (long long)n;
+          p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + sn;
         } else {
-          p = reinterpret_cast<S*>(a.hplane[s][j]) + (long long)nb.at(L::cx(j), L::cy(j), L::cz(j));
+          p = reinterpret_cast<S*>(a.hplane[s][j]) +
+              (long long)__ldg(a.slot + nb.at(L::cx(j), L::cy(j), L::cz(j)));
         }
         Store<S>::st(p, v);
       }
@@ -659,7 +674,7 @@ __global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename S
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     T f[L::Q];
-    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
+    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, a.slot[n], a.slot, m, nb, parity, f);
     T r = k.rref[s];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) r += f[i];
@@ -717,11 +732,12 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
     if (!(m & 1u)) continue;
     ++nfluid;
     const Nbr nb = make_nbr(a, n % a.nx, (n / a.nx) % a.ny, n / a.nx / a.ny);
+    const long long sn = a.slot[n];
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T f[Q];
-      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
+      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, sn, a.slot, m, nb, parity, f);
       T r = T(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -736,7 +752,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       T h[QC];
-      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, h);
+      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, sn, a.slot, m, nb, parity, h);
       T c = T(0);
 #pragma unroll
       for (int j = 0; j < QC; ++j) c += h[j];
@@ -788,11 +804,12 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const Nbr nb = make_nbr(a, n % a.nx, (n / a.nx) % a.ny, n / a.nx / a.ny);
+  const long long sn = a.slot[n];
   T rho[NC], jx[NC], jy[NC], jz[NC], Fx[NC], Fy[NC], Fz[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     T f[Q];
-    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, n, m, nb, parity, f);
+    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, sn, a.slot, m, nb, parity, f);
     T r = T(0), ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -851,7 +868,7 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T h[QC];
-    gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, n, m, nb, parity, h);
+    gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, sn, a.slot, m, nb, parity, h);
     if (s == 0) close_scalar<L, T>(h, m, k, [](int, T, T) {});
     T C = k.cref[s];
 #pragma unroll
@@ -925,6 +942,7 @@ __global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename 
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= a.N) return;
   const bool fluid = a.flags[n] == FL_FLUID;
+  const long long sn = a.slot[n];
   const T ux = T(a.d_u[n]), uy = T(a.d_u[a.N + n]), uz = (L::D == 3) ? T(a.d_u[2 * a.N + n]) : T(0);
   for (int s = 0; s < NC; ++s) {
     S* fs = reinterpret_cast<S*>(a.f[s]);
@@ -933,7 +951,7 @@ __global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename 
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const T v = fluid ? feq_dev<L, T>(i, r, dr, ux, uy, uz) : T(0);
-      Store<S>::st(fs + (long long)i * a.pitch + n, v);
+      Store<S>::st(fs + (long long)i * a.pitch + sn, v);
     }
   }
   for (int s = 0; s < NS; ++s) {
@@ -945,7 +963,7 @@ __global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename 
       const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
       const T wj = scal_w<T>(j, k);
       const T v = fluid ? wj * (dC + C * cu * k.ics2c) : T(0);
-      Store<S>::st(hs + (long long)j * a.pitch + n, v);
+      Store<S>::st(hs + (long long)j * a.pitch + sn, v);
     }
   }
 }
@@ -967,6 +985,7 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const Coef<typena
   const bool fluid = (m & 1u) != 0u;
   const Nbr nb = make_nbr(a, x, y, z);
   const long long N = a.N, P = a.pitch;
+  const long long sn = a.slot[n];
   if (fio) {
     for (int s = 0; s < NC; ++s) {
       S* fs = reinterpret_cast<S*>(a.f[s]);
@@ -979,9 +998,9 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const Coef<typena
         }
         S* p;
         if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
-          p = fs + (long long)i * P + n;
+          p = fs + (long long)i * P + sn;
         else
-          p = fs + (long long)L::opp(i) * P + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+          p = fs + (long long)L::opp(i) * P + a.slot[nb.at(-L::cx(i), -L::cy(i), -L::cz(i))];
         const double sh = L::w(i) * double(k.rref[s]);
         if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
         else Store<S>::st(p, T(*io - sh));
@@ -1000,9 +1019,9 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const Coef<typena
         }
         S* p;
         if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0u)
-          p = hs + (long long)j * P + n;
+          p = hs + (long long)j * P + sn;
         else
-          p = hs + (long long)L::opp(j) * P + nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+          p = hs + (long long)L::opp(j) * P + a.slot[nb.at(-L::cx(j), -L::cy(j), -L::cz(j))];
         const double sh = double(scal_w<T>(j, k)) * double(k.cref[s]);
         if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
         else Store<S>::st(p, T(*io - sh));
@@ -1100,7 +1119,7 @@ __global__ void __launch_bounds__(1024) k_list_count(const Args a) {
   }
 }
 
-// exclusive scan of the chunk counts by one block; the total goes to *count
+// exclusive scan of the chunk counts by one block; the total goes to count[0] and count[1]
 template <int DUMMY = 0>
 __global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int nchunks,
                                                     unsigned int* count) {
@@ -1124,9 +1143,14 @@ __global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int n
     if (threadIdx.x == 1023) carry += part[1023];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *count = carry;
+  if (threadIdx.x == 0) {
+    count[0] = carry;
+    count[1] = carry;
+  }
 }
 
+// PRED 0 also assigns the new storage slots: fluid nodes take their list position, solid
+// nodes follow from the fluid total on in node order (slot_new).
 template <class L, int PRED>
 __global__ void __launch_bounds__(1024) k_list_write(const Args a, uint32_t* list) {
   __shared__ unsigned int wsum[32];
@@ -1146,8 +1170,10 @@ __global__ void __launch_bounds__(1024) k_list_write(const Args a, uint32_t* lis
     wsum[threadIdx.x] = incl - v;
   }
   __syncthreads();
+  const unsigned int pos = a.block_counts[blockIdx.x] + wsum[wid] + __popc(b & ((1u << lane) - 1u));
+  if (PRED == 0 && n < a.N)
+    a.slot_new[n] = f ? pos : a.fluid_count[0] + (uint32_t)(n - (long long)pos);
   if (f) {
-    const unsigned int pos = a.block_counts[blockIdx.x] + wsum[wid] + __popc(b & ((1u << lane) - 1u));
     list[pos] = (uint32_t)n;
     if (PRED == 1) a.listed[n] = 1;
   }
@@ -1256,14 +1282,14 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         const uint32_t mq = a.mask[q];
         for (int c = 0; c < NC; ++c) {
           T f[Q];
-          gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(q), mq, nq, parity_next, f);
+          gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, a.slot[q], a.slot, mq, nq, parity_next, f);
           double r = double(k.rref[c]);
           for (int j = 0; j < Q; ++j) r += double(f[j]);
           sr[c] += r;
         }
         for (int c = 0; c < NS; ++c) {
           T h[QC];
-          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(q), mq, nq, parity_next, h);
+          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, h);
           if (c == 0) close_scalar<L, T>(h, mq, k, [](int, T, T) {});
           double C = double(k.cref[c]);
           for (int j = 0; j < QC; ++j) C += double(h[j]);
@@ -1285,14 +1311,14 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
       const uint32_t ms = a.mask[s];
       for (int c = 0; c < NC; ++c) {
         T f[Q];
-        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, int(s), ms, ns, parity_next, f);
+        gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, a.slot[s], a.slot, ms, ns, parity_next, f);
         double r = double(k.rref[c]);
         for (int j = 0; j < Q; ++j) r += double(f[j]);
         atomicAdd(&sred[4 + c], r);
       }
       for (int c = 0; c < NS; ++c) {
         T h[QC];
-        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, int(s), ms, ns, parity_next, h);
+        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[s], a.slot, ms, ns, parity_next, h);
         double C = double(k.cref[c]);
         for (int j = 0; j < QC; ++j) C += double(h[j]);
         atomicAdd(&sred[6 + c], C);
@@ -1304,6 +1330,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
   for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
     if (a.flip_list[e] == 0xffffffffu) continue;
     const long long s = a.flip_list[e];
+    const long long ss = a.slot[s];   // storage slot of the flipping node
     int x, y, z;
     coords_of(a, s, &x, &y, &z);
     int ax;
@@ -1316,19 +1343,19 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         for (int j = 0; j < Q; ++j) {
           const T tv = T(L::w(j) * (r - double(k.rref[c])));   // f_eq(rho_bar, u = 0) - w rref
           if (parity_next == 0 || j == 0) {
-            Store<S>::st(fs + (long long)j * P + s, tv);
+            Store<S>::st(fs + (long long)j * P + ss, tv);
             continue;
           }
           const long long src = nbr_checked(a, x, y, z, -L::cx(j), -L::cy(j), -L::cz(j), percf, &ax);
           const uint8_t fl = src < 0 ? FL_SOLID : a.flags[src];
           if (fl == FL_FLUID) {
-            S* from = fs + (long long)L::opp(j) * P + src;
-            *(fs + (long long)j * P + s) = *from;      // neighbour's bounced value moves
+            S* from = fs + (long long)L::opp(j) * P + a.slot[src];
+            *(fs + (long long)j * P + ss) = *from;     // neighbour's bounced value moves
             Store<S>::st(from, tv);
           } else if (fl == FL_FLIPPING) {
-            Store<S>::st(fs + (long long)L::opp(j) * P + src, tv);
+            Store<S>::st(fs + (long long)L::opp(j) * P + a.slot[src], tv);
           } else {
-            Store<S>::st(fs + (long long)j * P + s, tv);
+            Store<S>::st(fs + (long long)j * P + ss, tv);
           }
         }
       }
@@ -1340,19 +1367,19 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
           const double wj = double(scal_w<T>(j, k));
           const T tv = T(wj * (C - double(k.cref[c])));       // h_eq(C_bar, u = 0) - w cref
           if (parity_next == 0 || j == 0) {
-            Store<S>::st(hs + (long long)j * P + s, tv);
+            Store<S>::st(hs + (long long)j * P + ss, tv);
             continue;
           }
           const long long src = nbr_checked(a, x, y, z, -L::cx(j), -L::cy(j), -L::cz(j), percs, &ax);
           const uint8_t fl = src < 0 ? FL_SOLID : a.flags[src];
           if (fl == FL_FLUID) {
-            S* from = hs + (long long)L::opp(j) * P + src;
-            *(hs + (long long)j * P + s) = *from;
+            S* from = hs + (long long)L::opp(j) * P + a.slot[src];
+            *(hs + (long long)j * P + ss) = *from;
             Store<S>::st(from, tv);
           } else if (fl == FL_FLIPPING) {
-            Store<S>::st(hs + (long long)L::opp(j) * P + src, tv);
+            Store<S>::st(hs + (long long)L::opp(j) * P + a.slot[src], tv);
           } else {
-            Store<S>::st(hs + (long long)j * P + s, tv);
+            Store<S>::st(hs + (long long)j * P + ss, tv);
           }
         }
       }
@@ -1364,7 +1391,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         for (int d = 1; d < Q; ++d) {
           const long long yn = nbr_checked(a, x, y, z, L::cx(d), L::cy(d), L::cz(d), percf, &ax);
           if (yn < 0 || a.flags[yn] != FL_FLUID) continue;
-          *(fs + (long long)d * P + yn) = *(fs + (long long)L::opp(d) * P + s);
+          *(fs + (long long)d * P + a.slot[yn]) = *(fs + (long long)L::opp(d) * P + ss);
         }
       }
       for (int c = 0; c < NS; ++c) {
@@ -1372,7 +1399,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         for (int d = 1; d < QC; ++d) {
           const long long yn = nbr_checked(a, x, y, z, L::cx(d), L::cy(d), L::cz(d), percs, &ax);
           if (yn < 0 || a.flags[yn] != FL_FLUID) continue;
-          *(hs + (long long)d * P + yn) = *(hs + (long long)L::opp(d) * P + s);
+          *(hs + (long long)d * P + a.slot[yn]) = *(hs + (long long)L::opp(d) * P + ss);
         }
       }
     }

@@ -243,5 +243,9 @@ const KernelSet& kernels_d3_bf16();
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
                           int nonfin_slot, cudaStream_t st);
 cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st);
+cudaError_t launch_permute(const void* src, void* dst, int elem, long long pitch, int planes,
+                           const uint8_t* flags, long long N, const uint32_t* from, const uint32_t* to,
+                           cudaStream_t st);
+cudaError_t launch_iota(uint32_t* v, long long N, cudaStream_t st);
 
 }  // namespace lbm

@@ -40,6 +40,8 @@ struct lbm_ctx {
   std::string err;
   std::vector<void*> allocs;
   double* mon_host = nullptr;      // pinned [NMON + 8]
+  void* f_alt[2] = {nullptr, nullptr};   // second population buffers: targets of re-slotting
+  void* h_alt[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -192,11 +194,49 @@ int parity_of(long long step) { return int(step & 1); }
 
 constexpr long long kListRebuild = 1024;   // steps between sorted rebuilds of the fluid list
 
-lbm_status rebuild_geometry(lbm_ctx* c) {
-  LAUNCH(c->ks->masks(c->a, c->stream));
+void set_planes(lbm_ctx* c) {
+  for (int s = 0; s < c->p.n_comp; ++s)
+    for (int i = 0; i < c->Qf; ++i)
+      c->a.fplane[s][i] = static_cast<char*>(c->a.f[s]) + (size_t)i * c->pitch * c->elem;
+  for (int s = 0; s < c->p.n_scal; ++s)
+    for (int j = 0; j < c->Qc; ++j)
+      c->a.hplane[s][j] = static_cast<char*>(c->a.h[s]) + (size_t)j * c->pitch * c->elem;
+}
+
+// Copies the populations of every fluid node between two population buffers.  A NULL map
+// means node order; otherwise the map gives the slot of each node.
+lbm_status move_pops(lbm_ctx* c, void* const* src_f, void* const* dst_f, void* const* src_h,
+                     void* const* dst_h, const uint32_t* from, const uint32_t* to) {
+  for (int s = 0; s < c->p.n_comp; ++s)
+    LAUNCH(launch_permute(src_f[s], dst_f[s], (int)c->elem, c->pitch, c->Qf, c->a.flags, c->N, from, to,
+                          c->stream));
+  for (int s = 0; s < c->p.n_scal; ++s)
+    LAUNCH(launch_permute(src_h[s], dst_h[s], (int)c->elem, c->pitch, c->Qc, c->a.flags, c->N, from, to,
+                          c->stream));
+  return LBM_OK;
+}
+
+// Ordered rebuild of the fluid and interface lists and of the slot map (fluid nodes first, in
+// list order).  With carry, the populations follow their nodes into the new slots.
+lbm_status relist(lbm_ctx* c, bool carry) {
   CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
   LAUNCH(c->ks->lists(c->a, 3, c->stream));
+  if (carry) {
+    lbm_status st = move_pops(c, c->a.f, c->f_alt, c->a.h, c->h_alt, c->a.slot, c->a.slot_new);
+    if (st != LBM_OK) return st;
+    for (int s = 0; s < 2; ++s) {
+      std::swap(c->a.f[s], c->f_alt[s]);
+      std::swap(c->a.h[s], c->h_alt[s]);
+    }
+    set_planes(c);
+  }
+  std::swap(c->a.slot, c->a.slot_new);
   return LBM_OK;
+}
+
+lbm_status rebuild_geometry(lbm_ctx* c, bool carry) {
+  LAUNCH(c->ks->masks(c->a, c->stream));
+  return relist(c, carry);
 }
 
 double dissolve_threshold(const lbm_params& p) {
@@ -284,6 +324,50 @@ __global__ void __launch_bounds__(256) k_detect(const Args a, const double thr) 
   }
 }
 
+// Population copy of every fluid node between buffers of one lattice: dst[i][to(n)] =
+// src[i][from(n)], where a NULL map is node order.
+template <class E>
+__global__ void __launch_bounds__(256) k_permute(const E* __restrict__ src, E* __restrict__ dst, long long pitch,
+                                                 int planes, const uint8_t* __restrict__ flags, long long N,
+                                                 const uint32_t* __restrict__ from, const uint32_t* __restrict__ to) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N || flags[n] != FL_FLUID) return;
+  const long long s = from ? (long long)from[n] : n;
+  const long long d = to ? (long long)to[n] : n;
+  for (int i = 0; i < planes; ++i) dst[i * pitch + d] = src[i * pitch + s];
+}
+
+cudaError_t launch_permute(const void* src, void* dst, int elem, long long pitch, int planes,
+                           const uint8_t* flags, long long N, const uint32_t* from, const uint32_t* to,
+                           cudaStream_t st) {
+  const unsigned int nb = (unsigned int)((N + 255) / 256);
+  switch (elem) {
+    case 2:
+      k_permute<uint16_t><<<nb, 256, 0, st>>>(static_cast<const uint16_t*>(src), static_cast<uint16_t*>(dst),
+                                              pitch, planes, flags, N, from, to);
+      break;
+    case 4:
+      k_permute<uint32_t><<<nb, 256, 0, st>>>(static_cast<const uint32_t*>(src), static_cast<uint32_t*>(dst),
+                                              pitch, planes, flags, N, from, to);
+      break;
+    default:
+      k_permute<unsigned long long><<<nb, 256, 0, st>>>(static_cast<const unsigned long long*>(src),
+                                                        static_cast<unsigned long long*>(dst), pitch, planes,
+                                                        flags, N, from, to);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_iota(uint32_t* __restrict__ v, long long N) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n < N) v[n] = (uint32_t)n;
+}
+
+cudaError_t launch_iota(uint32_t* v, long long N, cudaStream_t st) {
+  k_iota<<<(unsigned int)((N + 255) / 256), 256, 0, st>>>(v, N);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st) {
   long long nb = (a.N / 8 + 255) / 256;
   if (nb < 1) nb = 1;
@@ -365,10 +449,11 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   } while (0)
   for (int s = 0; s < params->n_comp; ++s) DA(a.f[s], P * c->Qf * c->elem);
   for (int s = 0; s < params->n_scal; ++s) DA(a.h[s], P * c->Qc * c->elem);
-  for (int s = 0; s < params->n_comp; ++s)
-    for (int i = 0; i < c->Qf; ++i) a.fplane[s][i] = static_cast<char*>(a.f[s]) + (size_t)i * P * c->elem;
-  for (int s = 0; s < params->n_scal; ++s)
-    for (int j = 0; j < c->Qc; ++j) a.hplane[s][j] = static_cast<char*>(a.h[s]) + (size_t)j * P * c->elem;
+  for (int s = 0; s < params->n_comp; ++s) DA(c->f_alt[s], P * c->Qf * c->elem);
+  for (int s = 0; s < params->n_scal; ++s) DA(c->h_alt[s], P * c->Qc * c->elem);
+  set_planes(c);
+  DA(a.slot, N * 4);
+  DA(a.slot_new, N * 4);
   if (a.sc_on)
     for (int s = 0; s < params->n_comp; ++s) DA(a.psi[s], P * c->ks->psi_bytes);
   DA(a.flags, (N + 3) / 4 * 4);
@@ -416,6 +501,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.mon_out, 0, (NMON + 8) * 8, c->stream);
   for (int s = 0; s < params->n_comp && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.f[s], 0, P * c->Qf * c->elem, c->stream);
   for (int s = 0; s < params->n_scal && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem, c->stream);
+  if (e == cudaSuccess) e = launch_iota(a.slot, N, c->stream);   // node order until a geometry is set
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "initial memset"));
   *out = c;
@@ -429,7 +515,7 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, size_t n) {
     if (flags[k] > 2) return fail(c, LBM_ERR_INVALID_ARG, "flag %u at node %zu", flags[k], k);
   CK(cudaMemcpyAsync(c->a.flags, flags, n, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
-  lbm_status st = rebuild_geometry(c);
+  lbm_status st = rebuild_geometry(c, false);
   if (st != LBM_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
   c->fields_set = false;
@@ -487,10 +573,11 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
       c->ev_used.push_back({e0, e1});
     }
     c->step += 1;
-    // geometry updates append new fluid nodes to the list; restore its sorted order now and then
+    // geometry updates append new fluid nodes to the list (they keep their old slots); now and
+    // then restore the sorted order and the fluid-first slots
     if (c->p.geo_mode != LBM_GEO_NONE && (c->step % kListRebuild) == 0) {
-      CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
-      LAUNCH(c->ks->lists(c->a, 3, c->stream));
+      lbm_status st = relist(c, true);
+      if (st != LBM_OK) return st;
     }
     if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0) {
       if (c->p.geo_mode == LBM_GEO_DISSOLVE)
@@ -709,12 +796,17 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   std::memcpy(o, &hd, sizeof hd);
   o += sizeof hd;
   const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
+  // populations in node order (solid nodes 0), staged in the second population buffers
+  for (int s = 0; s < c->p.n_comp; ++s) CK(cudaMemsetAsync(c->f_alt[s], 0, c->Qf * P * c->elem, c->stream));
+  for (int s = 0; s < c->p.n_scal; ++s) CK(cudaMemsetAsync(c->h_alt[s], 0, c->Qc * P * c->elem, c->stream));
+  lbm_status st = move_pops(c, c->a.f, c->f_alt, c->a.h, c->h_alt, c->a.slot, nullptr);
+  if (st != LBM_OK) return st;
   for (int s = 0; s < c->p.n_comp; ++s) {
-    CK(cudaMemcpyAsync(o, c->a.f[s], c->Qf * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(o, c->f_alt[s], c->Qf * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
     o += c->Qf * P * c->elem;
   }
   for (int s = 0; s < c->p.n_scal; ++s) {
-    CK(cudaMemcpyAsync(o, c->a.h[s], c->Qc * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(o, c->h_alt[s], c->Qc * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
     o += c->Qc * P * c->elem;
   }
   CK(cudaMemcpyAsync(o, c->a.flags, (N + 3) / 4 * 4, cudaMemcpyDeviceToHost, c->stream)); o += (N + 3) / 4 * 4;
@@ -740,12 +832,14 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
     return fail(c, LBM_ERR_INVALID_ARG, "checkpoint does not match this context");
   o += sizeof hd;
   const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
+  // node-order populations go to the second buffers; they move to their slots once the slot
+  // map of the restored geometry exists
   for (int s = 0; s < c->p.n_comp; ++s) {
-    CK(cudaMemcpyAsync(c->a.f[s], o, c->Qf * P * c->elem, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->f_alt[s], o, c->Qf * P * c->elem, cudaMemcpyHostToDevice, c->stream));
     o += c->Qf * P * c->elem;
   }
   for (int s = 0; s < c->p.n_scal; ++s) {
-    CK(cudaMemcpyAsync(c->a.h[s], o, c->Qc * P * c->elem, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->h_alt[s], o, c->Qc * P * c->elem, cudaMemcpyHostToDevice, c->stream));
     o += c->Qc * P * c->elem;
   }
   CK(cudaMemcpyAsync(c->a.flags, o, (N + 3) / 4 * 4, cudaMemcpyHostToDevice, c->stream)); o += (N + 3) / 4 * 4;
@@ -756,7 +850,9 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   CK(cudaMemcpyAsync(c->a.flip_mon, o, 64, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
-  lbm_status st = rebuild_geometry(c);
+  lbm_status st = rebuild_geometry(c, false);
+  if (st != LBM_OK) return st;
+  st = move_pops(c, c->f_alt, c->a.f, c->h_alt, c->a.h, nullptr, c->a.slot);
   if (st != LBM_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
   c->step = hd.step;
