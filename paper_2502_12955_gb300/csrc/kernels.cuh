@@ -71,6 +71,18 @@ enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_CAS = 4 };
 enum : int { GEO_NONE = 0, GEO_DISSOLVE = 1, GEO_DEPOSIT = 2 };
 enum : uint8_t { FL_FLUID = 0, FL_SOLID = 1, FL_REACTIVE = 2, FL_FLIPPING = 3 };
 
+// Floor division by a fixed divisor d through a rounded-up reciprocal (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
+// M = ceil(2^(31 + l) / d), floor(n / d) = (n * M) >> (31 + l) for every n < 2^31 and
+// 1 <= d < 2^31.  The host builds M and the shift and checks them at every quotient boundary.
+struct FastDiv {
+  uint32_t M;
+  int sh;
+};
+__host__ __device__ __forceinline__ unsigned int fast_div(unsigned int n, FastDiv d) {
+  return (unsigned int)(((unsigned long long)n * d.M) >> d.sh);
+}
+
 // Everything a kernel needs, in double; kernels convert to their compute type.
 struct Args {
   void* f[2];
@@ -121,6 +133,7 @@ struct Args {
   double V_m, m_s0, DP;
   double rho_ref[2], C_ref[2];
   int bx, by;                // step-kernel block shape
+  FastDiv div_x, div_y;      // node index / nx, (node index / nx) / ny
 };
 
 // Compute-type constants derived on the host from Args (see make_coef).
@@ -134,7 +147,7 @@ struct Coef {
   T omc[2];         // 1 / tau_c
   T wc0, wca;       // scalar weights: rest, axis
   T ics2c;          // 1 / c_s^2 of the scalar lattice
-  T Kr;             // k tau_c / (tau_c - 1/2)
+  T icb;            // 1 / (2 w_a + K), K = k tau_c / (tau_c - 1/2): wet-node closure
   T kr;             // k
   T C_in[2];
   T DP, keep;       // deposition probability, 1 - DP
@@ -153,28 +166,25 @@ enum : int {
 // ------------------------------------------------------------- indexing
 
 struct Nbr {
-  int x, y, z;
-  int xm, xp, ym, yp, zm, zp;
-  int nx, ny;
+  int n;                              // linear node index
+  int oxm, oxp, oym, oyp, ozm, ozp;   // linear offsets to the -/+ neighbours, periodic wrap
   __device__ __forceinline__ int at(int dx, int dy, int dz) const {
-    const int X = dx < 0 ? xm : (dx > 0 ? xp : x);
-    const int Y = dy < 0 ? ym : (dy > 0 ? yp : y);
-    const int Z = dz < 0 ? zm : (dz > 0 ? zp : z);
-    return X + nx * (Y + ny * Z);
+    return n + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
+           (dz < 0 ? ozm : (dz > 0 ? ozp : 0));
   }
 };
 
 __device__ __forceinline__ Nbr make_nbr(const Args& a, int x, int y, int z) {
   Nbr b;
-  b.x = x; b.y = y; b.z = z;
-  b.nx = a.nx; b.ny = a.ny;
+  const int sy = a.nx, sz = a.nx * a.ny;
+  b.n = x + sy * y + sz * z;
   // always wrap: walls on closed axes are excluded by the link masks before any access
-  b.xm = x == 0 ? a.nx - 1 : x - 1;
-  b.xp = x == a.nx - 1 ? 0 : x + 1;
-  b.ym = y == 0 ? a.ny - 1 : y - 1;
-  b.yp = y == a.ny - 1 ? 0 : y + 1;
-  b.zm = z == 0 ? a.nz - 1 : z - 1;
-  b.zp = z == a.nz - 1 ? 0 : z + 1;
+  b.oxm = x == 0 ? a.nx - 1 : -1;
+  b.oxp = x == a.nx - 1 ? 1 - a.nx : 1;
+  b.oym = y == 0 ? (a.ny - 1) * sy : -sy;
+  b.oyp = y == a.ny - 1 ? (1 - a.ny) * sy : sy;
+  b.ozm = z == 0 ? (a.nz - 1) * sz : -sz;
+  b.ozp = z == a.nz - 1 ? (1 - a.nz) * sz : sz;
   return b;
 }
 
@@ -270,7 +280,7 @@ __device__ __forceinline__ void close_scalar(T* h, uint32_t m, const Coef<T>& k,
   for (int j = 1; j < L::QC; ++j) {
     if (MaskBits<L>::code(m, L::opp(j)) == 2u) {
       const T hb = old[L::opp(j)] + sh;
-      const T Cb = T(2) * hb / (T(2) * k.wca + k.Kr);
+      const T Cb = T(2) * hb * k.icb;
       const T hn = T(2) * k.wca * Cb - hb - sh;
       h[j] = hn;
       on_link(j, Cb, old[j] - hn);
@@ -315,6 +325,21 @@ __device__ __forceinline__ void push_flip(const Args& a, int n) {
     atomicOr(a.err, ERR_CAPACITY);
 }
 
+// Exact float -> double widening by re-biasing the IEEE-754 fields with integer operations; the
+// conversion instruction itself runs on the FP64 unit, which is narrow on this GPU.  Zero keeps
+// its sign; subnormal, infinite and NaN inputs (never produced on the hot path) take the
+// conversion instruction.
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) {
+  const unsigned int b = __float_as_uint(v);
+  const unsigned int ex = (b >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  if ((b << 1) == 0u) return __longlong_as_double((long long)sign);
+  if (ex == 0u || ex == 0xffu) return double(v);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + (1023u - 127u)) << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -331,319 +356,343 @@ __device__ __forceinline__ T warp_sum(T v) {
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 3   // resident 256-thread blocks per SM for one component (80 registers)
 #endif
+
+// Neighbour offsets of fluid node n from its coordinates (fast divisions by nx and ny).
+__device__ __forceinline__ Nbr nbr_of(const Args& a, int n) {
+  const unsigned int q = fast_div(unsigned(n), a.div_x);
+  const unsigned int z = fast_div(q, a.div_y);
+  return make_nbr(a, n - int(q) * a.nx, int(q - z * unsigned(a.ny)), int(z));
+}
+
+// Stored populations of list entry e (node n, link mask m) as the node gathers them.
+template <class L, class S, int NC, int NS, int parity>
+__device__ __forceinline__ void gather_entry(const Args& a, unsigned int e, unsigned int base, int n,
+                                             uint32_t m, typename Store<S>::T (&f)[NC][L::Q],
+                                             typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC]) {
+  const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+  const Nbr nb = parity ? nbr_of(a, n) : Nbr{};
+#pragma unroll
+  for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f[s]);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s]);
+}
+
+// Everything after the gather for one fluid node: wet-node closure and its bookkeeping,
+// deposition, moments, forces, velocity, flow and scalar collision, in-place scatter.
 template <class L, class S, int NC, int NS, int COLL, int parity>
-__global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
+__device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typename Store<S>::T>& k, int n,
+                                                uint32_t m, long long sn,
+                                                typename Store<S>::T (&f)[NC][L::Q],
+                                                typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC],
+                                                typename Store<S>::T& wallx) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
-  T wallx = T(0);
-  const unsigned int count = a.fluid_count[0];
-  const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
-  const unsigned int stride = gridDim.x * blockDim.x;
-  // threads walk the fluid-node list, so every lane of a warp updates a fluid node; the list
-  // entry is fetched two iterations and the link mask one iteration ahead
-  unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
-  int n_next = e < count ? int(a.fluid_list[e]) : 0;
-  int n_next2 = e + stride < count ? int(a.fluid_list[e + stride]) : 0;
-  uint32_t m_next = e < count ? a.mask[n_next] : 0u;
-  for (; e < count; e += stride) {
-  const int n = n_next;
-  const uint32_t m = m_next;
-  n_next = n_next2;
-  if (e + stride < count) m_next = a.mask[n_next];
-  if (e + 2 * stride < count) n_next2 = int(a.fluid_list[e + 2 * stride]);
-  if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
-  const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-  const int x = n % a.nx;
-  const int yz = n / a.nx;
-  const int y = yz % a.ny;
-  const int z = yz / a.ny;
-  {
-    const Nbr nb = make_nbr(a, x, y, z);
-    const long long P = a.pitch;
-    const int row = y + a.ny * z;
-    // ---- gather
-    T f[NC][Q];
+  const Nbr nb = nbr_of(a, n);
+  // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
+  if (NS > 0) {
+    // the consumed totals are reductions (no value returned): the threshold test runs in
+    // k_detect over the interface list before the geometry update
+    close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
+      const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+      atomicAdd(a.acc + src, widen(k.kr * Cb));
+      wallx += exch;
+    });
+    // ---- deposition at near-substrate nodes (Eq. surface_deposition)
+    if (a.geo_mode == GEO_DEPOSIT) {
+      bool near = false;
 #pragma unroll
-    for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f[s]);
-    T h[NS > 0 ? NS : 1][QC];
+      for (int j = 1; j < QC; ++j) {
+        const uint32_t c = MaskBits<L>::code(m, j);
+        near |= (c == 1u || c == 2u);
+      }
+      if (near) {
+        T sum = k.cref[0];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s]);
-    // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
-    if (NS > 0) {
-      // the consumed totals are reductions (no value returned): the threshold test runs in
-      // k_detect over the interface list before the geometry update
-      close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
-        const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
-        atomicAdd(a.acc + src, double(k.kr * Cb));
-        wallx += exch;
-      });
-      // ---- deposition at near-substrate nodes (Eq. surface_deposition)
-      if (a.geo_mode == GEO_DEPOSIT) {
-        bool near = false;
+        for (int j = 0; j < QC; ++j) sum += h[0][j];
+        const double dep = double(k.DP * sum);
+        const double old = a.acc[n];
+        a.acc[n] = old + dep;
+        if (old <= 1.0 && old + dep > 1.0) push_flip(a, n);
+        if (a.deposit_conservative) {
 #pragma unroll
-        for (int j = 1; j < QC; ++j) {
-          const uint32_t c = MaskBits<L>::code(m, j);
-          near |= (c == 1u || c == 2u);
-        }
-        if (near) {
-          T sum = k.cref[0];
-#pragma unroll
-          for (int j = 0; j < QC; ++j) sum += h[0][j];
-          const double dep = double(k.DP * sum);
-          const double old = a.acc[n];
-          a.acc[n] = old + dep;
-          if (old <= 1.0 && old + dep > 1.0) push_flip(a, n);
-          if (a.deposit_conservative) {
-#pragma unroll
-            for (int j = 0; j < QC; ++j) h[0][j] = h[0][j] * k.keep - scal_w<T>(j, k) * k.cref[0] * k.DP;
-          }
+          for (int j = 0; j < QC; ++j) h[0][j] = h[0][j] * k.keep - scal_w<T>(j, k) * k.cref[0] * k.DP;
         }
       }
     }
-    // ---- moments (Eq. 1.7, 1.8): rho = rref + sum of deviations
-    T drho[NC], rho[NC], jx[NC], jy[NC], jz[NC];
+  }
+  // ---- moments (Eq. 1.7, 1.8): rho = rref + sum of deviations
+  T drho[NC], rho[NC], jx[NC], jy[NC], jz[NC];
 #pragma unroll
-    for (int s = 0; s < NC; ++s) {
-      T r = T(0), ax = T(0), ay = T(0), az = T(0);
+  for (int s = 0; s < NC; ++s) {
+    T r = T(0), ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        r += f[s][i];
-        if (L::cx(i)) ax += T(L::cx(i)) * f[s][i];
-        if (L::cy(i)) ay += T(L::cy(i)) * f[s][i];
-        if (L::cz(i)) az += T(L::cz(i)) * f[s][i];
-      }
-      drho[s] = r;
-      rho[s] = k.rref[s] + r;
-      jx[s] = ax; jy[s] = ay; jz[s] = az;
+    for (int i = 0; i < Q; ++i) {
+      r += f[s][i];
+      if (L::cx(i)) ax += T(L::cx(i)) * f[s][i];
+      if (L::cy(i)) ay += T(L::cy(i)) * f[s][i];
+      if (L::cz(i)) az += T(L::cz(i)) * f[s][i];
     }
-    // ---- forces: Shan-Chen cohesion / solid psi (Eq. 1.13, 1.14), adhesion (1.15), body
-    T Fx[NC], Fy[NC], Fz[NC];
+    drho[s] = r;
+    rho[s] = k.rref[s] + r;
+    jx[s] = ax; jy[s] = ay; jz[s] = az;
+  }
+  // ---- forces: Shan-Chen cohesion / solid psi (Eq. 1.13, 1.14), adhesion (1.15), body
+  T Fx[NC], Fy[NC], Fz[NC];
 #pragma unroll
-    for (int s = 0; s < NC; ++s) {
-      Fx[s] = rho[s] * k.g[0];
-      Fy[s] = rho[s] * k.g[1];
-      Fz[s] = rho[s] * k.g[2];
-    }
-    if (a.sc_on) {
-      T sx[NC], sy[NC], sz[NC];
+  for (int s = 0; s < NC; ++s) {
+    Fx[s] = rho[s] * k.g[0];
+    Fy[s] = rho[s] * k.g[1];
+    Fz[s] = rho[s] * k.g[2];
+  }
+  if (a.sc_on) {
+    T sx[NC], sy[NC], sz[NC];
 #pragma unroll
-      for (int s2 = 0; s2 < NC; ++s2) {
-        const T* ps = reinterpret_cast<const T*>(a.psi[s2]);
-        T ax = T(0), ay = T(0), az = T(0);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const T pv = flow_wall<L>(m, i) ? k.psi_wall : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
-          const T wp = T(L::w(i)) * pv;
-          if (L::cx(i)) ax += T(L::cx(i)) * wp;
-          if (L::cy(i)) ay += T(L::cy(i)) * wp;
-          if (L::cz(i)) az += T(L::cz(i)) * wp;
-        }
-        sx[s2] = ax; sy[s2] = ay; sz[s2] = az;
-      }
-#pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        const T pself = reinterpret_cast<const T*>(a.psi[s])[n];
-#pragma unroll
-        for (int s2 = 0; s2 < NC; ++s2) {
-          const T Gss = k.G[s][s2];
-          Fx[s] -= pself * Gss * sx[s2];
-          Fy[s] -= pself * Gss * sy[s2];
-          Fz[s] -= pself * Gss * sz[s2];
-        }
-      }
-    }
-    if (a.ads_on) {
+    for (int s2 = 0; s2 < NC; ++s2) {
+      const T* ps = reinterpret_cast<const T*>(a.psi[s2]);
       T ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
-        if (flow_wall<L>(m, i)) {
-          ax += T(L::w(i)) * T(L::cx(i));
-          ay += T(L::w(i)) * T(L::cy(i));
-          az += T(L::w(i)) * T(L::cz(i));
-        }
+        const T pv = flow_wall<L>(m, i) ? k.psi_wall : ps[nb.at(L::cx(i), L::cy(i), L::cz(i))];
+        const T wp = T(L::w(i)) * pv;
+        if (L::cx(i)) ax += T(L::cx(i)) * wp;
+        if (L::cy(i)) ay += T(L::cy(i)) * wp;
+        if (L::cz(i)) az += T(L::cz(i)) * wp;
       }
-#pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        const T ga = k.G_ads[s] * rho[s];
-        Fx[s] -= ga * ax; Fy[s] -= ga * ay; Fz[s] -= ga * az;
-      }
+      sx[s2] = ax; sy[s2] = ay; sz[s2] = az;
     }
-    // ---- physical / barycentric velocity (Eq. 1.19, 1.20)
-    T rt = T(0), mx = T(0), my = T(0), mz = T(0);
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
-      rt += rho[s];
-      mx += jx[s] + T(0.5) * Fx[s];
-      my += jy[s] + T(0.5) * Fy[s];
-      mz += jz[s] + T(0.5) * Fz[s];
+      const T pself = reinterpret_cast<const T*>(a.psi[s])[n];
+#pragma unroll
+      for (int s2 = 0; s2 < NC; ++s2) {
+        const T Gss = k.G[s][s2];
+        Fx[s] -= pself * Gss * sx[s2];
+        Fy[s] -= pself * Gss * sy[s2];
+        Fz[s] -= pself * Gss * sz[s2];
+      }
     }
-    const T irt = T(1) / rt;
-    const T ux = mx * irt, uy = my * irt, uz = mz * irt;
-    // ---- flow collision
-    if (a.shift_forcing) {
-      // Shan-Chen velocity shift (Eq. 1.17, 1.18), BGK, F_i = 0
-      T nxs = T(0), nys = T(0), nzs = T(0), den = T(0);
+  }
+  if (a.ads_on) {
+    T ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        nxs += jx[s] * k.om[s]; nys += jy[s] * k.om[s]; nzs += jz[s] * k.om[s];
-        den += rho[s] * k.om[s];
+    for (int i = 1; i < Q; ++i) {
+      if (flow_wall<L>(m, i)) {
+        ax += T(L::w(i)) * T(L::cx(i));
+        ay += T(L::w(i)) * T(L::cy(i));
+        az += T(L::w(i)) * T(L::cz(i));
       }
-      const T iden = T(1) / den;
+    }
 #pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        const T ir = T(1) / rho[s];
-        const T ex = nxs * iden + k.tau[s] * Fx[s] * ir;
-        const T ey = nys * iden + k.tau[s] * Fy[s] * ir;
-        const T ez = nzs * iden + k.tau[s] * Fz[s] * ir;
+    for (int s = 0; s < NC; ++s) {
+      const T ga = k.G_ads[s] * rho[s];
+      Fx[s] -= ga * ax; Fy[s] -= ga * ay; Fz[s] -= ga * az;
+    }
+  }
+  // ---- physical / barycentric velocity (Eq. 1.19, 1.20)
+  T rt = T(0), mx = T(0), my = T(0), mz = T(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-          f[s][i] -= k.om[s] * (f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ex, ey, ez));
+  for (int s = 0; s < NC; ++s) {
+    rt += rho[s];
+    mx += jx[s] + T(0.5) * Fx[s];
+    my += jy[s] + T(0.5) * Fy[s];
+    mz += jz[s] + T(0.5) * Fz[s];
+  }
+  const T irt = T(1) / rt;
+  const T ux = mx * irt, uy = my * irt, uz = mz * irt;
+  // ---- flow collision
+  if (a.shift_forcing) {
+    // Shan-Chen velocity shift (Eq. 1.17, 1.18), BGK, F_i = 0
+    T nxs = T(0), nys = T(0), nzs = T(0), den = T(0);
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      nxs += jx[s] * k.om[s]; nys += jy[s] * k.om[s]; nzs += jz[s] * k.om[s];
+      den += rho[s] * k.om[s];
+    }
+    const T iden = T(1) / den;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const T ir = T(1) / rho[s];
+      const T ex = nxs * iden + k.tau[s] * Fx[s] * ir;
+      const T ey = nys * iden + k.tau[s] * Fy[s] * ir;
+      const T ez = nzs * iden + k.tau[s] * Fz[s] * ir;
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        f[s][i] -= k.om[s] * (f[s][i] - feq_dev<L, T>(i, rho[s], drho[s], ex, ey, ez));
+    }
+  } else {
+    // Eq. 1.16 with Guo forcing (Eq. 1.21): f* = f + F_i - omega (f - f_eq + F_i / 2), for BGK;
+    // MRT adds the projections of n = f - f_eq + F_i / 2 on the non-hydrodynamic groups with
+    // rate (s_g - 1/tau).  Opposite directions are handled as pairs: the equilibrium and the
+    // Guo term split into even and odd parts, even MRT rows see n_i + n_opp(i), odd rows see
+    // n_i - n_opp(i).
+    const T uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const T om = k.om[s];
+      const T uF = ux * Fx[s] + uy * Fy[s] + uz * Fz[s];
+      T sp[Q], dp[Q];   // pair sums / differences of n (MRT only), index of the first member
+      {
+        // rest population
+        const T w0 = T(L::w(0));
+        const T fe = w0 * (drho[s] - rho[s] * T(1.5) * uu);
+        const T Fi = w0 * (T(-3) * uF);
+        const T nq = f[s][0] - fe + T(0.5) * Fi;
+        if (COLL == 1) sp[0] = nq;
+        f[s][0] = f[s][0] + Fi - om * nq;
       }
-    } else {
-      // Eq. 1.16 with Guo forcing (Eq. 1.21): f* = f + F_i - omega (f - f_eq + F_i / 2), for BGK;
-      // MRT adds the projections of n = f - f_eq + F_i / 2 on the non-hydrodynamic groups with
-      // rate (s_g - 1/tau).  Opposite directions are handled as pairs: the equilibrium and the
-      // Guo term split into even and odd parts, even MRT rows see n_i + n_opp(i), odd rows see
-      // n_i - n_opp(i).
-      const T uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
-      for (int s = 0; s < NC; ++s) {
-        const T om = k.om[s];
-        const T uF = ux * Fx[s] + uy * Fy[s] + uz * Fz[s];
-        T sp[Q], dp[Q];   // pair sums / differences of n (MRT only), index of the first member
-        {
-          // rest population
-          const T w0 = T(L::w(0));
-          const T fe = w0 * (drho[s] - rho[s] * T(1.5) * uu);
-          const T Fi = w0 * (T(-3) * uF);
-          const T nq = f[s][0] - fe + T(0.5) * Fi;
-          if (COLL == 1) sp[0] = nq;
-          f[s][0] = f[s][0] + Fi - om * nq;
-        }
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          if (i > L::opp(i)) continue;
-          const int o = L::opp(i);
-          const T w = T(L::w(i));
-          const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
-          const T cF = T(L::cx(i)) * Fx[s] + T(L::cy(i)) * Fy[s] + T(L::cz(i)) * Fz[s];
-          const T fe_e = w * (drho[s] + rho[s] * (T(4.5) * cu * cu - T(1.5) * uu));
-          const T fe_o = w * (T(3) * rho[s] * cu);
-          const T Fi_e = w * (T(9) * cu * cF - T(3) * uF);
-          const T Fi_o = w * (T(3) * cF);
-          const T nq_i = f[s][i] - (fe_e + fe_o) + T(0.5) * (Fi_e + Fi_o);
-          const T nq_o = f[s][o] - (fe_e - fe_o) + T(0.5) * (Fi_e - Fi_o);
-          if (COLL == 1) {
-            sp[i] = nq_i + nq_o;
-            dp[i] = nq_i - nq_o;
-          }
-          f[s][i] = f[s][i] + (Fi_e + Fi_o) - om * nq_i;
-          f[s][o] = f[s][o] + (Fi_e - Fi_o) - om * nq_o;
-        }
+      for (int i = 1; i < Q; ++i) {
+        if (i > L::opp(i)) continue;
+        const int o = L::opp(i);
+        const T w = T(L::w(i));
+        const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+        const T cF = T(L::cx(i)) * Fx[s] + T(L::cy(i)) * Fy[s] + T(L::cz(i)) * Fz[s];
+        const T fe_e = w * (drho[s] + rho[s] * (T(4.5) * cu * cu - T(1.5) * uu));
+        const T fe_o = w * (T(3) * rho[s] * cu);
+        const T Fi_e = w * (T(9) * cu * cF - T(3) * uF);
+        const T Fi_o = w * (T(3) * cF);
+        const T nq_i = f[s][i] - (fe_e + fe_o) + T(0.5) * (Fi_e + Fi_o);
+        const T nq_o = f[s][o] - (fe_e - fe_o) + T(0.5) * (Fi_e - Fi_o);
         if (COLL == 1) {
-          T coef[L::NMRT];
+          sp[i] = nq_i + nq_o;
+          dp[i] = nq_i - nq_o;
+        }
+        f[s][i] = f[s][i] + (Fi_e + Fi_o) - om * nq_i;
+        f[s][o] = f[s][o] + (Fi_e - Fi_o) - om * nq_o;
+      }
+      if (COLL == 1) {
+        T coef[L::NMRT];
 #pragma unroll
-          for (int kk = 0; kk < L::NMRT; ++kk) {
-            T mk = T(0);
-            if (!mrt_odd<L>(kk)) {
-              const int r0 = Mrt<L>::row(kk, 0);
-              if (r0 != 0) mk += T(r0) * sp[0];
-            }
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-              if (i > L::opp(i)) continue;
-              const int r = Mrt<L>::row(kk, i);
-              if (r != 0) mk += T(r) * (mrt_odd<L>(kk) ? dp[i] : sp[i]);
-            }
-            coef[kk] = (k.s_grp[Mrt<L>::group(kk)] - om) * mk * k.inv_norm[kk];
-          }
-          {
-            T c = T(0);
-#pragma unroll
-            for (int kk = 0; kk < L::NMRT; ++kk) {
-              const int r = Mrt<L>::row(kk, 0);
-              if (r != 0 && !mrt_odd<L>(kk)) c += T(r) * coef[kk];
-            }
-            f[s][0] -= c;
+        for (int kk = 0; kk < L::NMRT; ++kk) {
+          T mk = T(0);
+          if (!mrt_odd<L>(kk)) {
+            const int r0 = Mrt<L>::row(kk, 0);
+            if (r0 != 0) mk += T(r0) * sp[0];
           }
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
             if (i > L::opp(i)) continue;
-            T ce = T(0), co = T(0);
-#pragma unroll
-            for (int kk = 0; kk < L::NMRT; ++kk) {
-              const int r = Mrt<L>::row(kk, i);
-              if (r == 0) continue;
-              if (mrt_odd<L>(kk)) co += T(r) * coef[kk];
-              else ce += T(r) * coef[kk];
-            }
-            f[s][i] -= ce + co;
-            f[s][L::opp(i)] -= ce - co;
+            const int r = Mrt<L>::row(kk, i);
+            if (r != 0) mk += T(r) * (mrt_odd<L>(kk) ? dp[i] : sp[i]);
           }
+          coef[kk] = (k.s_grp[Mrt<L>::group(kk)] - om) * mk * k.inv_norm[kk];
         }
-      }
-    }
-    // ---- scalar collision (Eq. therpop_species, therpopeq_species), u = physical velocity
+        {
+          T c = T(0);
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      T dC = T(0);
-#pragma unroll
-      for (int j = 0; j < QC; ++j) dC += h[s][j];
-      const T C = k.cref[s] + dC;
-#pragma unroll
-      for (int j = 0; j < QC; ++j) {
-        const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
-        const T he = scal_w<T>(j, k) * (dC + C * cu * k.ics2c);
-        h[s][j] -= k.omc[s] * (h[s][j] - he);
-      }
-    }
-    // ---- scatter flow
-#pragma unroll
-    for (int s = 0; s < NC; ++s) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        S* p;
-        if (parity == 0 || i == 0 || flow_wall<L>(m, i))
-          p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + sn;
-        else
-          p = reinterpret_cast<S*>(a.fplane[s][i]) +
-              (long long)__ldg(a.slot + nb.at(L::cx(i), L::cy(i), L::cz(i)));
-        Store<S>::st(p, f[s][i]);
-      }
-    }
-    // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-#pragma unroll
-      for (int j = 0; j < QC; ++j) {
-        const uint32_t code = j == 0 ? 0u : MaskBits<L>::code(m, j);
-        T v = h[s][j];
-        S* p;
-        if (code == 3u) {
-          // open face: the population arriving from outside replaces the one leaving
-          const int jb = L::opp(j);
-          T b;
-          const T sh = k.wca * k.cref[s];
-          if (L::cx(j) < 0) {
-            const T cu = T(L::cx(jb)) * ux + T(L::cy(jb)) * uy + T(L::cz(jb)) * uz;
-            b = k.wca * k.C_in[s] * (T(1) + cu * k.ics2c) - sh;
-            a.inflow_row[s * (a.ny * a.nz) + row] += double(b) - double(v);
-          } else {
-            b = h[s][jb];
-            a.outflow_row[s * (a.ny * a.nz) + row] += double(v) - double(b);
+          for (int kk = 0; kk < L::NMRT; ++kk) {
+            const int r = Mrt<L>::row(kk, 0);
+            if (r != 0 && !mrt_odd<L>(kk)) c += T(r) * coef[kk];
           }
-          v = b;
-          p = reinterpret_cast<S*>(a.hplane[s][jb]) + sn;
-        } else if (parity == 0 || j == 0 || code != 0u) {
-          p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + sn;
-        } else {
-          p = reinterpret_cast<S*>(a.hplane[s][j]) +
-              (long long)__ldg(a.slot + nb.at(L::cx(j), L::cy(j), L::cz(j)));
+          f[s][0] -= c;
         }
-        Store<S>::st(p, v);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if (i > L::opp(i)) continue;
+          T ce = T(0), co = T(0);
+#pragma unroll
+          for (int kk = 0; kk < L::NMRT; ++kk) {
+            const int r = Mrt<L>::row(kk, i);
+            if (r == 0) continue;
+            if (mrt_odd<L>(kk)) co += T(r) * coef[kk];
+            else ce += T(r) * coef[kk];
+          }
+          f[s][i] -= ce + co;
+          f[s][L::opp(i)] -= ce - co;
+        }
       }
     }
   }
+  // ---- scalar collision (Eq. therpop_species, therpopeq_species), u = physical velocity
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T dC = T(0);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) dC += h[s][j];
+    const T C = k.cref[s] + dC;
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
+      const T he = scal_w<T>(j, k) * (dC + C * cu * k.ics2c);
+      h[s][j] -= k.omc[s] * (h[s][j] - he);
+    }
+  }
+  // ---- scatter flow
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      S* p;
+      if (parity == 0 || i == 0 || flow_wall<L>(m, i))
+        p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + sn;
+      else
+        p = reinterpret_cast<S*>(a.fplane[s][i]) +
+            (long long)__ldg(a.slot + nb.at(L::cx(i), L::cy(i), L::cz(i)));
+      Store<S>::st(p, f[s][i]);
+    }
+  }
+  // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+      const uint32_t code = j == 0 ? 0u : MaskBits<L>::code(m, j);
+      T v = h[s][j];
+      S* p;
+      if (code == 3u) {
+        // open face: the population arriving from outside replaces the one leaving
+        const int jb = L::opp(j);
+        T b;
+        const T sh = k.wca * k.cref[s];
+        if (L::cx(j) < 0) {
+          const T cu = T(L::cx(jb)) * ux + T(L::cy(jb)) * uy + T(L::cz(jb)) * uz;
+          b = k.wca * k.C_in[s] * (T(1) + cu * k.ics2c) - sh;
+          a.inflow_row[s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x))] += widen(b) - widen(v);
+        } else {
+          b = h[s][jb];
+          a.outflow_row[s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x))] += widen(v) - widen(b);
+        }
+        v = b;
+        p = reinterpret_cast<S*>(a.hplane[s][jb]) + sn;
+      } else if (parity == 0 || j == 0 || code != 0u) {
+        p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + sn;
+      } else {
+        p = reinterpret_cast<S*>(a.hplane[s][j]) +
+            (long long)__ldg(a.slot + nb.at(L::cx(j), L::cy(j), L::cz(j)));
+      }
+      Store<S>::st(p, v);
+    }
+  }
+}
+
+// One fused time step for every fluid node: gather (A-A parity), wet-node closure and its
+// bookkeeping, deposition, moments, forces, velocity, flow collision (BGK / MRT, Guo or
+// velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
+// Registers hold deviations from w_i * ref throughout.
+template <class L, class S, int NC, int NS, int COLL, int parity>
+__global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC, NSD = NS > 0 ? NS : 1;
+  T wallx = T(0);
+  const unsigned int count = a.fluid_count[0];
+  const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
+  const unsigned int stride = gridDim.x * blockDim.x;
+  unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
+  // the list entry is fetched two iterations and the link mask one iteration ahead
+  int n_next = e < count ? int(a.fluid_list[e]) : 0;
+  int n_next2 = e + stride < count ? int(a.fluid_list[e + stride]) : 0;
+  uint32_t m_next = e < count ? a.mask[n_next] : 0u;
+  for (; e < count; e += stride) {
+    const int n = n_next;
+    const uint32_t m = m_next;
+    n_next = n_next2;
+    if (e + stride < count) m_next = a.mask[n_next];
+    if (e + 2 * stride < count) n_next2 = int(a.fluid_list[e + 2 * stride]);
+    if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
+    T f[NC][Q], h[NSD][QC];
+    gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
+    const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+    collide_scatter<L, S, NC, NS, COLL, parity>(a, k, n, m, sn, f, h, wallx);
   }
   // ---- wall-exchange monitor: one reduction per warp that saw a reactive link
   if (NS > 0) {
@@ -652,7 +701,7 @@ __global__ void __launch_bounds__(256, (NC == 1 ? LBM_STEP_MIN_BLOCKS : 2)) k_st
       const T w = warp_sum(wallx);
       if ((threadIdx.x & 31) == 0)
         atomicAdd(a.wallx_slot + ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
-                  double(w));
+                  widen(w));
     }
   }
 }

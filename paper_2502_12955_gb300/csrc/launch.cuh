@@ -63,7 +63,7 @@ Coef<T> make_coef(const Args& a, bool shifted) {
   k.wc0 = T(a.J0);
   k.wca = T((1.0 - a.J0) / double(L::QC - 1));
   k.ics2c = T(double(L::QC - 1) / (2.0 * (1.0 - a.J0)));
-  k.Kr = T(a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5));
+  k.icb = T(1.0 / (2.0 * (1.0 - a.J0) / double(L::QC - 1) + a.k_react * a.tau_c[0] / (a.tau_c[0] - 0.5)));
   k.kr = T(a.k_react);
   k.DP = T(a.DP);
   k.keep = T(1.0 - a.DP);

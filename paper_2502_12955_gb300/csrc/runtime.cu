@@ -145,6 +145,27 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
   return LBM_OK;
 }
 
+FastDiv make_fast_div(long long d) {
+  int l = 0;
+  while ((1ll << l) < d) ++l;
+  const unsigned long long num = 1ull << (31 + l);
+  FastDiv f;
+  f.M = (uint32_t)((num + (unsigned long long)d - 1) / (unsigned long long)d);
+  f.sh = 31 + l;
+  return f;
+}
+
+// The quotient of a monotone approximation is exact everywhere once it is exact on both sides
+// of every quotient boundary q * d below the limit.
+bool fast_div_exact(FastDiv f, long long d, long long limit) {
+  for (long long n = d; n < limit; n += d) {
+    const long long q = n / d;
+    if (fast_div((unsigned int)(n - 1), f) != (unsigned int)(q - 1) || fast_div((unsigned int)n, f) != (unsigned int)q)
+      return false;
+  }
+  return limit <= 1 || fast_div((unsigned int)(limit - 1), f) == (unsigned int)((limit - 1) / d);
+}
+
 void fill_args(lbm_ctx* c) {
   Args& a = c->a;
   const lbm_params& p = c->p;
@@ -188,6 +209,8 @@ void fill_args(lbm_ctx* c) {
   if (bx == 0) bx = c->nx >= 256 ? 256 : (c->nx >= 128 ? 128 : (c->nx > 32 ? 64 : 32));
   a.bx = bx;
   a.by = 1;
+  a.div_x = make_fast_div(c->nx);
+  a.div_y = make_fast_div(c->ny);
 }
 
 int parity_of(long long step) { return int(step & 1); }
@@ -437,6 +460,8 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaDeviceSetLimit(MaxL2FetchGranularity)"));
   }
   fill_args(c);
+  if (!fast_div_exact(c->a.div_x, nx, c->N) || !fast_div_exact(c->a.div_y, ny, (long long)ny * nz))
+    return bail(fail(c, LBM_ERR_INVALID_ARG, "internal: node-index division check failed"));
   Args& a = c->a;
   const long long N = c->N, P = c->pitch;
   const long long rows = (long long)ny * nz;
