@@ -42,6 +42,12 @@ struct lbm_ctx {
   double* mon_host = nullptr;      // pinned [NMON + 8]
   void* f_alt[2] = {nullptr, nullptr};   // second population buffers: targets of re-slotting
   void* h_alt[2] = {nullptr, nullptr};
+  // CUDA graphs of one even + odd step pair, keyed by which of the two steps end with a
+  // geometry update; rebuilt whenever the kernel arguments change (re-slotting)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pair_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long pair_launches[4] = {0, 0, 0, 0};
+  bool graphs_ok = true;
 };
 
 namespace {
@@ -216,6 +222,9 @@ void fill_args(lbm_ctx* c) {
 int parity_of(long long step) { return int(step & 1); }
 
 constexpr long long kListRebuild = 1024;   // steps between sorted rebuilds of the fluid list
+#ifndef LBM_STEP_GRAPHS
+#define LBM_STEP_GRAPHS 1
+#endif
 
 void set_planes(lbm_ctx* c) {
   for (int s = 0; s < c->p.n_comp; ++s)
@@ -241,7 +250,15 @@ lbm_status move_pops(lbm_ctx* c, void* const* src_f, void* const* dst_f, void* c
 
 // Ordered rebuild of the fluid and interface lists and of the slot map (fluid nodes first, in
 // list order).  With carry, the populations follow their nodes into the new slots.
+void drop_graphs(lbm_ctx* c) {
+  for (auto& g : c->pair_exec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
 lbm_status relist(lbm_ctx* c, bool carry) {
+  drop_graphs(c);   // the captured launches hold the old buffer pointers
   CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
   LAUNCH(c->ks->lists(c->a, 3, c->stream));
   if (carry) {
@@ -575,42 +592,117 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
   return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+double dissolve_thr(const lbm_ctx* c) { return dissolve_threshold(c->p); }
+
+bool geo_after(const lbm_ctx* c, long long step_done) {
+  return c->p.geo_mode != LBM_GEO_NONE && (step_done % c->p.N_geo) == 0;
+}
+
+// The kernels of one time step (the psi pass, the fused step, the geometry update when due)
+// on stream st; the step counter is not advanced.
+lbm_status enqueue_step(lbm_ctx* c, long long step, cudaStream_t st, bool timed) {
+  const int par = parity_of(step);
+  if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, par, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (timed) {
+    if (c->ev_free.size() < 2) {
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+    } else {
+      e0 = c->ev_free.back(); c->ev_free.pop_back();
+      e1 = c->ev_free.back(); c->ev_free.pop_back();
+    }
+    CK(cudaEventRecord(e0, st));
+  }
+  LAUNCH(c->ks->step(c->a, par, c->p.collision, st));
+  if (timed) {
+    CK(cudaEventRecord(e1, st));
+    c->ev_used.push_back({e0, e1});
+  }
+  if (geo_after(c, step + 1)) {
+    if (c->p.geo_mode == LBM_GEO_DISSOLVE) LAUNCH(launch_detect(c->a, dissolve_thr(c), st));
+    LAUNCH(c->ks->flip(c->a, parity_of(step + 1), st));
+  }
+  return LBM_OK;
+}
+
+// Steps step+1 and step+2 complete neither a list rebuild nor a monitor evaluation.
+bool plain_pair(const lbm_ctx* c, long long step) {
+  for (long long d = step + 1; d <= step + 2; ++d) {
+    if (c->p.geo_mode != LBM_GEO_NONE && (d % kListRebuild) == 0) return false;
+    if (c->p.N_mon > 0 && (d % c->p.N_mon) == 0) return false;
+  }
+  return true;
+}
+
+// Captures an even + odd step pair into a graph (once per geometry-update pattern).
+lbm_status pair_graph(lbm_ctx* c, long long step, cudaGraphExec_t* out, long long* launches) {
+  const int key = (geo_after(c, step + 1) ? 1 : 0) | (geo_after(c, step + 2) ? 2 : 0);
+  if (!c->pair_exec[key]) {
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = enqueue_step(c, step, c->cap_stream, false);
+    if (st == LBM_OK) st = enqueue_step(c, step + 1, c->cap_stream, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != LBM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&c->pair_exec[key], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      c->pair_exec[key] = nullptr;
+      return cuda_fail(c, ei, "cudaGraphInstantiate");
+    }
+    c->pair_launches[key] = c->launches - l0;
+    c->launches = l0;
+  }
+  *out = c->pair_exec[key];
+  *launches = c->pair_launches[key];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
   if (!c->fields_set) return fail(c, LBM_ERR_STATE, "lbm_set_fields must precede lbm_step");
-  for (int64_t k = 0; k < nsteps; ++k) {
-    const int par = parity_of(c->step);
-    if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, par, c->stream));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->profile) {
-      if (c->ev_free.size() < 2) {
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-      } else {
-        e0 = c->ev_free.back(); c->ev_free.pop_back();
-        e1 = c->ev_free.back(); c->ev_free.pop_back();
+  for (int64_t k = 0; k < nsteps;) {
+    // two plain steps from an even step: one graph launch
+    if (LBM_STEP_GRAPHS && c->graphs_ok && !c->profile && (c->step & 1) == 0 && nsteps - k >= 2 &&
+        plain_pair(c, c->step)) {
+      cudaGraphExec_t g = nullptr;
+      long long nl = 0;
+      if (pair_graph(c, c->step, &g, &nl) == LBM_OK) {
+        CK(cudaGraphLaunch(g, c->stream));
+        c->launches += nl;
+        c->step += 2;
+        k += 2;
+        continue;
       }
-      CK(cudaEventRecord(e0, c->stream));
+      c->graphs_ok = false;   // capture unavailable: launch the kernels one by one from now on
     }
-    LAUNCH(c->ks->step(c->a, par, c->p.collision, c->stream));
-    if (c->profile) {
-      CK(cudaEventRecord(e1, c->stream));
-      c->ev_used.push_back({e0, e1});
-    }
+    lbm_status st = enqueue_step(c, c->step, c->stream, c->profile);
+    if (st != LBM_OK) return st;
     c->step += 1;
+    k += 1;
     // geometry updates append new fluid nodes to the list (they keep their old slots); now and
     // then restore the sorted order and the fluid-first slots
     if (c->p.geo_mode != LBM_GEO_NONE && (c->step % kListRebuild) == 0) {
-      lbm_status st = relist(c, true);
+      st = relist(c, true);
       if (st != LBM_OK) return st;
     }
-    if (c->p.geo_mode != LBM_GEO_NONE && (c->step % c->p.N_geo) == 0) {
-      if (c->p.geo_mode == LBM_GEO_DISSOLVE)
-        LAUNCH(launch_detect(c->a, dissolve_threshold(c->p), c->stream));
-      LAUNCH(c->ks->flip(c->a, parity_of(c->step), c->stream));
-    }
     if (c->p.N_mon > 0 && (c->step % c->p.N_mon) == 0) {
-      lbm_status st = run_monitor(c);
+      st = run_monitor(c);
       if (st != LBM_OK) return st;
       st = run_residual(c);
       if (st != LBM_OK) return st;
@@ -921,6 +1013,8 @@ const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_cre
 void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->allocs) cudaFree(p);
   for (auto& pr : c->ev_used) {
     cudaEventDestroy(pr.first);
