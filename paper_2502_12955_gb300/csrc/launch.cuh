@@ -58,8 +58,8 @@ Coef<T> make_coef(const Args& a, bool shifted) {
   k.psi_wall = T(a.psi_wall);
   k.rho0 = T(a.rho0);
   for (int c = 0; c < 3; ++c) k.g[c] = T(a.g[c]);
-  for (int q = 0; q < 5; ++q) k.s_grp[q] = T(a.s_grp[q]);
-  for (int q = 0; q < 10; ++q) k.inv_norm[q] = q < L::NMRT ? T(1.0 / double(mrt_norm2<L>(q))) : T(0);
+  for (int q = 0; q < 10; ++q)
+    k.mrt_g[q] = q < L::NMRT ? T((a.s_grp[Mrt<L>::group(q)] - 1.0 / a.tau[0]) / double(mrt_norm2<L>(q))) : T(0);
   k.wc0 = T(a.J0);
   k.wca = T((1.0 - a.J0) / double(L::QC - 1));
   k.ics2c = T(double(L::QC - 1) / (2.0 * (1.0 - a.J0)));
