@@ -376,12 +376,18 @@ __device__ __forceinline__ void gather_entry(const Args& a, unsigned int e, unsi
   for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s]);
 }
 
+// ------------------------------------------------------------- collision helpers
+
+// Fused multiply-add of the compute types.
+__device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
+
 // MRT correction on top of the BGK update: with n = f - f_eq + F_i / 2 split into pair sums sp
 // and differences dp (indexed by the first member of each opposite pair, sp[0] = n_0),
 // f_i -= sum_k R_k(c_i) g_k m_k, m_k = sum_i R_k(c_i) n_i, g_k = (s_k - 1/tau) / |R_k|^2.
 // Generic form, row by row.
-template <class L, class T>
-__device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, const T* g) {
+template <class L, class T, class G>
+__device__ __forceinline__ void mrt_correct_rows(T* f, const T* sp, const T* dp, const G* g) {
   T coef[L::NMRT];
 #pragma unroll
   for (int kk = 0; kk < L::NMRT; ++kk) {
@@ -396,7 +402,7 @@ __device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, cons
       const int r = Mrt<L>::row(kk, i);
       if (r != 0) mk += T(r) * (mrt_odd<L>(kk) ? dp[i] : sp[i]);
     }
-    coef[kk] = g[kk] * mk;
+    coef[kk] = T(g[kk]) * mk;
   }
   {
     T c = T(0);
@@ -425,66 +431,63 @@ __device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, cons
 
 // D3Q19: the same rows (d'Humieres et al. 2002) evaluated through the sums their polynomials
 // share: axis pairs 1, 3, 5 (x, y, z), diagonal classes xy {7, 13}, xz {9, 15}, yz {11, 17}.
-template <class T>
-__device__ __forceinline__ void mrt_correct_d3q19(T* f, const T* sp, const T* dp, const T* g) {
+template <class T, class G>
+__device__ __forceinline__ void mrt_correct_d3q19(T* f, const T* sp, const T* dp, const G* g) {
   // even moments (e, eps, 3 pi_xx, pi_ww) from pair sums
   const T A = sp[1] + sp[3] + sp[5];
   const T Dxy = sp[7] + sp[13], Dxz = sp[9] + sp[15], Dyz = sp[11] + sp[17];
   const T D = Dxy + Dxz + Dyz;
-  const T m_e = T(-30) * sp[0] + (T(-11) * A + T(8) * D);
-  const T m_eps = T(12) * sp[0] + (T(-4) * A + D);
-  const T m_pxx = T(-4) * sp[1] + T(2) * (sp[3] + sp[5]) + (Dxy + Dxz) + T(-2) * Dyz;
-  const T m_pww = T(2) * (sp[5] - sp[3]) + (Dxy - Dxz);
+  const T m_e = fmad(T(-30), sp[0], fmad(T(-11), A, T(8) * D));
+  const T m_eps = fmad(T(12), sp[0], fmad(T(-4), A, D));
+  const T m_pxx = fmad(T(-4), sp[1], fmad(T(2), sp[3] + sp[5], fmad(T(-2), Dyz, Dxy + Dxz)));
+  const T m_pww = fmad(T(2), sp[5] - sp[3], Dxy - Dxz);
   // odd moments (q, m) from pair differences
   const T P = dp[7] + dp[13], Mxy = dp[7] - dp[13];
   const T R = dp[9] + dp[15], Mxz = dp[9] - dp[15];
   const T S = dp[11] + dp[17], Myz = dp[11] - dp[17];
-  const T m_qx = T(-4) * dp[1] + (P + R), m_mx = P - R;
-  const T m_qy = T(-4) * dp[3] + (Mxy + S), m_my = S - Mxy;
-  const T m_qz = T(-4) * dp[5] + (Mxz + Myz), m_mz = Mxz - Myz;
+  const T m_qx = fmad(T(-4), dp[1], P + R), m_mx = P - R;
+  const T m_qy = fmad(T(-4), dp[3], Mxy + S), m_my = S - Mxy;
+  const T m_qz = fmad(T(-4), dp[5], Mxz + Myz), m_mz = Mxz - Myz;
   // row order of g: e, eps, q_x, q_y, q_z, 3 pi_xx, pi_ww, m_x, m_y, m_z
-  const T ce = g[0] * m_e, cs = g[1] * m_eps;
-  const T cqx = g[2] * m_qx, cqy = g[3] * m_qy, cqz = g[4] * m_qz;
-  const T cpx = g[5] * m_pxx, cpw = g[6] * m_pww;
-  const T cmx = g[7] * m_mx, cmy = g[8] * m_my, cmz = g[9] * m_mz;
+  const T ce = T(g[0]) * m_e, cs = T(g[1]) * m_eps;
+  const T cqx = T(g[2]) * m_qx, cqy = T(g[3]) * m_qy, cqz = T(g[4]) * m_qz;
+  const T cpx = T(g[5]) * m_pxx, cpw = T(g[6]) * m_pww;
+  const T cmx = T(g[7]) * m_mx, cmy = T(g[8]) * m_my, cmz = T(g[9]) * m_mz;
   // redistribution: even part E of each pair, odd part O; f_i -= E + O, f_opp -= E - O
-  f[0] -= T(-30) * ce + T(12) * cs;
-  const T a0 = T(-11) * ce + T(-4) * cs;
-  const T Ex = a0 + T(-4) * cpx;
-  const T t = a0 + T(2) * cpx;
-  const T Ey = t - T(2) * cpw, Ez = t + T(2) * cpw;
-  f[1] -= Ex - T(4) * cqx;
-  f[2] -= Ex + T(4) * cqx;
-  f[3] -= Ey - T(4) * cqy;
-  f[4] -= Ey + T(4) * cqy;
-  f[5] -= Ez - T(4) * cqz;
-  f[6] -= Ez + T(4) * cqz;
-  const T d0 = T(8) * ce + cs;
-  const T Exy = d0 + (cpx + cpw), Exz = d0 + (cpx - cpw), Eyz = d0 + T(-2) * cpx;
+  f[0] = fmad(T(30), ce, fmad(T(-12), cs, f[0]));
+  const T a0 = fmad(T(-11), ce, T(-4) * cs);
+  const T Ex = fmad(T(-4), cpx, a0);
+  const T t = fmad(T(2), cpx, a0);
+  const T Ey = fmad(T(-2), cpw, t), Ez = fmad(T(2), cpw, t);
+  f[1] = fmad(T(4), cqx, f[1] - Ex);
+  f[2] = fmad(T(-4), cqx, f[2] - Ex);
+  f[3] = fmad(T(4), cqy, f[3] - Ey);
+  f[4] = fmad(T(-4), cqy, f[4] - Ey);
+  f[5] = fmad(T(4), cqz, f[5] - Ez);
+  f[6] = fmad(T(-4), cqz, f[6] - Ez);
+  const T d0 = fmad(T(8), ce, cs);
+  const T Exy = d0 + (cpx + cpw), Exz = d0 + (cpx - cpw), Eyz = fmad(T(-2), cpx, d0);
   const T u1 = cqx + cmx, v1 = cqy - cmy;   // pairs 7 (+x+y): u1 + v1, 13 (+x-y): u1 - v1
   const T u2 = cqx - cmx, v2 = cqz + cmz;   // pairs 9 (+x+z): u2 + v2, 15 (+x-z): u2 - v2
   const T u3 = cqy + cmy, v3 = cqz - cmz;   // pairs 11 (+y+z): u3 + v3, 17 (+y-z): u3 - v3
   const T O7 = u1 + v1, O13 = u1 - v1, O9 = u2 + v2, O15 = u2 - v2, O11 = u3 + v3, O17 = u3 - v3;
-  f[7] -= Exy + O7;
-  f[8] -= Exy - O7;
-  f[13] -= Exy + O13;
-  f[14] -= Exy - O13;
-  f[9] -= Exz + O9;
-  f[10] -= Exz - O9;
-  f[15] -= Exz + O15;
-  f[16] -= Exz - O15;
-  f[11] -= Eyz + O11;
-  f[12] -= Eyz - O11;
-  f[17] -= Eyz + O17;
-  f[18] -= Eyz - O17;
+  f[7] = (f[7] - Exy) - O7;
+  f[8] = (f[8] - Exy) + O7;
+  f[13] = (f[13] - Exy) - O13;
+  f[14] = (f[14] - Exy) + O13;
+  f[9] = (f[9] - Exz) - O9;
+  f[10] = (f[10] - Exz) + O9;
+  f[15] = (f[15] - Exz) - O15;
+  f[16] = (f[16] - Exz) + O15;
+  f[11] = (f[11] - Eyz) - O11;
+  f[12] = (f[12] - Eyz) + O11;
+  f[17] = (f[17] - Eyz) - O17;
+  f[18] = (f[18] - Eyz) + O17;
 }
-template <>
-__device__ __forceinline__ void mrt_correct<D3, float>(float* f, const float* sp, const float* dp, const float* g) {
-  mrt_correct_d3q19<float>(f, sp, dp, g);
-}
-template <>
-__device__ __forceinline__ void mrt_correct<D3, double>(double* f, const double* sp, const double* dp, const double* g) {
-  mrt_correct_d3q19<double>(f, sp, dp, g);
+template <class L, class T, class G>
+__device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, const G* g) {
+  if constexpr (L::Q == 19) mrt_correct_d3q19<T, G>(f, sp, dp, g);
+  else mrt_correct_rows<L, T, G>(f, sp, dp, g);
 }
 
 // Everything after the gather for one fluid node: wet-node closure and its bookkeeping,
@@ -670,7 +673,7 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
         f[s][i] = f[s][i] + (Fi_e + Fi_o) - om * nq_i;
         f[s][o] = f[s][o] + (Fi_e - Fi_o) - om * nq_o;
       }
-      if (COLL == 1) mrt_correct<L, T>(f[s], sp, dp, k.mrt_g);
+      if (COLL == 1) mrt_correct<L>(f[s], sp, dp, k.mrt_g);
     }
   }
   // ---- scalar collision (Eq. therpop_species, therpopeq_species), u = physical velocity
