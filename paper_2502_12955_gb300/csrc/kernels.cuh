@@ -355,6 +355,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 #ifndef LBM_STEP_MIN_BLOCKS
 #define LBM_STEP_MIN_BLOCKS 3   // resident 256-thread blocks per SM, one component in FP32 math (80 registers)
 #endif
+#ifndef LBM_STEP_MIN_BLOCKS_ODD
+#define LBM_STEP_MIN_BLOCKS_ODD 4   // the odd step waits on two dependent loads: more warps pay
+#endif
 
 // Neighbour offsets of fluid node n from its coordinates (fast divisions by nx and ny).
 __device__ __forceinline__ Nbr nbr_of(const Args& a, int n) {
@@ -743,7 +746,7 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
 // velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
 // Registers hold deviations from w_i * ref throughout.
 template <class L, class S, int NC, int NS, int COLL, int parity>
-__global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? LBM_STEP_MIN_BLOCKS : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
+__global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC, NSD = NS > 0 ? NS : 1;
   T wallx = T(0);
