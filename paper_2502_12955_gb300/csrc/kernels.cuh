@@ -118,7 +118,7 @@ struct Args {
   double* d_rho;             // FP64 staging [n_comp][N]
   double* d_u;               // [3][N]
   double* d_C;               // [n_scal][N]
-  void* snap;                // compute-type residual snapshots [4][N]: u_x, u_y, u_z, C
+  void* snap;                // compute-type residual snapshots [4][pitch] by slot: u_x, u_y, u_z, C
   long long pitch;           // elements per population plane (>= N, multiple of 32)
   long long N;
   int nx, ny, nz;
@@ -850,19 +850,19 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 #pragma unroll
   for (int s = 0; s < NS; ++s) dsp[s] = T(0);
   unsigned int nfluid = 0, nonfin = 0;
-  const unsigned int count = *a.fluid_count;
+  const unsigned int count = a.fluid_count[0], base = a.fluid_count[1];
   for (unsigned int e = tid; e < count; e += nthr) {
     const int n = int(a.fluid_list[e]);
     const uint32_t m = a.mask[n];
     if (!(m & 1u)) continue;
     ++nfluid;
-    const Nbr nb = make_nbr(a, n % a.nx, (n / a.nx) % a.ny, n / a.nx / a.ny);
-    const long long sn = a.slot[n];
+    const Nbr nb = parity ? nbr_of(a, n) : Nbr{};
+    const long long sn = e < base ? (long long)e : (long long)a.slot[n];
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T f[Q];
-      gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, sn, a.slot, m, nb, parity, f);
+      gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f);
       T r = T(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -877,7 +877,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       T h[QC];
-      gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, sn, a.slot, m, nb, parity, h);
+      gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h);
       T c = T(0);
 #pragma unroll
       for (int j = 0; j < QC; ++j) c += h[j];
@@ -924,17 +924,16 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 // current when Shan-Chen forces are on.
 template <class L, class S, int NC, int NS>
 __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename Store<S>::T>& k, int n,
-                                            uint32_t m, int parity, typename Store<S>::T* rho_out,
+                                            uint32_t m, long long sn, int parity, typename Store<S>::T* rho_out,
                                             typename Store<S>::T* u_out, typename Store<S>::T* C_out) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
-  const Nbr nb = make_nbr(a, n % a.nx, (n / a.nx) % a.ny, n / a.nx / a.ny);
-  const long long sn = a.slot[n];
+  const Nbr nb = nbr_of(a, n);
   T rho[NC], jx[NC], jy[NC], jz[NC], Fx[NC], Fy[NC], Fz[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     T f[Q];
-    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, sn, a.slot, m, nb, parity, f);
+    gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f);
     T r = T(0), ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -993,7 +992,7 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T h[QC];
-    gather_scal<L, S>(reinterpret_cast<const S*>(a.h[s]), a.pitch, sn, a.slot, m, nb, parity, h);
+    gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h);
     if (s == 0) close_scalar<L, T>(h, m, k, [](int, T, T) {});
     T C = k.cref[s];
 #pragma unroll
@@ -1013,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typena
   const uint32_t m = a.mask[n];
   T rho[NC], u[3], C[NS > 0 ? NS : 1];
   if (m & 1u) {
-    node_macros<L, S, NC, NS>(a, k, int(n), m, parity, rho, u, C);
+    node_macros<L, S, NC, NS>(a, k, int(n), m, (long long)a.slot[n], parity, rho, u, C);
   } else {
     for (int s = 0; s < NC; ++s) rho[s] = T(0);
     u[0] = u[1] = u[2] = T(0);
@@ -1024,33 +1023,35 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typena
   for (int s = 0; s < NS; ++s) a.d_C[s * N + n] = double(C[s]);
 }
 
-// Residual partials over the fluid list against compute-type snapshots [4][N] (u, C), which
-// are replaced: sum (u - u_s)^2, sum u^2, sum (C - C_s)^2, sum C^2.
+// Residual partials over the fluid list against compute-type snapshots [4][pitch] (u, C) held
+// at the nodes' storage slots, which are replaced: sum (u - u_s)^2, sum u^2, sum (C - C_s)^2,
+// sum C^2.  (A re-slotting invalidates the snapshots; the runtime then skips one evaluation.)
 template <class L, class S, int NC, int NS>
 __global__ void __launch_bounds__(256) k_resid(const Args a, const Coef<typename Store<S>::T> k,
                                                const int parity) {
   using T = typename Store<S>::T;
   T* snap = reinterpret_cast<T*>(a.snap);
-  const long long N = a.N;
+  const long long P = a.pitch;
   T du = T(0), uu = T(0), dc = T(0), cc = T(0);
-  const unsigned int count = *a.fluid_count;
+  const unsigned int count = a.fluid_count[0], base = a.fluid_count[1];
   for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
     const int n = int(a.fluid_list[e]);
     const uint32_t m = a.mask[n];
     if (!(m & 1u)) continue;
+    const long long sn = e < base ? (long long)e : (long long)a.slot[n];
     T rho[NC], u[3], C[NS > 0 ? NS : 1];
-    node_macros<L, S, NC, NS>(a, k, n, m, parity, rho, u, C);
+    node_macros<L, S, NC, NS>(a, k, n, m, sn, parity, rho, u, C);
     for (int c = 0; c < 3; ++c) {
-      const T d = u[c] - snap[c * N + n];
+      const T d = u[c] - snap[c * P + sn];
       du += d * d;
       uu += u[c] * u[c];
-      snap[c * N + n] = u[c];
+      snap[c * P + sn] = u[c];
     }
     if (NS > 0) {
-      const T d = C[0] - snap[3 * N + n];
+      const T d = C[0] - snap[3 * P + sn];
       dc += d * d;
       cc += C[0] * C[0];
-      snap[3 * N + n] = C[0];
+      snap[3 * P + sn] = C[0];
     }
   }
   double v[4] = {double(du), double(uu), double(dc), double(cc)};

@@ -259,6 +259,9 @@ void drop_graphs(lbm_ctx* c) {
 
 lbm_status relist(lbm_ctx* c, bool carry) {
   drop_graphs(c);   // the captured launches hold the old buffer pointers
+  // residual snapshots sit at the old slots: the next evaluation starts a new pair
+  c->have_snap = false;
+  c->res_evals = 0;
   CK(cudaMemsetAsync(c->a.listed, 0, (c->N + 3) / 4 * 4, c->stream));
   LAUNCH(c->ks->lists(c->a, 3, c->stream));
   if (carry) {
@@ -328,30 +331,42 @@ lbm_status check_err(lbm_ctx* c) {
 
 namespace lbm {
 
-// Fixed-order sum of the per-block partials (deterministic).
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restrict__ partials,
-                                                          long long nblocks, int K,
-                                                          double* __restrict__ out, int* err,
-                                                          int nonfin_slot) {
-  __shared__ double sh[1024];
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0;
-    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[b * K + k];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = sh[0];
-    __syncthreads();
+// Fixed-order sum of the per-block partials (deterministic): each thread adds a fixed set of
+// blocks for all K values at once (K <= 32), then warp shuffles and one pass over the warps.
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
+                                                         long long nblocks, int K,
+                                                         double* __restrict__ out, int* err,
+                                                         int nonfin_slot) {
+  __shared__ double sh[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double acc[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+  for (long long b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < K) acc[k] += partials[b * K + k];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k >= K) break;
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][k] = v;
   }
-  if (threadIdx.x == 0 && nonfin_slot >= 0 && out[nonfin_slot] > 0.0) atomicOr(err, ERR_NONFINITE);
+  __syncthreads();
+  if (wid == 0 && lane < K) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][lane];
+    out[lane] = v;
+    if (nonfin_slot == lane && v > 0.0) atomicOr(err, ERR_NONFINITE);
+  }
 }
 
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
                           int nonfin_slot, cudaStream_t st) {
-  k_reduce_partials<<<1, 1024, 0, st>>>(partials, nblocks, K, out, err, nonfin_slot);
+  if (K > 32) return cudaErrorInvalidValue;
+  k_reduce_partials<<<1, 256, 0, st>>>(partials, nblocks, K, out, err, nonfin_slot);
   return cudaGetLastError();
 }
 
@@ -523,7 +538,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   DA(a.d_rho, 2 * N * 8);
   DA(a.d_u, 3 * N * 8);
   DA(a.d_C, std::max<long long>(1, params->n_scal) * N * 8);
-  DA(a.snap, 4 * N * c->ks->psi_bytes);
+  DA(a.snap, 4 * P * c->ks->psi_bytes);
 #undef DA
   e = cudaMallocHost(reinterpret_cast<void**>(&c->mon_host), (NMON + 8) * sizeof(double));
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
@@ -583,7 +598,7 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
   CK(cudaMemsetAsync(c->a.inflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.outflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
-  CK(cudaMemsetAsync(c->a.snap, 0, 4 * c->N * c->ks->psi_bytes, c->stream));
+  CK(cudaMemsetAsync(c->a.snap, 0, 4 * c->pitch * c->ks->psi_bytes, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->step = 0;
   c->fields_set = true;
