@@ -100,7 +100,8 @@ struct Args {
   // slot e) and the solid nodes to F .. N-1; nodes that become fluid later keep their slot.
   uint32_t* slot;
   uint32_t* slot_new;         // rebuild scratch
-  unsigned int* block_counts; // ordered-compaction scratch [N / 1024 + 1]
+  unsigned int* block_counts; // ordered-compaction scratch [chunks + 1]
+  unsigned int* block_counts_v;   // the same for the in-domain positions of the fluid-list order
   double* wallx_slot;        // [WALLX_SLOTS] wall-exchange accumulators
   uint32_t* iface_list;       // reactive solids with a fluid scalar-lattice neighbour
   unsigned int* iface_count;
@@ -1213,41 +1214,89 @@ __global__ void __launch_bounds__(256) k_masks(const Args a) {
 
 // ================================================================ node lists
 
-// Ordered stream compaction of the nodes that satisfy a predicate, in chunks of 1024 nodes:
-// count, scan, write.  PRED 0: fluid nodes (the step kernel's work list).  PRED 1: reactive
-// solids touching the fluid through a scalar link (the dissolution interface list; also marks
-// listed[]).
+// Ordered stream compaction of the nodes that satisfy a predicate, in chunks of 1024 positions:
+// count, scan, write.  PRED 0: fluid nodes (the step kernel's work list), in brick order (below);
+// also assigns the storage slots.  PRED 1: reactive solids touching the fluid through a scalar
+// link (the dissolution interface list, node order; also marks listed[]).
+//
+// Brick order: the domain is cut into bricks of BX x BY x BZ nodes, visited x-fastest, with the
+// nodes x-fastest inside a brick.  A warp's 32 consecutive list entries then lie in a compact
+// block, so the neighbour cells an odd step reads and writes fall in a few nearby slot ranges
+// instead of nine distant rows.
+#ifndef LBM_BRICK_X
+#define LBM_BRICK_X 32
+#endif
+#ifndef LBM_BRICK_Y
+#define LBM_BRICK_Y 8
+#endif
+#ifndef LBM_BRICK_Z
+#define LBM_BRICK_Z 4
+#endif
+template <class L>
+struct Brick {
+  static constexpr int X = LBM_BRICK_X, Y = LBM_BRICK_Y, Z = L::D == 3 ? LBM_BRICK_Z : 1;
+  static constexpr long long V = (long long)X * Y * Z;
+};
+
+// node at position t of the brick order, or -1 for a position outside the domain
+template <class L>
+__device__ __forceinline__ long long brick_node(const Args& a, long long t) {
+  using B = Brick<L>;
+  const long long b = t / B::V;
+  const int l = int(t - b * B::V);
+  const long long nbx = (a.nx + B::X - 1) / B::X, nby = (a.ny + B::Y - 1) / B::Y;
+  const long long x = (b % nbx) * B::X + l % B::X;
+  const long long y = ((b / nbx) % nby) * B::Y + (l / B::X) % B::Y;
+  const long long z = (b / (nbx * nby)) * B::Z + l / (B::X * B::Y);
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return -1;
+  return x + a.nx * (y + a.ny * z);
+}
+
 template <class L>
 __device__ __forceinline__ bool has_fluid_scalar_neighbour(const Args& a, int x, int y, int z);
 
+// node of position t in the order of list PRED (-1: no node), and whether it enters the list
 template <class L, int PRED>
-__device__ __forceinline__ bool list_pred(const Args& a, long long n) {
-  if (n >= a.N) return false;
+__device__ __forceinline__ bool list_pred(const Args& a, long long t, long long* node) {
+  const long long n = PRED == 0 ? brick_node<L>(a, t) : (t < a.N ? t : -1);
+  *node = n;
+  if (n < 0) return false;
   if (PRED == 0) return a.flags[n] == FL_FLUID;
   if (a.flags[n] != FL_REACTIVE) return false;
   return has_fluid_scalar_neighbour<L>(a, int(n % a.nx), int((n / a.nx) % a.ny),
                                        int(n / ((long long)a.nx * a.ny)));
 }
 
+__device__ __forceinline__ unsigned int block_count(unsigned int b, unsigned int* wsum) {
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  unsigned int v = 0;
+  if (threadIdx.x < 32) {
+    v = wsum[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;
+}
+
 template <class L, int PRED>
 __global__ void __launch_bounds__(1024) k_list_count(const Args a) {
   __shared__ unsigned int wsum[32];
-  const long long n = blockIdx.x * 1024ll + threadIdx.x;
-  const bool f = list_pred<L, PRED>(a, n);
-  const unsigned int b = __ballot_sync(0xffffffffu, f);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned int v = wsum[threadIdx.x];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) a.block_counts[blockIdx.x] = v;
+  const long long t = blockIdx.x * 1024ll + threadIdx.x;
+  long long n;
+  const bool f = list_pred<L, PRED>(a, t, &n);
+  const unsigned int cf = block_count(__ballot_sync(0xffffffffu, f), wsum);
+  if (threadIdx.x == 0) a.block_counts[blockIdx.x] = cf;
+  if (PRED == 0) {
+    const unsigned int cv = block_count(__ballot_sync(0xffffffffu, n >= 0), wsum);
+    if (threadIdx.x == 0) a.block_counts_v[blockIdx.x] = cv;
   }
 }
 
 // exclusive scan of the chunk counts by one block; the total goes to count[0] and count[1]
 template <int DUMMY = 0>
-__global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int nchunks,
+__global__ void __launch_bounds__(1024) k_list_scan(unsigned int* counts, unsigned int nchunks,
                                                     unsigned int* count) {
   __shared__ unsigned int part[1024];
   __shared__ unsigned int carry;
@@ -1255,7 +1304,7 @@ __global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int n
   __syncthreads();
   for (unsigned int base = 0; base < nchunks; base += 1024) {
     const unsigned int i = base + threadIdx.x;
-    const unsigned int v = i < nchunks ? a.block_counts[i] : 0u;
+    const unsigned int v = i < nchunks ? counts[i] : 0u;
     part[threadIdx.x] = v;
     __syncthreads();
     for (unsigned int o = 1; o < 1024; o <<= 1) {
@@ -1264,7 +1313,7 @@ __global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int n
       part[threadIdx.x] += t;
       __syncthreads();
     }
-    if (i < nchunks) a.block_counts[i] = carry + part[threadIdx.x] - v;
+    if (i < nchunks) counts[i] = carry + part[threadIdx.x] - v;
     __syncthreads();
     if (threadIdx.x == 1023) carry += part[1023];
     __syncthreads();
@@ -1275,14 +1324,8 @@ __global__ void __launch_bounds__(1024) k_list_scan(const Args a, unsigned int n
   }
 }
 
-// PRED 0 also assigns the new storage slots: fluid nodes take their list position, solid
-// nodes follow from the fluid total on in node order (slot_new).
-template <class L, int PRED>
-__global__ void __launch_bounds__(1024) k_list_write(const Args a, uint32_t* list) {
-  __shared__ unsigned int wsum[32];
-  const long long n = blockIdx.x * 1024ll + threadIdx.x;
-  const bool f = list_pred<L, PRED>(a, n);
-  const unsigned int b = __ballot_sync(0xffffffffu, f);
+// exclusive prefix of ballot b over the block (chunk offset off added)
+__device__ __forceinline__ unsigned int block_prefix(unsigned int b, unsigned int off, unsigned int* wsum) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) wsum[wid] = __popc(b);
   __syncthreads();
@@ -1296,9 +1339,24 @@ __global__ void __launch_bounds__(1024) k_list_write(const Args a, uint32_t* lis
     wsum[threadIdx.x] = incl - v;
   }
   __syncthreads();
-  const unsigned int pos = a.block_counts[blockIdx.x] + wsum[wid] + __popc(b & ((1u << lane) - 1u));
-  if (PRED == 0 && n < a.N)
-    a.slot_new[n] = f ? pos : a.fluid_count[0] + (uint32_t)(n - (long long)pos);
+  const unsigned int pos = off + wsum[wid] + __popc(b & ((1u << lane) - 1u));
+  __syncthreads();
+  return pos;
+}
+
+// PRED 0 also assigns the new storage slots: fluid nodes take their list position, solid nodes
+// follow the fluid total in brick order (slot_new).
+template <class L, int PRED>
+__global__ void __launch_bounds__(1024) k_list_write(const Args a, uint32_t* list) {
+  __shared__ unsigned int wsum[32];
+  const long long t = blockIdx.x * 1024ll + threadIdx.x;
+  long long n;
+  const bool f = list_pred<L, PRED>(a, t, &n);
+  const unsigned int pos = block_prefix(__ballot_sync(0xffffffffu, f), a.block_counts[blockIdx.x], wsum);
+  if (PRED == 0) {
+    const unsigned int vpos = block_prefix(__ballot_sync(0xffffffffu, n >= 0), a.block_counts_v[blockIdx.x], wsum);
+    if (n >= 0) a.slot_new[n] = f ? pos : a.fluid_count[0] + (vpos - pos);
+  }
   if (f) {
     list[pos] = (uint32_t)n;
     if (PRED == 1) a.listed[n] = 1;

@@ -29,6 +29,13 @@ inline dim3 node_grid(const Args& a, dim3 blk) {
 
 inline dim3 step_block(const Args& a) { return dim3(a.bx, a.by, 1); }
 
+// positions of the brick order (whole bricks, so at least N)
+template <class L>
+long long brick_positions(const Args& a) {
+  using B = Brick<L>;
+  return ((a.nx + B::X - 1) / B::X) * (long long)((a.ny + B::Y - 1) / B::Y) * ((a.nz + B::Z - 1) / B::Z) * B::V;
+}
+
 // blocks of 256 threads for one resident wave (4 per SM) of the reduction kernels
 inline unsigned int wave_blocks() {
   static unsigned int cached = 0;
@@ -200,13 +207,15 @@ struct Launchers {
   static cudaError_t lists(const Args& a, int which, cudaStream_t st) {
     const unsigned int chunks = (unsigned int)((a.N + 1023) / 1024);
     if (which & 1) {
-      k_list_count<L, 0><<<chunks, 1024, 0, st>>>(a);
-      k_list_scan<<<1, 1024, 0, st>>>(a, chunks, a.fluid_count);
-      k_list_write<L, 0><<<chunks, 1024, 0, st>>>(a, a.fluid_list);
+      const unsigned int bchunks = (unsigned int)((brick_positions<L>(a) + 1023) / 1024);
+      k_list_count<L, 0><<<bchunks, 1024, 0, st>>>(a);
+      k_list_scan<<<1, 1024, 0, st>>>(a.block_counts, bchunks, a.fluid_count);
+      k_list_scan<<<1, 1024, 0, st>>>(a.block_counts_v, bchunks, a.fluid_count + 2);
+      k_list_write<L, 0><<<bchunks, 1024, 0, st>>>(a, a.fluid_list);
     }
     if (which & 2) {
       k_list_count<L, 1><<<chunks, 1024, 0, st>>>(a);
-      k_list_scan<<<1, 1024, 0, st>>>(a, chunks, a.iface_count);
+      k_list_scan<<<1, 1024, 0, st>>>(a.block_counts, chunks, a.iface_count);
       k_list_write<L, 1><<<chunks, 1024, 0, st>>>(a, a.iface_list);
     }
     return cudaGetLastError();

@@ -520,7 +520,15 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   a.flip_cap = cap;
   DA(a.fluid_list, N * 4);
   DA(a.fluid_count, 16);
-  DA(a.block_counts, ((N + 1023) / 1024 + 1) * 4);
+  {
+    // positions of the brick order: the domain padded to whole bricks
+    const long long bz = lattice == LBM_D3Q19_D3Q7 ? LBM_BRICK_Z : 1;
+    const long long pos = std::max<long long>(
+        N, ((nx + LBM_BRICK_X - 1) / LBM_BRICK_X) * (long long)LBM_BRICK_X * ((ny + LBM_BRICK_Y - 1) / LBM_BRICK_Y) *
+               LBM_BRICK_Y * ((nz + bz - 1) / bz) * bz);
+    DA(a.block_counts, ((pos + 1023) / 1024 + 1) * 4);
+    DA(a.block_counts_v, ((pos + 1023) / 1024 + 1) * 4);
+  }
   DA(a.wallx_slot, WALLX_SLOTS * 8);
   DA(a.iface_list, N * 4);
   DA(a.iface_count, 16);
