@@ -209,6 +209,56 @@ lbm_status lbm_launch_count(lbm_ctx* ctx, int64_t* launches);
 const char* lbm_last_error(const lbm_ctx* ctx);
 void lbm_destroy(lbm_ctx* ctx);
 
+/* ---------------------------------------------------------------- ensembles
+ *
+ * Many independent domains of one lattice, possibly of different sizes, advanced together: one
+ * persistent kernel walks a work list of tiles (blocks of consecutive fluid-list entries of one
+ * member) across all active members, and even + odd step pairs replay as one CUDA graph.  This
+ * is the batched form of the same per-step update (Sec. 2.1 Eq. 1.16 / 1.21 with Sec. 2.1.5),
+ * for sweeps of geometries run to steady state.
+ *
+ * Members share precision, n_comp, n_scal, collision, block_x, device and stream; each has its
+ * own size, geometry, relaxation times, forces and scalar parameters.  Ensembles keep their
+ * geometry (geo_mode LBM_GEO_NONE) and use Guo forcing without Shan-Chen forces; other
+ * parameters are rejected with LBM_ERR_INVALID_ARG.
+ */
+typedef struct lbm_ensemble lbm_ensemble;
+
+/* n members; member k has size dims[3k], dims[3k+1], dims[3k+2] and parameters params[k].
+   Allocates every member's device memory; on failure nothing is left allocated and
+   lbm_ensemble_last_error(NULL) says which member failed. */
+lbm_status lbm_ensemble_create(lbm_lattice lattice, int32_t n, const int32_t* dims,
+                               const lbm_params* params, lbm_ensemble** out);
+
+/* Context of member k, owned by the ensemble (do not lbm_destroy it): set its geometry and
+   fields, read fields, monitors and the residual through the single-domain calls.  Stepping a
+   member with lbm_step is allowed but leaves it out of step with the others. */
+lbm_status lbm_ensemble_member(lbm_ensemble* e, int32_t k, lbm_ctx** out);
+
+/* Advance every active member by nsteps.  Active members must share one step count
+   (LBM_ERR_STATE otherwise) and have their fields set.  Each member's monitors and residual
+   are evaluated every N_mon of its steps, as lbm_step does. */
+lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps);
+
+/* Step until every active member's residual (evaluated every N_mon steps; one common
+   N_mon > 0 is required) is <= r_tol, or max_steps have been taken.  A member that reaches the
+   tolerance stops stepping (leaves the work list).  Returns the steps taken and how many
+   members have stopped. */
+lbm_status lbm_ensemble_run_to_steady(lbm_ensemble* e, double r_tol, int64_t max_steps,
+                                      int64_t* steps_done, int32_t* n_converged);
+
+/* Time `steps` (even, >= 2) real steps of the ensemble with each tile size of 64, 128 and 256
+   entries and keep the fastest; the steps advance the simulation.  threads_out may be NULL. */
+lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int32_t steps, int32_t* threads_out);
+
+/* Kernel launches of the ensemble and its members since creation. */
+lbm_status lbm_ensemble_launch_count(lbm_ensemble* e, int64_t* launches);
+
+/* Message of the last failed ensemble call; with e == NULL, of the last failed
+   lbm_ensemble_create on the calling thread. */
+const char* lbm_ensemble_last_error(const lbm_ensemble* e);
+void lbm_ensemble_destroy(lbm_ensemble* e);
+
 #ifdef __cplusplus
 }
 #endif

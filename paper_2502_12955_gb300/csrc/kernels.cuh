@@ -783,6 +783,62 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   }
 }
 
+// ================================================================ ensembles
+
+// Work tile of an ensemble step: blockDim consecutive fluid-list entries of one member.
+struct Tile {
+  unsigned int member, first;
+};
+
+// One time step of every member of an ensemble in one launch.  Blocks walk a work list of
+// tiles; for each tile they stage the member's arguments and constants in shared memory and
+// update entries first .. first + blockDim - 1 exactly as k_step updates them.
+template <class L, class S, int NC, int NS, int COLL, int parity>
+__global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step_tiles(
+    const Args* __restrict__ args, const Coef<typename Store<S>::T>* __restrict__ coefs,
+    const Tile* __restrict__ tiles, unsigned int ntiles) {
+  using T = typename Store<S>::T;
+  constexpr int Q = L::Q, QC = L::QC, NSD = NS > 0 ? NS : 1;
+  static_assert(sizeof(Args) % 4 == 0 && sizeof(Coef<T>) % 4 == 0, "word copies");
+  __shared__ Args sa;
+  __shared__ Coef<T> sk;
+  for (unsigned int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tile = tiles[t];
+    __syncthreads();   // the previous tile is done with sa / sk
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(args + tile.member);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+      for (unsigned int i = threadIdx.x; i < sizeof(Args) / 4; i += blockDim.x) dst[i] = src[i];
+      const uint32_t* ksrc = reinterpret_cast<const uint32_t*>(coefs + tile.member);
+      uint32_t* kdst = reinterpret_cast<uint32_t*>(&sk);
+      for (unsigned int i = threadIdx.x; i < sizeof(Coef<T>) / 4; i += blockDim.x) kdst[i] = ksrc[i];
+    }
+    __syncthreads();
+    const Args& a = sa;
+    T wallx = T(0);
+    const unsigned int e = tile.first + threadIdx.x;
+    if (e < a.fluid_count[0]) {
+      const int n = int(a.fluid_list[e]);
+      const uint32_t m = a.mask[n];
+      if (m & 1u) {
+        const unsigned int base = a.fluid_count[1];
+        T f[NC][Q], h[NSD][QC];
+        gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
+        const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+        collide_scatter<L, S, NC, NS, COLL, parity>(a, sk, n, m, sn, f, h, wallx);
+      }
+    }
+    if (NS > 0) {
+      const unsigned int any = __ballot_sync(0xffffffffu, wallx != T(0));
+      if (any) {
+        const T w = warp_sum(wallx);
+        if ((threadIdx.x & 31) == 0)
+          atomicAdd(a.wallx_slot + ((t * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS), widen(w));
+      }
+    }
+  }
+}
+
 // ================================================================ psi
 
 template <class L, class S, int NC>

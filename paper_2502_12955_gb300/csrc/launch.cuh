@@ -20,7 +20,13 @@ struct KernelSet {
   cudaError_t (*masks)(const Args&, cudaStream_t);
   cudaError_t (*lists)(const Args&, int which, cudaStream_t);   // which: 1 fluid, 2 interface, 3 both
   cudaError_t (*resid)(const Args&, int parity, cudaStream_t, long long* nblocks);
+  // ensembles: compute-type constants of n members into host memory (coef_bytes each), and one
+  // step of every tile
+  void (*coefs)(const Args* a, int n, void* out);
+  cudaError_t (*step_tiles)(const Args* d_args, const void* d_coefs, const Tile* d_tiles, unsigned int ntiles,
+                            int n_comp, int n_scal, int coll, int parity, int threads, cudaStream_t);
   int psi_bytes;   // bytes per psi element (compute type)
+  int coef_bytes;
 };
 
 inline dim3 node_grid(const Args& a, dim3 blk) {
@@ -221,8 +227,49 @@ struct Launchers {
     return cudaGetLastError();
   }
 
+  static void coefs(const Args* a, int n, void* out) {
+    Coef<T>* o = static_cast<Coef<T>*>(out);
+    for (int i = 0; i < n; ++i) o[i] = coef(a[i]);
+  }
+  template <int NC, int NS, int COLL, int PAR>
+  static cudaError_t step_tiles_p(const Args* d_args, const void* d_coefs, const Tile* d_tiles, unsigned int ntiles,
+                                  int threads, cudaStream_t st) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tiles<L, S, NC, NS, COLL, PAR>, threads, 0);
+    const unsigned int wave = (unsigned int)((occ > 0 ? occ : 1) * (sms > 0 ? sms : 1));
+    const unsigned int blocks = ntiles < wave ? (ntiles > 0 ? ntiles : 1) : wave;
+    k_step_tiles<L, S, NC, NS, COLL, PAR><<<blocks, threads, 0, st>>>(
+        d_args, static_cast<const Coef<T>*>(d_coefs), d_tiles, ntiles);
+    return cudaGetLastError();
+  }
+  template <int NC, int NS>
+  static cudaError_t step_tiles_c(const Args* d, const void* k, const Tile* t, unsigned int nt, int coll, int parity,
+                                  int threads, cudaStream_t st) {
+    if (coll == 1) {
+      if (NC != 1) return cudaErrorInvalidValue;
+      return parity ? step_tiles_p<1, NS, 1, 1>(d, k, t, nt, threads, st) : step_tiles_p<1, NS, 1, 0>(d, k, t, nt, threads, st);
+    }
+    return parity ? step_tiles_p<NC, NS, 0, 1>(d, k, t, nt, threads, st) : step_tiles_p<NC, NS, 0, 0>(d, k, t, nt, threads, st);
+  }
+  static cudaError_t step_tiles(const Args* d, const void* k, const Tile* t, unsigned int nt, int n_comp, int n_scal,
+                                int coll, int parity, int threads, cudaStream_t st) {
+    if (n_comp == 1) {
+      if (n_scal == 0) return step_tiles_c<1, 0>(d, k, t, nt, coll, parity, threads, st);
+      if (n_scal == 1) return step_tiles_c<1, 1>(d, k, t, nt, coll, parity, threads, st);
+      return step_tiles_c<1, 2>(d, k, t, nt, coll, parity, threads, st);
+    }
+    if (n_scal == 0) return step_tiles_c<2, 0>(d, k, t, nt, coll, parity, threads, st);
+    if (n_scal == 1) return step_tiles_c<2, 1>(d, k, t, nt, coll, parity, threads, st);
+    return step_tiles_c<2, 2>(d, k, t, nt, coll, parity, threads, st);
+  }
+
   static KernelSet make() {
     KernelSet k;
+    k.coefs = &coefs;
+    k.step_tiles = &step_tiles;
+    k.coef_bytes = (int)sizeof(Coef<T>);
     k.step = &step;
     k.psi = &psi;
     k.moments = &moments;

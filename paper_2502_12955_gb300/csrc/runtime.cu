@@ -45,6 +45,7 @@ struct lbm_ctx {
   // CUDA graphs of one even + odd step pair, keyed by which of the two steps end with a
   // geometry update; rebuilt whenever the kernel arguments change (re-slotting)
   cudaStream_t cap_stream = nullptr;
+  long long gen = 0;               // bumped whenever the arguments or the fluid list change
   cudaGraphExec_t pair_exec[4] = {nullptr, nullptr, nullptr, nullptr};
   long long pair_launches[4] = {0, 0, 0, 0};
   bool graphs_ok = true;
@@ -259,6 +260,7 @@ void drop_graphs(lbm_ctx* c) {
 
 lbm_status relist(lbm_ctx* c, bool carry) {
   drop_graphs(c);   // the captured launches hold the old buffer pointers
+  c->gen += 1;
   // residual snapshots sit at the old slots: the next evaluation starts a new pair
   c->have_snap = false;
   c->res_evals = 0;
@@ -1046,6 +1048,365 @@ void lbm_destroy(lbm_ctx* c) {
   for (auto e : c->ev_free) cudaEventDestroy(e);
   if (c->mon_host) cudaFreeHost(c->mon_host);
   delete c;
+}
+
+}  // extern "C"
+
+// ====================================================================== ensembles
+
+struct lbm_ensemble {
+  int lattice = 0;
+  std::vector<lbm_ctx*> m;
+  std::vector<char> active;
+  std::vector<long long> built_gen;   // member generations the device work list was built from
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  const KernelSet* ks = nullptr;
+  int threads = 256;
+  Args* d_args = nullptr;
+  void* d_coefs = nullptr;
+  Tile* d_tiles = nullptr;
+  size_t tile_cap = 0;
+  unsigned int ntiles = 0;
+  bool dirty = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pair = nullptr;
+  long long pair_launches = 0;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_ens_create_err;
+
+lbm_status efail(lbm_ensemble* e, lbm_status st, const char* fmt, ...) {
+  if (e) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    e->err = buf;
+  }
+  return st;
+}
+
+#define ECK(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) return efail(e, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void ens_drop_graph(lbm_ensemble* e) {
+  if (e->pair) cudaGraphExecDestroy(e->pair);
+  e->pair = nullptr;
+}
+
+// (Re)build the device work list: one tile of `threads` entries at a time over every active
+// member's fluid list, plus the members' arguments and constants.
+lbm_status ens_prepare(lbm_ensemble* e) {
+  bool stale = e->dirty;
+  for (size_t k = 0; k < e->m.size(); ++k) stale |= e->built_gen[k] != e->m[k]->gen;
+  if (!stale) return LBM_OK;
+  ens_drop_graph(e);
+  const int n = (int)e->m.size();
+  std::vector<Args> args(n);
+  std::vector<unsigned int> counts(n, 0);
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx* c = e->m[k];
+    args[k] = c->a;
+    if (!e->active[k]) continue;
+    ECK(cudaMemcpyAsync(&counts[k], c->a.fluid_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+  }
+  for (int k = 0; k < n; ++k) ECK(cudaStreamSynchronize(e->m[k]->stream));
+  std::vector<Tile> tiles;
+  for (int k = 0; k < n; ++k) {
+    if (!e->active[k]) continue;
+    for (unsigned int f = 0; f < counts[k]; f += (unsigned int)e->threads) tiles.push_back(Tile{(unsigned int)k, f});
+  }
+  std::vector<char> coefs((size_t)n * e->ks->coef_bytes);
+  e->ks->coefs(args.data(), n, coefs.data());
+  if (!e->d_args) {
+    ECK(cudaMalloc(&e->d_args, n * sizeof(Args)));
+    ECK(cudaMalloc(&e->d_coefs, coefs.size()));
+  }
+  if (tiles.size() > e->tile_cap) {
+    if (e->d_tiles) cudaFree(e->d_tiles);
+    e->d_tiles = nullptr;
+    ECK(cudaMalloc(&e->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(Tile)));
+    e->tile_cap = tiles.size();
+  }
+  ECK(cudaMemcpyAsync(e->d_args, args.data(), n * sizeof(Args), cudaMemcpyHostToDevice, e->stream));
+  ECK(cudaMemcpyAsync(e->d_coefs, coefs.data(), coefs.size(), cudaMemcpyHostToDevice, e->stream));
+  if (!tiles.empty())
+    ECK(cudaMemcpyAsync(e->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, e->stream));
+  ECK(cudaStreamSynchronize(e->stream));
+  e->ntiles = (unsigned int)tiles.size();
+  for (int k = 0; k < n; ++k) e->built_gen[k] = e->m[k]->gen;
+  e->dirty = false;
+  return LBM_OK;
+}
+
+lbm_status ens_launch(lbm_ensemble* e, int parity, cudaStream_t st) {
+  if (e->ntiles == 0) return LBM_OK;
+  const lbm_params& p = e->m[0]->p;
+  const cudaError_t r = e->ks->step_tiles(e->d_args, e->d_coefs, e->d_tiles, e->ntiles, p.n_comp, p.n_scal,
+                                          p.collision, parity, e->threads, st);
+  e->launches += 1;
+  if (r != cudaSuccess) return efail(e, LBM_ERR_CUDA, "ensemble step: %s", cudaGetErrorString(r));
+  return LBM_OK;
+}
+
+// after a step: the members' counters, and their monitors when due
+lbm_status ens_after_step(lbm_ensemble* e) {
+  for (size_t k = 0; k < e->m.size(); ++k) {
+    if (!e->active[k]) continue;
+    lbm_ctx* c = e->m[k];
+    c->step += 1;
+    if (c->p.N_mon > 0 && (c->step % c->p.N_mon) == 0) {
+      lbm_status st = run_monitor(c);
+      if (st == LBM_OK) st = run_residual(c);
+      if (st != LBM_OK) return efail(e, st, "member %zu: %s", k, c->err.c_str());
+      c->have_snap = true;
+      c->res_evals += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+bool ens_plain_pair(const lbm_ensemble* e, long long step) {
+  for (size_t k = 0; k < e->m.size(); ++k) {
+    if (!e->active[k]) continue;
+    const long long Nm = e->m[k]->p.N_mon;
+    if (Nm > 0 && ((step + 1) % Nm == 0 || (step + 2) % Nm == 0)) return false;
+  }
+  return true;
+}
+
+long long ens_step_of(const lbm_ensemble* e) {
+  for (size_t k = 0; k < e->m.size(); ++k)
+    if (e->active[k]) return e->m[k]->step;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_ensemble_create(lbm_lattice lattice, int32_t n, const int32_t* dims, const lbm_params* params,
+                               lbm_ensemble** out) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  g_ens_create_err.clear();
+  if (n < 1 || !dims || !params) {
+    g_ens_create_err = "ensemble needs n >= 1, dims and params";
+    return LBM_ERR_INVALID_ARG;
+  }
+  const lbm_params& p0 = params[0];
+  for (int k = 0; k < n; ++k) {
+    const lbm_params& p = params[k];
+    const char* why = nullptr;
+    if (p.precision != p0.precision) why = "precision differs from member 0";
+    else if (p.n_comp != p0.n_comp || p.n_scal != p0.n_scal) why = "n_comp / n_scal differ from member 0";
+    else if (p.collision != p0.collision) why = "collision differs from member 0";
+    else if (p.device != p0.device || p.stream != p0.stream) why = "device / stream differ from member 0";
+    else if (p.geo_mode != LBM_GEO_NONE) why = "ensemble members keep their geometry (geo_mode none)";
+    else if (p.block_x != p0.block_x) why = "block_x differs from member 0";
+    else {
+      bool sc = false;
+      for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) sc |= (s < p.n_comp && t < p.n_comp) && p.G[s][t] != 0.0;
+      if (sc) why = "Shan-Chen forces are not available in ensembles";
+      else if (p.forcing != LBM_FORCING_GUO) why = "ensembles use Guo forcing";
+    }
+    if (why) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "member %d: %s", k, why);
+      g_ens_create_err = buf;
+      return LBM_ERR_INVALID_ARG;
+    }
+  }
+  lbm_ensemble* e = new (std::nothrow) lbm_ensemble();
+  if (!e) return LBM_ERR_OOM;
+  e->lattice = lattice;
+  e->stream = reinterpret_cast<cudaStream_t>(p0.stream);
+  e->device = p0.device;
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx* c = nullptr;
+    const lbm_status st = lbm_create(lattice, dims[3 * k], dims[3 * k + 1], dims[3 * k + 2], &params[k], &c);
+    if (st != LBM_OK) {
+      char buf[600];
+      snprintf(buf, sizeof buf, "member %d: %s", k, g_create_err.c_str());
+      g_ens_create_err = buf;
+      lbm_ensemble_destroy(e);
+      return st;
+    }
+    e->m.push_back(c);
+  }
+  e->active.assign(n, 1);
+  e->built_gen.assign(n, -1);
+  e->ks = e->m[0]->ks;
+  e->threads = e->m[0]->a.bx;
+  *out = e;
+  return LBM_OK;
+}
+
+lbm_status lbm_ensemble_member(lbm_ensemble* e, int32_t k, lbm_ctx** out) {
+  if (!e || !out || k < 0 || k >= (int32_t)e->m.size()) return LBM_ERR_INVALID_ARG;
+  *out = e->m[k];
+  return LBM_OK;
+}
+
+lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps) {
+  if (!e || nsteps < 0) return LBM_ERR_INVALID_ARG;
+  long long step = -1;
+  for (size_t k = 0; k < e->m.size(); ++k) {
+    if (!e->active[k]) continue;
+    if (!e->m[k]->fields_set) return efail(e, LBM_ERR_STATE, "member %zu: fields were never set", k);
+    if (step < 0) step = e->m[k]->step;
+    else if (e->m[k]->step != step) return efail(e, LBM_ERR_STATE, "active members must share one step count");
+  }
+  if (step < 0) return LBM_OK;   // nothing active
+  lbm_status st = ens_prepare(e);
+  if (st != LBM_OK) return st;
+  for (int64_t k = 0; k < nsteps;) {
+    const long long s = ens_step_of(e);
+    if ((s & 1) == 0 && nsteps - k >= 2 && ens_plain_pair(e, s)) {
+      if (!e->pair) {
+        if (!e->cap_stream) ECK(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+        const long long l0 = e->launches;
+        ECK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+        st = ens_launch(e, 0, e->cap_stream);
+        if (st == LBM_OK) st = ens_launch(e, 1, e->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(e->cap_stream, &g);
+        if (st != LBM_OK) {
+          if (g) cudaGraphDestroy(g);
+          return st;
+        }
+        if (ec != cudaSuccess) return efail(e, LBM_ERR_CUDA, "capture: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&e->pair, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+          e->pair = nullptr;
+          return efail(e, LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        }
+        e->pair_launches = e->launches - l0;
+        e->launches = l0;
+      }
+      ECK(cudaGraphLaunch(e->pair, e->stream));
+      e->launches += e->pair_launches;
+      for (int r = 0; r < 2; ++r) {
+        st = ens_after_step(e);
+        if (st != LBM_OK) return st;
+      }
+      k += 2;
+      continue;
+    }
+    st = ens_launch(e, int(s & 1), e->stream);
+    if (st == LBM_OK) st = ens_after_step(e);
+    if (st != LBM_OK) return st;
+    k += 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_ensemble_run_to_steady(lbm_ensemble* e, double r_tol, int64_t max_steps, int64_t* steps_done,
+                                      int32_t* n_converged) {
+  if (!e || !(r_tol > 0.0) || max_steps < 0) return LBM_ERR_INVALID_ARG;
+  const long long Nm = e->m[0]->p.N_mon;
+  for (auto* c : e->m)
+    if (c->p.N_mon != Nm || Nm <= 0)
+      return efail(e, LBM_ERR_INVALID_ARG, "run_to_steady needs one common N_mon > 0");
+  long long done = 0;
+  while (done < max_steps) {
+    bool any = false;
+    for (char a : e->active) any |= a != 0;
+    if (!any) break;
+    const long long s = ens_step_of(e);
+    const long long chunk = std::min<long long>(Nm - (s % Nm), max_steps - done);
+    lbm_status st = lbm_ensemble_step(e, chunk);
+    if (st != LBM_OK) return st;
+    done += chunk;
+    if ((ens_step_of(e) % Nm) != 0) continue;
+    // per-member exit: a member whose residual reached the tolerance stops stepping
+    for (size_t k = 0; k < e->m.size(); ++k) {
+      if (!e->active[k]) continue;
+      lbm_monitors mon;
+      st = lbm_get_monitors(e->m[k], &mon);
+      if (st != LBM_OK) return efail(e, st, "member %zu: %s", k, e->m[k]->err.c_str());
+      if (mon.residual >= 0.0 && mon.residual <= r_tol) {
+        e->active[k] = 0;
+        e->dirty = true;
+      }
+    }
+  }
+  int32_t conv = 0;
+  for (char a : e->active) conv += a ? 0 : 1;
+  if (steps_done) *steps_done = done;
+  if (n_converged) *n_converged = conv;
+  return LBM_OK;
+}
+
+lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int32_t steps, int32_t* threads_out) {
+  if (!e || steps < 2) return LBM_ERR_INVALID_ARG;
+  const int cand[3] = {64, 128, 256};
+  float best = -1.f;
+  int best_t = e->threads;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  ECK(cudaEventCreate(&t0));
+  ECK(cudaEventCreate(&t1));
+  lbm_status st = LBM_OK;
+  for (int c : cand) {
+    e->threads = c;
+    e->dirty = true;
+    st = ens_prepare(e);
+    if (st == LBM_OK) st = lbm_ensemble_step(e, 2);   // warm-up, graph capture
+    if (st != LBM_OK) break;
+    cudaEventRecord(t0, e->stream);
+    st = lbm_ensemble_step(e, steps & ~1);
+    if (st != LBM_OK) break;
+    cudaEventRecord(t1, e->stream);
+    cudaEventSynchronize(t1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (best < 0.f || ms < best) {
+      best = ms;
+      best_t = c;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (st != LBM_OK) return st;
+  e->threads = best_t;
+  e->dirty = true;
+  if (threads_out) *threads_out = best_t;
+  return LBM_OK;
+}
+
+lbm_status lbm_ensemble_launch_count(lbm_ensemble* e, int64_t* launches) {
+  if (!e || !launches) return LBM_ERR_INVALID_ARG;
+  long long total = e->launches;
+  for (auto* c : e->m) total += c->launches;
+  *launches = total;
+  return LBM_OK;
+}
+
+const char* lbm_ensemble_last_error(const lbm_ensemble* e) {
+  return e ? e->err.c_str() : g_ens_create_err.c_str();
+}
+
+void lbm_ensemble_destroy(lbm_ensemble* e) {
+  if (!e) return;
+  if (e->stream || !e->m.empty()) cudaStreamSynchronize(e->stream);
+  ens_drop_graph(e);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  for (auto* c : e->m) lbm_destroy(c);
+  if (e->d_args) cudaFree(e->d_args);
+  if (e->d_coefs) cudaFree(e->d_coefs);
+  if (e->d_tiles) cudaFree(e->d_tiles);
+  delete e;
 }
 
 }  // extern "C"

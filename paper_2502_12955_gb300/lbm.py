@@ -32,7 +32,9 @@ EXPORTS = ["lbm_params_default", "lbm_create", "lbm_set_geometry", "lbm_set_fiel
            "lbm_sync", "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_get_monitors",
            "lbm_residual", "lbm_get_state", "lbm_set_state", "lbm_profile_enable",
            "lbm_profile_read", "lbm_launch_count", "lbm_last_error", "lbm_destroy",
-           "lbm_get_pops_noalloc"]
+           "lbm_get_pops_noalloc", "lbm_ensemble_create", "lbm_ensemble_member", "lbm_ensemble_step",
+           "lbm_ensemble_run_to_steady", "lbm_ensemble_autotune", "lbm_ensemble_launch_count",
+           "lbm_ensemble_last_error", "lbm_ensemble_destroy"]
 
 
 class LbmParams(C.Structure):
@@ -111,10 +113,21 @@ def load(build_if_missing: bool = True):
         lib.lbm_last_error.argtypes = [vp]
         lib.lbm_last_error.restype = C.c_char_p
         lib.lbm_destroy.argtypes = [vp]
+        lib.lbm_ensemble_create.argtypes = [C.c_int, C.c_int32, P(C.c_int32), P(LbmParams), P(vp)]
+        lib.lbm_ensemble_member.argtypes = [vp, C.c_int32, P(vp)]
+        lib.lbm_ensemble_step.argtypes = [vp, C.c_int64]
+        lib.lbm_ensemble_run_to_steady.argtypes = [vp, C.c_double, C.c_int64, P(C.c_int64), P(C.c_int32)]
+        lib.lbm_ensemble_autotune.argtypes = [vp, C.c_int32, P(C.c_int32)]
+        lib.lbm_ensemble_launch_count.argtypes = [vp, P(C.c_int64)]
+        lib.lbm_ensemble_last_error.argtypes = [vp]
+        lib.lbm_ensemble_last_error.restype = C.c_char_p
+        lib.lbm_ensemble_destroy.argtypes = [vp]
         for name in EXPORTS:
             if name not in ("lbm_last_error", "lbm_destroy"):
                 getattr(lib, name).restype = C.c_int
         lib.lbm_destroy.restype = None
+        lib.lbm_ensemble_last_error.restype = C.c_char_p
+        lib.lbm_ensemble_destroy.restype = None
         _lib = lib
     return _lib
 
@@ -194,7 +207,7 @@ MON_KEYS = ["step", "mass0", "mass1", "momx", "momy", "momz", "species0", "speci
 class Solver:
     """One lattice Boltzmann domain on one GPU (owns an lbm_ctx)."""
 
-    def __init__(self, cfg: dict, stream=None):
+    def __init__(self, cfg: dict, stream=None, _handle=None):
         self.lib = load()
         self.cfg = dict(cfg)
         self.dim = int(cfg["dim"])
@@ -207,6 +220,10 @@ class Solver:
         if stream is not None:
             self.p.stream = C.c_void_p(int(stream))
         self.n_comp, self.n_scal = self.p.n_comp, self.p.n_scal
+        self._owner = _handle is None
+        if _handle is not None:   # a member context owned by an Ensemble
+            self.h = _handle
+            return
         h = C.c_void_p()
         lat = LBM_D3Q19_D3Q7 if self.dim == 3 else LBM_D2Q9_D2Q5
         st = self.lib.lbm_create(lat, nx, ny, nz, C.byref(self.p), C.byref(h))
@@ -221,7 +238,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.lbm_destroy(self.h)
+            if self._owner:
+                self.lib.lbm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -318,3 +336,73 @@ class Solver:
         n = C.c_int64()
         self._ck(self.lib.lbm_launch_count(self.h, C.byref(n)))
         return n.value
+
+
+class Ensemble:
+    """Independent domains of one lattice advanced together (owns an lbm_ensemble).
+
+    cfgs: one configuration dict per member (same keys as Solver).  members[k] is a Solver view
+    of member k for geometry, fields, monitors and read-back."""
+
+    def __init__(self, cfgs, stream=None):
+        self.lib = load()
+        cfgs = [dict(c) for c in cfgs]
+        dims = {int(c["dim"]) for c in cfgs}
+        if len(dims) != 1:
+            raise ValueError("ensemble members share one lattice")
+        dim = dims.pop()
+        n = len(cfgs)
+        params = (LbmParams * n)()
+        sizes = (C.c_int32 * (3 * n))()
+        for k, c in enumerate(cfgs):
+            params[k] = make_params(c, self.lib)
+            if stream is not None:
+                params[k].stream = C.c_void_p(int(stream))
+            sizes[3 * k:3 * k + 3] = [int(c["nx"]), int(c["ny"]), int(c.get("nz", 1))]
+        h = C.c_void_p()
+        lat = LBM_D3Q19_D3Q7 if dim == 3 else LBM_D2Q9_D2Q5
+        st = self.lib.lbm_ensemble_create(lat, n, sizes, params, C.byref(h))
+        if st != 0:
+            raise LbmError(st, self.lib.lbm_ensemble_last_error(None).decode())
+        self.h = h
+        self.members = []
+        for k, c in enumerate(cfgs):
+            mh = C.c_void_p()
+            self._ck(self.lib.lbm_ensemble_member(self.h, k, C.byref(mh)))
+            self.members.append(Solver(c, stream=stream, _handle=mh))
+
+    def _ck(self, st):
+        if st != 0:
+            raise LbmError(st, self.lib.lbm_ensemble_last_error(self.h).decode())
+
+    def step(self, n=1):
+        self._ck(self.lib.lbm_ensemble_step(self.h, int(n)))
+
+    def run_to_steady(self, r_tol, max_steps):
+        """(steps taken, number of members that reached r_tol and stopped)"""
+        s, c = C.c_int64(), C.c_int32()
+        self._ck(self.lib.lbm_ensemble_run_to_steady(self.h, float(r_tol), int(max_steps), C.byref(s), C.byref(c)))
+        return s.value, c.value
+
+    def autotune(self, steps=8):
+        t = C.c_int32()
+        self._ck(self.lib.lbm_ensemble_autotune(self.h, int(steps), C.byref(t)))
+        return t.value
+
+    def launch_count(self):
+        n = C.c_int64()
+        self._ck(self.lib.lbm_ensemble_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            self.lib.lbm_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -99,3 +99,18 @@ def test_null_context_calls_fail_cleanly():
     m = lbm.LbmMonitors()
     assert lib.lbm_get_monitors(None, C.byref(m)) == -1
     lib.lbm_destroy(None)
+
+
+@pytest.mark.parametrize("bad", [dict(precision="fp16"), dict(geo_mode="dissolve", n_scal=1),
+                                 dict(G=[[-5.0, 0], [0, 0]]), dict(forcing="sc_shift"), dict(collision="mrt")])
+def test_ensemble_create_rejects_mixed_or_unsupported_members(bad):
+    lib = lbm.load()
+    base = dict(dim=2, nx=8, ny=8, precision="fp32")
+    ps = (lbm.LbmParams * 2)()
+    ps[0] = lbm.make_params(base, lib)
+    ps[1] = lbm.make_params(dict(base, **bad), lib)
+    dims = (C.c_int32 * 6)(8, 8, 1, 8, 8, 1)
+    h = C.c_void_p()
+    assert lib.lbm_ensemble_create(lbm.LBM_D2Q9_D2Q5, 2, dims, ps, C.byref(h)) == -1 and not h.value
+    assert b"member 1" in lib.lbm_ensemble_last_error(None)
+    assert lib.lbm_ensemble_create(lbm.LBM_D2Q9_D2Q5, 0, dims, ps, C.byref(h)) == -1
