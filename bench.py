@@ -202,7 +202,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="dissolution", choices=["dissolution", "droplet", "channel"])
+    ap.add_argument("--workload", default="dissolution", choices=["dissolution", "droplet", "channel", "ensemble"])
+    ap.add_argument("--members", type=int, default=32,
+                    help="ensemble workload: members, half 2D squares and half 3D cubes (512 = the full set)")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--size", type=int, default=0)
     ap.add_argument("--block-x", type=int, default=0)
@@ -237,7 +239,12 @@ def run_reference(args):
     if rank != 0:
         return
     precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
-    cfg, geom, fields, label = workload(args.workload, args.size, precision)
+    if args.workload == "ensemble":
+        # the ensemble's members are independent 2D / 3D runs: sample the oracle on a 3D one
+        args.workload = "dissolution"
+        label = f"ensemble_{args.members}_members_{precision}"
+    else:
+        cfg, geom, fields, label = workload(args.workload, args.size, precision)
     # each timed step is one oracle step on a bounded sample of the workload (48^3 in 3D)
     res = oracle_sample(args.workload, precision, steps=args.steps, sample_n=48, warmup=args.warmup)
     value = res["value"]
@@ -251,6 +258,83 @@ def run_reference(args):
                              "sample": res["sample"]},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_ensemble(args, dist, ws, rank, local):
+    """Uneven ensemble (2D squares and 3D cubes of random porous media), every member advanced
+    by the persistent tile-list kernel; one lattice per ensemble, both in the timed region."""
+    import torch
+    from paper_2502_12955_gb300.lbm import Ensemble
+
+    precision = args.precision or "fp16"
+    n2d = args.members // 2
+    n3d = args.members - n2d
+    sets = inputs.ensemble_members(n2d, n3d, seed0=1000 * local, precision=precision)
+    stream = torch.cuda.Stream(device=local)
+    ens, nodes, fluid, bpn = [], 0, 0, 0.0
+    elem = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
+    for members in sets:
+        if not members:
+            continue
+        e = Ensemble([dict(c, device=local, N_mon=0) for c, _, _ in members], stream=stream.cuda_stream)
+        for (cfg, geom, fields), m in zip(members, e.members):
+            m.set_geometry(geom)
+            m.set_fields(*fields)
+            nf = int((geom == 0).sum())
+            nodes += geom.size
+            fluid += nf
+            q, qc = (19, 7) if cfg["dim"] == 3 else (9, 5)
+            bpn += nf * 2 * elem * (q + qc)
+        ens.append(e)
+    tiles = [e.autotune(steps=4) for e in ens]
+    for e in ens:
+        e.step(args.warmup + (args.warmup & 1))
+    torch.cuda.synchronize()
+    launches0 = sum(e.launch_count() for e in ens)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for e in ens:
+        e.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = sum(e.launch_count() for e in ens) - launches0
+    sec, nodes_all = reduce_over_ranks(dist, f"cuda:{local}", ms_total * 1e-3, nodes * args.steps)
+    ms_step = sec * 1e3 / args.steps
+    peak, peak_src = measured_peak()
+    achieved = bpn / (ms_step * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": nodes_all / sec / 1e6, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math",
+                      "bf16": "bf16 storage, f32 math"}[precision],
+            "data": "synthetic (seeded porous geometries, inputs.ensemble_members)",
+            "config": {"workload": f"ensemble_{args.members}_members_{n2d}x2d_{n3d}x3d_{precision}",
+                       "nodes": nodes, "fluid_nodes": fluid, "tile_threads": tiles,
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": f"population state {bpn / 2 / 1e9:.2f} GB > 0.13 GB L2: no flush needed"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_step_tiles (whole step time: one tile-list launch per step)",
+                         "algorithmic_bytes_per_launch": bpn},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for e in ens:
+        e.close()
+    if dist:
+        dist.destroy_process_group()
 
 
 def main():
@@ -271,6 +355,9 @@ def main():
 
     from paper_2502_12955_gb300.lbm import Solver
 
+    if args.workload == "ensemble":
+        run_ensemble(args, dist, ws, rank, local)
+        return
     precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
     cfg, geom, fields, label = workload(args.workload, args.size, precision)
     cfg = dict(cfg, device=local, block_x=args.block_x, l2_fetch_bytes=args.l2_fetch)

@@ -176,3 +176,56 @@ def dissolution_3d(n=256, seed=0, precision="fp32", shape=None, g=None, radius=(
     geom = sphere_packing_3d(n, radius[0], radius[1], 0.6, seed, REACTIVE, shape=shp)
     rho, u, C = uniform_fields(shp, 1, 1, rho=1.0, C=1.0)
     return cfg, geom, (rho, u, C)
+
+
+def circle_packing_2d(nx: int, ny: int, r_min: int = 4, r_max: int = 8, solid_fraction: float = 0.5,
+                      seed: int = 0, flag: int = REACTIVE, max_circles: int = 1_000_000) -> np.ndarray:
+    """Boolean random-circle packing: radius uniform integer in [r_min, r_max], centres
+    uniform, periodic wrap; circles are added until the solid fraction is reached."""
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((ny, nx), dtype=bool)
+    n_solid, count = 0, 0
+    while n_solid < solid_fraction * solid.size and count < max_circles:
+        r = int(rng.integers(r_min, r_max + 1))
+        cy, cx = rng.uniform(0, 1, size=2) * np.array([ny, nx])
+        offs = np.arange(-r, r + 1)
+        dy, dx = np.meshgrid(offs, offs, indexing="ij")
+        iy = np.floor(cy).astype(int) + dy
+        ix = np.floor(cx).astype(int) + dx
+        m = (iy + 0.5 - cy) ** 2 + (ix + 0.5 - cx) ** 2 <= r * r
+        idx = (iy[m] % ny, ix[m] % nx)
+        n_solid += int(np.count_nonzero(~solid[idx]))
+        solid[idx] = True
+        count += 1
+    g = np.zeros((1, ny, nx), dtype=np.uint8)
+    g[0][solid] = flag
+    return g
+
+
+def ensemble_members(n2d: int, n3d: int, seed0: int = 0, side_2d=(64, 512), side_3d=(64, 160),
+                     porosity=(0.35, 0.7), precision="fp16"):
+    """Uneven ensemble of steady-state flow + solute runs: n2d square 2D domains (side uniform
+    integer in side_2d, circles of radius 4-8) and n3d cubic 3D domains (side uniform in
+    side_3d, spheres of radius 6-12), porosity uniform in `porosity`, member k seeded with
+    seed0 + k.  Transport parameters of the reactive channel (2D) and the dissolution case (3D);
+    the geometry stays fixed.  Returns (list_2d, list_3d) of (cfg, geom, fields)."""
+    out2, out3 = [], []
+    for k in range(n2d + n3d):
+        rng = np.random.default_rng(seed0 + k)
+        phi = float(rng.uniform(*porosity))
+        if k < n2d:
+            s = int(rng.integers(side_2d[0], side_2d[1] + 1))
+            geom = circle_packing_2d(s, s, 4, 8, 1.0 - phi, seed0 + k)
+            cfg = dict(dim=2, nx=s, ny=s, nz=1, n_comp=1, tau=[0.8], g=[1e-5, 0.0, 0.0], collision="bgk",
+                       forcing="guo", n_scal=1, tau_c=[0.7], J0=0.4, k_react=1e-3, ade_open_x=True,
+                       C_in=[1.0], periodic=[1, 1, 1], geo_mode="none", C_ref=[1.0], precision=precision)
+            out2.append((cfg, geom, uniform_fields(geom.shape, 1, 1, rho=1.0, C=1.0)))
+        else:
+            s = int(rng.integers(side_3d[0], side_3d[1] + 1))
+            geom = sphere_packing_3d(s, 6.0, 12.0, 1.0 - phi, seed0 + k, REACTIVE)
+            cfg = dict(dim=3, nx=s, ny=s, nz=s, n_comp=1, tau=[1.0], g=[DISSOLUTION_G, 0.0, 0.0],
+                       collision="mrt", forcing="guo", n_scal=1, tau_c=[0.5667], J0=0.25, k_react=1.85e-4,
+                       ade_open_x=True, C_in=[1.0], periodic=[1, 1, 1], geo_mode="none", C_ref=[1.0],
+                       precision=precision)
+            out3.append((cfg, geom, uniform_fields(geom.shape, 1, 1, rho=1.0, C=1.0)))
+    return out2, out3
