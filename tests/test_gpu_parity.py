@@ -207,3 +207,36 @@ def test_state_errors():
     with pytest.raises(LbmError) as e:
         s.set_geometry(np.full((1, 8, 8), 3, np.uint8))
     assert e.value.status == -1
+
+
+def test_nonfinite_initial_field_is_reported():
+    """A NaN in a host-prepared initial field must surface as LBM_ERR_NONFINITE at the next
+    monitor evaluation (no device fault involved)."""
+    from paper_2502_12955_gb300.lbm import LbmError, Solver
+    cfg, geom, fields = inputs.dissolution_3d(shape=(6, 8, 10), g=1e-4, radius=(1.5, 2.5))
+    rho, u, C = fields
+    rho = rho.copy()
+    z, y, x = np.argwhere(geom == 0)[3]
+    rho[0, z, y, x] = np.nan
+    s = Solver(dict(cfg, precision="fp32", N_mon=2))
+    s.set_geometry(geom)
+    s.set_fields(rho, u, C)
+    s.step(2)
+    with pytest.raises(LbmError) as e:
+        s.sync()
+    assert e.value.status == -4
+    assert s.monitors()["nonfinite"] >= 1
+
+
+def test_allocation_failure_is_reported_and_cleaned_up():
+    """A domain larger than device memory fails with LBM_ERR_OOM and leaves nothing allocated
+    (a second, small context still works)."""
+    from paper_2502_12955_gb300.lbm import LbmError, Solver
+    with pytest.raises(LbmError) as e:
+        Solver(dict(dim=3, nx=1280, ny=1280, nz=1280, precision="fp64", n_scal=2))
+    assert e.value.status == -2
+    s = Solver(dict(dim=2, nx=16, ny=16, precision="fp64"))
+    s.set_geometry(np.zeros((1, 16, 16), np.uint8))
+    s.set_fields(np.ones((1, 1, 16, 16)), np.zeros((3, 1, 16, 16)), None)
+    s.step(3)
+    s.sync()

@@ -1,0 +1,52 @@
+"""Storage precision on the dissolution workload's recipe (64^3 sphere packing, D3Q19 MRT +
+D3Q7, transport numbers of the 256^3 case, geometry held fixed): FP32, FP16 and BF16 storage
+against the FP64 path (itself within 1e-10 of the oracle) after 500 steps, per field.  The
+bounds are the measured errors with a margin of about 3x.  FP16 stays within 1e-3 on every
+field; BF16 (8-bit mantissa) does not on u."""
+import numpy as np
+import pytest
+
+from paper_2502_12955_gb300 import inputs
+from paper_2502_12955_gb300.lbm import Solver
+from tests.gpu_common import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# relative L2 of the full fields over the fluid nodes (measured: FP32 2.8e-8 / 5.7e-7 / 8.7e-8,
+# FP16 2.4e-6 / 3.9e-4 / 8.1e-5, BF16 1.6e-5 / 2.9e-3 / 8.0e-4 for rho / u / C)
+BOUND = {"fp32": {"rho": 1e-7, "u": 2e-6, "C": 3e-7},
+         "fp16": {"rho": 1e-5, "u": 1e-3, "C": 3e-4},
+         "bf16": {"rho": 6e-5, "u": 1e-2, "C": 3e-3}}
+
+
+@pytest.fixture(scope="module")
+def fp64_reference():
+    cfg, geom, fields = inputs.dissolution_3d(64, precision="fp64")
+    cfg = dict(cfg, geo_mode="none")
+    s = Solver(cfg)
+    s.set_geometry(geom)
+    s.set_fields(*fields)
+    s.step(500)
+    ref = s.fields()
+    s.close()
+    return cfg, geom, fields, ref
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_storage_precision_errors_per_field(fp64_reference, precision):
+    cfg, geom, fields, ref = fp64_reference
+    s = Solver(dict(cfg, precision=precision))
+    s.set_geometry(geom)
+    s.set_fields(*fields)
+    s.step(500)
+    out = s.fields()
+    s.close()
+    fl = geom.reshape(-1) == 0
+    errs = {}
+    for k in ("rho", "u", "C"):
+        a = ref[k].reshape(ref[k].shape[0], -1)[:, fl]
+        b = out[k].reshape(out[k].shape[0], -1)[:, fl]
+        errs[k] = rel_l2(a, b)
+    print(precision, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v <= BOUND[precision][k], f"{precision} {k}: {v:.3e}"
