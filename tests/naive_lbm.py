@@ -1,0 +1,251 @@
+"""A second, deliberately naive formulation of one time step, for brute-force checks of the
+oracle on tiny lattices.
+
+Written independently of oracle/ (no shared code, tables or helpers) and structured
+differently on purpose:
+- It streams by pushing post-collision populations to their destinations, where the oracle
+  pulls them from their sources.
+- MRT is the full moment-space relaxation with the explicit d'Humieres (D3Q19) / Lallemand-Luo
+  (D2Q9) polynomial matrix and its numerical inverse, where the oracle builds rows by
+  Gram-Schmidt.
+- Every node and link is a plain Python loop.
+
+The velocity sets come from the paper's printed tables (tests/golden/lattice_tables.json), with
+the same readings the project documents: D2Q9 axis weights 1/9, D3Q7 as the first seven D3Q19
+directions with rest weight J0, the wet-node closure per link at gather time, inlet
+equilibrium ghost and zero-gradient outlet for the scalar, and flow walls on non-periodic
+faces.
+
+The state is the populations each fluid node holds at the start of a step (after streaming),
+the same quantity the oracle reports.  Fields are indexed [q][z][y][x].
+"""
+from __future__ import annotations
+
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+
+_GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lattice_tables.json")
+
+
+def velocity_sets(dim, J0):
+    t = json.load(open(_GOLD))
+    if dim == 3:
+        d = t["D3Q19"]
+        cf = np.array([d["cx"], d["cy"], d["cz"]], dtype=int).T
+        wf = np.array([float(Fraction(w)) for w in d["w"]])
+        cc = cf[:7].copy()
+        wc = np.array([J0] + [(1.0 - J0) / 6.0] * 6)
+    else:
+        d = t["D2Q9"]
+        cf = np.array([d["cx"], d["cy"], [0] * 9], dtype=int).T
+        wf = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)     # axis weights 1/9 (reading 1)
+        e = t["D2Q5"]
+        cc = np.array([e["cx"], e["cy"], [0] * 5], dtype=int).T
+        wc = np.array([J0] + [(1.0 - J0) / 4.0] * 4)
+    return cf, wf, cc, wc
+
+
+def opposite(c):
+    return [next(k for k in range(len(c)) if (c[k] == -c[i]).all()) for i in range(len(c))]
+
+
+def moment_matrix(dim, cf):
+    """Rows of the MRT moment basis as printed polynomials, with each row's relaxation group:
+    'c' conserved, 'nu' stress (1/tau), 'e', 'eps', 'q', 'pi', 'm'."""
+    rows, grp = [], []
+    x, y, z = cf[:, 0].astype(float), cf[:, 1].astype(float), cf[:, 2].astype(float)
+    c2 = x * x + y * y + z * z
+    one = np.ones_like(x)
+    if dim == 3:
+        table = [(one, "c"), (19 * c2 - 30, "e"), ((21 * c2 * c2 - 53 * c2 + 24) / 2, "eps"),
+                 (x, "c"), ((5 * c2 - 9) * x, "q"), (y, "c"), ((5 * c2 - 9) * y, "q"),
+                 (z, "c"), ((5 * c2 - 9) * z, "q"),
+                 (3 * x * x - c2, "nu"), ((3 * c2 - 5) * (3 * x * x - c2), "pi"),
+                 (y * y - z * z, "nu"), ((3 * c2 - 5) * (y * y - z * z), "pi"),
+                 (x * y, "nu"), (y * z, "nu"), (x * z, "nu"),
+                 (x * (y * y - z * z), "m"), (y * (z * z - x * x), "m"), (z * (x * x - y * y), "m")]
+    else:
+        table = [(one, "c"), (3 * c2 - 4, "e"), ((9 * c2 * c2 - 21 * c2 + 8) / 2, "eps"),
+                 (x, "c"), ((3 * c2 - 5) * x, "q"), (y, "c"), ((3 * c2 - 5) * y, "q"),
+                 (x * x - y * y, "nu"), (x * y, "nu")]
+    for r, g in table:
+        rows.append(r)
+        grp.append(g)
+    return np.array(rows), grp
+
+
+class NaiveLBM:
+    def __init__(self, cfg, flags, f, h):
+        self.cfg = cfg
+        self.dim = int(cfg["dim"])
+        self.nx, self.ny, self.nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg.get("nz", 1))
+        self.nc = int(cfg.get("n_comp", 1))
+        self.ns = int(cfg.get("n_scal", 0))
+        self.J0 = float(cfg.get("J0", 0.25))
+        self.cf, self.wf, self.cc, self.wc = velocity_sets(self.dim, self.J0)
+        self.of, self.oc = opposite(self.cf), opposite(self.cc)
+        self.flags = np.array(flags, dtype=np.uint8).reshape(self.nz, self.ny, self.nx)
+        self.f = np.array(f, dtype=np.float64).reshape(self.nc, len(self.cf), self.nz, self.ny, self.nx).copy()
+        self.h = np.array(h, dtype=np.float64).reshape(self.ns, len(self.cc), self.nz, self.ny, self.nx).copy() \
+            if self.ns else np.zeros((0, len(self.cc), self.nz, self.ny, self.nx))
+        self.acc = np.zeros((self.nz, self.ny, self.nx))
+        per = cfg.get("periodic", [1, 1, 1])
+        self.per_f = [bool(p) for p in per]
+        self.per_c = [bool(per[0]) and not cfg.get("ade_open_x", False), bool(per[1]), bool(per[2])]
+        if self.dim == 2:
+            self.per_f[2] = self.per_c[2] = True
+        self.M, self.grp = moment_matrix(self.dim, self.cf)
+        self.Minv = np.linalg.inv(self.M)
+
+    # node at (x, y, z) + c, or None outside a non-periodic face
+    def _shift(self, x, y, z, c, per):
+        p = [x + c[0], y + c[1], z + c[2]]
+        for a, n in enumerate((self.nx, self.ny, self.nz)):
+            if p[a] < 0 or p[a] >= n:
+                if not per[a]:
+                    return None
+                p[a] %= n
+        return p[0], p[1], p[2]
+
+    def _fluid(self, q):
+        return q is not None and self.flags[q[2], q[1], q[0]] == 0
+
+    def _feq(self, i, rho, u):
+        cu = float(np.dot(self.cf[i], u))
+        return self.wf[i] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * float(np.dot(u, u)))
+
+    def _guo(self, i, u, F):
+        c = self.cf[i].astype(float)
+        return self.wf[i] * (3 * np.dot(c - u, F) + 9 * np.dot(c, u) * np.dot(c, F))
+
+    def _psi(self, rho):
+        if self.cfg.get("psi_kind", "exp") == "identity":
+            return rho
+        r0 = float(self.cfg.get("rho0", 1.0))
+        return r0 * (1 - np.exp(-rho / r0))
+
+    def step(self):
+        cfg = self.cfg
+        nx, ny, nz = self.nx, self.ny, self.nz
+        Qf, Qc = len(self.cf), len(self.cc)
+        tau = [float(t) for t in cfg.get("tau", [1.0, 1.0])]
+        tauc = [float(t) for t in cfg.get("tau_c", [1.0, 1.0])]
+        g = np.array(cfg.get("g", [0, 0, 0]), dtype=float)
+        if self.dim == 2:
+            g[2] = 0.0
+        G = cfg.get("G", [[0, 0], [0, 0]])
+        Gads = cfg.get("G_ads", [0, 0])
+        k = float(cfg.get("k_react", 0.0))
+        nodes = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx) if self.flags[z, y, x] == 0]
+
+        # wet-node closure of scalar 0 at reactive links, from the stored populations
+        hc = self.h.copy()
+        if self.ns:
+            Kr = k * tauc[0] / (tauc[0] - 0.5)
+            for (x, y, z) in nodes:
+                for j in range(1, Qc):
+                    src = self._shift(x, y, z, -self.cc[j], self.per_c)
+                    if src is None or self.flags[src[2], src[1], src[0]] != 2:
+                        continue
+                    hb = self.h[0, self.oc[j], z, y, x]
+                    Cb = 2 * hb / (2 * self.wc[j] + Kr)
+                    hc[0, j, z, y, x] = 2 * self.wc[j] * Cb - hb
+                    self.acc[src[2], src[1], src[0]] += k * Cb
+
+        # densities, momenta and psi of every fluid node before any force
+        rho = {n: [float(self.f[s, :, n[2], n[1], n[0]].sum()) for s in range(self.nc)] for n in nodes}
+        mom = {n: [self.cf.T.astype(float) @ self.f[s, :, n[2], n[1], n[0]] for s in range(self.nc)] for n in nodes}
+        psi = {n: [self._psi(rho[n][s]) for s in range(self.nc)] for n in nodes}
+        psi_w = self._psi(float(cfg.get("rho_solid", 0.0)))
+        force, vel = {}, {}
+        for n in nodes:
+            x, y, z = n
+            Fs = []
+            for s in range(self.nc):
+                F = rho[n][s] * g
+                for s2 in range(self.nc):
+                    if G[s][s2] == 0:
+                        continue
+                    acc = np.zeros(3)
+                    for i in range(1, Qf):
+                        q = self._shift(x, y, z, self.cf[i], self.per_f)
+                        p = psi[q][s2] if self._fluid(q) else psi_w
+                        acc += self.wf[i] * p * self.cf[i]
+                    F = F - psi[n][s] * G[s][s2] * acc
+                if Gads[s] != 0:
+                    acc = np.zeros(3)
+                    for i in range(1, Qf):
+                        q = self._shift(x, y, z, self.cf[i], self.per_f)
+                        acc += self.wf[i] * (0.0 if self._fluid(q) else 1.0) * self.cf[i]
+                    F = F - Gads[s] * rho[n][s] * acc
+                Fs.append(F)
+            force[n] = Fs
+            vel[n] = sum(mom[n][s] + 0.5 * Fs[s] for s in range(self.nc)) / sum(rho[n])
+
+        # collision
+        fpost = np.zeros_like(self.f)
+        hpost = np.zeros_like(self.h)
+        rate = {"e": cfg.get("s_e", 1.19), "eps": cfg.get("s_eps", 1.4), "q": cfg.get("s_q", 1.2),
+                "pi": cfg.get("s_pi", 1.0), "m": cfg.get("s_m", 1.98)}
+        for n in nodes:
+            x, y, z = n
+            u = vel[n]
+            for s in range(self.nc):
+                fv = self.f[s, :, z, y, x]
+                if cfg.get("forcing", "guo") == "sc_shift":
+                    up = sum(mom[n][t] / tau[t] for t in range(self.nc)) / sum(rho[n][t] / tau[t] for t in range(self.nc))
+                    ueq = up + tau[s] * force[n][s] / rho[n][s]
+                    fpost[s, :, z, y, x] = [fv[i] - (fv[i] - self._feq(i, rho[n][s], ueq)) / tau[s] for i in range(Qf)]
+                elif cfg.get("collision", "bgk") == "mrt":
+                    fe = np.array([self._feq(i, rho[n][s], u) for i in range(Qf)])
+                    Fi = np.array([self._guo(i, u, force[n][s]) for i in range(Qf)])
+                    S = np.array([1.0 / tau[s] if gr in ("c", "nu") else rate[gr] for gr in self.grp])
+                    m, me, mF = self.M @ fv, self.M @ fe, self.M @ Fi
+                    fpost[s, :, z, y, x] = self.Minv @ (m - S * (m - me) + (1 - S / 2) * mF)
+                else:
+                    fpost[s, :, z, y, x] = [fv[i] - (fv[i] - self._feq(i, rho[n][s], u)) / tau[s]
+                                           + (1 - 1 / (2 * tau[s])) * self._guo(i, u, force[n][s]) for i in range(Qf)]
+            cs2 = (1.0 - self.J0) / self.dim   # the scalar lattice's own sound speed (reading 3)
+            for s in range(self.ns):
+                C = float(hc[s, :, z, y, x].sum())
+                for j in range(Qc):
+                    heq = self.wc[j] * C * (1 + float(np.dot(self.cc[j], u)) / cs2)
+                    hpost[s, j, z, y, x] = hc[s, j, z, y, x] - (hc[s, j, z, y, x] - heq) / tauc[s]
+
+        # push streaming with halfway bounce-back, inlet ghost and zero-gradient outlet
+        cs2 = (1.0 - self.J0) / self.dim
+        fnew = np.zeros_like(self.f)
+        hnew = np.zeros_like(self.h)
+        for n in nodes:
+            x, y, z = n
+            for s in range(self.nc):
+                for i in range(Qf):
+                    t = self._shift(x, y, z, self.cf[i], self.per_f)
+                    if self._fluid(t):
+                        fnew[s, i, t[2], t[1], t[0]] = fpost[s, i, z, y, x]
+                    else:
+                        fnew[s, self.of[i], z, y, x] = fpost[s, i, z, y, x]
+            for s in range(self.ns):
+                for j in range(Qc):
+                    t = self._shift(x, y, z, self.cc[j], self.per_c)
+                    xt = x + self.cc[j][0]
+                    if self._fluid(t):
+                        hnew[s, j, t[2], t[1], t[0]] = hpost[s, j, z, y, x]
+                    elif t is None and cfg.get("ade_open_x", False) and (xt < 0 or xt >= nx):
+                        pass   # leaves through an open face
+                    else:
+                        hnew[s, self.oc[j], z, y, x] = hpost[s, j, z, y, x]
+                # populations entering through the open faces
+                for j in range(Qc):
+                    xs = x - self.cc[j][0]
+                    if not cfg.get("ade_open_x", False) or self.cc[j][1] or self.cc[j][2]:
+                        continue
+                    if xs < 0:
+                        C_in = float(cfg.get("C_in", [0.0, 0.0])[s])
+                        hnew[s, j, z, y, x] = self.wc[j] * C_in * (1 + float(np.dot(self.cc[j], vel[n])) / cs2)
+                    elif xs >= nx:
+                        hnew[s, j, z, y, x] = hpost[s, j, z, y, x]
+        self.f, self.h = fnew, hnew
