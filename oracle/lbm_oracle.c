@@ -309,6 +309,10 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
     if (!(p->tau_c[s] > 0.5)) st = -1;
   if (p && !st && p->n_scal > 0 && !(p->J0 >= 0.0 && p->J0 < 1.0)) st = -1;
   if (p && !st && p->ade_open_x && p->nx < 2) st = -1;
+  /* a moving top plate needs a closed y axis and moves in its own plane */
+  if (p && !st && (p->u_wall_ymax[0] != 0.0 || p->u_wall_ymax[1] != 0.0 || p->u_wall_ymax[2] != 0.0) &&
+      (p->periodic[1] || p->u_wall_ymax[1] != 0.0))
+    st = -1;
   if (st) {
     if (status) *status = st;
     return NULL;
@@ -549,10 +553,19 @@ static void stream(orc_ctx* c) {
     for (int s = 0; s < c->p.n_comp; ++s)
       for (int i = 0; i < Qf; ++i) {
         int64_t src = nbr(c, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2], c->p.periodic);
-        if (is_fluid_idx(c, src))
+        if (is_fluid_idx(c, src)) {
           c->f[s][n * Qf + i] = c->fp[s][src * Qf + i];          /* Eq. 5 */
-        else
-          c->f[s][n * Qf + i] = c->fp[s][n * Qf + L->opp[i]];    /* halfway bounce-back */
+        } else {
+          double v = c->fp[s][n * Qf + L->opp[i]];                /* halfway bounce-back */
+          if (src < 0 && y - L->c[i][1] >= c->p.ny) {
+            /* moving top plate (Sec. 3.1.1): the reflected population carries the momentum
+               exchange 2 w rho (c . u_wall) / c_s^2, c_s^2 = 1/3, rho the node's density */
+            double cu = 0.0;
+            for (int a = 0; a < 3; ++a) cu += (double)L->c[i][a] * c->p.u_wall_ymax[a];
+            v += 6.0 * L->w[i] * c->rho[s][n] * cu;
+          }
+          c->f[s][n * Qf + i] = v;
+        }
       }
     for (int s = 0; s < c->p.n_scal; ++s)
       for (int i = 0; i < Qc; ++i) {

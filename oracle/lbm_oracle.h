@@ -45,6 +45,8 @@ typedef struct orc_params {
   double DP;                   /* deposition probability (Eq. surface_deposition) */
   int32_t deposit_conservative;/* 1: deposited particle mass leaves the populations */
   int32_t N_geo;               /* geometry flips evaluated every N_geo steps */
+  double u_wall_ymax[3];       /* velocity of the closed face beyond y = ny-1 (moving-wall
+                                  bounce-back, Sec. 3.1.1 Couette flow); needs periodic[1] == 0 */
 } orc_params;
 
 /* Monitor vector layout (doubles). */

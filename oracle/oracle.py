@@ -51,7 +51,7 @@ class OrcParams(C.Structure):
         ("k_react", C.c_double), ("ade_open_x", C.c_int32), ("C_in", C.c_double * 2),
         ("periodic", C.c_int32 * 3), ("geo_mode", C.c_int32), ("V_m", C.c_double),
         ("m_s0", C.c_double), ("DP", C.c_double), ("deposit_conservative", C.c_int32),
-        ("N_geo", C.c_int32),
+        ("N_geo", C.c_int32), ("u_wall_ymax", C.c_double * 3),
     ]
 
 
@@ -141,6 +141,9 @@ def make_params(cfg: dict) -> OrcParams:
     p.DP = float(d.get("DP", 0.0))
     p.deposit_conservative = int(bool(d.get("deposit_conservative", True)))
     p.N_geo = int(d.get("N_geo", 1))
+    uw = d.get("u_wall_ymax", [0.0, 0.0, 0.0])
+    for a in range(3):
+        p.u_wall_ymax[a] = float(uw[a])
     return p
 
 

@@ -188,8 +188,10 @@ class NaiveLBM:
         # collision
         fpost = np.zeros_like(self.f)
         hpost = np.zeros_like(self.h)
-        rate = {"e": cfg.get("s_e", 1.19), "eps": cfg.get("s_eps", 1.4), "q": cfg.get("s_q", 1.2),
-                "pi": cfg.get("s_pi", 1.0), "m": cfg.get("s_m", 1.98)}
+        # MRT rates of the run (documented defaults: s_e 1.19, s_eps 1.4, s_q 1.2, s_pi = 1/tau, s_m 1.98)
+        mr = cfg.get("mrt_rates", {})
+        rate = {"e": mr.get("s_e", 1.19), "eps": mr.get("s_eps", 1.4), "q": mr.get("s_q", 1.2),
+                "pi": mr.get("s_pi", 1.0 / tau[0]), "m": mr.get("s_m", 1.98)}
         for n in nodes:
             x, y, z = n
             u = vel[n]
@@ -227,7 +229,12 @@ class NaiveLBM:
                     if self._fluid(t):
                         fnew[s, i, t[2], t[1], t[0]] = fpost[s, i, z, y, x]
                     else:
-                        fnew[s, self.of[i], z, y, x] = fpost[s, i, z, y, x]
+                        v = fpost[s, i, z, y, x]
+                        if t is None and y + self.cf[i][1] >= ny:
+                            # Ladd's moving wall: the plate beyond y = ny - 1 moves with u_wall
+                            uw = np.array(cfg.get("u_wall_ymax", [0, 0, 0]), dtype=float)
+                            v -= 2 * self.wf[i] * rho[n][s] * float(np.dot(self.cf[i], uw)) * 3.0
+                        fnew[s, self.of[i], z, y, x] = v
             for s in range(self.ns):
                 for j in range(Qc):
                     t = self._shift(x, y, z, self.cc[j], self.per_c)

@@ -21,6 +21,10 @@ CASES = {
     "3d_mrt_reactive_open": dict(dim=3, nx=8, ny=8, nz=8, tau=[1.0], g=[3e-4, 1e-4, 0], collision="mrt",
                                  n_scal=1, tau_c=[0.5667], J0=0.25, k_react=0.02, ade_open_x=True,
                                  C_in=[1.0], periodic=[1, 1, 0]),
+    "2d_couette_moving_plate_scalar": dict(dim=2, nx=8, ny=8, tau=[0.7], u_wall_ymax=[0.03, 0, 0], n_scal=1,
+                                          tau_c=[0.8], J0=0.4, k_react=0.04, periodic=[1, 0, 1]),
+    "3d_mrt_moving_plate": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", g=[1e-4, 0, 0],
+                                u_wall_ymax=[0.02, 0, -0.01], periodic=[1, 0, 1]),
     "3d_bgk_single_sc_walls": dict(dim=3, nx=8, ny=8, nz=8, tau=[1.0], G=[[-4.5, 0], [0, 0]], psi_kind="exp",
                                    rho_solid=0.3, periodic=[0, 1, 1]),
 }
