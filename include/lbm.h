@@ -99,6 +99,10 @@ typedef struct lbm_params {
                                  (cudaLimitMaxL2FetchGranularity: 32, 64 or 128; 0, the default,
                                  leaves the context's current value).  Smaller fetches move fewer
                                  bytes on porous geometries but expose more latency. */
+  double u_wall_ymax[3];      /* velocity of the closed face beyond y = ny-1 (moving top plate,
+                                 Sec. 3.1.1 Couette flow): its links reflect with Ladd's momentum
+                                 term 2 w_i rho (c_i . u) / c_s^2.  Needs periodic[1] == 0 and a
+                                 tangential velocity (component 1 zero); zero disables it. */
 } lbm_params;
 
 /* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */

@@ -135,6 +135,8 @@ struct Args {
   double rho_ref[2], C_ref[2];
   int bx, by;                // step-kernel block shape
   FastDiv div_x, div_y;      // node index / nx, (node index / nx) / ny
+  double u_wall[3];          // velocity of the top plate beyond y = ny - 1
+  int moving_wall;           // the top plate moves (closed y axis)
 };
 
 // Compute-type constants derived on the host from Args (see make_coef).
@@ -152,6 +154,7 @@ struct Coef {
   T C_in[2];
   T DP, keep;       // deposition probability, 1 - DP
   T rref[2], cref[2];   // storage references (0 in FP64 mode)
+  T uw6[3];         // 6 u_wall = 2 u_wall / c_s^2 of the moving top plate
   double thr;       // dissolution threshold on acc: m_s0 / V_m (+inf if V_m == 0)
 };
 
@@ -695,17 +698,28 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
     }
   }
   // ---- scatter flow
+  // a node under a moving top plate (Sec. 3.1.1): links through the face beyond y = ny - 1
+  // reflect with Ladd's momentum exchange 2 w_i rho (c_i . u_wall) / c_s^2
+  bool top = false;
+  if (a.moving_wall) {
+    const unsigned int q = fast_div(unsigned(n), a.div_x);
+    top = int(q - fast_div(q, a.div_y) * unsigned(a.ny)) == a.ny - 1;
+  }
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       S* p;
-      if (parity == 0 || i == 0 || flow_wall<L>(m, i))
+      T v = f[s][i];
+      if (parity == 0 || i == 0 || flow_wall<L>(m, i)) {
         p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + sn;
-      else
+        if (L::cy(i) > 0 && top && flow_wall<L>(m, i))
+          v -= T(L::w(i)) * rho[s] * (T(L::cx(i)) * k.uw6[0] + T(L::cz(i)) * k.uw6[2] + k.uw6[1]);
+      } else {
         p = reinterpret_cast<S*>(a.fplane[s][i]) +
             (long long)__ldg(a.slot + nb.at(L::cx(i), L::cy(i), L::cz(i)));
-      Store<S>::st(p, f[s][i]);
+      }
+      Store<S>::st(p, v);
     }
   }
   // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces

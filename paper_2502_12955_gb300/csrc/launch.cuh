@@ -81,6 +81,7 @@ Coef<T> make_coef(const Args& a, bool shifted) {
   k.DP = T(a.DP);
   k.keep = T(1.0 - a.DP);
   k.thr = a.V_m > 0.0 ? a.m_s0 / a.V_m : __builtin_huge_val();
+  for (int c = 0; c < 3; ++c) k.uw6[c] = T(6.0 * a.u_wall[c]);
   return k;
 }
 

@@ -149,6 +149,10 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
     return fail(c, LBM_ERR_INVALID_ARG, "l2_fetch_bytes must be 0, 32, 64 or 128");
   if (p->block_x < 0 || p->block_x > 256 || (p->block_x % 32) != 0)
     return fail(c, LBM_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [0, 256]");
+  if (p->u_wall_ymax[0] != 0.0 || p->u_wall_ymax[1] != 0.0 || p->u_wall_ymax[2] != 0.0) {
+    if (p->periodic[1]) return fail(c, LBM_ERR_INVALID_ARG, "a moving top plate needs a closed y axis");
+    if (p->u_wall_ymax[1] != 0.0) return fail(c, LBM_ERR_INVALID_ARG, "the top plate moves in its own plane");
+  }
   return LBM_OK;
 }
 
@@ -218,6 +222,8 @@ void fill_args(lbm_ctx* c) {
   a.by = 1;
   a.div_x = make_fast_div(c->nx);
   a.div_y = make_fast_div(c->ny);
+  for (int k = 0; k < 3; ++k) a.u_wall[k] = p.u_wall_ymax[k];
+  a.moving_wall = (p.u_wall_ymax[0] != 0.0 || p.u_wall_ymax[2] != 0.0) ? 1 : 0;
 }
 
 int parity_of(long long step) { return int(step & 1); }

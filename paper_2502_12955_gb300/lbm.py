@@ -50,7 +50,7 @@ class LbmParams(C.Structure):
         ("m_s0", C.c_double), ("DP", C.c_double), ("deposit_conservative", C.c_int32),
         ("N_geo", C.c_int32), ("N_mon", C.c_int32), ("rho_ref", C.c_double * 2),
         ("C_ref", C.c_double * 2), ("stream", C.c_void_p), ("block_x", C.c_int32),
-        ("device", C.c_int32), ("l2_fetch_bytes", C.c_int32),
+        ("device", C.c_int32), ("l2_fetch_bytes", C.c_int32), ("u_wall_ymax", C.c_double * 3),
     ]
 
 
@@ -191,6 +191,9 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     p.block_x = int(d.get("block_x", 0))
     p.device = int(d.get("device", 0))
     p.l2_fetch_bytes = int(d.get("l2_fetch_bytes", 0))
+    uw = d.get("u_wall_ymax", [0.0, 0.0, 0.0])
+    for a in range(3):
+        p.u_wall_ymax[a] = float(uw[a])
     return p
 
 

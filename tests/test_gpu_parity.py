@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2502_12955_gb300 import inputs
+from paper_2502_12955_gb300.lbm import Solver
 from tests.gpu_common import FP64_TOL, compare, make_pair, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -240,3 +241,26 @@ def test_allocation_failure_is_reported_and_cleaned_up():
     s.set_fields(np.ones((1, 1, 16, 16)), np.zeros((3, 1, 16, 16)), None)
     s.step(3)
     s.sync()
+
+
+@pytest.mark.parametrize("dim,steps", [(2, 3000), (3, 1500)])
+def test_couette_moving_plate(dim, steps):
+    """Sec. 3.1.1: top plate at U_wall = 0.02, Re = 10 on Ny = 15 (tau 0.59), periodic x and z;
+    the plate's Ladd bounce-back against the oracle in FP64, then the converged FP32 profile
+    against Eq. couette_velocity_profile."""
+    ny, U = 15, 0.02
+    nx, nz = 15, (15 if dim == 3 else 1)
+    cfg = dict(dim=dim, nx=nx, ny=ny, nz=nz, tau=[0.59], periodic=[1, 0, 1], u_wall_ymax=[U, 0, 0])
+    shape = (nz, ny, nx)
+    rho, u, _ = inputs.perturbed_fields(shape, 1, 0, seed=31, amp_rho=0.01, amp_u=0.005)
+    o, g = make_pair(cfg, np.zeros(shape, np.uint8), (rho, u, None))
+    o.step(steps)
+    g.step(steps)
+    compare(o, g, what=f"couette {dim}d")
+    s = Solver(dict(cfg, precision="fp32"))
+    s.set_geometry(np.zeros(shape, np.uint8))
+    s.set_fields(*inputs.uniform_fields(shape, 1, 0, rho=1.0)[:2], None)
+    s.step(40000)
+    prof = s.fields()["u"][0].mean(axis=(0, 2))
+    exact = U * (np.arange(ny) + 0.5) / ny
+    assert np.abs(prof - exact).max() < 1e-4 * U, np.abs(prof - exact).max()   # FP32 storage of O(1) values
