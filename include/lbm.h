@@ -38,7 +38,9 @@ typedef enum lbm_status {
   LBM_ERR_NONFINITE = -4,    /* a monitor evaluation found non-finite populations */
   LBM_ERR_TIMEOUT = -5,      /* a bounded device wait ran out */
   LBM_ERR_STATE = -6,        /* call out of order (e.g. step before fields were set) */
-  LBM_ERR_CAPACITY = -7      /* a device work list overflowed; results after it are invalid */
+  LBM_ERR_CAPACITY = -7,     /* a device work list overflowed; results after it are invalid */
+  LBM_ERR_BOUNDS = -8        /* bounds-checked build only (-DLBM_BOUNDS_CHECK): a step kernel
+                                computed an index outside its buffer and used 0 instead */
 } lbm_status;
 
 typedef enum lbm_lattice {

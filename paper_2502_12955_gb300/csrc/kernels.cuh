@@ -67,7 +67,7 @@ struct Store<__nv_bfloat16> {
 
 // ------------------------------------------------------------- arguments
 
-enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_CAS = 4 };
+enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_CAS = 4, ERR_BOUNDS = 8 };
 enum : int { GEO_NONE = 0, GEO_DISSOLVE = 1, GEO_DEPOSIT = 2 };
 enum : uint8_t { FL_FLUID = 0, FL_SOLID = 1, FL_REACTIVE = 2, FL_FLIPPING = 3 };
 
@@ -138,6 +138,22 @@ struct Args {
   double u_wall[3];          // velocity of the top plate beyond y = ny - 1
   int moving_wall;           // the top plate moves (closed y axis)
 };
+
+// Index guard of the bounds-checked build (-DLBM_BOUNDS_CHECK): an index outside [0, bound)
+// sets ERR_BOUNDS and is replaced by 0, so the access stays inside its buffer.  In normal
+// builds LBM_CHK is the bare index expression and the generated code is unchanged.
+#ifdef LBM_BOUNDS_CHECK
+__device__ __forceinline__ long long chk_index(int* err, long long i, long long bound) {
+  if (i < 0 || i >= bound) {
+    atomicOr(err, ERR_BOUNDS);
+    return 0;
+  }
+  return i;
+}
+#define LBM_CHK(err, i, bound) chk_index((err), (long long)(i), (long long)(bound))
+#else
+#define LBM_CHK(err, i, bound) (i)
+#endif
 
 // Compute-type constants derived on the host from Args (see make_coef).
 template <class T>
@@ -220,15 +236,16 @@ __device__ __forceinline__ void gather_flow(const S* __restrict__ f, long long p
 template <class L, class S>
 __device__ __forceinline__ void gather_flow_pl(void* const* planes, long long sn,
                                                const uint32_t* __restrict__ slot, uint32_t m,
-                                               const Nbr& nb, int parity, typename Store<S>::T* out) {
+                                               const Nbr& nb, int parity, typename Store<S>::T* out,
+                                               int* err, long long n_nodes, long long pitch) {
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const S* p;
     if (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
-      p = reinterpret_cast<const S*>(planes[i]) + sn;
+      p = reinterpret_cast<const S*>(planes[i]) + LBM_CHK(err, sn, pitch);
     else
       p = reinterpret_cast<const S*>(planes[L::opp(i)]) +
-          (long long)__ldg(slot + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)));
+          (long long)LBM_CHK(err, __ldg(slot + LBM_CHK(err, nb.at(-L::cx(i), -L::cy(i), -L::cz(i)), n_nodes)), pitch);
     out[i] = Store<S>::ld(p);
   }
 }
@@ -236,15 +253,16 @@ __device__ __forceinline__ void gather_flow_pl(void* const* planes, long long sn
 template <class L, class S>
 __device__ __forceinline__ void gather_scal_pl(void* const* planes, long long sn,
                                                const uint32_t* __restrict__ slot, uint32_t m,
-                                               const Nbr& nb, int parity, typename Store<S>::T* out) {
+                                               const Nbr& nb, int parity, typename Store<S>::T* out,
+                                               int* err, long long n_nodes, long long pitch) {
 #pragma unroll
   for (int j = 0; j < L::QC; ++j) {
     const S* p;
     if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
-      p = reinterpret_cast<const S*>(planes[j]) + sn;
+      p = reinterpret_cast<const S*>(planes[j]) + LBM_CHK(err, sn, pitch);
     else
       p = reinterpret_cast<const S*>(planes[L::opp(j)]) +
-          (long long)__ldg(slot + nb.at(-L::cx(j), -L::cy(j), -L::cz(j)));
+          (long long)LBM_CHK(err, __ldg(slot + LBM_CHK(err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), n_nodes)), pitch);
     out[j] = Store<S>::ld(p);
   }
 }
@@ -378,9 +396,9 @@ __device__ __forceinline__ void gather_entry(const Args& a, unsigned int e, unsi
   const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
   const Nbr nb = parity ? nbr_of(a, n) : Nbr{};
 #pragma unroll
-  for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f[s]);
+  for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f[s], a.err, a.N, a.pitch);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s]);
+  for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s], a.err, a.N, a.pitch);
 }
 
 // ------------------------------------------------------------- collision helpers
@@ -513,7 +531,7 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
     // the consumed totals are reductions (no value returned): the threshold test runs in
     // k_detect over the interface list before the geometry update
     close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
-      const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+      const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
       atomicAdd(a.acc + src, widen(k.kr * Cb));
       wallx += exch;
     });
@@ -712,12 +730,12 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
       S* p;
       T v = f[s][i];
       if (parity == 0 || i == 0 || flow_wall<L>(m, i)) {
-        p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + sn;
+        p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + LBM_CHK(a.err, sn, a.pitch);
         if (L::cy(i) > 0 && top && flow_wall<L>(m, i))
           v -= T(L::w(i)) * rho[s] * (T(L::cx(i)) * k.uw6[0] + T(L::cz(i)) * k.uw6[2] + k.uw6[1]);
       } else {
         p = reinterpret_cast<S*>(a.fplane[s][i]) +
-            (long long)__ldg(a.slot + nb.at(L::cx(i), L::cy(i), L::cz(i)));
+            LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N)), a.pitch);
       }
       Store<S>::st(p, v);
     }
@@ -738,18 +756,20 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
         if (L::cx(j) < 0) {
           const T cu = T(L::cx(jb)) * ux + T(L::cy(jb)) * uy + T(L::cz(jb)) * uz;
           b = k.wca * k.C_in[s] * (T(1) + cu * k.ics2c) - sh;
-          a.inflow_row[s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x))] += widen(b) - widen(v);
+          a.inflow_row[LBM_CHK(a.err, s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x)), 2ll * a.ny * a.nz)] +=
+              widen(b) - widen(v);
         } else {
           b = h[s][jb];
-          a.outflow_row[s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x))] += widen(v) - widen(b);
+          a.outflow_row[LBM_CHK(a.err, s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x)), 2ll * a.ny * a.nz)] +=
+              widen(v) - widen(b);
         }
         v = b;
-        p = reinterpret_cast<S*>(a.hplane[s][jb]) + sn;
+        p = reinterpret_cast<S*>(a.hplane[s][jb]) + LBM_CHK(a.err, sn, a.pitch);
       } else if (parity == 0 || j == 0 || code != 0u) {
-        p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + sn;
+        p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + LBM_CHK(a.err, sn, a.pitch);
       } else {
         p = reinterpret_cast<S*>(a.hplane[s][j]) +
-            (long long)__ldg(a.slot + nb.at(L::cx(j), L::cy(j), L::cz(j)));
+            LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(j), L::cy(j), L::cz(j)), a.N)), a.pitch);
       }
       Store<S>::st(p, v);
     }
@@ -770,15 +790,15 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   const unsigned int stride = gridDim.x * blockDim.x;
   unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
   // the list entry is fetched two iterations and the link mask one iteration ahead
-  int n_next = e < count ? int(a.fluid_list[e]) : 0;
-  int n_next2 = e + stride < count ? int(a.fluid_list[e + stride]) : 0;
+  int n_next = e < count ? int(LBM_CHK(a.err, a.fluid_list[e], a.N)) : 0;
+  int n_next2 = e + stride < count ? int(LBM_CHK(a.err, a.fluid_list[e + stride], a.N)) : 0;
   uint32_t m_next = e < count ? a.mask[n_next] : 0u;
   for (; e < count; e += stride) {
     const int n = n_next;
     const uint32_t m = m_next;
     n_next = n_next2;
     if (e + stride < count) m_next = a.mask[n_next];
-    if (e + 2 * stride < count) n_next2 = int(a.fluid_list[e + 2 * stride]);
+    if (e + 2 * stride < count) n_next2 = int(LBM_CHK(a.err, a.fluid_list[e + 2 * stride], a.N));
     if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
     T f[NC][Q], h[NSD][QC];
     gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
@@ -832,7 +852,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
     T wallx = T(0);
     const unsigned int e = tile.first + threadIdx.x;
     if (e < a.fluid_count[0]) {
-      const int n = int(a.fluid_list[e]);
+      const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
       const uint32_t m = a.mask[n];
       if (m & 1u) {
         const unsigned int base = a.fluid_count[1];
@@ -933,7 +953,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T f[Q];
-      gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f);
+      gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f, a.err, a.N, a.pitch);
       T r = T(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -948,7 +968,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       T h[QC];
-      gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h);
+      gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h, a.err, a.N, a.pitch);
       T c = T(0);
 #pragma unroll
       for (int j = 0; j < QC; ++j) c += h[j];
@@ -1004,7 +1024,7 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     T f[Q];
-    gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f);
+    gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f, a.err, a.N, a.pitch);
     T r = T(0), ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -1063,7 +1083,7 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T h[QC];
-    gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h);
+    gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h, a.err, a.N, a.pitch);
     if (s == 0) close_scalar<L, T>(h, m, k, [](int, T, T) {});
     T C = k.cref[s];
 #pragma unroll

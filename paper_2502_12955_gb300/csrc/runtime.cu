@@ -329,6 +329,7 @@ lbm_status check_err(lbm_ctx* c) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, c->a.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (e & ERR_BOUNDS) return fail(c, LBM_ERR_BOUNDS, "a step kernel index left its buffer");
   if (e & ERR_CAPACITY) return fail(c, LBM_ERR_CAPACITY, "geometry flip list overflowed");
   if (e & ERR_CAS) return fail(c, LBM_ERR_TIMEOUT, "flag update retry limit reached");
   if (e & ERR_NONFINITE) return fail(c, LBM_ERR_NONFINITE, "non-finite populations detected");

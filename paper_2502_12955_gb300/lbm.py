@@ -25,7 +25,8 @@ COLLISION = {"bgk": 0, "mrt": 1}
 PSI = {"exp": 0, "identity": 1}
 GEO = {"none": 0, "dissolve": 1, "deposit": 2}
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
-          -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE", -7: "LBM_ERR_CAPACITY"}
+          -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE", -7: "LBM_ERR_CAPACITY",
+          -8: "LBM_ERR_BOUNDS"}
 
 # Names of every entry point declared in include/lbm.h.
 EXPORTS = ["lbm_params_default", "lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step",

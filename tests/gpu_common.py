@@ -27,6 +27,7 @@ def make_pair(cfg, geom, fields, precision="fp64"):
 
 
 def compare(o, g, tol=FP64_TOL, pops=True, mon=True, flags_exact=True, what=""):
+    g.sync()   # raises if a kernel set a device error flag (capacity, retry limit, bounds)
     fo, fg = o.fields(), g.fields()
     report = {}
     if flags_exact:
