@@ -313,6 +313,12 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
   if (p && !st && (p->u_wall_ymax[0] != 0.0 || p->u_wall_ymax[1] != 0.0 || p->u_wall_ymax[2] != 0.0) &&
       (p->periodic[1] || p->u_wall_ymax[1] != 0.0))
     st = -1;
+  /* the velocity inlet / zero-gradient outlet closes the x axis of the flow lattice, needs the
+     channel walls on y, and is defined for one component without Shan-Chen forces */
+  if (p && !st && p->flow_open_x &&
+      (p->periodic[0] || p->periodic[1] || p->nx < 2 || p->n_comp != 1 || p->G[0][0] != 0.0 ||
+       p->G_ads[0] != 0.0 || p->rho_solid != 0.0))
+    st = -1;
   if (st) {
     if (status) *status = st;
     return NULL;
@@ -555,6 +561,17 @@ static void stream(orc_ctx* c) {
         int64_t src = nbr(c, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2], c->p.periodic);
         if (is_fluid_idx(c, src)) {
           c->f[s][n * Qf + i] = c->fp[s][src * Qf + i];          /* Eq. 5 */
+        } else if (src < 0 && c->p.flow_open_x && x - L->c[i][0] < 0) {
+          /* velocity inlet (Sec. 3.4): bounce-back off a face moving with the inlet profile
+             u_x = 6 U s (1 - s), s = (y + 1/2) / ny, carrying 2 w rho (c . u) / c_s^2 */
+          const double sy = ((double)y + 0.5) / (double)c->p.ny;
+          const double ux = 6.0 * c->p.u_in * sy * (1.0 - sy);
+          c->f[s][n * Qf + i] =
+              c->fp[s][n * Qf + L->opp[i]] + 6.0 * L->w[i] * c->rho[s][n] * ((double)L->c[i][0] * ux);
+        } else if (src < 0 && c->p.flow_open_x && x - L->c[i][0] >= c->p.nx) {
+          /* zero-gradient outlet: f_i(nx-1) takes the post-collision f_i of the node itself,
+             as the scalar outlet does */
+          c->f[s][n * Qf + i] = c->fp[s][n * Qf + i];
         } else {
           double v = c->fp[s][n * Qf + L->opp[i]];                /* halfway bounce-back */
           if (src < 0 && y - L->c[i][1] >= c->p.ny) {

@@ -47,6 +47,11 @@ typedef struct orc_params {
   int32_t N_geo;               /* geometry flips evaluated every N_geo steps */
   double u_wall_ymax[3];       /* velocity of the closed face beyond y = ny-1 (moving-wall
                                   bounce-back, Sec. 3.1.1 Couette flow); needs periodic[1] == 0 */
+  int32_t flow_open_x;         /* 1: flow velocity inlet at x = 0 and zero-gradient outlet at
+                                  x = nx-1 (Sec. 3.4); needs periodic[0] == periodic[1] == 0 and
+                                  one component without Shan-Chen forces */
+  double u_in;                 /* mean inlet velocity U of the profile u_x = 6 U s (1 - s),
+                                  s = (y + 1/2) / ny */
 } orc_params;
 
 /* Monitor vector layout (doubles). */

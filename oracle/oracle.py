@@ -51,7 +51,8 @@ class OrcParams(C.Structure):
         ("k_react", C.c_double), ("ade_open_x", C.c_int32), ("C_in", C.c_double * 2),
         ("periodic", C.c_int32 * 3), ("geo_mode", C.c_int32), ("V_m", C.c_double),
         ("m_s0", C.c_double), ("DP", C.c_double), ("deposit_conservative", C.c_int32),
-        ("N_geo", C.c_int32), ("u_wall_ymax", C.c_double * 3),
+        ("N_geo", C.c_int32), ("u_wall_ymax", C.c_double * 3), ("flow_open_x", C.c_int32),
+        ("u_in", C.c_double),
     ]
 
 
@@ -144,6 +145,8 @@ def make_params(cfg: dict) -> OrcParams:
     uw = d.get("u_wall_ymax", [0.0, 0.0, 0.0])
     for a in range(3):
         p.u_wall_ymax[a] = float(uw[a])
+    p.flow_open_x = int(bool(d.get("flow_open_x", False)))
+    p.u_in = float(d.get("u_in", 0.0))
     return p
 
 

@@ -226,8 +226,18 @@ class NaiveLBM:
             for s in range(self.nc):
                 for i in range(Qf):
                     t = self._shift(x, y, z, self.cf[i], self.per_f)
+                    xt = x + self.cf[i][0]
                     if self._fluid(t):
                         fnew[s, i, t[2], t[1], t[0]] = fpost[s, i, z, y, x]
+                    elif t is None and cfg.get("flow_open_x", False) and xt < 0:
+                        # velocity inlet: a face moving with u_x = 6 U s (1 - s) reflects f_i
+                        sy = (y + 0.5) / ny
+                        uin = np.array([6.0 * cfg["u_in"] * sy * (1.0 - sy), 0.0, 0.0])
+                        fnew[s, self.of[i], z, y, x] = (fpost[s, i, z, y, x]
+                                                        - 2 * self.wf[i] * rho[n][s] * float(np.dot(self.cf[i], uin)) * 3.0)
+                    elif t is None and cfg.get("flow_open_x", False) and xt >= nx:
+                        # zero-gradient outlet: the entering population repeats the node's own
+                        fnew[s, self.of[i], z, y, x] = fpost[s, self.of[i], z, y, x]
                     else:
                         v = fpost[s, i, z, y, x]
                         if t is None and y + self.cf[i][1] >= ny:

@@ -564,3 +564,77 @@ def test_moving_wall_needs_closed_tangential_plate():
                 dict(periodic=[1, 0, 1], u_wall_ymax=[0.0, 0.01, 0])):
         with pytest.raises(Exception):
             Oracle(dict(dim=2, nx=4, ny=8, **bad))
+
+
+# ---------------------------------------------------------------- velocity inlet (Sec. 3.4)
+
+@pytest.mark.parametrize("dim,collision", [(2, "bgk"), (3, "mrt")])
+def test_velocity_inlet_mass_budget_per_step(dim, collision):
+    """Sec. 3.4 inlet u = 6y(1-y) (here u_x = 6 U s (1 - s), s = (y + 1/2) / ny) as a face moving
+    with that velocity: the populations arriving with c_x = +1 gain 2 w_i rho u_x / c_s^2 =
+    6 w_i rho u_x.  Those directions' weights sum to 1/6, so each inlet node gains exactly
+    rho u_x(y) per step.  The zero-gradient outlet gives each population entering through
+    x = nx - 1 the node's own post-collision value of the same direction, so each outlet node
+    loses its post-collision x momentum, j_x + F_x (collision keeps mass and adds the force).
+    Walls and solids move no mass.  So the total mass changes per step by
+    sum_inlet rho u_x - sum_outlet (j_x + F_x), computed here from the stored populations."""
+    nx, ny, nz = 10, 8, (5 if dim == 3 else 1)
+    U = 0.03
+    g = [2e-4, 0.0, 1e-4 if dim == 3 else 0.0]
+    cfg = dict(dim=dim, nx=nx, ny=ny, nz=nz, tau=[0.8], collision=collision, flow_open_x=True, u_in=U,
+               g=g, periodic=[0, 0, 1])
+    shape = (nz, ny, nx)
+    geom = inputs.random_solids(shape, 0.15, seed=41, reactive_fraction=0.0)
+    geom[:, :, 0] = 0
+    geom[:, :, -1] = 0
+    rho, u, _ = inputs.perturbed_fields(shape, 1, 0, seed=42, amp_rho=0.02, amp_u=0.01)
+    o = make(cfg, geom, (rho, u, None))
+    o.step(4)
+    cv, _ = o.lattice(0)
+    sy = (np.arange(ny) + 0.5) / ny
+    u_in = 6.0 * U * sy * (1.0 - sy)
+    fluid = geom == 0
+    for _ in range(3):
+        f, _ = o.pops()
+        fr = f[0].reshape((len(cv),) + shape)
+        r = fr.sum(axis=0)
+        jx = np.tensordot(cv[:, 0].astype(float), fr, axes=1)
+        inflow = float((r[:, :, 0] * u_in[None, :]).sum())
+        outflow = float((jx[:, :, -1] + r[:, :, -1] * g[0]).sum())
+        m0 = float(r[fluid].sum())
+        o.step(1)
+        m1 = o.monitors()["mass0"]
+        assert abs((m1 - m0) - (inflow - outflow)) < 1e-13 * m0, (m1 - m0, inflow - outflow)
+        assert inflow > 0.5 * U * ny * nz
+
+
+def test_velocity_inlet_profile_is_carried_downstream():
+    """The inlet profile 6 U s (1 - s) is the developed plane-Poiseuille profile between walls at
+    y = -1/2 and y = ny - 1/2, where halfway bounce-back puts the BGK no-slip wall exactly for
+    (tau - 1/2)^2 = 3/16.  At steady state the mass flux sum_y rho u_x through every column equals
+    what the inlet injects, and mid-channel the profile keeps the parabolic shape (its amplitude
+    grows slightly downstream as the density falls along the pressure drop)."""
+    nx, ny, U = 40, 12, 0.01
+    o = make(dict(dim=2, nx=nx, ny=ny, tau=[0.5 + np.sqrt(3.0) / 4.0], flow_open_x=True, u_in=U,
+                  periodic=[0, 0, 1]))
+    o.step(6000)
+    f = o.fields()
+    ux, r = f["u"][0, 0], f["rho"][0, 0]
+    sy = (np.arange(ny) + 0.5) / ny
+    shape = 6.0 * sy * (1.0 - sy)
+    q_in = float((r[:, 0] * U * shape).sum())
+    for x in range(nx):
+        assert abs(float((r[:, x] * ux[:, x]).sum()) / q_in - 1.0) < 1e-5, x
+    col = ux[:, nx // 2]
+    a = float(col @ shape / (shape @ shape))
+    assert abs(a / U - 1.0) < 0.02
+    assert np.abs(col - a * shape).max() < 2e-4 * U
+    assert np.abs(f["u"][1, 0, :, nx // 2]).max() < 1e-3 * U
+
+
+def test_velocity_inlet_needs_a_closed_channel():
+    for bad in (dict(periodic=[1, 0, 1]), dict(periodic=[0, 1, 1]),
+                dict(periodic=[0, 0, 1], n_comp=2, tau=[1.0, 1.0]),
+                dict(periodic=[0, 0, 1], G=[[-5.0, 0], [0, 0]])):
+        with pytest.raises(Exception):
+            Oracle(dict(dim=2, nx=8, ny=8, flow_open_x=True, u_in=0.01, **bad))
