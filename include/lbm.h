@@ -105,6 +105,14 @@ typedef struct lbm_params {
                                  Sec. 3.1.1 Couette flow): its links reflect with Ladd's momentum
                                  term 2 w_i rho (c_i . u) / c_s^2.  Needs periodic[1] == 0 and a
                                  tangential velocity (component 1 zero); zero disables it. */
+  int32_t flow_open_x;        /* 1: the flow lattice has a velocity inlet at x = 0 and a zero-gradient
+                                 outlet at x = nx-1 (Sec. 3.4).  Links leaving through x = 0
+                                 reflect off a face moving with u_x = 6 u_in s (1 - s),
+                                 s = (y + 1/2) / ny (Ladd's term 2 w_i rho (c_i . u) / c_s^2); the
+                                 population entering through x = nx-1 repeats the node's own
+                                 post-collision value.  Needs periodic[0] == periodic[1] == 0,
+                                 nx >= 2 and one component without Shan-Chen or adhesion forces. */
+  double u_in;                /* mean velocity U of the inlet profile (flow_open_x only) */
 } lbm_params;
 
 /* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */

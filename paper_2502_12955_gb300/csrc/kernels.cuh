@@ -137,6 +137,8 @@ struct Args {
   FastDiv div_x, div_y;      // node index / nx, (node index / nx) / ny
   double u_wall[3];          // velocity of the top plate beyond y = ny - 1
   int moving_wall;           // the top plate moves (closed y axis)
+  int flow_open_x;           // flow velocity inlet at x = 0, zero-gradient outlet at x = nx - 1
+  double* u_in_row;          // [ny] inlet velocity u_x(y)
 };
 
 // Index guard of the bounds-checked build (-DLBM_BOUNDS_CHECK): an index outside [0, bound)
@@ -718,10 +720,21 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
   // ---- scatter flow
   // a node under a moving top plate (Sec. 3.1.1): links through the face beyond y = ny - 1
   // reflect with Ladd's momentum exchange 2 w_i rho (c_i . u_wall) / c_s^2
-  bool top = false;
-  if (a.moving_wall) {
+  // a node on the inlet face (Sec. 3.4): links leaving through x = 0 reflect off a face moving
+  // with the inlet profile (the same momentum exchange); on the outlet face the population
+  // entering through x = nx - 1 repeats the node's own post-collision value (zero gradient)
+  bool top = false, xin = false, xout = false;
+  T uin = T(0);
+  if (a.moving_wall || a.flow_open_x) {
     const unsigned int q = fast_div(unsigned(n), a.div_x);
-    top = int(q - fast_div(q, a.div_y) * unsigned(a.ny)) == a.ny - 1;
+    const int yy = int(q - fast_div(q, a.div_y) * unsigned(a.ny));
+    top = a.moving_wall && yy == a.ny - 1;
+    if (a.flow_open_x) {
+      const int xx = n - int(q) * a.nx;
+      xin = xx == 0;
+      xout = xx == a.nx - 1;
+      if (xin) uin = T(a.u_in_row[yy]);
+    }
   }
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
@@ -731,7 +744,11 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
       T v = f[s][i];
       if (parity == 0 || i == 0 || flow_wall<L>(m, i)) {
         p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + LBM_CHK(a.err, sn, a.pitch);
-        if (L::cy(i) > 0 && top && flow_wall<L>(m, i))
+        if (L::cx(i) < 0 && xin && flow_wall<L>(m, i))
+          v += T(6.0 * L::w(i)) * rho[s] * uin;
+        else if (L::cx(i) > 0 && xout && flow_wall<L>(m, i))
+          v = f[s][L::opp(i)];
+        else if (L::cy(i) > 0 && top && flow_wall<L>(m, i))
           v -= T(L::w(i)) * rho[s] * (T(L::cx(i)) * k.uw6[0] + T(L::cz(i)) * k.uw6[2] + k.uw6[1]);
       } else {
         p = reinterpret_cast<S*>(a.fplane[s][i]) +

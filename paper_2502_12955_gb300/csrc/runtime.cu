@@ -153,6 +153,13 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
     if (p->periodic[1]) return fail(c, LBM_ERR_INVALID_ARG, "a moving top plate needs a closed y axis");
     if (p->u_wall_ymax[1] != 0.0) return fail(c, LBM_ERR_INVALID_ARG, "the top plate moves in its own plane");
   }
+  if (p->flow_open_x) {
+    if (p->periodic[0] || p->periodic[1])
+      return fail(c, LBM_ERR_INVALID_ARG, "a velocity inlet needs closed x and y axes");
+    if (nx < 2) return fail(c, LBM_ERR_INVALID_ARG, "a velocity inlet needs nx >= 2");
+    if (p->n_comp != 1 || p->G[0][0] != 0.0 || p->G_ads[0] != 0.0 || p->rho_solid != 0.0)
+      return fail(c, LBM_ERR_INVALID_ARG, "a velocity inlet needs one component without Shan-Chen forces");
+  }
   return LBM_OK;
 }
 
@@ -224,6 +231,7 @@ void fill_args(lbm_ctx* c) {
   a.div_y = make_fast_div(c->ny);
   for (int k = 0; k < 3; ++k) a.u_wall[k] = p.u_wall_ymax[k];
   a.moving_wall = (p.u_wall_ymax[0] != 0.0 || p.u_wall_ymax[2] != 0.0) ? 1 : 0;
+  a.flow_open_x = p.flow_open_x ? 1 : 0;
 }
 
 int parity_of(long long step) { return int(step & 1); }
@@ -539,6 +547,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     DA(a.block_counts_v, ((pos + 1023) / 1024 + 1) * 4);
   }
   DA(a.wallx_slot, WALLX_SLOTS * 8);
+  DA(a.u_in_row, ny * 8);
   DA(a.iface_list, N * 4);
   DA(a.iface_count, 16);
   DA(a.listed, (N + 3) / 4 * 4);
@@ -576,6 +585,16 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   for (int s = 0; s < params->n_comp && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.f[s], 0, P * c->Qf * c->elem, c->stream);
   for (int s = 0; s < params->n_scal && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem, c->stream);
   if (e == cudaSuccess) e = launch_iota(a.slot, N, c->stream);   // node order until a geometry is set
+  if (e == cudaSuccess) {
+    // inlet profile u_x(y) = 6 U s (1 - s), s = (y + 1/2) / ny (zero without a velocity inlet)
+    std::vector<double> row(ny, 0.0);
+    if (params->flow_open_x)
+      for (int y = 0; y < ny; ++y) {
+        const double sy = ((double)y + 0.5) / (double)ny;
+        row[y] = 6.0 * params->u_in * sy * (1.0 - sy);
+      }
+    e = cudaMemcpyAsync(a.u_in_row, row.data(), ny * 8, cudaMemcpyHostToDevice, c->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "initial memset"));
   *out = c;

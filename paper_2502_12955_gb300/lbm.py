@@ -52,6 +52,7 @@ class LbmParams(C.Structure):
         ("N_geo", C.c_int32), ("N_mon", C.c_int32), ("rho_ref", C.c_double * 2),
         ("C_ref", C.c_double * 2), ("stream", C.c_void_p), ("block_x", C.c_int32),
         ("device", C.c_int32), ("l2_fetch_bytes", C.c_int32), ("u_wall_ymax", C.c_double * 3),
+        ("flow_open_x", C.c_int32), ("u_in", C.c_double),
     ]
 
 
@@ -195,6 +196,8 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     uw = d.get("u_wall_ymax", [0.0, 0.0, 0.0])
     for a in range(3):
         p.u_wall_ymax[a] = float(uw[a])
+    p.flow_open_x = int(bool(d.get("flow_open_x", False)))
+    p.u_in = float(d.get("u_in", 0.0))
     return p
 
 

@@ -264,3 +264,43 @@ def test_couette_moving_plate(dim, steps):
     prof = s.fields()["u"][0].mean(axis=(0, 2))
     exact = U * (np.arange(ny) + 0.5) / ny
     assert np.abs(prof - exact).max() < 1e-4 * U, np.abs(prof - exact).max()   # FP32 storage of O(1) values
+
+
+@pytest.mark.parametrize("dim,steps", [(2, 61), (2, 60), (3, 41)])
+def test_velocity_inlet_channel(dim, steps):
+    """Sec. 3.4: flow velocity inlet u_x = 6 U s (1 - s) at x = 0 and zero-gradient outlet at
+    x = nx - 1.  2D: BGK with the reactive scalar's inlet / outlet on the same faces and random
+    solids (reactive and inert).  3D: MRT with a moving top plate meeting the inlet at the
+    corner links, a body force and two scalars."""
+    if dim == 2:
+        nx, ny, nz = 26, 14, 1
+        cfg = dict(dim=2, nx=nx, ny=ny, tau=[0.8], flow_open_x=True, u_in=0.03, n_scal=1, tau_c=[0.7],
+                   J0=0.4, k_react=0.05, ade_open_x=True, C_in=[1.0], periodic=[0, 0, 1])
+    else:
+        nx, ny, nz = 16, 10, 8
+        cfg = dict(dim=3, nx=nx, ny=ny, nz=nz, tau=[0.9], collision="mrt", flow_open_x=True, u_in=0.02,
+                   u_wall_ymax=[0.01, 0, 0.005], g=[0, 0, 1e-4], n_scal=2, tau_c=[0.6, 0.9], J0=0.25,
+                   k_react=0.03, periodic=[0, 0, 1])
+    shape = (nz, ny, nx)
+    geom = inputs.random_solids(shape, 0.12, seed=33 + dim)
+    rho, u, C = inputs.perturbed_fields(shape, 1, cfg["n_scal"], seed=34, amp_rho=0.01, amp_u=0.01)
+    o, g = make_pair(cfg, geom, (rho, u, C))
+    o.step(steps)
+    g.step(steps)
+    compare(o, g, what=f"velocity inlet {dim}d")
+
+
+def test_velocity_inlet_steady_channel_fp32():
+    """The converged FP32 channel against the converged FP64 oracle: the inlet parabola carried to
+    the outlet with the mass flux of the inlet in every column."""
+    nx, ny, U = 40, 12, 0.01
+    cfg = dict(dim=2, nx=nx, ny=ny, tau=[0.5 + np.sqrt(3.0) / 4.0], flow_open_x=True, u_in=U,
+               periodic=[0, 0, 1])
+    shape = (1, ny, nx)
+    fields = inputs.uniform_fields(shape, 1, 0)
+    o, g = make_pair(cfg, np.zeros(shape, np.uint8), fields, precision="fp32")
+    o.step(6000)
+    g.step(6000)
+    fo, fg = o.fields(), g.fields()
+    assert rel_l2(fo["rho"], fg["rho"]) < 1e-6
+    assert rel_l2(fo["u"], fg["u"]) < 1e-4
