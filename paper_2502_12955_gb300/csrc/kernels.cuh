@@ -519,7 +519,7 @@ __device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, cons
 
 // Everything after the gather for one fluid node: wet-node closure and its bookkeeping,
 // deposition, moments, forces, velocity, flow and scalar collision, in-place scatter.
-template <class L, class S, int NC, int NS, int COLL, int parity>
+template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
 __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typename Store<S>::T>& k, int n,
                                                 uint32_t m, long long sn,
                                                 typename Store<S>::T (&f)[NC][L::Q],
@@ -723,9 +723,10 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
   // a node on the inlet face (Sec. 3.4): links leaving through x = 0 reflect off a face moving
   // with the inlet profile (the same momentum exchange); on the outlet face the population
   // entering through x = nx - 1 repeats the node's own post-collision value (zero gradient)
+  // (BND: the kernel variant for contexts with a moving plate or a velocity inlet)
   bool top = false, xin = false, xout = false;
   T uin = T(0);
-  if (a.moving_wall || a.flow_open_x) {
+  if (BND && (a.moving_wall || a.flow_open_x)) {
     const unsigned int q = fast_div(unsigned(n), a.div_x);
     const int yy = int(q - fast_div(q, a.div_y) * unsigned(a.ny));
     top = a.moving_wall && yy == a.ny - 1;
@@ -742,19 +743,26 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
     for (int i = 0; i < Q; ++i) {
       S* p;
       T v = f[s][i];
+      bool keep = true;
       if (parity == 0 || i == 0 || flow_wall<L>(m, i)) {
         p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + LBM_CHK(a.err, sn, a.pitch);
-        if (L::cx(i) < 0 && xin && flow_wall<L>(m, i))
-          v += T(6.0 * L::w(i)) * rho[s] * uin;
-        else if (L::cx(i) > 0 && xout && flow_wall<L>(m, i))
-          v = f[s][L::opp(i)];
-        else if (L::cy(i) > 0 && top && flow_wall<L>(m, i))
-          v -= T(L::w(i)) * rho[s] * (T(L::cx(i)) * k.uw6[0] + T(L::cz(i)) * k.uw6[2] + k.uw6[1]);
+        if (BND) {
+          if (L::cx(i) < 0 && xin && flow_wall<L>(m, i))
+            v += T(6.0 * L::w(i)) * rho[s] * uin;
+          else if (L::cx(i) > 0 && xout)
+            keep = false;   // leaves through the outlet; the cell is written below with opp(i)
+          else if (L::cy(i) > 0 && top && flow_wall<L>(m, i))
+            v -= T(L::w(i)) * rho[s] * (T(L::cx(i)) * k.uw6[0] + T(L::cz(i)) * k.uw6[2] + k.uw6[1]);
+        }
       } else {
         p = reinterpret_cast<S*>(a.fplane[s][i]) +
             LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N)), a.pitch);
       }
-      Store<S>::st(p, v);
+      if (keep) Store<S>::st(p, v);
+      // zero-gradient outlet: the population entering through x = nx - 1 with direction i
+      // repeats the node's own post-collision f_i, in the cell where link opp(i) reflects
+      if (BND && L::cx(i) < 0 && xout)
+        Store<S>::st(reinterpret_cast<S*>(a.fplane[s][i]) + LBM_CHK(a.err, sn, a.pitch), f[s][i]);
     }
   }
   // ---- scatter scalars: bounce-back at walls, inlet ghost / zero-gradient outlet at open faces
@@ -797,7 +805,7 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
 // bookkeeping, deposition, moments, forces, velocity, flow collision (BGK / MRT, Guo or
 // velocity shift), scalar collision, in-place scatter with bounce-back / inlet / outlet.
 // Registers hold deviations from w_i * ref throughout.
-template <class L, class S, int NC, int NS, int COLL, int parity>
+template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
 __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC, NSD = NS > 0 ? NS : 1;
@@ -820,7 +828,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
     T f[NC][Q], h[NSD][QC];
     gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
     const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-    collide_scatter<L, S, NC, NS, COLL, parity>(a, k, n, m, sn, f, h, wallx);
+    collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, k, n, m, sn, f, h, wallx);
   }
   // ---- wall-exchange monitor: one reduction per warp that saw a reactive link
   if (NS > 0) {
@@ -844,7 +852,7 @@ struct Tile {
 // One time step of every member of an ensemble in one launch.  Blocks walk a work list of
 // tiles; for each tile they stage the member's arguments and constants in shared memory and
 // update entries first .. first + blockDim - 1 exactly as k_step updates them.
-template <class L, class S, int NC, int NS, int COLL, int parity>
+template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
 __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step_tiles(
     const Args* __restrict__ args, const Coef<typename Store<S>::T>* __restrict__ coefs,
     const Tile* __restrict__ tiles, unsigned int ntiles) {
@@ -876,7 +884,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         T f[NC][Q], h[NSD][QC];
         gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
         const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-        collide_scatter<L, S, NC, NS, COLL, parity>(a, sk, n, m, sn, f, h, wallx);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx);
       }
     }
     if (NS > 0) {

@@ -24,7 +24,7 @@ struct KernelSet {
   // step of every tile
   void (*coefs)(const Args* a, int n, void* out);
   cudaError_t (*step_tiles)(const Args* d_args, const void* d_coefs, const Tile* d_tiles, unsigned int ntiles,
-                            int n_comp, int n_scal, int coll, int parity, int threads, cudaStream_t);
+                            int n_comp, int n_scal, int coll, int parity, int bnd, int threads, cudaStream_t);
   int psi_bytes;   // bytes per psi element (compute type)
   int coef_bytes;
 };
@@ -92,7 +92,7 @@ struct Launchers {
   static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
 
   // one resident wave of blocks; the kernel walks the fluid list with a grid-stride loop
-  template <int NC, int NS, int COLL, int PAR>
+  template <int NC, int NS, int COLL, int PAR, bool BND>
   static cudaError_t step_p(const Args& a, cudaStream_t st) {
     const int threads = a.bx;
     static int cached_threads = -1, cached_blocks = 0;
@@ -100,18 +100,21 @@ struct Launchers {
       int dev = 0, sms = 0, occ = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL, PAR>, threads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<L, S, NC, NS, COLL, PAR, BND>, threads, 0);
       cached_blocks = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
       cached_threads = threads;
     }
     long long need = (a.N + threads - 1) / threads;
     const unsigned int blocks = (unsigned int)(need < cached_blocks ? need : cached_blocks);
-    k_step<L, S, NC, NS, COLL, PAR><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a));
+    k_step<L, S, NC, NS, COLL, PAR, BND><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a));
     return cudaGetLastError();
   }
+  // BND: a moving plate or a velocity inlet needs the boundary-rule variant of the step kernel
   template <int NC, int NS, int COLL>
   static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
-    return parity ? step_p<NC, NS, COLL, 1>(a, st) : step_p<NC, NS, COLL, 0>(a, st);
+    if (a.moving_wall || a.flow_open_x)
+      return parity ? step_p<NC, NS, COLL, 1, true>(a, st) : step_p<NC, NS, COLL, 0, true>(a, st);
+    return parity ? step_p<NC, NS, COLL, 1, false>(a, st) : step_p<NC, NS, COLL, 0, false>(a, st);
   }
   template <int NC, int NS>
   static cudaError_t step_c(const Args& a, int parity, int coll, cudaStream_t st) {
@@ -232,38 +235,47 @@ struct Launchers {
     Coef<T>* o = static_cast<Coef<T>*>(out);
     for (int i = 0; i < n; ++i) o[i] = coef(a[i]);
   }
-  template <int NC, int NS, int COLL, int PAR>
+  template <int NC, int NS, int COLL, int PAR, bool BND>
   static cudaError_t step_tiles_p(const Args* d_args, const void* d_coefs, const Tile* d_tiles, unsigned int ntiles,
                                   int threads, cudaStream_t st) {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tiles<L, S, NC, NS, COLL, PAR>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tiles<L, S, NC, NS, COLL, PAR, BND>, threads, 0);
     const unsigned int wave = (unsigned int)((occ > 0 ? occ : 1) * (sms > 0 ? sms : 1));
     const unsigned int blocks = ntiles < wave ? (ntiles > 0 ? ntiles : 1) : wave;
-    k_step_tiles<L, S, NC, NS, COLL, PAR><<<blocks, threads, 0, st>>>(
+    k_step_tiles<L, S, NC, NS, COLL, PAR, BND><<<blocks, threads, 0, st>>>(
         d_args, static_cast<const Coef<T>*>(d_coefs), d_tiles, ntiles);
     return cudaGetLastError();
   }
+  template <int NC, int NS, int COLL>
+  static cudaError_t step_tiles_b(const Args* d, const void* k, const Tile* t, unsigned int nt, int parity, int bnd,
+                                  int threads, cudaStream_t st) {
+    if (bnd)
+      return parity ? step_tiles_p<NC, NS, COLL, 1, true>(d, k, t, nt, threads, st)
+                    : step_tiles_p<NC, NS, COLL, 0, true>(d, k, t, nt, threads, st);
+    return parity ? step_tiles_p<NC, NS, COLL, 1, false>(d, k, t, nt, threads, st)
+                  : step_tiles_p<NC, NS, COLL, 0, false>(d, k, t, nt, threads, st);
+  }
   template <int NC, int NS>
   static cudaError_t step_tiles_c(const Args* d, const void* k, const Tile* t, unsigned int nt, int coll, int parity,
-                                  int threads, cudaStream_t st) {
+                                  int bnd, int threads, cudaStream_t st) {
     if (coll == 1) {
       if (NC != 1) return cudaErrorInvalidValue;
-      return parity ? step_tiles_p<1, NS, 1, 1>(d, k, t, nt, threads, st) : step_tiles_p<1, NS, 1, 0>(d, k, t, nt, threads, st);
+      return step_tiles_b<1, NS, 1>(d, k, t, nt, parity, bnd, threads, st);
     }
-    return parity ? step_tiles_p<NC, NS, 0, 1>(d, k, t, nt, threads, st) : step_tiles_p<NC, NS, 0, 0>(d, k, t, nt, threads, st);
+    return step_tiles_b<NC, NS, 0>(d, k, t, nt, parity, bnd, threads, st);
   }
   static cudaError_t step_tiles(const Args* d, const void* k, const Tile* t, unsigned int nt, int n_comp, int n_scal,
-                                int coll, int parity, int threads, cudaStream_t st) {
+                                int coll, int parity, int bnd, int threads, cudaStream_t st) {
     if (n_comp == 1) {
-      if (n_scal == 0) return step_tiles_c<1, 0>(d, k, t, nt, coll, parity, threads, st);
-      if (n_scal == 1) return step_tiles_c<1, 1>(d, k, t, nt, coll, parity, threads, st);
-      return step_tiles_c<1, 2>(d, k, t, nt, coll, parity, threads, st);
+      if (n_scal == 0) return step_tiles_c<1, 0>(d, k, t, nt, coll, parity, bnd, threads, st);
+      if (n_scal == 1) return step_tiles_c<1, 1>(d, k, t, nt, coll, parity, bnd, threads, st);
+      return step_tiles_c<1, 2>(d, k, t, nt, coll, parity, bnd, threads, st);
     }
-    if (n_scal == 0) return step_tiles_c<2, 0>(d, k, t, nt, coll, parity, threads, st);
-    if (n_scal == 1) return step_tiles_c<2, 1>(d, k, t, nt, coll, parity, threads, st);
-    return step_tiles_c<2, 2>(d, k, t, nt, coll, parity, threads, st);
+    if (n_scal == 0) return step_tiles_c<2, 0>(d, k, t, nt, coll, parity, bnd, threads, st);
+    if (n_scal == 1) return step_tiles_c<2, 1>(d, k, t, nt, coll, parity, bnd, threads, st);
+    return step_tiles_c<2, 2>(d, k, t, nt, coll, parity, bnd, threads, st);
   }
 
   static KernelSet make() {

@@ -1177,8 +1177,10 @@ lbm_status ens_prepare(lbm_ensemble* e) {
 lbm_status ens_launch(lbm_ensemble* e, int parity, cudaStream_t st) {
   if (e->ntiles == 0) return LBM_OK;
   const lbm_params& p = e->m[0]->p;
+  int bnd = 0;   // the boundary-rule kernel variant when any member has a moving plate or an inlet
+  for (size_t k = 0; k < e->m.size(); ++k) bnd |= e->m[k]->a.moving_wall | e->m[k]->a.flow_open_x;
   const cudaError_t r = e->ks->step_tiles(e->d_args, e->d_coefs, e->d_tiles, e->ntiles, p.n_comp, p.n_scal,
-                                          p.collision, parity, e->threads, st);
+                                          p.collision, parity, bnd, e->threads, st);
   e->launches += 1;
   if (r != cudaSuccess) return efail(e, LBM_ERR_CUDA, "ensemble step: %s", cudaGetErrorString(r));
   return LBM_OK;

@@ -96,6 +96,21 @@ def droplet_fields(shape, radius: float, rho_in: float = 1.0, rho_out: float = 0
     return rho, u
 
 
+def sessile_droplet_2d(nx=200, ny=80, radius=30.0, G=2.7, g_ads=0.0, precision="fp32"):
+    """Two-component Shan-Chen sessile droplet for the contact angle (Sec. 3.2, contact angle):
+    a half disc of component 0 (density 1.0, 0.05 of component 1) centred on the bottom wall
+    (the halfway face y = -1/2 of a closed y axis), component 1 elsewhere; psi = rho, cross
+    cohesion G, adhesion G_ads = (g, -g), periodic x, tau 1."""
+    cfg = dict(dim=2, nx=nx, ny=ny, nz=1, n_comp=2, tau=[1.0, 1.0], G=[[0.0, G], [G, 0.0]],
+               psi_kind="identity", G_ads=[g_ads, -g_ads], periodic=[1, 0, 1], precision=precision)
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    inside = (xx - nx / 2.0) ** 2 + (yy + 0.5) ** 2 < radius * radius
+    rho = np.empty((2, 1, ny, nx))
+    rho[0, 0] = np.where(inside, 1.0, 0.05)
+    rho[1, 0] = np.where(inside, 0.05, 1.0)
+    return cfg, np.zeros((1, ny, nx), np.uint8), (rho, np.zeros((3, 1, ny, nx)), None)
+
+
 def uniform_fields(shape, n_comp: int = 1, n_scal: int = 0, rho=1.0, C=0.0, u=(0.0, 0.0, 0.0)):
     rho_a = np.empty((n_comp,) + tuple(shape))
     for s in range(n_comp):
