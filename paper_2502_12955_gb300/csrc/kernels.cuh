@@ -403,6 +403,57 @@ __device__ __forceinline__ void gather_entry(const Args& a, unsigned int e, unsi
   for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s], a.err, a.N, a.pitch);
 }
 
+// Neighbour-slot cache of the odd step.  An odd step reads cell (n - c_i, opp i) and writes
+// cell (n + c_i, i): every neighbour slot it needs on the way in, it needs again on the way out,
+// and the scalar lattice's axis links use the flow lattice's neighbours.  The gather of the first
+// flow component looks each slot up once and keeps it in shared memory, in row i for the
+// neighbour n + c_i (row-major [direction][thread], rows of LBM_SLOT_CACHE_STRIDE threads);
+// the later gathers and the scatters read it back.  A scalar link to a fluid neighbour is always
+// a fluid flow link too, so every row they read was written.
+#define LBM_SLOT_CACHE_STRIDE 256   // >= the largest step block (256 threads)
+#ifndef LBM_ODD_SLOT_CACHE
+#define LBM_ODD_SLOT_CACHE 1
+#endif
+template <class L, class S, int NC, int NS>
+__device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long sn, int n, uint32_t m,
+                                                        uint32_t* cache, typename Store<S>::T (&f)[NC][L::Q],
+                                                        typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC]) {
+  const Nbr nb = nbr_of(a, n);
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const S* p;
+      if (i == 0 || flow_wall<L>(m, L::opp(i))) {
+        p = reinterpret_cast<const S*>(a.fplane[s][i]) + LBM_CHK(a.err, sn, a.pitch);
+      } else {
+        uint32_t q;
+        if (s == 0) {
+          q = (uint32_t)LBM_CHK(a.err, __ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(i), -L::cy(i), -L::cz(i)), a.N)),
+                                a.pitch);
+          cache[(L::opp(i) - 1) * LBM_SLOT_CACHE_STRIDE] = q;
+        } else {
+          q = cache[(L::opp(i) - 1) * LBM_SLOT_CACHE_STRIDE];
+        }
+        p = reinterpret_cast<const S*>(a.fplane[s][L::opp(i)]) + q;
+      }
+      f[s][i] = Store<S>::ld(p);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int j = 0; j < L::QC; ++j) {
+      const S* p;
+      if (j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
+        p = reinterpret_cast<const S*>(a.hplane[s][j]) + LBM_CHK(a.err, sn, a.pitch);
+      else
+        p = reinterpret_cast<const S*>(a.hplane[s][L::opp(j)]) + cache[(L::opp(j) - 1) * LBM_SLOT_CACHE_STRIDE];
+      h[s][j] = Store<S>::ld(p);
+    }
+  }
+}
+
 // ------------------------------------------------------------- collision helpers
 
 // Fused multiply-add of the compute types.
@@ -519,12 +570,12 @@ __device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, cons
 
 // Everything after the gather for one fluid node: wet-node closure and its bookkeeping,
 // deposition, moments, forces, velocity, flow and scalar collision, in-place scatter.
-template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
+template <class L, class S, int NC, int NS, int COLL, int parity, bool BND, bool CACHE = false>
 __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typename Store<S>::T>& k, int n,
                                                 uint32_t m, long long sn,
                                                 typename Store<S>::T (&f)[NC][L::Q],
                                                 typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC],
-                                                typename Store<S>::T& wallx) {
+                                                typename Store<S>::T& wallx, const uint32_t* cache = nullptr) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const Nbr nb = nbr_of(a, n);
@@ -755,8 +806,11 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
             v -= T(L::w(i)) * rho[s] * (T(L::cx(i)) * k.uw6[0] + T(L::cz(i)) * k.uw6[2] + k.uw6[1]);
         }
       } else {
-        p = reinterpret_cast<S*>(a.fplane[s][i]) +
-            LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N)), a.pitch);
+        if (CACHE)
+          p = reinterpret_cast<S*>(a.fplane[s][i]) + cache[(i - 1) * LBM_SLOT_CACHE_STRIDE];
+        else
+          p = reinterpret_cast<S*>(a.fplane[s][i]) +
+              LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N)), a.pitch);
       }
       if (keep) Store<S>::st(p, v);
       // zero-gradient outlet: the population entering through x = nx - 1 with direction i
@@ -793,8 +847,11 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
       } else if (parity == 0 || j == 0 || code != 0u) {
         p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + LBM_CHK(a.err, sn, a.pitch);
       } else {
-        p = reinterpret_cast<S*>(a.hplane[s][j]) +
-            LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(j), L::cy(j), L::cz(j)), a.N)), a.pitch);
+        if (CACHE)
+          p = reinterpret_cast<S*>(a.hplane[s][j]) + cache[(j - 1) * LBM_SLOT_CACHE_STRIDE];
+        else
+          p = reinterpret_cast<S*>(a.hplane[s][j]) +
+              LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(j), L::cy(j), L::cz(j)), a.N)), a.pitch);
       }
       Store<S>::st(p, v);
     }
@@ -814,6 +871,10 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
   const unsigned int stride = gridDim.x * blockDim.x;
   unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
+#if LBM_ODD_SLOT_CACHE
+  __shared__ uint32_t slot_cache[parity ? (L::Q - 1) * LBM_SLOT_CACHE_STRIDE : 1];
+  uint32_t* cache = slot_cache + threadIdx.x;
+#endif
   // the list entry is fetched two iterations and the link mask one iteration ahead
   int n_next = e < count ? int(LBM_CHK(a.err, a.fluid_list[e], a.N)) : 0;
   int n_next2 = e + stride < count ? int(LBM_CHK(a.err, a.fluid_list[e + stride], a.N)) : 0;
@@ -826,6 +887,14 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
     if (e + 2 * stride < count) n_next2 = int(LBM_CHK(a.err, a.fluid_list[e + 2 * stride], a.N));
     if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
     T f[NC][Q], h[NSD][QC];
+#if LBM_ODD_SLOT_CACHE
+    if (parity) {
+      const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+      gather_entry_odd_cached<L, S, NC, NS>(a, sn, n, m, cache, f, h);
+      collide_scatter<L, S, NC, NS, COLL, parity, BND, true>(a, k, n, m, sn, f, h, wallx, cache);
+      continue;
+    }
+#endif
     gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
     const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
     collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, k, n, m, sn, f, h, wallx);
