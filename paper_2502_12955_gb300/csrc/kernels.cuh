@@ -930,6 +930,10 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   static_assert(sizeof(Args) % 4 == 0 && sizeof(Coef<T>) % 4 == 0, "word copies");
   __shared__ Args sa;
   __shared__ Coef<T> sk;
+#if LBM_ODD_SLOT_CACHE
+  __shared__ uint32_t slot_cache[parity ? (L::Q - 1) * LBM_SLOT_CACHE_STRIDE : 1];
+  uint32_t* cache = slot_cache + threadIdx.x;
+#endif
   for (unsigned int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tile = tiles[t];
     __syncthreads();   // the previous tile is done with sa / sk
@@ -951,9 +955,17 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       if (m & 1u) {
         const unsigned int base = a.fluid_count[1];
         T f[NC][Q], h[NSD][QC];
-        gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
         const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-        collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx);
+#if LBM_ODD_SLOT_CACHE
+        if (parity) {
+          gather_entry_odd_cached<L, S, NC, NS>(a, sn, n, m, cache, f, h);
+          collide_scatter<L, S, NC, NS, COLL, parity, BND, true>(a, sk, n, m, sn, f, h, wallx, cache);
+        } else
+#endif
+        {
+          gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
+          collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx);
+        }
       }
     }
     if (NS > 0) {
