@@ -9,6 +9,8 @@ flips, monitors every N_mon steps).  Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload dissolution|droplet|channel] [--precision fp32|fp16|bf16|fp64]
                   [--size S] [--no-e2e] [--no-cpu]
+  python bench.py --workload dissolution --size 128 --to-steady 1e-6
+                  (time to steady state from rest, geometry frozen; its own JSON line)
 """
 from __future__ import annotations
 
@@ -211,6 +213,9 @@ def parse():
     ap.add_argument("--l2-fetch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--to-steady", type=float, default=None,
+                    help="instead of the timed steps: run from rest to residual <= this tolerance")
+    ap.add_argument("--max-steps", type=int, default=2_000_000)
     return ap.parse_args()
 
 
@@ -337,6 +342,53 @@ def run_ensemble(args, dist, ws, rank, local):
         dist.destroy_process_group()
 
 
+def run_to_steady(args, local):
+    """Time to steady state of plain LBM from rest (the baseline a warm start is judged
+    against): the geometry update is frozen, the residual r (relative L2 change of u and C over
+    N_mon = 100 steps, the larger of the two) is evaluated on the device every 100 steps, and
+    the run stops at the first evaluation with r <= tol.  Wall time between CUDA events on the
+    solver's stream, including the host reads of r."""
+    import torch
+    from paper_2502_12955_gb300.lbm import Solver
+
+    precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
+    cfg, geom, fields, label = workload(args.workload, args.size, precision)
+    cfg = dict(cfg, device=local, geo_mode="none", N_mon=100)
+    stream = torch.cuda.Stream(device=local)
+    s = Solver(cfg, stream=stream.cuda_stream)
+    s.set_geometry(geom)
+    rho, u, C = fields
+    s.set_fields(rho, u, C if s.n_scal else None)
+    s.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    steps, r = 0, float("inf")
+    while steps < args.max_steps:
+        s.step(100)
+        steps += 100
+        r = s.monitors()["residual"]
+        if 0.0 <= r <= args.to_steady:
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    clk = clocks.stop()
+    line = {"metric": "time_to_steady", "value": sec, "unit": "s", "n_gpus": 1, "steps": steps,
+            "higher_is_better": False, "converged": bool(0.0 <= r <= args.to_steady),
+            "residual": r, "tol": args.to_steady, "start": "rest (uniform density, zero velocity)",
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math",
+                      "bf16": "bf16 storage, f32 math"}[precision],
+            "data": "synthetic (seeded geometry, inputs/ recipe), geometry update frozen",
+            "config": {"workload": label, "nodes": int(geom.size), "fluid_nodes": int((geom == 0).sum())},
+            "mlups": geom.size * steps / sec / 1e6, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -357,6 +409,10 @@ def main():
 
     if args.workload == "ensemble":
         run_ensemble(args, dist, ws, rank, local)
+        return
+    if args.to_steady is not None:
+        if rank == 0:
+            run_to_steady(args, local)
         return
     precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
     cfg, geom, fields, label = workload(args.workload, args.size, precision)

@@ -94,8 +94,8 @@ typedef struct lbm_params {
   double rho_ref[2];          /* storage shift references for 16-bit modes (flow) */
   double C_ref[2];            /* storage shift references for 16-bit modes (scalars) */
   void* stream;               /* cudaStream_t for all work of this context */
-  int32_t block_x;            /* threads per block along x for the step kernel: 0 (automatic)
-                                 or a multiple of 32 up to 256 */
+  int32_t block_x;            /* threads per block of the step kernel: 0 (automatic: 256) or a
+                                 multiple of 32 up to 256 */
   int32_t device;             /* CUDA device ordinal */
   int32_t l2_fetch_bytes;     /* L2 fetch granularity hint for this process's context
                                  (cudaLimitMaxL2FetchGranularity: 32, 64 or 128; 0, the default,

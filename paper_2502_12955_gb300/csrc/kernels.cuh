@@ -380,7 +380,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 #define LBM_STEP_MIN_BLOCKS 3   // resident 256-thread blocks per SM, one component in FP32 math (80 registers)
 #endif
 #ifndef LBM_STEP_MIN_BLOCKS_ODD
-#define LBM_STEP_MIN_BLOCKS_ODD 4   // the odd step waits on two dependent loads: more warps pay
+#define LBM_STEP_MIN_BLOCKS_ODD 3   // k_step's odd parity: the slot prefetch hides the lookups, registers pay
+#endif
+#ifndef LBM_TILES_MIN_BLOCKS_ODD
+#define LBM_TILES_MIN_BLOCKS_ODD 4  // k_step_tiles' odd parity waits on the lookups: more warps pay
 #endif
 
 // Neighbour offsets of fluid node n from its coordinates (fast divisions by nx and ny).
@@ -406,17 +409,19 @@ __device__ __forceinline__ void gather_entry(const Args& a, unsigned int e, unsi
 // Neighbour-slot cache of the odd step.  An odd step reads cell (n - c_i, opp i) and writes
 // cell (n + c_i, i): every neighbour slot it needs on the way in, it needs again on the way out,
 // and the scalar lattice's axis links use the flow lattice's neighbours.  The gather of the first
-// flow component looks each slot up once and keeps it in shared memory, in row i for the
-// neighbour n + c_i (row-major [direction][thread], rows of LBM_SLOT_CACHE_STRIDE threads);
-// the later gathers and the scatters read it back.  A scalar link to a fluid neighbour is always
-// a fluid flow link too, so every row they read was written.
-#define LBM_SLOT_CACHE_STRIDE 256   // >= the largest step block (256 threads)
+// flow component looks each slot up once and keeps it in shared memory, entry i - 1 for the
+// neighbour n + c_i; the later gathers and the scatters read it back.  A scalar link to a fluid
+// neighbour is always a fluid flow link too, so every entry they read was written.
 #ifndef LBM_ODD_SLOT_CACHE
 #define LBM_ODD_SLOT_CACHE 1
 #endif
+// k_step keeps the cache as rows of LBM_STEP_CACHE_STRIDE threads per direction (consecutive
+// threads in consecutive words; its blocks have at most that many threads); the ensemble's
+// tile kernel gives each thread Q consecutive words of dynamic shared memory instead, sized
+// to its block (Q - 1 used; the odd stride puts the threads of a warp on distinct banks).
+#define LBM_STEP_CACHE_STRIDE 256
 #ifndef LBM_ODD_SLOT_PREFETCH
-#define LBM_ODD_SLOT_PREFETCH 1   // the slots of the next node are copied in while this one runs (k_step;
-                                  // 1: where it pays, 2: every odd-parity variant)
+#define LBM_ODD_SLOT_PREFETCH 1   // k_step: the slots of the next node are copied in while this one runs
 #endif
 // Asynchronous copies (cp.async, sm_80 and later) of one 4-byte word from global to shared
 // memory; a thread waits for its own groups with cp_async_wait.
@@ -431,15 +436,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Start copying the slots of all Q - 1 neighbours n + c_i of node n into the cache rows (row i
 // for n + c_i), one step of the grid-stride loop ahead of their use.  Links into walls copy a
 // slot that is never read (the periodic image is always a valid node).
-template <class L>
+template <class L, int CS>
 __device__ __forceinline__ void prefetch_slots(const Args& a, int n, uint32_t* cache) {
   const Nbr nb = nbr_of(a, n);
 #pragma unroll
   for (int i = 1; i < L::Q; ++i)
-    cp_async4(cache + (i - 1) * LBM_SLOT_CACHE_STRIDE, a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N));
+    cp_async4(cache + (i - 1) * CS, a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N));
 }
 
-template <class L, class S, int NC, int NS, bool PREFETCHED = false>
+template <class L, class S, int NC, int NS, int CS, bool PREFETCHED = false>
 __device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long sn, int n, uint32_t m,
                                                         uint32_t* cache, typename Store<S>::T (&f)[NC][L::Q],
                                                         typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC]) {
@@ -454,13 +459,13 @@ __device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long
       } else {
         uint32_t q;
         if (s == 0 && PREFETCHED) {
-          q = (uint32_t)LBM_CHK(a.err, cache[(L::opp(i) - 1) * LBM_SLOT_CACHE_STRIDE], a.pitch);
+          q = (uint32_t)LBM_CHK(a.err, cache[(L::opp(i) - 1) * CS], a.pitch);
         } else if (s == 0) {
           q = (uint32_t)LBM_CHK(a.err, __ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(i), -L::cy(i), -L::cz(i)), a.N)),
                                 a.pitch);
-          cache[(L::opp(i) - 1) * LBM_SLOT_CACHE_STRIDE] = q;
+          cache[(L::opp(i) - 1) * CS] = q;
         } else {
-          q = cache[(L::opp(i) - 1) * LBM_SLOT_CACHE_STRIDE];
+          q = cache[(L::opp(i) - 1) * CS];
         }
         p = reinterpret_cast<const S*>(a.fplane[s][L::opp(i)]) + q;
       }
@@ -475,7 +480,7 @@ __device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long
       if (j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
         p = reinterpret_cast<const S*>(a.hplane[s][j]) + LBM_CHK(a.err, sn, a.pitch);
       else
-        p = reinterpret_cast<const S*>(a.hplane[s][L::opp(j)]) + cache[(L::opp(j) - 1) * LBM_SLOT_CACHE_STRIDE];
+        p = reinterpret_cast<const S*>(a.hplane[s][L::opp(j)]) + cache[(L::opp(j) - 1) * CS];
       h[s][j] = Store<S>::ld(p);
     }
   }
@@ -597,7 +602,7 @@ __device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, cons
 
 // Everything after the gather for one fluid node: wet-node closure and its bookkeeping,
 // deposition, moments, forces, velocity, flow and scalar collision, in-place scatter.
-template <class L, class S, int NC, int NS, int COLL, int parity, bool BND, bool CACHE = false>
+template <class L, class S, int NC, int NS, int COLL, int parity, bool BND, bool CACHE = false, int CS = 1>
 __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typename Store<S>::T>& k, int n,
                                                 uint32_t m, long long sn,
                                                 typename Store<S>::T (&f)[NC][L::Q],
@@ -834,7 +839,7 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
         }
       } else {
         if (CACHE)
-          p = reinterpret_cast<S*>(a.fplane[s][i]) + cache[(i - 1) * LBM_SLOT_CACHE_STRIDE];
+          p = reinterpret_cast<S*>(a.fplane[s][i]) + cache[(i - 1) * CS];
         else
           p = reinterpret_cast<S*>(a.fplane[s][i]) +
               LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N)), a.pitch);
@@ -875,7 +880,7 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
         p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + LBM_CHK(a.err, sn, a.pitch);
       } else {
         if (CACHE)
-          p = reinterpret_cast<S*>(a.hplane[s][j]) + cache[(j - 1) * LBM_SLOT_CACHE_STRIDE];
+          p = reinterpret_cast<S*>(a.hplane[s][j]) + cache[(j - 1) * CS];
         else
           p = reinterpret_cast<S*>(a.hplane[s][j]) +
               LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(j), L::cy(j), L::cz(j)), a.N)), a.pitch);
@@ -899,20 +904,17 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   const unsigned int stride = gridDim.x * blockDim.x;
   unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
   // Odd parity with two cache buffers: the neighbour slots of the next entry are copied
-  // asynchronously into one while the current entry works from the other.  Measured at 256^3
-  // and 128^3 it pays for two components (-8 %) and for 16-bit storage (-2 %), and costs 1 %
-  // for one FP32 component, which keeps the single buffer.
-  constexpr bool kPrefetch = LBM_ODD_SLOT_CACHE && LBM_ODD_SLOT_PREFETCH && parity == 1 &&
-                             (LBM_ODD_SLOT_PREFETCH == 2 || NC == 2 || sizeof(S) < 4);
+  // asynchronously into one while the current entry works from the other.
+  constexpr bool kPrefetch = LBM_ODD_SLOT_CACHE && LBM_ODD_SLOT_PREFETCH && parity == 1;
 #if LBM_ODD_SLOT_CACHE && LBM_ODD_SLOT_PREFETCH
   if (kPrefetch) {
-    __shared__ uint32_t slot_buf[kPrefetch ? 2 * (L::Q - 1) * LBM_SLOT_CACHE_STRIDE : 1];
+    __shared__ uint32_t slot_buf[kPrefetch ? 2 * (L::Q - 1) * LBM_STEP_CACHE_STRIDE : 1];
     uint32_t* cb = slot_buf + threadIdx.x;
-    uint32_t* cn = slot_buf + (L::Q - 1) * LBM_SLOT_CACHE_STRIDE + threadIdx.x;
+    uint32_t* cn = slot_buf + (L::Q - 1) * LBM_STEP_CACHE_STRIDE + threadIdx.x;
     int n_cur = e < count ? int(LBM_CHK(a.err, a.fluid_list[e], a.N)) : 0;
     int n_nx = e + stride < count ? int(LBM_CHK(a.err, a.fluid_list[e + stride], a.N)) : 0;
     uint32_t m_cur = e < count ? a.mask[n_cur] : 0u;
-    if (e < count) prefetch_slots<L>(a, n_cur, cb);
+    if (e < count) prefetch_slots<L, LBM_STEP_CACHE_STRIDE>(a, n_cur, cb);
     cp_async_commit();
     for (; e < count; e += stride) {
       const int n = n_cur;
@@ -920,7 +922,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       if (e + stride < count) {
         n_cur = n_nx;
         m_cur = a.mask[n_cur];
-        prefetch_slots<L>(a, n_cur, cn);
+        prefetch_slots<L, LBM_STEP_CACHE_STRIDE>(a, n_cur, cn);
       }
       if (e + 2 * stride < count) n_nx = int(LBM_CHK(a.err, a.fluid_list[e + 2 * stride], a.N));
       cp_async_commit();
@@ -928,8 +930,8 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       if (m & 1u) {
         T f[NC][Q], h[NSD][QC];
         const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-        gather_entry_odd_cached<L, S, NC, NS, true>(a, sn, n, m, cb, f, h);
-        collide_scatter<L, S, NC, NS, COLL, parity, BND, true>(a, k, n, m, sn, f, h, wallx, cb);
+        gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE, true>(a, sn, n, m, cb, f, h);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, cb);
       }
       uint32_t* t = cb;
       cb = cn;
@@ -940,7 +942,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 #endif
   {
 #if LBM_ODD_SLOT_CACHE
-  __shared__ uint32_t slot_cache[(parity && !kPrefetch) ? (L::Q - 1) * LBM_SLOT_CACHE_STRIDE : 1];
+  __shared__ uint32_t slot_cache[(parity && !kPrefetch) ? (L::Q - 1) * LBM_STEP_CACHE_STRIDE : 1];
   uint32_t* cache = slot_cache + threadIdx.x;
 #endif
   // the list entry is fetched two iterations and the link mask one iteration ahead
@@ -958,8 +960,8 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 #if LBM_ODD_SLOT_CACHE
     if (parity) {
       const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-      gather_entry_odd_cached<L, S, NC, NS>(a, sn, n, m, cache, f, h);
-      collide_scatter<L, S, NC, NS, COLL, parity, BND, true>(a, k, n, m, sn, f, h, wallx, cache);
+      gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE>(a, sn, n, m, cache, f, h);
+      collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, cache);
       continue;
     }
 #endif
@@ -991,7 +993,7 @@ struct Tile {
 // tiles; for each tile they stage the member's arguments and constants in shared memory and
 // update entries first .. first + blockDim - 1 exactly as k_step updates them.
 template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
-__global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step_tiles(
+__global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_TILES_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step_tiles(
     const Args* __restrict__ args, const Coef<typename Store<S>::T>* __restrict__ coefs,
     const Tile* __restrict__ tiles, unsigned int ntiles) {
   using T = typename Store<S>::T;
@@ -1000,8 +1002,8 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   __shared__ Args sa;
   __shared__ Coef<T> sk;
 #if LBM_ODD_SLOT_CACHE
-  __shared__ uint32_t slot_cache[parity ? (L::Q - 1) * LBM_SLOT_CACHE_STRIDE : 1];
-  uint32_t* cache = slot_cache + threadIdx.x;
+  extern __shared__ uint32_t slot_smem[];   // blockDim.x * Q words at odd parity (launcher)
+  uint32_t* cache = slot_smem + threadIdx.x * L::Q;
 #endif
   for (unsigned int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tile = tiles[t];
@@ -1027,8 +1029,8 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
 #if LBM_ODD_SLOT_CACHE
         if (parity) {
-          gather_entry_odd_cached<L, S, NC, NS>(a, sn, n, m, cache, f, h);
-          collide_scatter<L, S, NC, NS, COLL, parity, BND, true>(a, sk, n, m, sn, f, h, wallx, cache);
+          gather_entry_odd_cached<L, S, NC, NS, 1>(a, sn, n, m, cache, f, h);
+          collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1>(a, sk, n, m, sn, f, h, wallx, cache);
         } else
 #endif
         {

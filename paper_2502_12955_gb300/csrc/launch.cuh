@@ -92,6 +92,12 @@ struct Launchers {
   static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
 
   // one resident wave of blocks; the kernel walks the fluid list with a grid-stride loop
+  // dynamic shared memory of the tile kernel's odd-step neighbour-slot cache: Q words per thread
+  static size_t slot_smem_bytes(int parity, int threads) {
+    if (!parity || !LBM_ODD_SLOT_CACHE) return 0;
+    return (size_t)threads * L::Q * sizeof(uint32_t);
+  }
+
   template <int NC, int NS, int COLL, int PAR, bool BND>
   static cudaError_t step_p(const Args& a, cudaStream_t st) {
     const int threads = a.bx;
@@ -241,10 +247,11 @@ struct Launchers {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tiles<L, S, NC, NS, COLL, PAR, BND>, threads, 0);
+    const size_t smem = slot_smem_bytes(PAR, threads);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tiles<L, S, NC, NS, COLL, PAR, BND>, threads, smem);
     const unsigned int wave = (unsigned int)((occ > 0 ? occ : 1) * (sms > 0 ? sms : 1));
     const unsigned int blocks = ntiles < wave ? (ntiles > 0 ? ntiles : 1) : wave;
-    k_step_tiles<L, S, NC, NS, COLL, PAR, BND><<<blocks, threads, 0, st>>>(
+    k_step_tiles<L, S, NC, NS, COLL, PAR, BND><<<blocks, threads, smem, st>>>(
         d_args, static_cast<const Coef<T>*>(d_coefs), d_tiles, ntiles);
     return cudaGetLastError();
   }

@@ -224,7 +224,7 @@ void fill_args(lbm_ctx* c) {
   a.deposit_conservative = p.deposit_conservative ? 1 : 0;
   a.V_m = p.V_m; a.m_s0 = p.m_s0; a.DP = p.DP;
   int bx = p.block_x;
-  if (bx == 0) bx = c->nx >= 256 ? 256 : (c->nx >= 128 ? 128 : (c->nx > 32 ? 64 : 32));
+  if (bx == 0) bx = 256;   // the step kernel walks the fluid list: the block shape is not tied to nx
   a.bx = bx;
   a.by = 1;
   a.div_x = make_fast_div(c->nx);
