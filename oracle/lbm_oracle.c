@@ -315,6 +315,11 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
     st = -1;
   /* the velocity inlet / zero-gradient outlet closes the x axis of the flow lattice, needs the
      channel walls on y, and is defined for one component without Shan-Chen forces */
+  /* the temperature-dependent rate needs the temperature as scalar 1, a positive temperature
+     scale and a bounded iteration */
+  if (p && !st && p->arrhenius &&
+      (p->n_scal != 2 || !(p->arr_A >= 0.0) || !(p->arr_Ta >= 0.0) || p->n_it < 0 || p->n_it > 64))
+    st = -1;
   if (p && !st && p->flow_open_x &&
       (p->periodic[0] || p->periodic[1] || p->nx < 2 || p->n_comp != 1 || p->G[0][0] != 0.0 ||
        p->G_ads[0] != 0.0 || p->rho_solid != 0.0))
@@ -648,8 +653,67 @@ static void close_node(orc_ctx* c, int s, int64_t n, double* dst, int book) {
   }
 }
 
+/* Reactive link with a temperature-dependent rate and heat release (Sec. 2.1.5): scalar 0 is
+   the reacting species (C), scalar 1 the temperature (T).  At a link whose source n - c_i is a
+   reactive solid, with hb, gb the gathered C and T populations moving toward the wall and w the
+   link weight, the interface values satisfy
+       C_b = 2 hb / (2 w + k(T_b) tau_c / (tau_c - 1/2)),      k(T) = A exp(-Ta / T)  (Eq. reactO2)
+       Q   = h_r k(T_b) C_b                                                             (Eq. reacRate)
+       T_b = (2 gb + Q tau_T / (tau_T - 1/2)) / (2 w),
+   the last from the same per-link wet-node ansatz as the species closure: h_T,i + gb = 2 w T_b
+   and (1 - 1/(2 tau_T)) (h_T,i - gb) = Q, the heat flux entering the fluid through the link
+   (Eq. fluxCon with an adiabatic solid).  The coupled pair is solved by n_it fixed-point
+   iterations from the zero-flux value T_b = gb / w; then
+       h_C,i = 2 w C_b - hb,      h_T,i = gb + Q tau_T / (tau_T - 1/2). */
+static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book) {
+  int Qc = c->lc.q;
+  const lattice_t* K = &c->lc;
+  const double* h0 = &c->h[0][n * Qc];
+  const double* h1 = &c->h[1][n * Qc];
+  for (int i = 0; i < Qc; ++i) {
+    dst0[i] = h0[i];
+    dst1[i] = h1[i];
+  }
+  if (c->flag[n] != 0) return;
+  const double fc = c->p.tau_c[0] / (c->p.tau_c[0] - 0.5);
+  const double fT = c->p.tau_c[1] / (c->p.tau_c[1] - 0.5);
+  int x, y, z;
+  coords(c, n, &x, &y, &z);
+  for (int i = 1; i < Qc; ++i) {
+    int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
+    if (src < 0 || c->flag[src] != 2) continue;
+    const double w = K->w[i];
+    const double hb = h0[K->opp[i]];
+    const double gb = h1[K->opp[i]];
+    double Tb = gb / w;
+    for (int it = 0; it < c->p.n_it; ++it) {
+      const double k = c->p.arr_A * exp(-c->p.arr_Ta / Tb);
+      const double Cb = 2.0 * hb / (2.0 * w + k * fc);
+      const double Q = c->p.heat_release * k * Cb;
+      Tb = (2.0 * gb + Q * fT) / (2.0 * w);
+    }
+    const double k = c->p.arr_A * exp(-c->p.arr_Ta / Tb);
+    const double Cb = 2.0 * hb / (2.0 * w + k * fc);
+    const double Q = c->p.heat_release * k * Cb;
+    dst0[i] = 2.0 * w * Cb - hb;
+    dst1[i] = gb + Q * fT;
+    if (book) {
+      const double r = k * Cb;
+      c->acc[src] += r;
+      c->mon[ORC_MON_REACTED] += r;
+      c->mon[ORC_MON_WALLX] += h0[i] - dst0[i];
+      c->mon[ORC_MON_HEAT] += dst1[i] - h1[i];
+    }
+  }
+}
+
 static void close_all(orc_ctx* c, int book) {
   int Qc = c->lc.q;
+  if (c->p.arrhenius) {
+    for (int64_t n = 0; n < c->N; ++n)
+      close_node_thermal(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
+    return;
+  }
   for (int s = 0; s < c->p.n_scal; ++s)
     for (int64_t n = 0; n < c->N; ++n) close_node(c, s, n, &c->hc[s][n * Qc], book);
 }

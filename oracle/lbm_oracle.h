@@ -52,6 +52,14 @@ typedef struct orc_params {
                                   one component without Shan-Chen forces */
   double u_in;                 /* mean inlet velocity U of the profile u_x = 6 U s (1 - s),
                                   s = (y + 1/2) / ny */
+  int32_t arrhenius;           /* 1: scalar 1 is the temperature T; the surface rate of scalar 0 is
+                                  k(T_b) = A exp(-Ta / T_b) at each reactive link's interface
+                                  temperature, and the reaction releases heat into T (Sec. 2.1.5,
+                                  Eq. reactO2, reacRate, fluxCon with an adiabatic solid) */
+  double arr_A;                /* pre-exponential factor A */
+  double arr_Ta;               /* activation temperature E / R_u */
+  double heat_release;         /* h_r: heat flux released per unit reaction rate */
+  int32_t n_it;                /* fixed-point iterations of the C_b - T_b coupling per link */
 } orc_params;
 
 /* Monitor vector layout (doubles). */
@@ -72,7 +80,8 @@ enum {
   ORC_MON_NFLUID = 23,
   ORC_MON_NONFINITE = 24,
   ORC_MON_WALLX = 25,      /* cumulative scalar-0 population loss through reactive links */
-  ORC_MON_COUNT = 26
+  ORC_MON_HEAT = 26,       /* cumulative temperature-population gain through reactive links */
+  ORC_MON_COUNT = 27
 };
 
 typedef struct orc_ctx orc_ctx;

@@ -52,7 +52,8 @@ class OrcParams(C.Structure):
         ("periodic", C.c_int32 * 3), ("geo_mode", C.c_int32), ("V_m", C.c_double),
         ("m_s0", C.c_double), ("DP", C.c_double), ("deposit_conservative", C.c_int32),
         ("N_geo", C.c_int32), ("u_wall_ymax", C.c_double * 3), ("flow_open_x", C.c_int32),
-        ("u_in", C.c_double),
+        ("u_in", C.c_double), ("arrhenius", C.c_int32), ("arr_A", C.c_double), ("arr_Ta", C.c_double),
+        ("heat_release", C.c_double), ("n_it", C.c_int32),
     ]
 
 
@@ -60,7 +61,7 @@ MON_NAMES = [
     "step", "mass0", "mass1", "momx", "momy", "momz", "species0", "species1", "reacted",
     "inflow0", "inflow1", "outflow0", "outflow1", "inj_mass0", "inj_mass1", "inj_spec0",
     "inj_spec1", "rem_mass0", "rem_mass1", "rem_spec0", "rem_spec1", "deposited", "nsolid",
-    "nfluid", "nonfinite", "wallx",
+    "nfluid", "nonfinite", "wallx", "heat",
 ]
 
 _ENUMS = {
@@ -147,6 +148,11 @@ def make_params(cfg: dict) -> OrcParams:
         p.u_wall_ymax[a] = float(uw[a])
     p.flow_open_x = int(bool(d.get("flow_open_x", False)))
     p.u_in = float(d.get("u_in", 0.0))
+    p.arrhenius = int(bool(d.get("arrhenius", False)))
+    p.arr_A = float(d.get("arr_A", 0.0))
+    p.arr_Ta = float(d.get("arr_Ta", 0.0))
+    p.heat_release = float(d.get("heat_release", 0.0))
+    p.n_it = int(d.get("n_it", 8))
     return p
 
 

@@ -143,7 +143,39 @@ class NaiveLBM:
 
         # wet-node closure of scalar 0 at reactive links, from the stored populations
         hc = self.h.copy()
-        if self.ns:
+        if self.ns and cfg.get("arrhenius", False):
+            # temperature-dependent rate k(T) = A exp(-Ta / T) at the interface temperature, heat
+            # h_r k C_b entering the temperature lattice (scalar 1) through the link; the
+            # interface temperature is the root of its balance, found here by bracketing
+            from scipy.optimize import brentq
+            A, Ta, hr = float(cfg["arr_A"]), float(cfg["arr_Ta"]), float(cfg["heat_release"])
+            fc = tauc[0] / (tauc[0] - 0.5)
+            fT = tauc[1] / (tauc[1] - 0.5)
+            for (x, y, z) in nodes:
+                for j in range(1, Qc):
+                    src = self._shift(x, y, z, -self.cc[j], self.per_c)
+                    if src is None or self.flags[src[2], src[1], src[0]] != 2:
+                        continue
+                    w = self.wc[j]
+                    hb = self.h[0, self.oc[j], z, y, x]
+                    gb = self.h[1, self.oc[j], z, y, x]
+
+                    def interface(T):
+                        kk = A * np.exp(-Ta / T)
+                        return kk, 2 * hb / (2 * w + kk * fc)
+
+                    def balance(T):
+                        kk, cb = interface(T)
+                        return T - (2 * gb + hr * kk * cb * fT) / (2 * w)
+
+                    T0 = gb / w
+                    T1 = T0 + hr * A * (hb / w) * fT / (2 * w) + 1e-9
+                    Tb = T0 if hr == 0.0 else brentq(balance, T0, T1, xtol=1e-15, rtol=1e-15, maxiter=500)
+                    kk, cb = interface(Tb)
+                    hc[0, j, z, y, x] = 2 * w * cb - hb
+                    hc[1, j, z, y, x] = gb + hr * kk * cb * fT
+                    self.acc[src[2], src[1], src[0]] += kk * cb
+        elif self.ns:
             Kr = k * tauc[0] / (tauc[0] - 0.5)
             for (x, y, z) in nodes:
                 for j in range(1, Qc):

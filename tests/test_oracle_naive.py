@@ -32,6 +32,12 @@ CASES = {
     "2d_velocity_inlet_reactive": dict(dim=2, nx=8, ny=8, tau=[0.8], flow_open_x=True, u_in=0.03, n_scal=1,
                                        tau_c=[0.7], J0=0.4, k_react=0.05, ade_open_x=True, C_in=[1.0],
                                        periodic=[0, 0, 1]),
+    "2d_arrhenius_heat_open": dict(dim=2, nx=8, ny=8, tau=[0.8], g=[2e-4, 0, 0], n_scal=2, tau_c=[0.7, 0.9],
+                                   J0=0.4, arrhenius=True, arr_A=0.4, arr_Ta=1.0, heat_release=0.02, n_it=24,
+                                   ade_open_x=True, C_in=[1.0, 0.6], periodic=[1, 1, 1]),
+    "3d_mrt_arrhenius_heat_walls": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", g=[1e-4, 0, 0],
+                                        n_scal=2, tau_c=[0.6, 0.8], J0=0.25, arrhenius=True, arr_A=0.3,
+                                        arr_Ta=0.8, heat_release=0.03, n_it=24, periodic=[1, 0, 1]),
     "3d_mrt_velocity_inlet": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", flow_open_x=True,
                                   u_in=0.02, g=[0, 0, 1e-4], u_wall_ymax=[0.01, 0, 0], periodic=[0, 0, 1]),
 }

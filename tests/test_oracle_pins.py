@@ -638,3 +638,74 @@ def test_velocity_inlet_needs_a_closed_channel():
                 dict(periodic=[0, 0, 1], G=[[-5.0, 0], [0, 0]])):
         with pytest.raises(Exception):
             Oracle(dict(dim=2, nx=8, ny=8, flow_open_x=True, u_in=0.01, **bad))
+
+
+# ------------------------------------------- temperature-dependent rate and heat release
+
+def _thermal_case(seed, **over):
+    shape = (1, 12, 14)
+    geom = inputs.random_solids(shape, 0.2, seed=seed, reactive_fraction=0.7)
+    cfg = dict(dim=2, nx=14, ny=12, tau=[0.8], n_scal=2, tau_c=[0.7, 0.9], J0=0.4, periodic=[1, 0, 1])
+    cfg.update(over)
+    return cfg, geom, shape
+
+
+def test_arrhenius_without_activation_or_heat_is_the_constant_rate():
+    """k(T) = A exp(-Ta / T) with Ta = 0 and no heat release is the constant rate k = A: the
+    species, the flow and the reaction bookkeeping equal those of the Eq. wetnode9 closure."""
+    cfg, geom, shape = _thermal_case(51, g=[2e-4, 0, 0])
+    rho, u, C = inputs.perturbed_fields(shape, 1, 2, seed=52, amp_rho=0.01, amp_u=0.01, C0=0.8)
+    a = make(dict(cfg, arrhenius=True, arr_A=0.05, arr_Ta=0.0, heat_release=0.0), geom, (rho, u, C))
+    b = make(dict(cfg, k_react=0.05), geom, (rho, u, C))
+    a.step(40)
+    b.step(40)
+    fa, fb = a.fields(), b.fields()
+    for k in ("rho", "u", "acc"):
+        assert np.abs(fa[k] - fb[k]).max() < 1e-13 * max(1.0, np.abs(fb[k]).max()), k
+    assert np.abs(fa["C"][0] - fb["C"][0]).max() < 1e-13
+    ma, mb = a.monitors(), b.monitors()
+    assert abs(ma["reacted"] - mb["reacted"]) < 1e-13 * mb["reacted"]
+    assert mb["reacted"] > 0
+
+
+def test_arrhenius_at_uniform_temperature_is_the_rate_at_that_temperature():
+    """At rest with a uniform temperature T0 and no heat release, every interface sits at T0, so
+    the rate is the constant A exp(-Ta / T0)."""
+    cfg, geom, shape = _thermal_case(53)
+    T0, A, Ta = 1.3, 0.2, 0.9
+    rho, u, _ = inputs.uniform_fields(shape, 1, 0)
+    rng = np.random.default_rng(54)
+    C = np.stack([0.8 + 0.1 * rng.uniform(size=shape), np.full(shape, T0)])
+    a = make(dict(cfg, arrhenius=True, arr_A=A, arr_Ta=Ta, heat_release=0.0), geom, (rho, u, C))
+    b = make(dict(cfg, k_react=A * np.exp(-Ta / T0)), geom, (rho, u, C))
+    a.step(30)
+    b.step(30)
+    fa, fb = a.fields(), b.fields()
+    assert np.abs(fa["C"][0] - fb["C"][0]).max() < 1e-13
+    assert np.abs(fa["C"][1][geom == 0] - T0).max() < 1e-13     # heat-free, at rest: T stays uniform
+    assert abs(a.monitors()["reacted"] - b.monitors()["reacted"]) < 1e-12 * b.monitors()["reacted"]
+
+
+def test_heat_release_budget_per_step():
+    """With reaction heat, flow, walls and a closed box, the temperature lattice gains per step
+    exactly what the reactive links add (the heat monitor: closed minus stored populations at
+    those links), and the species loses exactly the wall exchange."""
+    cfg, geom, shape = _thermal_case(55, g=[3e-4, 0, 0], arrhenius=True, arr_A=0.4, arr_Ta=1.0,
+                                     heat_release=0.05, n_it=24)
+    rho, u, C = inputs.perturbed_fields(shape, 1, 2, seed=56, amp_rho=0.01, amp_u=0.01, C0=0.9)
+    o = make(cfg, geom, (rho, u, C))
+    o.step(3)
+    for _ in range(4):
+        m0 = o.monitors()
+        o.step(1)
+        m1 = o.monitors()
+        dheat = m1["heat"] - m0["heat"]
+        assert dheat > 0
+        assert abs((m1["species1"] - m0["species1"]) - dheat) < 1e-12 * m0["species1"]
+        assert abs((m1["species0"] - m0["species0"]) + (m1["wallx"] - m0["wallx"])) < 1e-12 * m0["species0"]
+
+
+def test_thermal_closure_needs_the_temperature_scalar():
+    for bad in (dict(n_scal=1), dict(n_scal=2, arr_A=-1.0), dict(n_scal=2, n_it=65)):
+        with pytest.raises(Exception):
+            Oracle(dict(dim=2, nx=8, ny=8, arrhenius=True, arr_A=0.1, arr_Ta=1.0, **bad))
