@@ -783,10 +783,16 @@ static void flips(orc_ctx* c) {
           for (int j = 0; j < Qf; ++j) r += c->f[s][m * Qf + j];
           sr[s] += r;
         }
+        /* the neighbour's scalars after its closure (the same closure the step applies) */
+        double hm[2][QMAX];
+        if (c->p.arrhenius) {
+          close_node_thermal(c, m, hm[0], hm[1], 0);
+        } else {
+          for (int s = 0; s < c->p.n_scal; ++s) close_node(c, s, m, hm[s], 0);
+        }
         for (int s = 0; s < c->p.n_scal; ++s) {
-          double hm[QMAX], C = 0.0;
-          close_node(c, s, m, hm, 0);
-          for (int j = 0; j < Qc; ++j) C += hm[j];
+          double C = 0.0;
+          for (int j = 0; j < Qc; ++j) C += hm[s][j];
           sc[s] += C;
         }
       }

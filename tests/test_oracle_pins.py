@@ -650,10 +650,12 @@ def _thermal_case(seed, **over):
     return cfg, geom, shape
 
 
-def test_arrhenius_without_activation_or_heat_is_the_constant_rate():
+@pytest.mark.parametrize("geo", [dict(), dict(geo_mode="dissolve", V_m=60.0)])
+def test_arrhenius_without_activation_or_heat_is_the_constant_rate(geo):
     """k(T) = A exp(-Ta / T) with Ta = 0 and no heat release is the constant rate k = A: the
-    species, the flow and the reaction bookkeeping equal those of the Eq. wetnode9 closure."""
-    cfg, geom, shape = _thermal_case(51, g=[2e-4, 0, 0])
+    species, the flow, the geometry flips (new nodes take the neighbours' closed species) and the
+    reaction bookkeeping equal those of the Eq. wetnode9 closure."""
+    cfg, geom, shape = _thermal_case(51, g=[2e-4, 0, 0], **geo)
     rho, u, C = inputs.perturbed_fields(shape, 1, 2, seed=52, amp_rho=0.01, amp_u=0.01, C0=0.8)
     a = make(dict(cfg, arrhenius=True, arr_A=0.05, arr_Ta=0.0, heat_release=0.0), geom, (rho, u, C))
     b = make(dict(cfg, k_react=0.05), geom, (rho, u, C))
@@ -666,6 +668,9 @@ def test_arrhenius_without_activation_or_heat_is_the_constant_rate():
     ma, mb = a.monitors(), b.monitors()
     assert abs(ma["reacted"] - mb["reacted"]) < 1e-13 * mb["reacted"]
     assert mb["reacted"] > 0
+    assert np.array_equal(fa["flags"], fb["flags"])
+    if geo:
+        assert mb["inj_mass0"] > 0, "no flip happened"
 
 
 def test_arrhenius_at_uniform_temperature_is_the_rate_at_that_temperature():
