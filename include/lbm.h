@@ -113,6 +113,17 @@ typedef struct lbm_params {
                                  post-collision value.  Needs periodic[0] == periodic[1] == 0,
                                  nx >= 2 and one component without Shan-Chen or adhesion forces. */
   double u_in;                /* mean velocity U of the inlet profile (flow_open_x only) */
+  int32_t arrhenius;          /* 1: scalar 1 is the temperature T.  The surface rate of scalar 0 at
+                                 each reactive link is k(T_b) = arr_A exp(-arr_Ta / T_b) at the
+                                 link's interface temperature, and the reaction releases the heat
+                                 flux heat_release * k C_b into T (Sec. 2.1.5, Eq. reactO2, reacRate,
+                                 fluxCon with an adiabatic solid).  C_b and T_b are solved together
+                                 per link by n_it fixed-point iterations from the zero-flux value.
+                                 Needs n_scal == 2; k_react is not used. */
+  double arr_A;               /* pre-exponential factor A (>= 0) */
+  double arr_Ta;              /* activation temperature E / R_u (>= 0) */
+  double heat_release;        /* h_r: heat flux per unit reaction rate */
+  int32_t n_it;               /* iterations of the C_b - T_b coupling, 0..64 (default 16) */
 } lbm_params;
 
 /* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */
@@ -134,6 +145,8 @@ typedef struct lbm_monitors {
   double nonfinite;           /* fluid nodes holding a non-finite population */
   double wall_exchange;       /* cumulative scalar-0 population loss through reactive links */
   double residual;            /* last automatic residual (-1 if none yet) */
+  double heat;                /* cumulative temperature-population gain through reactive links
+                                 (arrhenius only) */
 } lbm_monitors;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -152,7 +152,7 @@ def make_params(cfg: dict) -> OrcParams:
     p.arr_A = float(d.get("arr_A", 0.0))
     p.arr_Ta = float(d.get("arr_Ta", 0.0))
     p.heat_release = float(d.get("heat_release", 0.0))
-    p.n_it = int(d.get("n_it", 8))
+    p.n_it = int(d.get("n_it", 16))
     return p
 
 

@@ -139,6 +139,9 @@ struct Args {
   int moving_wall;           // the top plate moves (closed y axis)
   int flow_open_x;           // flow velocity inlet at x = 0, zero-gradient outlet at x = nx - 1
   double* u_in_row;          // [ny] inlet velocity u_x(y)
+  int arrhenius;             // scalar 1 is the temperature: rate k(T_b), reaction heat into T
+  int n_it;                  // fixed-point iterations of the C_b - T_b coupling per link
+  double arr_A, arr_Ta, heat_release;
 };
 
 // Index guard of the bounds-checked build (-DLBM_BOUNDS_CHECK): an index outside [0, bound)
@@ -173,6 +176,9 @@ struct Coef {
   T DP, keep;       // deposition probability, 1 - DP
   T rref[2], cref[2];   // storage references (0 in FP64 mode)
   T uw6[3];         // 6 u_wall = 2 u_wall / c_s^2 of the moving top plate
+  T arrA, arrTa;    // temperature-dependent rate A exp(-Ta / T)
+  T fc, fT;         // tau / (tau - 1/2) of scalar 0 and of the temperature (scalar 1)
+  T hr;             // reaction heat per unit rate
   double thr;       // dissolution threshold on acc: m_s0 / V_m (+inf if V_m == 0)
 };
 
@@ -181,7 +187,7 @@ constexpr int WALLX_SLOTS = 4096;
 // partial-sum slots
 enum : int {
   M_MASS = 0, M_MOM = 2, M_SPEC = 5, M_REACT = 7, M_DEPO = 8, M_IN = 9, M_OUT = 11,
-  M_WALLX = 13, M_NSOLID = 14, M_NFLUID = 15, M_NONFIN = 16, M_SPARE = 17
+  M_WALLX = 13, M_NSOLID = 14, M_NFLUID = 15, M_NONFIN = 16, M_HEAT = 17
 };
 
 // ------------------------------------------------------------- indexing
@@ -307,6 +313,50 @@ __device__ __forceinline__ void close_scalar(T* h, uint32_t m, const Coef<T>& k,
       const T hn = T(2) * k.wca * Cb - hb - sh;
       h[j] = hn;
       on_link(j, Cb, old[j] - hn);
+    }
+  }
+}
+
+// Reactive link with a temperature-dependent rate and reaction heat (Sec. 2.1.5, Eq. reactO2,
+// reacRate, fluxCon with an adiabatic solid): scalar 0 is the reacting species, scalar 1 the
+// temperature.  With hb, gb the gathered species and temperature populations moving toward the
+// wall (full values), per link
+//   C_b = 2 hb / (2 w + k(T_b) fc),  k(T) = A exp(-Ta / T),  Q = h_r k(T_b) C_b,
+//   T_b = (2 gb + Q fT) / (2 w),     fc, fT = tau / (tau - 1/2) of the two scalars,
+// solved by n_it fixed-point iterations from the zero-flux value T_b = gb / w; then
+//   h_C = 2 w C_b - hb and h_T = gb + Q fT.  All closures of a node read the values before
+// any closure.  on_link(j, rate k C_b, species exchange, heat exchange) does the bookkeeping.
+template <class L, class T, class OnLink>
+__device__ __forceinline__ void close_thermal(T* h0, T* h1, uint32_t m, const Coef<T>& k, int n_it,
+                                              OnLink on_link) {
+  T old0[L::QC], old1[L::QC];
+#pragma unroll
+  for (int j = 0; j < L::QC; ++j) {
+    old0[j] = h0[j];
+    old1[j] = h1[j];
+  }
+  const T sh0 = k.wca * k.cref[0], sh1 = k.wca * k.cref[1];
+  const T w2 = T(2) * k.wca;
+#pragma unroll
+  for (int j = 1; j < L::QC; ++j) {
+    if (MaskBits<L>::code(m, L::opp(j)) == 2u) {
+      const T hb = old0[L::opp(j)] + sh0;
+      const T gb = old1[L::opp(j)] + sh1;
+      T Tb = gb / k.wca;
+      for (int it = 0; it < n_it; ++it) {
+        const T kt = k.arrA * exp(-k.arrTa / Tb);
+        const T Cb = T(2) * hb / (w2 + kt * k.fc);
+        const T Q = k.hr * kt * Cb;
+        Tb = (T(2) * gb + Q * k.fT) / w2;
+      }
+      const T kt = k.arrA * exp(-k.arrTa / Tb);
+      const T Cb = T(2) * hb / (w2 + kt * k.fc);
+      const T Q = k.hr * kt * Cb;
+      const T hn0 = w2 * Cb - hb - sh0;
+      const T hn1 = gb + Q * k.fT - sh1;
+      h0[j] = hn0;
+      h1[j] = hn1;
+      on_link(j, kt * Cb, old0[j] - hn0, hn1 - old1[j]);
     }
   }
 }
@@ -607,7 +657,8 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
                                                 uint32_t m, long long sn,
                                                 typename Store<S>::T (&f)[NC][L::Q],
                                                 typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC],
-                                                typename Store<S>::T& wallx, const uint32_t* cache = nullptr) {
+                                                typename Store<S>::T& wallx, typename Store<S>::T& heatx,
+                                                const uint32_t* cache = nullptr) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const Nbr nb = nbr_of(a, n);
@@ -615,11 +666,21 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
   if (NS > 0) {
     // the consumed totals are reductions (no value returned): the threshold test runs in
     // k_detect over the interface list before the geometry update
-    close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
-      const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
-      atomicAdd(a.acc + src, widen(k.kr * Cb));
-      wallx += exch;
-    });
+    if (BND && NS > 1 && a.arrhenius) {
+      // temperature-dependent rate and reaction heat (the full kernel variant only)
+      close_thermal<L, T>(h[0], h[NS > 1 ? 1 : 0], m, k, a.n_it, [&](int j, T r, T exch, T heat) {
+        const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
+        atomicAdd(a.acc + src, widen(r));
+        wallx += exch;
+        heatx += heat;
+      });
+    } else {
+      close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
+        const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
+        atomicAdd(a.acc + src, widen(k.kr * Cb));
+        wallx += exch;
+      });
+    }
     // ---- deposition at near-substrate nodes (Eq. surface_deposition)
     if (a.geo_mode == GEO_DEPOSIT) {
       bool near = false;
@@ -898,7 +959,7 @@ template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
 __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC, NSD = NS > 0 ? NS : 1;
-  T wallx = T(0);
+  T wallx = T(0), heatx = T(0);
   const unsigned int count = a.fluid_count[0];
   const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
   const unsigned int stride = gridDim.x * blockDim.x;
@@ -931,7 +992,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         T f[NC][Q], h[NSD][QC];
         const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
         gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE, true>(a, sn, n, m, cb, f, h);
-        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, cb);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, heatx, cb);
       }
       uint32_t* t = cb;
       cb = cn;
@@ -961,13 +1022,13 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
     if (parity) {
       const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
       gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE>(a, sn, n, m, cache, f, h);
-      collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, cache);
+      collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, heatx, cache);
       continue;
     }
 #endif
     gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
     const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-    collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, k, n, m, sn, f, h, wallx);
+    collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, k, n, m, sn, f, h, wallx, heatx);
   }
   }
   // ---- wall-exchange monitor: one reduction per warp that saw a reactive link
@@ -977,6 +1038,17 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       const T w = warp_sum(wallx);
       if ((threadIdx.x & 31) == 0)
         atomicAdd(a.wallx_slot + ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
+                  widen(w));
+    }
+  }
+  // ---- reaction heat monitor (second half of the slots)
+  if (BND && NS > 1) {
+    const unsigned int any = __ballot_sync(0xffffffffu, heatx != T(0));
+    if (any) {
+      const T w = warp_sum(heatx);
+      if ((threadIdx.x & 31) == 0)
+        atomicAdd(a.wallx_slot + WALLX_SLOTS +
+                      ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
                   widen(w));
     }
   }
@@ -1018,7 +1090,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
     }
     __syncthreads();
     const Args& a = sa;
-    T wallx = T(0);
+    T wallx = T(0), heatx = T(0);
     const unsigned int e = tile.first + threadIdx.x;
     if (e < a.fluid_count[0]) {
       const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
@@ -1030,12 +1102,12 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 #if LBM_ODD_SLOT_CACHE
         if (parity) {
           gather_entry_odd_cached<L, S, NC, NS, 1>(a, sn, n, m, cache, f, h);
-          collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1>(a, sk, n, m, sn, f, h, wallx, cache);
+          collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1>(a, sk, n, m, sn, f, h, wallx, heatx, cache);
         } else
 #endif
         {
           gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
-          collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx);
+          collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx, heatx);
         }
       }
     }
@@ -1045,6 +1117,15 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         const T w = warp_sum(wallx);
         if ((threadIdx.x & 31) == 0)
           atomicAdd(a.wallx_slot + ((t * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS), widen(w));
+      }
+    }
+    if (BND && NS > 1) {
+      const unsigned int any = __ballot_sync(0xffffffffu, heatx != T(0));
+      if (any) {
+        const T w = warp_sum(heatx);
+        if ((threadIdx.x & 31) == 0)
+          atomicAdd(a.wallx_slot + WALLX_SLOTS + ((t * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
+                    widen(w));
       }
     }
   }
@@ -1182,7 +1263,10 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
       v[M_IN + s] += a.inflow_row[s * rows + r];
       v[M_OUT + s] += a.outflow_row[s * rows + r];
     }
-  for (int q = tid; q < WALLX_SLOTS; q += nthr) v[M_WALLX] += a.wallx_slot[q];
+  for (int q = tid; q < WALLX_SLOTS; q += nthr) {
+    v[M_WALLX] += a.wallx_slot[q];
+    v[M_HEAT] += a.wallx_slot[WALLX_SLOTS + q];
+  }
   block_reduce_store<NMON>(v, a.partials + (long long)blockIdx.x * NMON);
 }
 
@@ -1257,14 +1341,19 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
   u_out[0] = mx / rt;
   u_out[1] = my / rt;
   u_out[2] = mz / rt;
+  T hh[NS > 0 ? NS : 1][QC];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, hh[s], a.err, a.N, a.pitch);
+  if (NS > 1 && a.arrhenius)
+    close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], m, k, a.n_it, [](int, T, T, T) {});
+  else if (NS > 0)
+    close_scalar<L, T>(hh[0], m, k, [](int, T, T) {});
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    T h[QC];
-    gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h, a.err, a.N, a.pitch);
-    if (s == 0) close_scalar<L, T>(h, m, k, [](int, T, T) {});
     T C = k.cref[s];
 #pragma unroll
-    for (int j = 0; j < QC; ++j) C += h[j];
+    for (int j = 0; j < QC; ++j) C += hh[s][j];
     C_out[s] = C;
   }
 }
@@ -1738,12 +1827,16 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
           for (int j = 0; j < Q; ++j) r += double(f[j]);
           sr[c] += r;
         }
+        T hh[NS > 0 ? NS : 1][QC];
+        for (int c = 0; c < NS; ++c)
+          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, hh[c]);
+        if (NS > 1 && a.arrhenius)
+          close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], mq, k, a.n_it, [](int, T, T, T) {});
+        else if (NS > 0)
+          close_scalar<L, T>(hh[0], mq, k, [](int, T, T) {});
         for (int c = 0; c < NS; ++c) {
-          T h[QC];
-          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, h);
-          if (c == 0) close_scalar<L, T>(h, mq, k, [](int, T, T) {});
           double C = double(k.cref[c]);
-          for (int j = 0; j < QC; ++j) C += double(h[j]);
+          for (int j = 0; j < QC; ++j) C += double(hh[c][j]);
           sc[c] += C;
         }
       }

@@ -82,6 +82,11 @@ Coef<T> make_coef(const Args& a, bool shifted) {
   k.keep = T(1.0 - a.DP);
   k.thr = a.V_m > 0.0 ? a.m_s0 / a.V_m : __builtin_huge_val();
   for (int c = 0; c < 3; ++c) k.uw6[c] = T(6.0 * a.u_wall[c]);
+  k.arrA = T(a.arr_A);
+  k.arrTa = T(a.arr_Ta);
+  k.hr = T(a.heat_release);
+  k.fc = T(a.tau_c[0] / (a.tau_c[0] - 0.5));
+  k.fT = T(a.tau_c[1] / (a.tau_c[1] - 0.5));
   return k;
 }
 
@@ -115,10 +120,11 @@ struct Launchers {
     k_step<L, S, NC, NS, COLL, PAR, BND><<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a, coef(a));
     return cudaGetLastError();
   }
-  // BND: a moving plate or a velocity inlet needs the boundary-rule variant of the step kernel
+  // BND: a moving plate, a velocity inlet or the temperature-dependent reaction needs the full
+  // variant of the step kernel
   template <int NC, int NS, int COLL>
   static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
-    if (a.moving_wall || a.flow_open_x)
+    if (a.moving_wall || a.flow_open_x || a.arrhenius)
       return parity ? step_p<NC, NS, COLL, 1, true>(a, st) : step_p<NC, NS, COLL, 0, true>(a, st);
     return parity ? step_p<NC, NS, COLL, 1, false>(a, st) : step_p<NC, NS, COLL, 0, false>(a, st);
   }

@@ -153,6 +153,11 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
     if (p->periodic[1]) return fail(c, LBM_ERR_INVALID_ARG, "a moving top plate needs a closed y axis");
     if (p->u_wall_ymax[1] != 0.0) return fail(c, LBM_ERR_INVALID_ARG, "the top plate moves in its own plane");
   }
+  if (p->arrhenius) {
+    if (p->n_scal != 2) return fail(c, LBM_ERR_INVALID_ARG, "the temperature-dependent rate needs n_scal == 2 (temperature)");
+    if (!(p->arr_A >= 0.0) || !(p->arr_Ta >= 0.0)) return fail(c, LBM_ERR_INVALID_ARG, "arr_A and arr_Ta must be >= 0");
+    if (p->n_it < 0 || p->n_it > 64) return fail(c, LBM_ERR_INVALID_ARG, "n_it must be in [0, 64]");
+  }
   if (p->flow_open_x) {
     if (p->periodic[0] || p->periodic[1])
       return fail(c, LBM_ERR_INVALID_ARG, "a velocity inlet needs closed x and y axes");
@@ -232,6 +237,11 @@ void fill_args(lbm_ctx* c) {
   for (int k = 0; k < 3; ++k) a.u_wall[k] = p.u_wall_ymax[k];
   a.moving_wall = (p.u_wall_ymax[0] != 0.0 || p.u_wall_ymax[2] != 0.0) ? 1 : 0;
   a.flow_open_x = p.flow_open_x ? 1 : 0;
+  a.arrhenius = p.arrhenius ? 1 : 0;
+  a.n_it = p.n_it;
+  a.arr_A = p.arr_A;
+  a.arr_Ta = p.arr_Ta;
+  a.heat_release = p.heat_release;
 }
 
 int parity_of(long long step) { return int(step & 1); }
@@ -472,6 +482,7 @@ lbm_status lbm_params_default(lbm_params* p) {
   p->N_geo = 1;
   p->rho_ref[0] = p->rho_ref[1] = 1.0;
   p->l2_fetch_bytes = 0;
+  p->n_it = 16;
   return LBM_OK;
 }
 
@@ -546,7 +557,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     DA(a.block_counts, ((pos + 1023) / 1024 + 1) * 4);
     DA(a.block_counts_v, ((pos + 1023) / 1024 + 1) * 4);
   }
-  DA(a.wallx_slot, WALLX_SLOTS * 8);
+  DA(a.wallx_slot, 2 * WALLX_SLOTS * 8);
   DA(a.u_in_row, ny * 8);
   DA(a.iface_list, N * 4);
   DA(a.iface_count, 16);
@@ -577,7 +588,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.listed, 0, (N + 3) / 4 * 4, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 64, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 16, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, WALLX_SLOTS * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, 2 * WALLX_SLOTS * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.fluid_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.inflow_row, 0, 2 * rows * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 2 * rows * 8, c->stream);
@@ -630,7 +641,7 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.flip_mon, 0, 64, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
-  CK(cudaMemsetAsync(c->a.wallx_slot, 0, WALLX_SLOTS * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.wallx_slot, 0, 2 * WALLX_SLOTS * 8, c->stream));
   CK(cudaMemsetAsync(c->a.inflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.outflow_row, 0, 2 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
@@ -904,6 +915,7 @@ lbm_status lbm_get_monitors(lbm_ctx* c, lbm_monitors* out) {
     out->removed_species[s] = hm[NMON + 6 + s];
   }
   out->wall_exchange = hm[M_WALLX];
+  out->heat = hm[M_HEAT];
   out->n_solid = hm[M_NSOLID];
   out->n_fluid = hm[M_NFLUID];
   out->nonfinite = hm[M_NONFIN];
@@ -943,7 +955,7 @@ struct StateHeader {
 size_t state_bytes(const lbm_ctx* c) {
   const size_t N = (size_t)c->N, P = (size_t)c->pitch, rows = (size_t)c->ny * c->nz;
   return sizeof(StateHeader) + (c->p.n_comp * c->Qf + c->p.n_scal * c->Qc) * P * c->elem +
-         (N + 3) / 4 * 4 + N * 8 + WALLX_SLOTS * 8 + 4 * rows * 8 + 8 * 8;
+         (N + 3) / 4 * 4 + N * 8 + 2 * WALLX_SLOTS * 8 + 4 * rows * 8 + 8 * 8;
 }
 }  // namespace
 
@@ -979,7 +991,7 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   }
   CK(cudaMemcpyAsync(o, c->a.flags, (N + 3) / 4 * 4, cudaMemcpyDeviceToHost, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(o, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream)); o += N * 8;
-  CK(cudaMemcpyAsync(o, c->a.wallx_slot, WALLX_SLOTS * 8, cudaMemcpyDeviceToHost, c->stream)); o += WALLX_SLOTS * 8;
+  CK(cudaMemcpyAsync(o, c->a.wallx_slot, 2 * WALLX_SLOTS * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * WALLX_SLOTS * 8;
   CK(cudaMemcpyAsync(o, c->a.inflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(o, c->a.outflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(o, c->a.flip_mon, 64, cudaMemcpyDeviceToHost, c->stream));
@@ -1012,7 +1024,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   }
   CK(cudaMemcpyAsync(c->a.flags, o, (N + 3) / 4 * 4, cudaMemcpyHostToDevice, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(c->a.acc, o, N * 8, cudaMemcpyHostToDevice, c->stream)); o += N * 8;
-  CK(cudaMemcpyAsync(c->a.wallx_slot, o, WALLX_SLOTS * 8, cudaMemcpyHostToDevice, c->stream)); o += WALLX_SLOTS * 8;
+  CK(cudaMemcpyAsync(c->a.wallx_slot, o, 2 * WALLX_SLOTS * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * WALLX_SLOTS * 8;
   CK(cudaMemcpyAsync(c->a.inflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(c->a.outflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
   CK(cudaMemcpyAsync(c->a.flip_mon, o, 64, cudaMemcpyHostToDevice, c->stream));
@@ -1178,7 +1190,7 @@ lbm_status ens_launch(lbm_ensemble* e, int parity, cudaStream_t st) {
   if (e->ntiles == 0) return LBM_OK;
   const lbm_params& p = e->m[0]->p;
   int bnd = 0;   // the boundary-rule kernel variant when any member has a moving plate or an inlet
-  for (size_t k = 0; k < e->m.size(); ++k) bnd |= e->m[k]->a.moving_wall | e->m[k]->a.flow_open_x;
+  for (size_t k = 0; k < e->m.size(); ++k) bnd |= e->m[k]->a.moving_wall | e->m[k]->a.flow_open_x | e->m[k]->a.arrhenius;
   const cudaError_t r = e->ks->step_tiles(e->d_args, e->d_coefs, e->d_tiles, e->ntiles, p.n_comp, p.n_scal,
                                           p.collision, parity, bnd, e->threads, st);
   e->launches += 1;

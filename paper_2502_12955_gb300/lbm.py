@@ -52,7 +52,8 @@ class LbmParams(C.Structure):
         ("N_geo", C.c_int32), ("N_mon", C.c_int32), ("rho_ref", C.c_double * 2),
         ("C_ref", C.c_double * 2), ("stream", C.c_void_p), ("block_x", C.c_int32),
         ("device", C.c_int32), ("l2_fetch_bytes", C.c_int32), ("u_wall_ymax", C.c_double * 3),
-        ("flow_open_x", C.c_int32), ("u_in", C.c_double),
+        ("flow_open_x", C.c_int32), ("u_in", C.c_double), ("arrhenius", C.c_int32),
+        ("arr_A", C.c_double), ("arr_Ta", C.c_double), ("heat_release", C.c_double), ("n_it", C.c_int32),
     ]
 
 
@@ -64,7 +65,7 @@ class LbmMonitors(C.Structure):
         ("injected_species", C.c_double * 2), ("removed_mass", C.c_double * 2),
         ("removed_species", C.c_double * 2), ("deposited", C.c_double), ("n_solid", C.c_double),
         ("n_fluid", C.c_double), ("nonfinite", C.c_double), ("wall_exchange", C.c_double),
-        ("residual", C.c_double),
+        ("residual", C.c_double), ("heat", C.c_double),
     ]
 
 
@@ -198,6 +199,11 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
         p.u_wall_ymax[a] = float(uw[a])
     p.flow_open_x = int(bool(d.get("flow_open_x", False)))
     p.u_in = float(d.get("u_in", 0.0))
+    p.arrhenius = int(bool(d.get("arrhenius", False)))
+    p.arr_A = float(d.get("arr_A", 0.0))
+    p.arr_Ta = float(d.get("arr_Ta", 0.0))
+    p.heat_release = float(d.get("heat_release", 0.0))
+    p.n_it = int(d.get("n_it", 16))
     return p
 
 
@@ -208,7 +214,7 @@ def _dp(a):
 MON_KEYS = ["step", "mass0", "mass1", "momx", "momy", "momz", "species0", "species1", "reacted",
             "inflow0", "inflow1", "outflow0", "outflow1", "inj_mass0", "inj_mass1", "inj_spec0",
             "inj_spec1", "rem_mass0", "rem_mass1", "rem_spec0", "rem_spec1", "deposited", "nsolid",
-            "nfluid", "nonfinite", "wallx", "residual"]
+            "nfluid", "nonfinite", "wallx", "residual", "heat"]
 
 
 class Solver:
@@ -311,7 +317,7 @@ class Solver:
                 m.inflow[0], m.inflow[1], m.outflow[0], m.outflow[1], m.injected_mass[0],
                 m.injected_mass[1], m.injected_species[0], m.injected_species[1],
                 m.removed_mass[0], m.removed_mass[1], m.removed_species[0], m.removed_species[1],
-                m.deposited, m.n_solid, m.n_fluid, m.nonfinite, m.wall_exchange, m.residual]
+                m.deposited, m.n_solid, m.n_fluid, m.nonfinite, m.wall_exchange, m.residual, m.heat]
         return dict(zip(MON_KEYS, vals))
 
     def residual(self):

@@ -65,6 +65,7 @@ def test_params_default():
     assert lib.lbm_params_default(C.byref(p)) == 0
     assert p.precision == 1 and p.n_comp == 1 and p.tau[0] == 1.0 and p.N_geo == 1
     assert list(p.periodic) == [1, 1, 1] and p.deposit_conservative == 1
+    assert p.n_it == 16 and p.arrhenius == 0
 
 
 @pytest.mark.parametrize("bad", [
@@ -76,6 +77,8 @@ def test_params_default():
     dict(flow_open_x=True, periodic=[0, 0, 1], n_comp=2, tau=[1, 1]),
     dict(flow_open_x=True, periodic=[0, 0, 1], G=[[-5, 0], [0, 0]]),
     dict(flow_open_x=True, periodic=[0, 0, 1], G_ads=[0.1, 0]),
+    dict(arrhenius=True, n_scal=1, arr_A=0.1), dict(arrhenius=True, n_scal=2, arr_A=-0.1),
+    dict(arrhenius=True, n_scal=2, arr_A=0.1, n_it=65),
 ])
 def test_create_rejects_invalid_parameters(bad):
     lib = lbm.load()

@@ -304,3 +304,49 @@ def test_velocity_inlet_steady_channel_fp32():
     fo, fg = o.fields(), g.fields()
     assert rel_l2(fo["rho"], fg["rho"]) < 1e-6
     assert rel_l2(fo["u"], fg["u"]) < 1e-4
+
+
+@pytest.mark.parametrize("dim,steps", [(2, 61), (2, 60), (3, 47)])
+def test_temperature_dependent_reaction_with_heat(dim, steps):
+    """Sec. 2.1.5: rate k(T_b) = A exp(-Ta / T_b) at each reactive link's interface temperature,
+    reaction heat into the temperature scalar, C_b - T_b solved per link.  2D: BGK with open
+    faces for both scalars; 3D: MRT with closed walls and dissolution flips (new nodes take the
+    neighbours' closed species and temperature)."""
+    if dim == 2:
+        shape = (1, 14, 18)
+        cfg = dict(dim=2, nx=18, ny=14, tau=[0.8], g=[2e-4, 0, 0], n_scal=2, tau_c=[0.7, 0.9], J0=0.4,
+                   arrhenius=True, arr_A=0.4, arr_Ta=1.0, heat_release=0.02, n_it=24,
+                   ade_open_x=True, C_in=[1.0, 0.6], periodic=[1, 1, 1])
+    else:
+        shape = (8, 10, 12)
+        cfg = dict(dim=3, nx=12, ny=10, nz=8, tau=[0.9], collision="mrt", g=[1e-4, 0, 0], n_scal=2,
+                   tau_c=[0.6, 0.8], J0=0.25, arrhenius=True, arr_A=0.3, arr_Ta=0.8, heat_release=0.03,
+                   n_it=24, periodic=[1, 0, 1], geo_mode="dissolve", V_m=40.0, m_s0=1.0)
+    geom = inputs.random_solids(shape, 0.18, seed=60 + dim, reactive_fraction=0.7)
+    rho, u, C = inputs.perturbed_fields(shape, 1, 2, seed=61, amp_rho=0.01, amp_u=0.01, C0=0.9)
+    o, g = make_pair(cfg, geom, (rho, u, C))
+    o.step(steps)
+    g.step(steps)
+    compare(o, g, what=f"thermal reaction {dim}d")
+    if dim == 3:
+        assert o.monitors()["inj_mass0"] > 0, "no dissolution flip happened"
+
+
+def test_temperature_dependent_reaction_fp32():
+    """The FP32 kernel variant of the coupled closure (single-precision exponential and
+    iteration) against the FP64 oracle after 200 steps."""
+    shape = (1, 14, 18)
+    cfg = dict(dim=2, nx=18, ny=14, tau=[0.8], g=[2e-4, 0, 0], n_scal=2, tau_c=[0.7, 0.9], J0=0.4,
+               arrhenius=True, arr_A=0.4, arr_Ta=1.0, heat_release=0.02, n_it=24,
+               ade_open_x=True, C_in=[1.0, 0.6], periodic=[1, 1, 1])
+    geom = inputs.random_solids(shape, 0.18, seed=62, reactive_fraction=0.7)
+    rho, u, C = inputs.perturbed_fields(shape, 1, 2, seed=61, amp_rho=0.01, amp_u=0.01, C0=0.9)
+    o, g = make_pair(cfg, geom, (rho, u, C), precision="fp32")
+    o.step(200)
+    g.step(200)
+    fo, fg = o.fields(), g.fields()
+    for k, tol in (("rho", 1e-6), ("u", 1e-4), ("C", 1e-5), ("acc", 1e-5)):
+        e = rel_l2(fo[k], fg[k])
+        assert e < tol, (k, e)
+    mo, mg = o.monitors(), g.monitors()
+    assert abs(mg["heat"] - mo["heat"]) < 1e-4 * abs(mo["heat"])
