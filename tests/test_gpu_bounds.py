@@ -3,7 +3,8 @@ storage slots, inlet/outlet rows, adhesion targets) is checked against its buffe
 outside it sets a device error flag instead of touching memory.  The library is rebuilt with
 -DLBM_BOUNDS_CHECK into its own directory and a representative set of parity cases (walls and
 periodic axes, inlet/outlet, MRT with dissolution flips and list rebuilds, deposition,
-two components with adhesion, reduced storage, ensembles) runs against it in a child process;
+two components with adhesion, reduced storage, the velocity inlet and the temperature-dependent
+reaction (the full kernel variant), ensembles) runs against it in a child process;
 each comparison first synchronises, so any out-of-range index fails the case."""
 import os
 import subprocess
@@ -25,6 +26,8 @@ CASES = [
     "test_gpu_parity.py::test_two_component_3d_with_solid_and_adhesion",
     "test_gpu_parity.py::test_pops_roundtrip_and_odd_layout",
     "test_gpu_parity.py::test_reduced_precision_against_fp64_oracle",
+    "test_gpu_parity.py::test_velocity_inlet_channel",
+    "test_gpu_parity.py::test_temperature_dependent_reaction_with_heat",
     "test_gpu_ensemble.py",
 ]
 
