@@ -1056,14 +1056,18 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 
 // ================================================================ ensembles
 
+#ifndef LBM_TILE_CHUNK
+#define LBM_TILE_CHUNK 8
+#endif
 // Work tile of an ensemble step: blockDim consecutive fluid-list entries of one member.
 struct Tile {
   unsigned int member, first;
 };
 
-// One time step of every member of an ensemble in one launch.  Blocks walk a work list of
-// tiles; for each tile they stage the member's arguments and constants in shared memory and
-// update entries first .. first + blockDim - 1 exactly as k_step updates them.
+// One time step of every member of an ensemble in one launch.  Blocks take chunks of the work
+// list of tiles in turn; whenever a block enters another member it stages that member's
+// arguments and constants in shared memory, and for each tile it updates entries first ..
+// first + blockDim - 1 exactly as k_step updates them.
 template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
 __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_TILES_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step_tiles(
     const Args* __restrict__ args, const Coef<typename Store<S>::T>* __restrict__ coefs,
@@ -1077,18 +1081,25 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   extern __shared__ uint32_t slot_smem[];   // blockDim.x * Q words at odd parity (launcher)
   uint32_t* cache = slot_smem + threadIdx.x * L::Q;
 #endif
-  for (unsigned int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // blocks take chunks of LBM_TILE_CHUNK consecutive tiles in turn: the work list holds each
+  // member's tiles together, so a chunk mostly stays within one member and its arguments are
+  // staged again only when the chunk crosses into another; taking chunks in turn keeps a mix of
+  // 2D and 3D members on every block
+  unsigned int staged = 0xffffffffu;
+  for (unsigned int t = blockIdx.x * LBM_TILE_CHUNK; t < ntiles;
+       t += (t % LBM_TILE_CHUNK == LBM_TILE_CHUNK - 1) ? (gridDim.x - 1) * LBM_TILE_CHUNK + 1 : 1) {
     const Tile tile = tiles[t];
-    __syncthreads();   // the previous tile is done with sa / sk
-    {
+    if (tile.member != staged) {   // block-uniform
+      __syncthreads();   // the previous member's tiles are done with sa / sk
       const uint32_t* src = reinterpret_cast<const uint32_t*>(args + tile.member);
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
       for (unsigned int i = threadIdx.x; i < sizeof(Args) / 4; i += blockDim.x) dst[i] = src[i];
       const uint32_t* ksrc = reinterpret_cast<const uint32_t*>(coefs + tile.member);
       uint32_t* kdst = reinterpret_cast<uint32_t*>(&sk);
       for (unsigned int i = threadIdx.x; i < sizeof(Coef<T>) / 4; i += blockDim.x) kdst[i] = ksrc[i];
+      __syncthreads();
+      staged = tile.member;
     }
-    __syncthreads();
     const Args& a = sa;
     T wallx = T(0), heatx = T(0);
     const unsigned int e = tile.first + threadIdx.x;
