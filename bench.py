@@ -343,7 +343,7 @@ def run_ensemble(args, dist, ws, rank, local):
 
 
 def run_to_steady(args, local):
-    """Time to steady state of plain LBM from rest (the baseline a warm start is judged
+    """Time to steady state of plain LBM from rest (the baseline a warm start is compared
     against): the geometry update is frozen, the residual r (relative L2 change of u and C over
     N_mon = 100 steps, the larger of the two) is evaluated on the device every 100 steps, and
     the run stops at the first evaluation with r <= tol.  Wall time between CUDA events on the
