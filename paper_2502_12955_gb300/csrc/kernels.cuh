@@ -139,6 +139,7 @@ struct Args {
   int moving_wall;           // the top plate moves (closed y axis)
   int flow_open_x;           // flow velocity inlet at x = 0, zero-gradient outlet at x = nx - 1
   double* u_in_row;          // [ny] inlet velocity u_x(y)
+  int voff_ok;               // 3 * pitch < 2^31: wall links can be addressed by 32-bit offsets
   int arrhenius;             // scalar 1 is the temperature: rate k(T_b), reaction heat into T
   int n_it;                  // fixed-point iterations of the C_b - T_b coupling per link
   double arr_A, arr_Ta, heat_release;
@@ -494,7 +495,19 @@ __device__ __forceinline__ void prefetch_slots(const Args& a, int n, uint32_t* c
     cp_async4(cache + (i - 1) * CS, a.slot + LBM_CHK(a.err, nb.at(L::cx(i), L::cy(i), L::cz(i)), a.N));
 }
 
-template <class L, class S, int NC, int NS, int CS, bool PREFETCHED = false>
+// Flow links into walls read and write the node's own cell: (n, i) for the population arriving
+// in direction i, which sits in plane i while a fluid link's cell sits in plane opp(i).  Writing
+// into a wall link's cache entry the offset of that own cell relative to the neighbour's plane,
+// slot + (opp(k) - k) * pitch, lets every flow access take plane + entry without testing the
+// link (signed 32-bit: needs 3 * pitch < 2^31, checked on the host).
+template <class L, int CS>
+__device__ __forceinline__ void wall_offsets(const Args& a, long long sn, uint32_t m, uint32_t* cache) {
+#pragma unroll
+  for (int k = 1; k < L::Q; ++k)
+    if (flow_wall<L>(m, k)) cache[(k - 1) * CS] = (uint32_t)(int)(sn + (long long)(L::opp(k) - k) * a.pitch);
+}
+
+template <class L, class S, int NC, int NS, int CS, bool PREFETCHED = false, bool VOFF = false>
 __device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long sn, int n, uint32_t m,
                                                         uint32_t* cache, typename Store<S>::T (&f)[NC][L::Q],
                                                         typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC]) {
@@ -504,7 +517,14 @@ __device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const S* p;
-      if (i == 0 || flow_wall<L>(m, L::opp(i))) {
+      if (VOFF && i != 0) {
+        // the entry holds the plane-relative offset of the cell, own or neighbour (see
+        // wall_offsets)
+        const long long off = (long long)(int)cache[(L::opp(i) - 1) * CS];
+        const long long base_k = (long long)L::opp(i) * a.pitch;   // the plane's start in the array
+        p = reinterpret_cast<const S*>(a.fplane[s][L::opp(i)]) +
+            (LBM_CHK(a.err, off + base_k, (long long)L::Q * a.pitch) - base_k);
+      } else if (i == 0 || flow_wall<L>(m, L::opp(i))) {
         p = reinterpret_cast<const S*>(a.fplane[s][i]) + LBM_CHK(a.err, sn, a.pitch);
       } else {
         uint32_t q;
@@ -652,7 +672,8 @@ __device__ __forceinline__ void mrt_correct(T* f, const T* sp, const T* dp, cons
 
 // Everything after the gather for one fluid node: wet-node closure and its bookkeeping,
 // deposition, moments, forces, velocity, flow and scalar collision, in-place scatter.
-template <class L, class S, int NC, int NS, int COLL, int parity, bool BND, bool CACHE = false, int CS = 1>
+template <class L, class S, int NC, int NS, int COLL, int parity, bool BND, bool CACHE = false, int CS = 1,
+          bool VOFF = false>
 __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typename Store<S>::T>& k, int n,
                                                 uint32_t m, long long sn,
                                                 typename Store<S>::T (&f)[NC][L::Q],
@@ -888,7 +909,11 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
       S* p;
       T v = f[s][i];
       bool keep = true;
-      if (parity == 0 || i == 0 || flow_wall<L>(m, i)) {
+      if (VOFF && i != 0) {
+        const long long off = (long long)(int)cache[(i - 1) * CS];
+        const long long base_k = (long long)i * a.pitch;   // the plane's start in the array
+        p = reinterpret_cast<S*>(a.fplane[s][i]) + (LBM_CHK(a.err, off + base_k, (long long)L::Q * a.pitch) - base_k);
+      } else if (parity == 0 || i == 0 || flow_wall<L>(m, i)) {
         p = reinterpret_cast<S*>(a.fplane[s][L::opp(i)]) + LBM_CHK(a.err, sn, a.pitch);
         if (BND) {
           if (L::cx(i) < 0 && xin && flow_wall<L>(m, i))
@@ -991,8 +1016,12 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       if (m & 1u) {
         T f[NC][Q], h[NSD][QC];
         const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-        gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE, true>(a, sn, n, m, cb, f, h);
-        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, heatx, cb);
+        // the plain variant addresses every flow link through its cache entry (wall_offsets);
+        // the full variant keeps the per-link tests its boundary rules need
+        if (!BND) wall_offsets<L, LBM_STEP_CACHE_STRIDE>(a, sn, m, cb);
+        gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE, true, !BND>(a, sn, n, m, cb, f, h);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE, !BND>(a, k, n, m, sn, f, h, wallx,
+                                                                                          heatx, cb);
       }
       uint32_t* t = cb;
       cb = cn;

@@ -121,10 +121,11 @@ struct Launchers {
     return cudaGetLastError();
   }
   // BND: a moving plate, a velocity inlet or the temperature-dependent reaction needs the full
-  // variant of the step kernel
+  // variant of the step kernel, and so does a domain too large for the plain variant's 32-bit
+  // wall offsets
   template <int NC, int NS, int COLL>
   static cudaError_t step_t(const Args& a, int parity, cudaStream_t st) {
-    if (a.moving_wall || a.flow_open_x || a.arrhenius)
+    if (a.moving_wall || a.flow_open_x || a.arrhenius || !a.voff_ok)
       return parity ? step_p<NC, NS, COLL, 1, true>(a, st) : step_p<NC, NS, COLL, 0, true>(a, st);
     return parity ? step_p<NC, NS, COLL, 1, false>(a, st) : step_p<NC, NS, COLL, 0, false>(a, st);
   }

@@ -193,6 +193,7 @@ void fill_args(lbm_ctx* c) {
   Args& a = c->a;
   const lbm_params& p = c->p;
   a.pitch = c->pitch;
+  a.voff_ok = 3ll * c->pitch < (1ll << 31) ? 1 : 0;
   a.N = c->N;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.n_comp = p.n_comp; a.n_scal = p.n_scal;
