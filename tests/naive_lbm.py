@@ -92,6 +92,7 @@ class NaiveLBM:
         self.h = np.array(h, dtype=np.float64).reshape(self.ns, len(self.cc), self.nz, self.ny, self.nx).copy() \
             if self.ns else np.zeros((0, len(self.cc), self.nz, self.ny, self.nx))
         self.acc = np.zeros((self.nz, self.ny, self.nx))
+        self.t = 0
         per = cfg.get("periodic", [1, 1, 1])
         self.per_f = [bool(p) for p in per]
         self.per_c = [bool(per[0]) and not cfg.get("ade_open_x", False), bool(per[1]), bool(per[2])]
@@ -127,6 +128,97 @@ class NaiveLBM:
         r0 = float(self.cfg.get("rho0", 1.0))
         return r0 * (1 - np.exp(-rho / r0))
 
+    def _close(self, hstate, x, y, z):
+        """Closed scalar populations of fluid node (x, y, z) in state hstate, and the reaction
+        rate of each reactive link [(solid node, k C_b)]."""
+        cfg = self.cfg
+        Qc = len(self.cc)
+        tauc = [float(t) for t in cfg.get("tau_c", [1.0, 1.0])]
+        closed = hstate[:, :, z, y, x].copy()
+        reactions = []
+        arr = bool(cfg.get("arrhenius", False))
+        if arr:
+            # temperature-dependent rate k(T) = A exp(-Ta / T) at the interface temperature, heat
+            # h_r k C_b entering the temperature lattice (scalar 1) through the link; the
+            # interface temperature is the root of its balance, found here by bracketing
+            from scipy.optimize import brentq
+            A, Ta, hr = float(cfg["arr_A"]), float(cfg["arr_Ta"]), float(cfg["heat_release"])
+            fc = tauc[0] / (tauc[0] - 0.5)
+            fT = tauc[1] / (tauc[1] - 0.5)
+        else:
+            k = float(cfg.get("k_react", 0.0))
+            Kr = k * tauc[0] / (tauc[0] - 0.5)
+        for j in range(1, Qc):
+            src = self._shift(x, y, z, -self.cc[j], self.per_c)
+            if src is None or self.flags[src[2], src[1], src[0]] != 2:
+                continue
+            w = self.wc[j]
+            hb = hstate[0, self.oc[j], z, y, x]
+            if not arr:
+                Cb = 2 * hb / (2 * w + Kr)
+                closed[0, j] = 2 * w * Cb - hb
+                reactions.append((src, k * Cb))
+                continue
+            gb = hstate[1, self.oc[j], z, y, x]
+
+            def interface(T):
+                kk = A * np.exp(-Ta / T)
+                return kk, 2 * hb / (2 * w + kk * fc)
+
+            def balance(T):
+                kk, cb = interface(T)
+                return T - (2 * gb + hr * kk * cb * fT) / (2 * w)
+
+            T0 = gb / w
+            T1 = T0 + hr * A * (hb / w) * fT / (2 * w) + 1e-9
+            Tb = T0 if hr == 0.0 else brentq(balance, T0, T1, xtol=1e-15, rtol=1e-15, maxiter=500)
+            kk, cb = interface(Tb)
+            closed[0, j] = 2 * w * cb - hb
+            closed[1, j] = gb + hr * kk * cb * fT
+            reactions.append((src, kk * cb))
+        return closed, reactions
+
+    def _flips(self):
+        """Geometry update after the step's streaming (Sec. 2.1.5 solid consumption, Sec. 3.3
+        deposition), every N_geo steps; all flips of one update see the state before any."""
+        cfg = self.cfg
+        mode = cfg.get("geo_mode", "none")
+        if mode == "none" or (self.t + 1) % int(cfg.get("N_geo", 1)) != 0:
+            return
+        nx, ny, nz = self.nx, self.ny, self.nz
+        cells = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx)]
+        if mode == "deposit":
+            for (x, y, z) in cells:
+                if self.flags[z, y, x] == 0 and self.acc[z, y, x] > 1.0:
+                    self.flags[z, y, x] = 1
+                    self.f[:, :, z, y, x] = 0.0
+                    self.h[:, :, z, y, x] = 0.0
+            return
+        V_m = float(cfg.get("V_m", 1.0))
+        thr = float(cfg.get("m_s0", 1.0)) / V_m if V_m > 0 else np.inf
+        new = []
+        for (x, y, z) in cells:
+            if self.flags[z, y, x] != 2 or self.acc[z, y, x] < thr:
+                continue
+            rs, cs, cnt = np.zeros(self.nc), np.zeros(self.ns), 0
+            for i in range(1, len(self.cf)):
+                q = self._shift(x, y, z, self.cf[i], self.per_f)
+                if not self._fluid(q):
+                    continue
+                cnt += 1
+                rs += self.f[:, :, q[2], q[1], q[0]].sum(axis=1)
+                if self.ns:
+                    closed, _ = self._close(self.h, *q)
+                    cs += closed.sum(axis=1)
+            if cnt:
+                new.append(((x, y, z), rs / cnt, cs / cnt))
+        for (x, y, z), rbar, cbar in new:
+            for s in range(self.nc):
+                self.f[s, :, z, y, x] = [self._feq(i, rbar[s], np.zeros(3)) for i in range(len(self.cf))]
+            for s in range(self.ns):
+                self.h[s, :, z, y, x] = self.wc * cbar[s]
+            self.flags[z, y, x] = 0
+
     def step(self):
         cfg = self.cfg
         nx, ny, nz = self.nx, self.ny, self.nz
@@ -141,51 +233,31 @@ class NaiveLBM:
         k = float(cfg.get("k_react", 0.0))
         nodes = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx) if self.flags[z, y, x] == 0]
 
-        # wet-node closure of scalar 0 at reactive links, from the stored populations
+        # wet-node closure at reactive links, from the stored populations
         hc = self.h.copy()
-        if self.ns and cfg.get("arrhenius", False):
-            # temperature-dependent rate k(T) = A exp(-Ta / T) at the interface temperature, heat
-            # h_r k C_b entering the temperature lattice (scalar 1) through the link; the
-            # interface temperature is the root of its balance, found here by bracketing
-            from scipy.optimize import brentq
-            A, Ta, hr = float(cfg["arr_A"]), float(cfg["arr_Ta"]), float(cfg["heat_release"])
-            fc = tauc[0] / (tauc[0] - 0.5)
-            fT = tauc[1] / (tauc[1] - 0.5)
+        if self.ns:
             for (x, y, z) in nodes:
-                for j in range(1, Qc):
-                    src = self._shift(x, y, z, -self.cc[j], self.per_c)
-                    if src is None or self.flags[src[2], src[1], src[0]] != 2:
-                        continue
-                    w = self.wc[j]
-                    hb = self.h[0, self.oc[j], z, y, x]
-                    gb = self.h[1, self.oc[j], z, y, x]
+                closed, reactions = self._close(self.h, x, y, z)
+                hc[:, :, z, y, x] = closed
+                for (src, r) in reactions:
+                    self.acc[src[2], src[1], src[0]] += r
 
-                    def interface(T):
-                        kk = A * np.exp(-Ta / T)
-                        return kk, 2 * hb / (2 * w + kk * fc)
-
-                    def balance(T):
-                        kk, cb = interface(T)
-                        return T - (2 * gb + hr * kk * cb * fT) / (2 * w)
-
-                    T0 = gb / w
-                    T1 = T0 + hr * A * (hb / w) * fT / (2 * w) + 1e-9
-                    Tb = T0 if hr == 0.0 else brentq(balance, T0, T1, xtol=1e-15, rtol=1e-15, maxiter=500)
-                    kk, cb = interface(Tb)
-                    hc[0, j, z, y, x] = 2 * w * cb - hb
-                    hc[1, j, z, y, x] = gb + hr * kk * cb * fT
-                    self.acc[src[2], src[1], src[0]] += kk * cb
-        elif self.ns:
-            Kr = k * tauc[0] / (tauc[0] - 0.5)
+        # deposition at near-substrate fluid nodes (Sec. 3.3): C_p,s += DP sum_j h_p,j
+        if self.ns and cfg.get("geo_mode", "none") == "deposit":
+            DP = float(cfg.get("DP", 0.0))
             for (x, y, z) in nodes:
+                near = False
                 for j in range(1, Qc):
-                    src = self._shift(x, y, z, -self.cc[j], self.per_c)
-                    if src is None or self.flags[src[2], src[1], src[0]] != 2:
-                        continue
-                    hb = self.h[0, self.oc[j], z, y, x]
-                    Cb = 2 * hb / (2 * self.wc[j] + Kr)
-                    hc[0, j, z, y, x] = 2 * self.wc[j] * Cb - hb
-                    self.acc[src[2], src[1], src[0]] += k * Cb
+                    t = self._shift(x, y, z, self.cc[j], self.per_c)
+                    if t is None:
+                        xt = x + self.cc[j][0]
+                        near |= not (cfg.get("ade_open_x", False) and (xt < 0 or xt >= nx))
+                    else:
+                        near |= self.flags[t[2], t[1], t[0]] != 0
+                if near:
+                    self.acc[z, y, x] += DP * float(hc[0, :, z, y, x].sum())
+                    if cfg.get("deposit_conservative", True):
+                        hc[0, :, z, y, x] *= (1.0 - DP)
 
         # densities, momenta and psi of every fluid node before any force
         rho = {n: [float(self.f[s, :, n[2], n[1], n[0]].sum()) for s in range(self.nc)] for n in nodes}
@@ -298,3 +370,5 @@ class NaiveLBM:
                     elif xs >= nx:
                         hnew[s, j, z, y, x] = hpost[s, j, z, y, x]
         self.f, self.h = fnew, hnew
+        self._flips()
+        self.t += 1
