@@ -1,5 +1,6 @@
 """Validation cases of the paper run through the CUDA path: the sessile-droplet contact angle
-of the two-component Shan-Chen model with adhesion (contact-angle section of Sec. 3.2).
+of the two-component Shan-Chen model with adhesion (contact-angle section of Sec. 3.2), and the
+Laplace law of the full-size static droplets (Sec. 3.2.2).
 
 The angle is measured as the paper does: the droplet height h and contact length b give the
 cap radius r = (4h^2 + b^2) / (8h) and theta = pi - arctan(b / (2(h - r))), the arctangent
@@ -69,3 +70,64 @@ def test_contact_angle_of_sessile_droplet():
         c_h = -2.0 * g / (G * (hi - lo) / 2.0)
         ratio = np.cos(np.radians(theta)) / c_h
         assert 0.5 < ratio < 3.0, ratio
+
+
+def _coexistence_3d(G, steps=6000):
+    """Bulk densities of the two phases across flat interfaces in a periodic 3D slab."""
+    nx = 64
+    x = np.arange(nx)
+    inside = ((x >= 16) & (x < 48))[None, None, :] * np.ones((2, 2, 1), bool)
+    rho = np.stack([np.where(inside, 1.0, 0.05), np.where(inside, 0.05, 1.0)])
+    cfg = dict(dim=3, nx=nx, ny=2, nz=2, n_comp=2, tau=[1.0, 1.0], G=[[0.0, G], [G, 0.0]],
+               psi_kind="identity", periodic=[1, 1, 1], precision="fp32")
+    s = Solver(cfg)
+    s.set_geometry(np.zeros((2, 2, nx), np.uint8))
+    s.set_fields(rho, np.zeros((3, 2, 2, nx)), None)
+    s.step(steps)
+    r = s.fields()["rho"][0, 0, 0]
+    s.close()
+    return float(r[32]), float(r[0])
+
+
+def test_laplace_law_full_size_droplets():
+    """The two-component droplet at its full size (128^3, D3Q19 per component, psi = rho,
+    G = 2.7, FP32 storage, 10,000 steps) for R = 16, 24 and 32, started from the bulk
+    coexistence densities of a flat interface: the pressure jump of the EOS
+    p = c_s^2 (rho_1 + rho_2 + G rho_1 rho_2) between the inner half of the droplet and the
+    fluid beyond its interface layer follows the 3D Laplace law Delta p = 2 gamma / R (linear in
+    1/R, small intercept), and the spurious currents stay small."""
+    G, cs2 = 2.7, 1.0 / 3.0
+    hi, lo = _coexistence_3d(G)
+    print(f"coexistence densities {hi:.4f} / {lo:.4f}")
+    Rs, dps, umax = [], [], []
+    for R in (16.0, 24.0, 32.0):
+        cfg, geom, _ = inputs.droplet_3d(n=128, radius=R, precision="fp32")
+        rho, u = inputs.droplet_fields((128, 128, 128), R, rho_in=hi, rho_out=lo)
+        s = Solver(dict(cfg, N_mon=1000))
+        s.set_geometry(geom)
+        s.set_fields(rho, u, None)
+        s.step(10000)
+        f = s.fields()
+        m = s.monitors()
+        s.close()
+        r = f["rho"]
+        p = cs2 * (r[0] + r[1]) + cs2 * G * r[0] * r[1]
+        zz, yy, xx = np.meshgrid(*(np.arange(128) - 64.0,) * 3, indexing="ij")
+        d = np.sqrt(xx * xx + yy * yy + zz * zz)
+        # bulk pressures: the inner half of the droplet against the fluid beyond its interface layer
+        dps.append(float(p[d < R / 2].mean() - p[d > R + 12].mean()))
+        phi = (r[0] - r[0].min()) / (r[0].max() - r[0].min())
+        Rs.append(float((3.0 * phi.sum() / (4.0 * np.pi)) ** (1.0 / 3.0)))
+        umax.append(float(np.sqrt((f["u"] ** 2).sum(axis=0)).max()))
+        assert m["nonfinite"] == 0
+        assert abs(Rs[-1] - R) < 2.0, "the droplet did not keep its size"
+        print(f"R {R}: measured radius {Rs[-1]:.2f}, Delta p {dps[-1]:.4e}, max |u| {umax[-1]:.2e}")
+    Rs, dps = np.array(Rs), np.array(dps)
+    A = np.vstack([1.0 / Rs, np.ones_like(Rs)]).T
+    coef, *_ = np.linalg.lstsq(A, dps, rcond=None)
+    pred = A @ coef
+    r2 = 1.0 - ((dps - pred) ** 2).sum() / ((dps - dps.mean()) ** 2).sum()
+    print(f"Laplace fit: 2 gamma = {coef[0]:.4e}, intercept {coef[1]:.2e}, R^2 {r2:.5f}")
+    assert r2 > 0.99
+    assert coef[0] > 0 and abs(coef[1]) < 0.2 * dps.min()
+    assert max(umax) < 0.05
