@@ -217,6 +217,16 @@ MON_KEYS = ["step", "mass0", "mass1", "momx", "momy", "momz", "species0", "speci
             "nfluid", "nonfinite", "wallx", "residual", "heat"]
 
 
+def save_fields(fields, path):
+    """Write a fields dict (as Solver.fields returns it) to `path` (.npz, uncompressed) and
+    return the path written."""
+    path = str(path)
+    if not path.endswith(".npz"):
+        path += ".npz"
+    np.savez(path, **{k: np.asarray(v) for k, v in fields.items()})
+    return path
+
+
 class Solver:
     """One lattice Boltzmann domain on one GPU (owns an lbm_ctx)."""
 
@@ -291,6 +301,11 @@ class Solver:
         sh = self.shape
         return {"rho": rho.reshape((nc,) + sh), "u": u.reshape((3,) + sh),
                 "C": Cs[:ns].reshape((ns,) + sh), "flags": flags.reshape(sh), "acc": acc.reshape(sh)}
+
+    def save_fields(self, path):
+        """Write the macroscopic fields (rho, u, C, flags, acc; x fastest) to an .npz file for
+        offline plotting."""
+        return save_fields(self.fields(), path)
 
     def pops(self):
         f = np.zeros((self.n_comp, self.qf, self.N))

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2502_12955_gb300 import lbm
@@ -122,3 +123,15 @@ def test_ensemble_create_rejects_mixed_or_unsupported_members(bad):
     assert lib.lbm_ensemble_create(lbm.LBM_D2Q9_D2Q5, 2, dims, ps, C.byref(h)) == -1 and not h.value
     assert b"member 1" in lib.lbm_ensemble_last_error(None)
     assert lib.lbm_ensemble_create(lbm.LBM_D2Q9_D2Q5, 0, dims, ps, C.byref(h)) == -1
+
+
+def test_save_fields_round_trip(tmp_path):
+    """Fields are exported as arrays for offline plotting (no graphics stack)."""
+    rng = np.random.default_rng(3)
+    fields = {"rho": rng.uniform(size=(1, 1, 4, 5)), "u": rng.uniform(size=(3, 1, 4, 5)),
+              "C": rng.uniform(size=(1, 1, 4, 5)), "flags": rng.integers(0, 3, size=(1, 4, 5)).astype(np.uint8),
+              "acc": np.zeros((1, 4, 5))}
+    path = lbm.save_fields(fields, tmp_path / "state")
+    back = np.load(path)
+    for k, v in fields.items():
+        assert np.array_equal(back[k], v) and back[k].dtype == v.dtype
