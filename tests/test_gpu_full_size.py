@@ -73,6 +73,9 @@ def test_full_size_fp64_and_fp32_two_steps(full_case):
         del f_o, h_o
         mo, m64 = o.monitors(), g64.monitors()
         for k, v in mo.items():
+            if k not in m64:   # an oracle-only monitor of a feature this case does not use
+                assert v == 0.0, k
+                continue
             assert abs(m64[k] - v) <= MON_TOL * max(abs(v), abs(mo["mass0"])), (k, m64[k], v)
     g64.close()
     g32.close()
