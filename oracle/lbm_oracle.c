@@ -62,9 +62,6 @@ struct orc_ctx {
   double* F[2];                   /* [N][3] total force per component */
   double* ub;                     /* [N][3] barycentric / physical velocity */
   double* Cs[2];                  /* scalar value per node */
-  double* gs;                     /* [N][Qc] solid thermal populations, stored (conjugate) */
-  double* gsc;                    /* after the interface closure */
-  double* gsp;                    /* post-collision */
   double mon[ORC_MON_COUNT];
   int64_t t;
   double* snap_u;
@@ -323,8 +320,6 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
   if (p && !st && p->arrhenius &&
       (p->n_scal != 2 || !(p->arr_A >= 0.0) || !(p->arr_Ta >= 0.0) || p->n_it < 0 || p->n_it > 64))
     st = -1;
-  /* conduction in the solid couples to the temperature scalar of the temperature-dependent mode */
-  if (p && !st && p->conjugate && (!p->arrhenius || !(p->tau_s > 0.5) || !(p->c_fs > 0.0))) st = -1;
   if (p && !st && p->flow_open_x &&
       (p->periodic[0] || p->periodic[1] || p->nx < 2 || p->n_comp != 1 || p->G[0][0] != 0.0 ||
        p->G_ads[0] != 0.0 || p->rho_solid != 0.0))
@@ -353,11 +348,6 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
     c->h[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
     c->hc[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
     c->hp[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
-    if (s == 1 && p->conjugate) {
-      c->gs = (double*)zalloc(sizeof(double) * N * c->lc.q);
-      c->gsc = (double*)zalloc(sizeof(double) * N * c->lc.q);
-      c->gsp = (double*)zalloc(sizeof(double) * N * c->lc.q);
-    }
     c->Cs[s] = (double*)zalloc(sizeof(double) * N);
   }
   c->flag = (uint8_t*)zalloc(N);
@@ -380,7 +370,6 @@ void orc_destroy(orc_ctx* c) {
     free(c->f[s]); free(c->fp[s]); free(c->rho[s]); free(c->jm[s]); free(c->psi[s]); free(c->F[s]);
     free(c->h[s]); free(c->hc[s]); free(c->hp[s]); free(c->Cs[s]);
   }
-  free(c->gs); free(c->gsc); free(c->gsp);
   free(c->flag); free(c->acc); free(c->ub); free(c->snap_u); free(c->snap_C);
   free(c);
 }
@@ -404,11 +393,6 @@ int orc_set_fields(orc_ctx* c, const double* rho, const double* u, const double*
       for (int i = 0; i < Qf; ++i) c->f[s][n * Qf + i] = fluid ? feq(&c->lf, i, rho[s * N + n], un) : 0.0;
     for (int s = 0; s < c->p.n_scal; ++s)
       for (int i = 0; i < Qc; ++i) c->h[s][n * Qc + i] = fluid ? heq(&c->lc, i, C[s * N + n], un) : 0.0;
-    if (c->p.conjugate) {
-      /* the solid starts at rest equilibrium with the temperature field given for it */
-      double zero[3] = {0.0, 0.0, 0.0};
-      for (int i = 0; i < Qc; ++i) c->gs[n * Qc + i] = fluid ? 0.0 : heq(&c->lc, i, C[N + n], zero);
-    }
   }
   memset(c->mon, 0, sizeof(c->mon));
   c->t = 0;
@@ -490,13 +474,6 @@ static void macros(orc_ctx* c) {
         for (int i = 0; i < c->lc.q; ++i) C += c->hc[s][n * c->lc.q + i];  /* Eq. macroreacb_species */
       c->Cs[s][n] = C;
     }
-  if (c->p.conjugate)
-    for (int64_t n = 0; n < N; ++n) {
-      if (c->flag[n] == 0) continue;
-      double T = 0.0;
-      for (int i = 0; i < c->lc.q; ++i) T += c->gsc[n * c->lc.q + i];
-      c->Cs[1][n] = T;   /* the solid temperature (Eq. macroreacb_solid, per unit rho c_p) */
-    }
 }
 
 /* ------------------------------------------------------ step, part C */
@@ -569,38 +546,6 @@ static void collide(orc_ctx* c) {
         double hi = c->hc[s][n * Qc + i];
         c->hp[s][n * Qc + i] = hi - (hi - heq(&c->lc, i, C, u)) / c->p.tau_c[s];
       }
-    }
-  }
-}
-
-/* Eq. therpop_solid with Eq. therpopeq_solid: pure conduction in the solid, g_s^eq = w T_s */
-static void collide_solid(orc_ctx* c) {
-  if (!c->p.conjugate) return;
-  int Qc = c->lc.q;
-  double zero[3] = {0.0, 0.0, 0.0};
-  for (int64_t n = 0; n < c->N; ++n) {
-    if (c->flag[n] == 0) continue;
-    const double T = c->Cs[1][n];
-    for (int i = 0; i < Qc; ++i) {
-      const double gi = c->gsc[n * Qc + i];
-      c->gsp[n * Qc + i] = gi - (gi - heq(&c->lc, i, T, zero)) / c->p.tau_s;
-    }
-  }
-}
-
-/* Streaming inside the solid.  A population that would arrive from a fluid node is unknown and
-   holds the bounce-back value until the interface closure replaces it; closed faces reflect. */
-static void stream_solid(orc_ctx* c) {
-  if (!c->p.conjugate) return;
-  int Qc = c->lc.q;
-  const lattice_t* K = &c->lc;
-  for (int64_t n = 0; n < c->N; ++n) {
-    if (c->flag[n] == 0) continue;
-    int x, y, z;
-    coords(c, n, &x, &y, &z);
-    for (int i = 0; i < Qc; ++i) {
-      int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
-      c->gs[n * Qc + i] = (src >= 0 && c->flag[src] != 0) ? c->gsp[src * Qc + i] : c->gsp[n * Qc + K->opp[i]];
     }
   }
 }
@@ -762,78 +707,8 @@ static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1
   }
 }
 
-/* Conjugate interface (Sec. 2.1.5, Eq. tempCon, fluxCon, reacRate): at a fluid node n and a
-   scalar link i whose source s = n - c_i is a solid, the fluid population h_T,i arriving from
-   the solid and the solid population g_s,opp(i) arriving at s from the fluid are unknown.  With
-   gb = h_T,opp(i)(n) (fluid, moving toward the solid), gs = g_s,i(s) (solid, moving toward the
-   fluid), a_f = (tau_T - 1/2) / tau_T, a_s = (tau_s - 1/2) / tau_s and c_fs the heat-capacity
-   ratio, the link takes one interface temperature T_b on both sides,
-       h_T,i + gb = 2 w T_b,     g_s,opp(i) + gs = 2 w T_b,
-   and the heat entering the fluid is what leaves the solid plus the reaction heat Q:
-       a_f (h_T,i - gb) = (a_s / c_fs) (gs - g_s,opp(i)) + Q,
-   which gives T_b = (2 a_f gb + 2 (a_s / c_fs) gs + Q) / (2 w (a_f + a_s / c_fs)).  At a reactive
-   link Q = h_r k(T_b) C_b with the species closure of close_node_thermal, solved by n_it
-   fixed-point iterations from the value without Q; at an inert solid link Q = 0.  With a_s -> 0
-   (no conduction) this is close_node_thermal's adiabatic closure. */
-static void close_node_conjugate(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book) {
-  int Qc = c->lc.q;
-  const lattice_t* K = &c->lc;
-  const double* h0 = &c->h[0][n * Qc];
-  const double* h1 = &c->h[1][n * Qc];
-  for (int i = 0; i < Qc; ++i) {
-    dst0[i] = h0[i];
-    dst1[i] = h1[i];
-  }
-  if (c->flag[n] != 0) return;
-  const double fc = c->p.tau_c[0] / (c->p.tau_c[0] - 0.5);
-  const double af = (c->p.tau_c[1] - 0.5) / c->p.tau_c[1];
-  const double as = (c->p.tau_s - 0.5) / c->p.tau_s / c->p.c_fs;
-  int x, y, z;
-  coords(c, n, &x, &y, &z);
-  for (int i = 1; i < Qc; ++i) {
-    int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
-    if (src < 0 || c->flag[src] == 0) continue;
-    const double w = K->w[i];
-    const double gb = h1[K->opp[i]];
-    const double gsi = c->gs[src * Qc + i];
-    double Tb = (af * gb + as * gsi) / (w * (af + as));
-    double k = 0.0, Cb = 0.0, Q = 0.0;
-    if (c->flag[src] == 2) {
-      const double hb = h0[K->opp[i]];
-      for (int it = 0; it < c->p.n_it; ++it) {
-        k = c->p.arr_A * exp(-c->p.arr_Ta / Tb);
-        Cb = 2.0 * hb / (2.0 * w + k * fc);
-        Q = c->p.heat_release * k * Cb;
-        Tb = (2.0 * af * gb + 2.0 * as * gsi + Q) / (2.0 * w * (af + as));
-      }
-      k = c->p.arr_A * exp(-c->p.arr_Ta / Tb);
-      Cb = 2.0 * hb / (2.0 * w + k * fc);
-      dst0[i] = 2.0 * w * Cb - hb;
-    }
-    dst1[i] = 2.0 * w * Tb - gb;
-    const double gnew = 2.0 * w * Tb - gsi;
-    if (book) {
-      if (c->flag[src] == 2) {
-        const double r = k * Cb;
-        c->acc[src] += r;
-        c->mon[ORC_MON_REACTED] += r;
-        c->mon[ORC_MON_WALLX] += h0[i] - dst0[i];
-      }
-      c->mon[ORC_MON_HEAT] += dst1[i] - h1[i];
-      c->mon[ORC_MON_HEAT_S] += gnew - c->gs[src * Qc + K->opp[i]];
-    }
-    c->gsc[src * Qc + K->opp[i]] = gnew;
-  }
-}
-
 static void close_all(orc_ctx* c, int book) {
   int Qc = c->lc.q;
-  if (c->p.conjugate) {
-    memcpy(c->gsc, c->gs, sizeof(double) * (size_t)c->N * (size_t)Qc);
-    for (int64_t n = 0; n < c->N; ++n)
-      close_node_conjugate(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
-    return;
-  }
   if (c->p.arrhenius) {
     for (int64_t n = 0; n < c->N; ++n)
       close_node_thermal(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
@@ -941,22 +816,14 @@ static void flips(orc_ctx* c) {
         for (int i = 0; i < Qc; ++i) c->h[s][n * Qc + i] = heq(&c->lc, i, C, zero);
         c->mon[ORC_MON_INJ_SPEC + s] += C;
       }
-      if (c->p.conjugate)
-        for (int i = 0; i < Qc; ++i) c->gs[n * Qc + i] = 0.0;   /* the solid's heat goes with it */
       c->flag[n] = 0;
     }
     free(mean);
     free(ok);
   } else {
-    /* deposition: node becomes an inert solid; its populations are removed (with conduction
-       in the solid, it keeps its temperature as the new solid's) */
+    /* deposition: node becomes an inert solid; its populations are removed */
     for (int64_t k = 0; k < cnt; ++k) {
       int64_t n = list[k];
-      if (c->p.conjugate) {
-        double T = 0.0, zero[3] = {0.0, 0.0, 0.0};
-        for (int i = 0; i < Qc; ++i) T += c->h[1][n * Qc + i];
-        for (int i = 0; i < Qc; ++i) c->gs[n * Qc + i] = heq(&c->lc, i, T, zero);
-      }
       for (int s = 0; s < c->p.n_comp; ++s) {
         double r = 0.0;
         for (int i = 0; i < Qf; ++i) {
@@ -985,9 +852,7 @@ int orc_step(orc_ctx* c, int64_t nsteps) {
     deposit(c);
     macros(c);
     collide(c);
-    collide_solid(c);
     stream(c);
-    stream_solid(c);
     flips(c);
     c->t += 1;
   }
@@ -1046,12 +911,10 @@ int orc_get_monitors(orc_ctx* c, double* out) {
   int Qf = c->lf.q, Qc = c->lc.q;
   const lattice_t* L = &c->lf;
   double mass[2] = {0.0, 0.0}, mom[3] = {0.0, 0.0, 0.0}, spec[2] = {0.0, 0.0};
-  double nsolid = 0.0, nfluid = 0.0, nonfinite = 0.0, tsolid = 0.0;
+  double nsolid = 0.0, nfluid = 0.0, nonfinite = 0.0;
   for (int64_t n = 0; n < N; ++n) {
     if (c->flag[n] != 0) {
       nsolid += 1.0;
-      if (c->p.conjugate)
-        for (int i = 0; i < Qc; ++i) tsolid += c->gs[n * Qc + i];
       continue;
     }
     nfluid += 1.0;
@@ -1079,7 +942,6 @@ int orc_get_monitors(orc_ctx* c, double* out) {
   out[ORC_MON_NSOLID] = nsolid;
   out[ORC_MON_NFLUID] = nfluid;
   out[ORC_MON_NONFINITE] = nonfinite;
-  out[ORC_MON_TSOLID] = tsolid;
   return 0;
 }
 

@@ -60,11 +60,6 @@ typedef struct orc_params {
   double arr_Ta;               /* activation temperature E / R_u */
   double heat_release;         /* h_r: heat flux released per unit reaction rate */
   int32_t n_it;                /* fixed-point iterations of the C_b - T_b coupling per link */
-  int32_t conjugate;           /* 1 (with arrhenius): heat conduction in the solid on its own scalar
-                                  lattice, coupled to the fluid temperature at every solid link by
-                                  temperature and flux continuity (Sec. 2.1.5, Eq. tempCon, fluxCon) */
-  double tau_s;                /* relaxation time of the solid thermal lattice */
-  double c_fs;                 /* heat-capacity ratio (rho c_p)_fluid / (rho c_p)_solid */
 } orc_params;
 
 /* Monitor vector layout (doubles). */
@@ -85,11 +80,8 @@ enum {
   ORC_MON_NFLUID = 23,
   ORC_MON_NONFINITE = 24,
   ORC_MON_WALLX = 25,      /* cumulative scalar-0 population loss through reactive links */
-  ORC_MON_HEAT = 26,       /* cumulative temperature-population gain through reactive links
-                              (conjugate: through every solid link, fluid side) */
-  ORC_MON_TSOLID = 27,     /* conjugate: sum of the solid temperature over solid nodes */
-  ORC_MON_HEAT_S = 28,     /* conjugate: cumulative solid-population gain through solid links */
-  ORC_MON_COUNT = 29
+  ORC_MON_HEAT = 26,       /* cumulative temperature-population gain through reactive links */
+  ORC_MON_COUNT = 27
 };
 
 typedef struct orc_ctx orc_ctx;
