@@ -714,3 +714,41 @@ def test_thermal_closure_needs_the_temperature_scalar():
     for bad in (dict(n_scal=1), dict(n_scal=2, arr_A=-1.0), dict(n_scal=2, n_it=65)):
         with pytest.raises(Exception):
             Oracle(dict(dim=2, nx=8, ny=8, arrhenius=True, arr_A=0.1, arr_Ta=1.0, **bad))
+
+
+# ---------------------------------------------------------------- residual (reading 16)
+
+def test_residual_of_a_decaying_mode_is_its_closed_form():
+    """The steady-state residual r is the relative L2 change of u and C over the fluid nodes
+    between two evaluations.  For a cosine concentration mode at rest the field at step t is
+    exactly C = 1 + a Re(1^T A^t w) cos(k x) (the single-mode update of the Fourier pin) and u = 0,
+    so r between steps t0 and t1 is |c(t1) - c(t0)| |cos| / |1 + a c(t1) cos| in closed form;
+    a field at rest that does not change has r = 0."""
+    L, tau_c, J0, a = 32, 0.8, 0.4, 0.1
+    shape = (1, 1, L)
+    cfg = dict(dim=2, nx=L, ny=1, nz=1, n_comp=1, tau=[1.0], n_scal=1, tau_c=[tau_c], J0=J0,
+               periodic=[1, 1, 1])
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    C0 = (1.0 + a * np.cos(k * x)).reshape(shape)
+    rho, u, _ = inputs.uniform_fields(shape, 1, 0)
+    o = make(cfg, None, (rho, u, C0[None]))
+    cc, w = o.lattice(1)
+    A = np.diag(np.exp(-1j * k * cc[:, 0])) @ ((1 - 1 / tau_c) * np.eye(len(w)) + np.outer(w, np.ones(len(w))) / tau_c)
+
+    def mode(t):
+        return (np.linalg.matrix_power(A, t) @ w.astype(complex)).sum().real
+
+    o.step(40)
+    assert o.residual() == -1.0          # the first evaluation only takes the snapshot
+    o.step(30)
+    r = o.residual()
+    c0, c1 = mode(40), mode(70)
+    cosx = np.cos(k * x)
+    expect = np.linalg.norm(a * (c1 - c0) * cosx) / np.linalg.norm(1.0 + a * c1 * cosx)
+    assert abs(r - expect) < 1e-10 * expect, (r, expect)
+    # uniform fields at rest do not change: r = 0
+    q = make(cfg, None, (rho, u, np.ones((1,) + shape)))
+    q.residual()
+    q.step(25)
+    assert q.residual() == 0.0
