@@ -11,10 +11,17 @@
  *   Sec. 2.1.5  species advection-diffusion LBGK (Eq. therpop_species,
  *               therpopeq_species) and the Kang wet-node reactive boundary
  *               (Eq. wetnode9)
+ *   Sec. 2.1.5  temperature-dependent rate and reaction heat (Eq. reactO2,
+ *               reacRate, fluxCon); conduction in the solid and its link
+ *               exchange with the fluid temperature (Eq. therpop_solid,
+ *               macroreacb_solid, tempCon, fluxCon, unknownpopTempS)
+ *   Sec. 3.1.1  moving plate; Sec. 3.4 velocity inlet and outlet
  *   Sec. 3.3    particle deposition (Eq. surface_deposition)
- * Readings where the paper is silent or garbled are those listed in the design doc
- * (D2Q9 weights normalised; D3Q7 for 3D scalars; wet node applied per link;
- * dissolution by solid-mass bookkeeping; synchronous psi evaluation).
+ * Where the paper is silent or garbled this file takes these readings: D2Q9
+ * weights normalised; D3Q7 for 3D scalars; the wet node applied per link;
+ * dissolution by solid-mass bookkeeping; synchronous psi evaluation; the
+ * solid-fluid heat exchange in a per-link, energy-conserving form (at
+ * exchange_solid).
  *
  * Every step is a full sweep with two population arrays (pull streaming):
  *   A. wet-node closure of the unknown scalar populations at reactive links
@@ -23,7 +30,10 @@
  *   B. rho, psi for ALL nodes, then forces, then velocities
  *   C. flow collision (BGK or MRT, Guo or velocity shift); scalar collision
  *   D. pull streaming with halfway bounce-back at walls (reactive links keep
- *      the bounce-back value until the next closure), inlet/outlet, periodic wrap
+ *      the bounce-back value until the next closure), inlet/outlet, periodic wrap;
+ *      with conduction in the solid, the solid collision comes after C, and the
+ *      exchange across solid links of the temperature and the streaming inside
+ *      the solid after D
  *   E. geometry flips (every N_geo steps), effective from the next step
  * No blocking, fusion or reordering beyond that; sums run i = 0..Q-1.
  * Compile with -ffp-contract=off.
@@ -62,6 +72,11 @@ struct orc_ctx {
   double* F[2];                   /* [N][3] total force per component */
   double* ub;                     /* [N][3] barycentric / physical velocity */
   double* Cs[2];                  /* scalar value per node */
+  double* gs;                     /* [N][Qc] solid thermal populations, stored (conjugate) */
+  double* gsp;                    /* post-collision */
+  double* kb;                     /* [N][Qc] rate constant k(T_b) of each fluid node's reactive
+                                     link, set by the last exchange (conjugate) */
+  uint8_t* kb_ok;                 /* 1 once kb of the link was set by an exchange */
   double mon[ORC_MON_COUNT];
   int64_t t;
   double* snap_u;
@@ -320,6 +335,10 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
   if (p && !st && p->arrhenius &&
       (p->n_scal != 2 || !(p->arr_A >= 0.0) || !(p->arr_Ta >= 0.0) || p->n_it < 0 || p->n_it > 64))
     st = -1;
+  /* conduction in the solid couples to the temperature scalar of the temperature-dependent mode */
+  if (p && !st && p->conjugate &&
+      (!p->arrhenius || !(p->tau_s > 0.5) || !(p->c_fs > 0.0) || p->geo_mode == 2))
+    st = -1;
   if (p && !st && p->flow_open_x &&
       (p->periodic[0] || p->periodic[1] || p->nx < 2 || p->n_comp != 1 || p->G[0][0] != 0.0 ||
        p->G_ads[0] != 0.0 || p->rho_solid != 0.0))
@@ -348,6 +367,12 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
     c->h[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
     c->hc[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
     c->hp[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
+    if (s == 1 && p->conjugate) {
+      c->gs = (double*)zalloc(sizeof(double) * N * c->lc.q);
+      c->gsp = (double*)zalloc(sizeof(double) * N * c->lc.q);
+      c->kb = (double*)zalloc(sizeof(double) * N * c->lc.q);
+      c->kb_ok = (uint8_t*)zalloc(N * c->lc.q);
+    }
     c->Cs[s] = (double*)zalloc(sizeof(double) * N);
   }
   c->flag = (uint8_t*)zalloc(N);
@@ -370,6 +395,7 @@ void orc_destroy(orc_ctx* c) {
     free(c->f[s]); free(c->fp[s]); free(c->rho[s]); free(c->jm[s]); free(c->psi[s]); free(c->F[s]);
     free(c->h[s]); free(c->hc[s]); free(c->hp[s]); free(c->Cs[s]);
   }
+  free(c->gs); free(c->gsp); free(c->kb); free(c->kb_ok);
   free(c->flag); free(c->acc); free(c->ub); free(c->snap_u); free(c->snap_C);
   free(c);
 }
@@ -393,6 +419,15 @@ int orc_set_fields(orc_ctx* c, const double* rho, const double* u, const double*
       for (int i = 0; i < Qf; ++i) c->f[s][n * Qf + i] = fluid ? feq(&c->lf, i, rho[s * N + n], un) : 0.0;
     for (int s = 0; s < c->p.n_scal; ++s)
       for (int i = 0; i < Qc; ++i) c->h[s][n * Qc + i] = fluid ? heq(&c->lc, i, C[s * N + n], un) : 0.0;
+    if (c->p.conjugate) {
+      /* the solid starts at rest equilibrium with the temperature given for it */
+      double zero[3] = {0.0, 0.0, 0.0};
+      for (int i = 0; i < Qc; ++i) {
+        c->gs[n * Qc + i] = fluid ? 0.0 : heq(&c->lc, i, C[N + n], zero);
+        c->kb_ok[n * Qc + i] = 0;
+        c->kb[n * Qc + i] = 0.0;
+      }
+    }
   }
   memset(c->mon, 0, sizeof(c->mon));
   c->t = 0;
@@ -474,6 +509,13 @@ static void macros(orc_ctx* c) {
         for (int i = 0; i < c->lc.q; ++i) C += c->hc[s][n * c->lc.q + i];  /* Eq. macroreacb_species */
       c->Cs[s][n] = C;
     }
+  if (c->p.conjugate)
+    for (int64_t n = 0; n < N; ++n) {
+      if (c->flag[n] == 0) continue;
+      double T = 0.0;
+      for (int i = 0; i < c->lc.q; ++i) T += c->gs[n * c->lc.q + i];
+      c->Cs[1][n] = T;   /* the solid temperature (Eq. macroreacb_solid, per unit rho c_p) */
+    }
 }
 
 /* ------------------------------------------------------ step, part C */
@@ -550,6 +592,96 @@ static void collide(orc_ctx* c) {
   }
 }
 
+/* Eq. therpop_solid with Eq. therpopeq_solid: conduction in the solid, g_s^eq = w T_s */
+static void collide_solid(orc_ctx* c) {
+  if (!c->p.conjugate) return;
+  int Qc = c->lc.q;
+  double zero[3] = {0.0, 0.0, 0.0};
+  for (int64_t n = 0; n < c->N; ++n) {
+    if (c->flag[n] == 0) continue;
+    const double T = c->Cs[1][n];
+    for (int i = 0; i < Qc; ++i) {
+      const double gi = c->gs[n * Qc + i];
+      c->gsp[n * Qc + i] = gi - (gi - heq(&c->lc, i, T, zero)) / c->p.tau_s;
+    }
+  }
+}
+
+/* The exchange across a solid link (Sec. 2.1.5, Eq. tempCon, fluxCon, reacRate), after the
+   streaming of every fluid population.  For fluid node n and direction i whose source
+   s = n - c_i is solid, the fluid temperature population ho = h*_T,opp(i)(n) leaving n toward s
+   and the solid population go = g*_s,i(s) leaving s toward n meet at one interface temperature
+   T_b.  Each side receives 2 w T_b minus what it sent (anti-bounce-back on the common T_b), and
+   the energy of the link, in units of the fluid's rho c_p, grows by the reaction heat Qp:
+       (h_T,i - ho) + (g_s,opp(i) - go) / c_fs = Qp,
+       h_T,i = 2 w T_b - ho,   g_s,opp(i) = 2 w T_b - go,
+   so that T_b = (c_fs ho + go + c_fs Qp / 2) / (w (c_fs + 1)).  With c_fs = 1, tau_s = tau_T
+   and Qp = 0 this is plain streaming (h_T,i = go, g_s,opp(i) = ho).  At a reactive link
+   Qp = h_r k(T_b) C_b tau_T / (tau_T - 1/2), the heat source scaled as the fluid's missing
+   populations carry it, with C_b = 2 hb / (2 w + k tau_c / (tau_c - 1/2)) the closure of the
+   species population hb = h_C,opp(i)(n) that has just streamed in; T_b and C_b are solved
+   together by n_it fixed-point iterations from the source-free T_b, and k is kept for the
+   species closure of the next step, which then finds the same C_b. */
+static void exchange_solid(orc_ctx* c) {
+  if (!c->p.conjugate) return;
+  int Qc = c->lc.q;
+  const lattice_t* K = &c->lc;
+  const double cf = c->p.c_fs;
+  const double fc = c->p.tau_c[0] / (c->p.tau_c[0] - 0.5);
+  const double fT = c->p.tau_c[1] / (c->p.tau_c[1] - 0.5);
+  for (int64_t n = 0; n < c->N; ++n) {
+    if (c->flag[n] != 0) continue;
+    int x, y, z;
+    coords(c, n, &x, &y, &z);
+    for (int i = 1; i < Qc; ++i) {
+      int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
+      if (src < 0 || c->flag[src] == 0) continue;
+      const double w = K->w[i];
+      const double ho = c->hp[1][n * Qc + K->opp[i]];
+      const double go = c->gsp[src * Qc + i];
+      double Tb = (cf * ho + go) / (w * (cf + 1.0));
+      double Qp = 0.0;
+      if (c->flag[src] == 2) {
+        const double hb = c->h[0][n * Qc + K->opp[i]];
+        double k = 0.0;
+        for (int it = 0; it <= c->p.n_it; ++it) {
+          k = c->p.arr_A * exp(-c->p.arr_Ta / Tb);
+          const double Cb = 2.0 * hb / (2.0 * w + k * fc);
+          Qp = c->p.heat_release * k * Cb * fT;
+          Tb = (cf * ho + go + 0.5 * cf * Qp) / (w * (cf + 1.0));
+        }
+        c->kb[n * Qc + i] = k;
+        c->kb_ok[n * Qc + i] = 1;
+      }
+      const double hin = 2.0 * w * Tb - ho;
+      const double gin = 2.0 * w * Tb - go;
+      c->h[1][n * Qc + i] = hin;
+      c->gs[src * Qc + K->opp[i]] = gin;
+      c->mon[ORC_MON_HEAT] += hin - ho;
+      c->mon[ORC_MON_HEAT_S] += gin - go;
+      c->mon[ORC_MON_HEAT_SRC] += Qp;
+    }
+  }
+}
+
+/* Streaming inside the solid; populations arriving from a fluid node were set by the exchange,
+   closed faces reflect. */
+static void stream_solid(orc_ctx* c) {
+  if (!c->p.conjugate) return;
+  int Qc = c->lc.q;
+  const lattice_t* K = &c->lc;
+  for (int64_t n = 0; n < c->N; ++n) {
+    if (c->flag[n] == 0) continue;
+    int x, y, z;
+    coords(c, n, &x, &y, &z);
+    for (int i = 0; i < Qc; ++i) {
+      int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
+      if (src >= 0 && c->flag[src] == 0) continue;
+      c->gs[n * Qc + i] = (src >= 0) ? c->gsp[src * Qc + i] : c->gsp[n * Qc + K->opp[i]];
+    }
+  }
+}
+
 /* ------------------------------------------------------ step, part D */
 
 static void stream(orc_ctx* c) {
@@ -607,7 +739,9 @@ static void stream(orc_ctx* c) {
           c->mon[ORC_MON_OUTFLOW + s] += hout - hin;
         } else {
           /* wall: bounce-back; at a reactive link of scalar 0 this value is
-             replaced by the wet-node closure at the start of the next step */
+             replaced by the wet-node closure at the start of the next step, and at a
+             solid link of the temperature with conduction in the solid, by the
+             exchange that follows the streaming */
           hin = hout;
         }
         c->h[s][n * Qc + i] = hin;
@@ -707,8 +841,56 @@ static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1
   }
 }
 
+/* Species closure with conduction in the solid: the wet-node closure of close_node at each
+   reactive link, with the rate constant k(T_b) that the link's last exchange (exchange_solid)
+   found together with C_b; before a link's first exchange k is taken at the heat-capacity-
+   weighted mean of the two sides' temperatures.  The heat of the reaction was put into the
+   temperature fields by that exchange, so the closure leaves the temperature unchanged. */
+static void close_node_conjugate(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book) {
+  int Qc = c->lc.q;
+  const lattice_t* K = &c->lc;
+  const double* h0 = &c->h[0][n * Qc];
+  const double* h1 = &c->h[1][n * Qc];
+  for (int i = 0; i < Qc; ++i) {
+    dst0[i] = h0[i];
+    dst1[i] = h1[i];
+  }
+  if (c->flag[n] != 0) return;
+  const double fc = c->p.tau_c[0] / (c->p.tau_c[0] - 0.5);
+  int x, y, z;
+  coords(c, n, &x, &y, &z);
+  for (int i = 1; i < Qc; ++i) {
+    int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
+    if (src < 0 || c->flag[src] != 2) continue;
+    double k = c->kb[n * Qc + i];
+    if (!c->kb_ok[n * Qc + i]) {
+      double Tf = 0.0, Ts = 0.0;
+      for (int j = 0; j < Qc; ++j) {
+        Tf += h1[j];
+        Ts += c->gs[src * Qc + j];
+      }
+      k = c->p.arr_A * exp(-c->p.arr_Ta / ((c->p.c_fs * Tf + Ts) / (c->p.c_fs + 1.0)));
+    }
+    const double w = K->w[i];
+    const double hb = h0[K->opp[i]];
+    const double Cb = 2.0 * hb / (2.0 * w + k * fc);
+    dst0[i] = 2.0 * w * Cb - hb;
+    if (book) {
+      const double r = k * Cb;
+      c->acc[src] += r;
+      c->mon[ORC_MON_REACTED] += r;
+      c->mon[ORC_MON_WALLX] += h0[i] - dst0[i];
+    }
+  }
+}
+
 static void close_all(orc_ctx* c, int book) {
   int Qc = c->lc.q;
+  if (c->p.conjugate) {
+    for (int64_t n = 0; n < c->N; ++n)
+      close_node_conjugate(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
+    return;
+  }
   if (c->p.arrhenius) {
     for (int64_t n = 0; n < c->N; ++n)
       close_node_thermal(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
@@ -785,7 +967,9 @@ static void flips(orc_ctx* c) {
         }
         /* the neighbour's scalars after its closure (the same closure the step applies) */
         double hm[2][QMAX];
-        if (c->p.arrhenius) {
+        if (c->p.conjugate) {
+          close_node_conjugate(c, m, hm[0], hm[1], 0);
+        } else if (c->p.arrhenius) {
           close_node_thermal(c, m, hm[0], hm[1], 0);
         } else {
           for (int s = 0; s < c->p.n_scal; ++s) close_node(c, s, m, hm[s], 0);
@@ -813,6 +997,16 @@ static void flips(orc_ctx* c) {
       }
       for (int s = 0; s < c->p.n_scal; ++s) {
         double C = mean[k * 4 + 2 + s];
+        if (s == 1 && c->p.conjugate) {
+          /* with conduction in the solid the node keeps its own temperature; its solid
+             populations leave the solid lattice */
+          C = 0.0;
+          for (int i = 0; i < Qc; ++i) {
+            C += c->gs[n * Qc + i];
+            c->gs[n * Qc + i] = 0.0;
+          }
+          c->mon[ORC_MON_SOLID_REM] += C;
+        }
         for (int i = 0; i < Qc; ++i) c->h[s][n * Qc + i] = heq(&c->lc, i, C, zero);
         c->mon[ORC_MON_INJ_SPEC + s] += C;
       }
@@ -852,7 +1046,10 @@ int orc_step(orc_ctx* c, int64_t nsteps) {
     deposit(c);
     macros(c);
     collide(c);
+    collide_solid(c);
     stream(c);
+    exchange_solid(c);
+    stream_solid(c);
     flips(c);
     c->t += 1;
   }
@@ -942,6 +1139,12 @@ int orc_get_monitors(orc_ctx* c, double* out) {
   out[ORC_MON_NSOLID] = nsolid;
   out[ORC_MON_NFLUID] = nfluid;
   out[ORC_MON_NONFINITE] = nonfinite;
+  double ts = 0.0;
+  if (c->p.conjugate)
+    for (int64_t n = 0; n < N; ++n)
+      if (c->flag[n] != 0)
+        for (int i = 0; i < Qc; ++i) ts += c->gs[n * Qc + i];
+  out[ORC_MON_TSOLID] = ts;
   return 0;
 }
 

@@ -55,11 +55,18 @@ typedef struct orc_params {
   int32_t arrhenius;           /* 1: scalar 1 is the temperature T; the surface rate of scalar 0 is
                                   k(T_b) = A exp(-Ta / T_b) at each reactive link's interface
                                   temperature, and the reaction releases heat into T (Sec. 2.1.5,
-                                  Eq. reactO2, reacRate, fluxCon with an adiabatic solid) */
+                                  Eq. reactO2, reacRate, fluxCon; an adiabatic solid unless
+                                  conjugate is set) */
   double arr_A;                /* pre-exponential factor A */
   double arr_Ta;               /* activation temperature E / R_u */
   double heat_release;         /* h_r: heat flux released per unit reaction rate */
   int32_t n_it;                /* fixed-point iterations of the C_b - T_b coupling per link */
+  int32_t conjugate;           /* 1 (with arrhenius): heat conduction in the solid on its own scalar
+                                  lattice, exchanged with the fluid temperature link by link
+                                  (Sec. 2.1.5, Eq. therpop_solid, tempCon, fluxCon, reacRate);
+                                  not with deposition */
+  double tau_s;                /* relaxation time of the solid thermal lattice (tau_e,s) */
+  double c_fs;                 /* heat-capacity ratio (rho c_p)_f / (rho c_p)_s */
 } orc_params;
 
 /* Monitor vector layout (doubles). */
@@ -80,8 +87,14 @@ enum {
   ORC_MON_NFLUID = 23,
   ORC_MON_NONFINITE = 24,
   ORC_MON_WALLX = 25,      /* cumulative scalar-0 population loss through reactive links */
-  ORC_MON_HEAT = 26,       /* cumulative temperature-population gain through reactive links */
-  ORC_MON_COUNT = 27
+  ORC_MON_HEAT = 26,       /* cumulative temperature-population gain through reactive links
+                              (conjugate: through every solid link, fluid side) */
+  ORC_MON_TSOLID = 27,     /* conjugate: sum of the stored solid temperature populations */
+  ORC_MON_HEAT_S = 28,     /* conjugate: cumulative solid-population gain through solid links */
+  ORC_MON_HEAT_SRC = 29,   /* conjugate: cumulative reaction heat put into the link exchanges,
+                              in units of the fluid's rho c_p */
+  ORC_MON_SOLID_REM = 30,  /* conjugate: cumulative solid populations removed by dissolution */
+  ORC_MON_COUNT = 31
 };
 
 typedef struct orc_ctx orc_ctx;

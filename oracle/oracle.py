@@ -53,7 +53,8 @@ class OrcParams(C.Structure):
         ("m_s0", C.c_double), ("DP", C.c_double), ("deposit_conservative", C.c_int32),
         ("N_geo", C.c_int32), ("u_wall_ymax", C.c_double * 3), ("flow_open_x", C.c_int32),
         ("u_in", C.c_double), ("arrhenius", C.c_int32), ("arr_A", C.c_double), ("arr_Ta", C.c_double),
-        ("heat_release", C.c_double), ("n_it", C.c_int32),
+        ("heat_release", C.c_double), ("n_it", C.c_int32), ("conjugate", C.c_int32),
+        ("tau_s", C.c_double), ("c_fs", C.c_double),
     ]
 
 
@@ -61,7 +62,7 @@ MON_NAMES = [
     "step", "mass0", "mass1", "momx", "momy", "momz", "species0", "species1", "reacted",
     "inflow0", "inflow1", "outflow0", "outflow1", "inj_mass0", "inj_mass1", "inj_spec0",
     "inj_spec1", "rem_mass0", "rem_mass1", "rem_spec0", "rem_spec1", "deposited", "nsolid",
-    "nfluid", "nonfinite", "wallx", "heat",
+    "nfluid", "nonfinite", "wallx", "heat", "tsolid", "heat_s", "heat_src", "solid_rem",
 ]
 
 _ENUMS = {
@@ -153,6 +154,9 @@ def make_params(cfg: dict) -> OrcParams:
     p.arr_Ta = float(d.get("arr_Ta", 0.0))
     p.heat_release = float(d.get("heat_release", 0.0))
     p.n_it = int(d.get("n_it", 16))
+    p.conjugate = int(bool(d.get("conjugate", False)))
+    p.tau_s = float(d.get("tau_s", 1.0))
+    p.c_fs = float(d.get("c_fs", 1.0))
     return p
 
 

@@ -78,7 +78,7 @@ def moment_matrix(dim, cf):
 
 
 class NaiveLBM:
-    def __init__(self, cfg, flags, f, h):
+    def __init__(self, cfg, flags, f, h, T_solid=None):
         self.cfg = cfg
         self.dim = int(cfg["dim"])
         self.nx, self.ny, self.nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg.get("nz", 1))
@@ -93,6 +93,14 @@ class NaiveLBM:
             if self.ns else np.zeros((0, len(self.cc), self.nz, self.ny, self.nx))
         self.acc = np.zeros((self.nz, self.ny, self.nx))
         self.t = 0
+        # conduction in the solid: its own populations, at rest equilibrium w_j T_s to start, and
+        # the rate constant that each reactive link's last exchange found
+        self.conj = bool(cfg.get("conjugate", False))
+        self.g = np.zeros((len(self.cc), self.nz, self.ny, self.nx))
+        if self.conj:
+            Ts = np.asarray(T_solid, dtype=np.float64).reshape(self.nz, self.ny, self.nx)
+            self.g = self.wc[:, None, None, None] * np.where(self.flags != 0, Ts, 0.0)[None]
+        self.kb = {}
         per = cfg.get("periodic", [1, 1, 1])
         self.per_f = [bool(p) for p in per]
         self.per_c = [bool(per[0]) and not cfg.get("ade_open_x", False), bool(per[1]), bool(per[2])]
@@ -154,6 +162,18 @@ class NaiveLBM:
                 continue
             w = self.wc[j]
             hb = hstate[0, self.oc[j], z, y, x]
+            if self.conj:
+                # the rate constant of the link's last exchange; before its first, k at the heat-
+                # capacity-weighted mean of the fluid node's and the solid node's temperatures
+                kk = self.kb.get((x, y, z, j))
+                if kk is None:
+                    cfs = float(cfg["c_fs"])
+                    Tm = (cfs * hstate[1, :, z, y, x].sum() + self.g[:, src[2], src[1], src[0]].sum()) / (cfs + 1)
+                    kk = A * np.exp(-Ta / Tm)
+                cb = 2 * hb / (2 * w + kk * fc)
+                closed[0, j] = 2 * w * cb - hb
+                reactions.append((src, kk * cb))
+                continue
             if not arr:
                 Cb = 2 * hb / (2 * w + Kr)
                 closed[0, j] = 2 * w * Cb - hb
@@ -217,7 +237,71 @@ class NaiveLBM:
                 self.f[s, :, z, y, x] = [self._feq(i, rbar[s], np.zeros(3)) for i in range(len(self.cf))]
             for s in range(self.ns):
                 self.h[s, :, z, y, x] = self.wc * cbar[s]
+            if self.conj:
+                # the new fluid node keeps the temperature its solid had
+                self.h[1, :, z, y, x] = self.wc * self.g[:, z, y, x].sum()
+                self.g[:, z, y, x] = 0.0
             self.flags[z, y, x] = 0
+
+    def _conduct(self, hpost, hnew):
+        """Conduction in the solid and its exchange with the fluid temperature (Sec. 2.1.5, Eq.
+        therpop_solid, tempCon, fluxCon, reacRate), pushed: a solid link carries ho out of the
+        fluid node and go out of the solid node; both sides get back 2 w T_b minus what they
+        sent, with T_b the root of
+            (h_in - ho) + (g_in - go) / c_fs = h_r k(T_b) C_b(T_b) tau_T / (tau_T - 1/2)
+        found by bracketing; C_b closes the species population that has just streamed into the
+        fluid node against the wall."""
+        from scipy.optimize import brentq
+        cfg = self.cfg
+        Qc = len(self.cc)
+        cfs, taus = float(cfg["c_fs"]), float(cfg["tau_s"])
+        A, Ta, hr = float(cfg["arr_A"]), float(cfg["arr_Ta"]), float(cfg["heat_release"])
+        tauc = [float(t) for t in cfg.get("tau_c", [1.0, 1.0])]
+        fc = tauc[0] / (tauc[0] - 0.5)
+        fT = tauc[1] / (tauc[1] - 0.5)
+        cells = [(x, y, z) for z in range(self.nz) for y in range(self.ny) for x in range(self.nx)]
+        solid = [q for q in cells if self.flags[q[2], q[1], q[0]] != 0]
+        gpost = np.zeros_like(self.g)
+        for (x, y, z) in solid:
+            Ts = float(self.g[:, z, y, x].sum())
+            gpost[:, z, y, x] = self.g[:, z, y, x] - (self.g[:, z, y, x] - self.wc * Ts) / taus
+        gnew = np.zeros_like(self.g)
+        for (x, y, z) in solid:
+            for j in range(Qc):
+                t = self._shift(x, y, z, self.cc[j], self.per_c)
+                if t is None:
+                    gnew[self.oc[j], z, y, x] = gpost[j, z, y, x]       # closed face: reflected
+                elif self.flags[t[2], t[1], t[0]] != 0:
+                    gnew[j, t[2], t[1], t[0]] = gpost[j, z, y, x]
+        for (x, y, z) in cells:
+            if self.flags[z, y, x] != 0:
+                continue
+            for j in range(1, Qc):
+                t = self._shift(x, y, z, self.cc[j], self.per_c)
+                if t is None or self.flags[t[2], t[1], t[0]] == 0:
+                    continue
+                w = self.wc[j]
+                ho = hpost[1, j, z, y, x]
+                go = gpost[self.oc[j], t[2], t[1], t[0]]
+                T0 = (cfs * ho + go) / (w * (cfs + 1))
+                Tb = T0
+                if self.flags[t[2], t[1], t[0]] == 2:
+                    hb = hnew[0, j, z, y, x]
+
+                    def source(T):
+                        kk = A * np.exp(-Ta / T)
+                        return kk, hr * kk * (2 * hb / (2 * w + kk * fc)) * fT
+
+                    def balance(T):
+                        return T - (cfs * ho + go + 0.5 * cfs * source(T)[1]) / (w * (cfs + 1))
+
+                    if hr != 0.0:
+                        T1 = T0 + 0.5 * cfs * hr * A * (hb / w) * fT / (w * (cfs + 1)) + 1e-9
+                        Tb = brentq(balance, T0, T1, xtol=1e-15, rtol=1e-15, maxiter=500)
+                    self.kb[(x, y, z, self.oc[j])] = source(Tb)[0]
+                hnew[1, self.oc[j], z, y, x] = 2 * w * Tb - ho
+                gnew[j, t[2], t[1], t[0]] = 2 * w * Tb - go
+        self.g = gnew
 
     def step(self):
         cfg = self.cfg
@@ -369,6 +453,8 @@ class NaiveLBM:
                         hnew[s, j, z, y, x] = self.wc[j] * C_in * (1 + float(np.dot(self.cc[j], vel[n])) / cs2)
                     elif xs >= nx:
                         hnew[s, j, z, y, x] = hpost[s, j, z, y, x]
+        if self.conj:
+            self._conduct(hpost, hnew)
         self.f, self.h = fnew, hnew
         self._flips()
         self.t += 1

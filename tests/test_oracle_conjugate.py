@@ -1,0 +1,201 @@
+"""Pins of the oracle's heat conduction in the solid and its exchange with the fluid temperature
+(Sec. 2.1.5, Eq. therpop_solid, macroreacb_solid, tempCon, fluxCon, reacRate).
+
+The exchange is checked against what the physics fixes without it: two identical media must
+behave as one medium, two half-spaces put in contact must reach the contact temperature of the
+erf solution of the heat equation, the energy of both lattices must change by exactly the
+reaction heat and what the open faces and the flips carry, and the heat of each link must match
+the reaction that the species closure books for it.
+"""
+from math import erf, sqrt
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2502_12955_gb300 import inputs
+
+
+def make(cfg, geom, fields):
+    o = Oracle(cfg)
+    o.set_geometry(geom)
+    rho, u, C = fields
+    o.set_fields(rho, u, C)
+    return o
+
+
+def _at_rest(shape, seed, T_lo=0.5, T_hi=0.8):
+    """Uniform density, zero velocity (so the flow stays exactly at rest) and random
+    species and temperature on every node, solids included."""
+    rng = np.random.default_rng(seed)
+    rho = np.ones((1,) + shape)
+    u = np.zeros((3,) + shape)
+    C = np.stack([1.0 + 0.1 * rng.random(shape), T_lo + (T_hi - T_lo) * rng.random(shape)])
+    return rho, u, C
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_identical_media_are_one_medium(dim):
+    """With c_fs = 1, tau_s = tau_T and no reaction heat, the solid conducts exactly as the fluid
+    at rest: the temperature of a domain with solids equals that of the same domain without
+    them, on every node, to round-off."""
+    shape = (1, 12, 16) if dim == 2 else (6, 8, 10)
+    nz, ny, nx = shape
+    geom = inputs.random_solids(shape, 0.3, seed=3 + dim, reactive_fraction=0.6)
+    fields = _at_rest(shape, 11 + dim)
+    base = dict(dim=dim, nx=nx, ny=ny, nz=nz, tau=[0.8], n_scal=2, tau_c=[0.7, 0.9],
+                J0=0.4 if dim == 2 else 0.25, periodic=[1, 0, 1])
+    a = make(dict(base, arrhenius=True, arr_A=0.3, arr_Ta=0.8, heat_release=0.0, n_it=8,
+                  conjugate=True, tau_s=0.9, c_fs=1.0), geom, fields)
+    b = make(base, np.zeros_like(geom), fields)
+    a.step(25)
+    b.step(25)
+    Ta, Tb = a.fields()["C"][1], b.fields()["C"][1]
+    assert np.abs(Ta - Tb).max() < 1e-14
+    assert np.ptp(Tb) > 0.005         # the field has not flattened: the comparison has content
+    assert a.monitors()["reacted"] > 0
+
+
+def _contact(dim, t_steps, tau_T=0.9, tau_s=0.7, c_fs=2.0, Tf0=1.0, Ts0=0.5):
+    n = 160
+    shape = (1, 2, n) if dim == 2 else (2, 2, n)
+    geom = np.zeros(shape, np.uint8)
+    geom[..., : n // 2] = 1
+    rho, u = np.ones((1,) + shape), np.zeros((3,) + shape)
+    C = np.stack([np.ones(shape), np.where(geom == 1, Ts0, Tf0)])
+    J0 = 0.4 if dim == 2 else 0.25
+    cfg = dict(dim=dim, nx=n, ny=2, nz=shape[0], tau=[0.8], n_scal=2, tau_c=[0.7, tau_T], J0=J0,
+               periodic=[0, 1, 1], arrhenius=True, arr_A=0.0, arr_Ta=0.0, heat_release=0.0,
+               conjugate=True, tau_s=tau_s, c_fs=c_fs)
+    o = make(cfg, geom, (rho, u, C))
+    cs2 = (1.0 - J0) / dim               # the scalar lattice's c_s^2; alpha = c_s^2 (tau - 1/2)
+    a_f, a_s = cs2 * (tau_T - 0.5), cs2 * (tau_s - 0.5)
+    # contact temperature of two semi-infinite bodies: effusivities e = rho c_p sqrt(alpha),
+    # in units of the solid's rho c_p
+    e_f, e_s = c_fs * sqrt(a_f), sqrt(a_s)
+    Tc = (e_f * Tf0 + e_s * Ts0) / (e_f + e_s)
+    errs = []
+    xi = n // 2 - 0.5                    # the interface lies halfway between the two nodes
+    for t in t_steps:
+        o.step(t - int(o.monitors()["step"]))
+        T = o.fields()["C"][1][0, 0]
+        ex = np.array([Tc + (Tf0 - Tc) * erf((x - xi) / (2 * sqrt(a_f * t))) if x > xi else
+                       Tc + (Ts0 - Tc) * erf((xi - x) / (2 * sqrt(a_s * t))) for x in range(n)])
+        errs.append(np.abs(T - ex).max() / (Tf0 - Ts0))
+    return errs
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_two_half_spaces_reach_the_contact_temperature(dim):
+    """A fluid half-space at T_f and a solid one at T_s, put in contact at t = 0, follow the erf
+    solutions of the heat equation on each side about the contact temperature
+    (e_f T_f + e_s T_s) / (e_f + e_s), e = rho c_p sqrt(alpha): the error falls as 1/t (second
+    order in the lattice spacing over the diffusion length).  Swapping c_fs, or the two
+    relaxation times, moves the contact temperature by tens of percent of T_f - T_s."""
+    e200, e400 = _contact(dim, (200, 400))
+    assert e400 < 1.5e-3
+    assert 1.7 < e200 / e400 < 2.3
+
+
+def _energy(m, c_fs):
+    """Heat in both lattices, in units of the fluid's rho c_p."""
+    return m["species1"] + m["tsolid"] / c_fs
+
+
+@pytest.mark.parametrize("geo", [dict(), dict(geo_mode="dissolve", V_m=60.0)])
+def test_energy_budget_per_step(geo):
+    """With flow, reaction heat, c_fs != 1 and tau_s != tau_T, the heat in both lattices changes
+    each step by exactly the reaction heat put into the exchanges, plus what the dissolution
+    flips move from the solid into the fluid (the node keeps its temperature, so the fluid gains
+    T_s while the solid loses T_s / c_fs)."""
+    c_fs = 2.5
+    shape = (1, 12, 14)
+    geom = inputs.random_solids(shape, 0.25, seed=61, reactive_fraction=0.7)
+    rho, u, C = inputs.perturbed_fields(shape, 1, 2, seed=62, amp_rho=0.01, amp_u=0.01, C0=0.9)
+    cfg = dict(dim=2, nx=14, ny=12, tau=[0.8], g=[3e-4, 0, 0], n_scal=2, tau_c=[0.7, 0.9], J0=0.4,
+               periodic=[1, 0, 1], arrhenius=True, arr_A=0.4, arr_Ta=0.8, heat_release=0.05, n_it=24,
+               conjugate=True, tau_s=0.65, c_fs=c_fs, **geo)
+    o = make(cfg, geom, (rho, u, C))
+    for _ in range(40):
+        m0 = o.monitors()
+        o.step(1)
+        m1 = o.monitors()
+        d = {k: m1[k] - m0[k] for k in ("heat_src", "heat", "heat_s", "inj_spec1", "solid_rem")}
+        dE = _energy(m1, c_fs) - _energy(m0, c_fs)
+        assert abs(dE - (d["heat_src"] + d["inj_spec1"] - d["solid_rem"] / c_fs)) < 1e-12 * _energy(m0, c_fs)
+        assert abs(d["heat"] + d["heat_s"] / c_fs - d["heat_src"]) < 1e-13
+        assert d["inj_spec1"] == d["solid_rem"]
+    assert m1["heat_src"] > 0
+    if geo:
+        assert m1["solid_rem"] > 0, "no flip happened"
+
+
+def test_reaction_heat_matches_the_booked_reaction():
+    """The exchange of step t solves C_b and T_b together and keeps k(T_b); the species closure
+    of step t + 1 books k C_b for the same link.  So the heat of steps 1..K equals
+    h_r tau_T / (tau_T - 1/2) times the reaction booked by the closures of steps 2..K+1 (the
+    scaling of the heat source in the missing populations, Eq. unknownpopTempS)."""
+    shape = (1, 12, 14)
+    geom = inputs.random_solids(shape, 0.25, seed=63, reactive_fraction=0.7)
+    fields = inputs.perturbed_fields(shape, 1, 2, seed=64, amp_rho=0.01, amp_u=0.01, C0=0.9)
+    hr, tau_T = 0.05, 0.9
+    cfg = dict(dim=2, nx=14, ny=12, tau=[0.8], g=[2e-4, 0, 0], n_scal=2, tau_c=[0.7, tau_T], J0=0.4,
+               periodic=[1, 0, 1], arrhenius=True, arr_A=0.4, arr_Ta=0.8, heat_release=hr, n_it=32,
+               conjugate=True, tau_s=0.65, c_fs=2.5)
+    first = make(cfg, geom, fields)
+    first.step(1)
+    o = make(cfg, geom, fields)
+    K = 20
+    o.step(K)
+    heat = o.monitors()["heat_src"]
+    o.step(1)
+    booked = o.monitors()["reacted"] - first.monitors()["reacted"]
+    assert heat > 0
+    assert abs(heat - hr * tau_T / (tau_T - 0.5) * booked) < 1e-12 * heat
+
+
+def test_uniform_temperature_gives_the_rate_at_that_temperature():
+    """Fluid at rest and solid at one temperature T0, no reaction heat: every link's T_b is T0
+    whatever c_fs and tau_s, so the species equal those of the constant rate A exp(-Ta / T0) and
+    the temperature stays T0 on every node."""
+    shape = (1, 12, 14)
+    geom = inputs.random_solids(shape, 0.25, seed=65, reactive_fraction=0.7)
+    T0, A, Ta = 1.3, 0.2, 0.9
+    rho, u, C = _at_rest(shape, 66)
+    C[1] = T0
+    cfg = dict(dim=2, nx=14, ny=12, tau=[0.8], n_scal=2, tau_c=[0.7, 0.9], J0=0.4, periodic=[1, 0, 1])
+    a = make(dict(cfg, arrhenius=True, arr_A=A, arr_Ta=Ta, heat_release=0.0, conjugate=True,
+                  tau_s=0.6, c_fs=3.0), geom, (rho, u, C))
+    b = make(dict(cfg, k_react=A * np.exp(-Ta / T0)), geom, (rho, u, C))
+    a.step(30)
+    b.step(30)
+    fa, fb = a.fields(), b.fields()
+    assert np.abs(fa["C"][0] - fb["C"][0]).max() < 1e-13
+    assert np.abs(fa["C"][1] - T0).max() < 1e-13
+    assert abs(a.monitors()["reacted"] - b.monitors()["reacted"]) < 1e-12 * b.monitors()["reacted"]
+
+
+def test_coupling_converges_in_the_iterations():
+    """The fixed-point iterations of the C_b - T_b coupling converge: 40 and 80 iterations give
+    the same fields to round-off, while a single one does not."""
+    shape = (1, 12, 14)
+    geom = inputs.random_solids(shape, 0.25, seed=67, reactive_fraction=0.7)
+    fields = inputs.perturbed_fields(shape, 1, 2, seed=68, amp_rho=0.01, amp_u=0.01, C0=0.9)
+    cfg = dict(dim=2, nx=14, ny=12, tau=[0.8], n_scal=2, tau_c=[0.7, 0.9], J0=0.4, periodic=[1, 0, 1],
+               arrhenius=True, arr_A=0.6, arr_Ta=1.5, heat_release=0.3, conjugate=True, tau_s=0.65, c_fs=2.5)
+    runs = {}
+    for n_it in (0, 40, 64):
+        o = make(dict(cfg, n_it=n_it), geom, fields)
+        o.step(10)
+        runs[n_it] = o.fields()["C"]
+    assert np.abs(runs[40] - runs[64]).max() < 1e-13
+    assert np.abs(runs[0] - runs[64]).max() > 1e-8
+
+
+def test_conduction_needs_the_temperature_rate_and_valid_media():
+    ok = dict(dim=2, nx=8, ny=8, n_scal=2, arrhenius=True, arr_A=0.1, arr_Ta=1.0, conjugate=True,
+              tau_s=0.8, c_fs=1.0)
+    Oracle(ok)
+    for bad in (dict(arrhenius=False), dict(tau_s=0.5), dict(c_fs=0.0), dict(geo_mode="deposit")):
+        with pytest.raises(Exception):
+            Oracle(dict(ok, **bad))

@@ -50,6 +50,16 @@ CASES = {
                                            tau_c=[0.6, 0.8], J0=0.25, arrhenius=True, arr_A=0.3,
                                            arr_Ta=0.8, heat_release=0.03, n_it=24, geo_mode="dissolve",
                                            V_m=40.0, N_geo=2, periodic=[1, 1, 1]),
+    "2d_conjugate_heat_walls": dict(dim=2, nx=8, ny=8, tau=[0.8], g=[2e-4, 0, 0], n_scal=2, tau_c=[0.7, 0.9],
+                                    J0=0.4, arrhenius=True, arr_A=0.4, arr_Ta=1.0, heat_release=0.05, n_it=40,
+                                    conjugate=True, tau_s=0.65, c_fs=2.5, periodic=[1, 0, 1]),
+    "2d_conjugate_open": dict(dim=2, nx=8, ny=8, tau=[0.9], g=[1e-4, 0, 0], n_scal=2, tau_c=[0.8, 0.7], J0=0.4,
+                              arrhenius=True, arr_A=0.3, arr_Ta=0.6, heat_release=0.04, n_it=40, conjugate=True,
+                              tau_s=1.1, c_fs=0.7, ade_open_x=True, C_in=[1.0, 0.9], periodic=[1, 1, 1]),
+    "3d_mrt_conjugate_dissolution": dict(dim=3, nx=8, ny=8, nz=8, tau=[1.0], collision="mrt", g=[1e-4, 0, 0],
+                                         n_scal=2, tau_c=[0.6, 0.8], J0=0.25, arrhenius=True, arr_A=0.3,
+                                         arr_Ta=0.8, heat_release=0.03, n_it=40, conjugate=True, tau_s=0.7,
+                                         c_fs=0.6, geo_mode="dissolve", V_m=40.0, N_geo=2, periodic=[1, 1, 1]),
     "3d_mrt_velocity_inlet": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", flow_open_x=True,
                                   u_in=0.02, g=[0, 0, 1e-4], u_wall_ymax=[0.01, 0, 0], periodic=[0, 0, 1]),
 }
@@ -70,7 +80,7 @@ def test_oracle_matches_naive_formulation(name):
     o.set_geometry(geom)
     o.set_fields(rho, u, C if ns else None)
     f0, h0 = o.pops()
-    nv = NaiveLBM(cfg, geom, f0, h0)
+    nv = NaiveLBM(cfg, geom, f0, h0, T_solid=C[1] if cfg.get("conjugate") else None)
     for step in range(4):
         o.step(1)
         nv.step()
@@ -85,3 +95,7 @@ def test_oracle_matches_naive_formulation(name):
             assert dh < 1e-13, f"{name} step {step + 1}: scalar populations differ by {dh:.3e}"
             acc = o.fields()["acc"]
             assert np.abs(acc - nv.acc).max() < 1e-13, f"{name} step {step + 1}: reaction bookkeeping"
+        if cfg.get("conjugate"):
+            sol = flags != 0
+            dT = np.abs(o.fields()["C"][1][sol] - nv.g.sum(axis=0)[sol]).max()
+            assert dT < 1e-13, f"{name} step {step + 1}: solid temperatures differ by {dT:.3e}"
