@@ -14,7 +14,8 @@
  *   Sec. 2.1.5  temperature-dependent rate and reaction heat (Eq. reactO2,
  *               reacRate, fluxCon); conduction in the solid and its link
  *               exchange with the fluid temperature (Eq. therpop_solid,
- *               macroreacb_solid, tempCon, fluxCon, unknownpopTempS)
+ *               macroreacb_solid, tempCon, fluxCon, unknownpopTempS); the
+ *               reaction product (Eq. react, reactCO2)
  *   Sec. 3.1.1  moving plate; Sec. 3.4 velocity inlet and outlet
  *   Sec. 3.3    particle deposition (Eq. surface_deposition)
  * Where the paper is silent or garbled this file takes these readings: D2Q9
@@ -61,9 +62,10 @@ struct orc_ctx {
   int per_c[3];                   /* scalar-lattice periodicity */
   double* f[2];                   /* [N][Qf] pre-collision, per component */
   double* fp[2];                  /* post-collision */
-  double* h[2];                   /* [N][Qc] stored state (reactive links hold bounce-back value) */
-  double* hc[2];                  /* [N][Qc] state after the wet-node closure (per-step scratch) */
-  double* hp[2];
+  double* h[3];                   /* [N][Qc] stored state (reactive links hold bounce-back value);
+                                     scalars 0 .. n_scal-1, then the product lattice */
+  double* hc[3];                  /* [N][Qc] state after the wet-node closure (per-step scratch) */
+  double* hp[3];
   uint8_t* flag;
   double* acc;                    /* reacted amount (solid) / deposited fraction (fluid) */
   double* rho[2];
@@ -71,7 +73,7 @@ struct orc_ctx {
   double* psi[2];
   double* F[2];                   /* [N][3] total force per component */
   double* ub;                     /* [N][3] barycentric / physical velocity */
-  double* Cs[2];                  /* scalar value per node */
+  double* Cs[3];                  /* scalar value per node */
   double* gs;                     /* [N][Qc] solid thermal populations, stored (conjugate) */
   double* gsp;                    /* post-collision */
   double* kb;                     /* [N][Qc] rate constant k(T_b) of each fluid node's reactive
@@ -312,6 +314,23 @@ static double heq(const lattice_t* K, int i, double C, const double* u) {
 
 static void* zalloc(size_t n) { return calloc(n ? n : 1, 1); }
 
+/* scalar lattices: the n_scal given ones, then the product lattice if there is one */
+static inline int n_lat(const orc_ctx* c) { return c->p.n_scal + (c->p.product ? 1 : 0); }
+static inline double tau_of(const orc_ctx* c, int s) { return s < c->p.n_scal ? c->p.tau_c[s] : c->p.tau_p; }
+static inline double cin_of(const orc_ctx* c, int s) { return s < c->p.n_scal ? c->p.C_in[s] : c->p.C_in_p; }
+
+/* monitor entry of scalar s for a per-scalar quantity: the product lattice has its own */
+static int mon_of(const orc_ctx* c, int base, int s) {
+  if (s < c->p.n_scal) return base + s;
+  switch (base) {
+    case ORC_MON_SPECIES: return ORC_MON_SPECIES_P;
+    case ORC_MON_INFLOW: return ORC_MON_INFLOW_P;
+    case ORC_MON_OUTFLOW: return ORC_MON_OUTFLOW_P;
+    case ORC_MON_INJ_SPEC: return ORC_MON_INJ_SPEC_P;
+    default: return ORC_MON_REM_SPEC_P;
+  }
+}
+
 orc_ctx* orc_create(const orc_params* p, int* status) {
   int st = 0;
   if (!p || (p->dim != 2 && p->dim != 3) || p->nx < 1 || p->ny < 1 || p->nz < 1 ||
@@ -328,8 +347,6 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
   if (p && !st && (p->u_wall_ymax[0] != 0.0 || p->u_wall_ymax[1] != 0.0 || p->u_wall_ymax[2] != 0.0) &&
       (p->periodic[1] || p->u_wall_ymax[1] != 0.0))
     st = -1;
-  /* the velocity inlet / zero-gradient outlet closes the x axis of the flow lattice, needs the
-     channel walls on y, and is defined for one component without Shan-Chen forces */
   /* the temperature-dependent rate needs the temperature as scalar 1, a positive temperature
      scale and a bounded iteration */
   if (p && !st && p->arrhenius &&
@@ -339,6 +356,10 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
   if (p && !st && p->conjugate &&
       (!p->arrhenius || !(p->tau_s > 0.5) || !(p->c_fs > 0.0) || p->geo_mode == 2))
     st = -1;
+  /* the product needs the reacting scalar 0; deposition has no reaction to produce it */
+  if (p && !st && p->product && (p->n_scal < 1 || !(p->tau_p > 0.5) || p->geo_mode == 2)) st = -1;
+  /* the velocity inlet / zero-gradient outlet closes the x axis of the flow lattice, needs the
+     channel walls on y, and is defined for one component without Shan-Chen forces */
   if (p && !st && p->flow_open_x &&
       (p->periodic[0] || p->periodic[1] || p->nx < 2 || p->n_comp != 1 || p->G[0][0] != 0.0 ||
        p->G_ads[0] != 0.0 || p->rho_solid != 0.0))
@@ -363,7 +384,7 @@ orc_ctx* orc_create(const orc_params* p, int* status) {
     c->psi[s] = (double*)zalloc(sizeof(double) * N);
     c->F[s] = (double*)zalloc(sizeof(double) * N * 3);
   }
-  for (int s = 0; s < p->n_scal; ++s) {
+  for (int s = 0; s < n_lat(c); ++s) {
     c->h[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
     c->hc[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
     c->hp[s] = (double*)zalloc(sizeof(double) * N * c->lc.q);
@@ -393,6 +414,8 @@ void orc_destroy(orc_ctx* c) {
   if (!c) return;
   for (int s = 0; s < 2; ++s) {
     free(c->f[s]); free(c->fp[s]); free(c->rho[s]); free(c->jm[s]); free(c->psi[s]); free(c->F[s]);
+  }
+  for (int s = 0; s < 3; ++s) {
     free(c->h[s]); free(c->hc[s]); free(c->hp[s]); free(c->Cs[s]);
   }
   free(c->gs); free(c->gsp); free(c->kb); free(c->kb_ok);
@@ -417,7 +440,7 @@ int orc_set_fields(orc_ctx* c, const double* rho, const double* u, const double*
     int fluid = (c->flag[n] == 0);
     for (int s = 0; s < c->p.n_comp; ++s)
       for (int i = 0; i < Qf; ++i) c->f[s][n * Qf + i] = fluid ? feq(&c->lf, i, rho[s * N + n], un) : 0.0;
-    for (int s = 0; s < c->p.n_scal; ++s)
+    for (int s = 0; s < n_lat(c); ++s)
       for (int i = 0; i < Qc; ++i) c->h[s][n * Qc + i] = fluid ? heq(&c->lc, i, C[s * N + n], un) : 0.0;
     if (c->p.conjugate) {
       /* the solid starts at rest equilibrium with the temperature given for it */
@@ -502,7 +525,7 @@ static void macros(orc_ctx* c) {
     }
     for (int a = 0; a < 3; ++a) c->ub[n * 3 + a] = m[a] / rt;
   }
-  for (int s = 0; s < c->p.n_scal; ++s)
+  for (int s = 0; s < n_lat(c); ++s)
     for (int64_t n = 0; n < N; ++n) {
       double C = 0.0;
       if (c->flag[n] == 0)
@@ -582,11 +605,11 @@ static void collide(orc_ctx* c) {
       }
     }
     /* Eq. therpop_species with Eq. therpopeq_species, u = physical velocity */
-    for (int s = 0; s < c->p.n_scal; ++s) {
+    for (int s = 0; s < n_lat(c); ++s) {
       double C = c->Cs[s][n];
       for (int i = 0; i < Qc; ++i) {
         double hi = c->hc[s][n * Qc + i];
-        c->hp[s][n * Qc + i] = hi - (hi - heq(&c->lc, i, C, u)) / c->p.tau_c[s];
+        c->hp[s][n * Qc + i] = hi - (hi - heq(&c->lc, i, C, u)) / tau_of(c, s);
       }
     }
   }
@@ -721,7 +744,7 @@ static void stream(orc_ctx* c) {
           c->f[s][n * Qf + i] = v;
         }
       }
-    for (int s = 0; s < c->p.n_scal; ++s)
+    for (int s = 0; s < n_lat(c); ++s)
       for (int i = 0; i < Qc; ++i) {
         int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
         double hout = c->hp[s][n * Qc + K->opp[i]];
@@ -731,12 +754,12 @@ static void stream(orc_ctx* c) {
           hin = c->hp[s][src * Qc + i];
         } else if (src < 0 && c->p.ade_open_x && xs < 0) {
           /* inlet ghost at equilibrium with C_in and the node's own velocity */
-          hin = heq(K, i, c->p.C_in[s], &c->ub[n * 3]);
-          c->mon[ORC_MON_INFLOW + s] += hin - hout;
+          hin = heq(K, i, cin_of(c, s), &c->ub[n * 3]);
+          c->mon[mon_of(c, ORC_MON_INFLOW, s)] += hin - hout;
         } else if (src < 0 && c->p.ade_open_x && xs >= c->p.nx) {
           /* zero-gradient outlet: h_i(nx-1) = h_i(nx-2) = own post-collision h_i */
           hin = c->hp[s][n * Qc + i];
-          c->mon[ORC_MON_OUTFLOW + s] += hout - hin;
+          c->mon[mon_of(c, ORC_MON_OUTFLOW, s)] += hout - hin;
         } else {
           /* wall: bounce-back; at a reactive link of scalar 0 this value is
              replaced by the wet-node closure at the start of the next step, and at a
@@ -760,7 +783,7 @@ static void stream(orc_ctx* c) {
    populations of node n.  When book != 0 the reaction rate k C_b of each link is
    added to acc of that solid node and to the reacted total, and the stored-minus-
    closed value (what left the lattice through the link) to the wall exchange. */
-static void close_node(orc_ctx* c, int s, int64_t n, double* dst, int book) {
+static void close_node(orc_ctx* c, int s, int64_t n, double* dst, int book, double* rl) {
   int Qc = c->lc.q;
   const lattice_t* K = &c->lc;
   const double* hs = &c->h[s][n * Qc];
@@ -776,6 +799,7 @@ static void close_node(orc_ctx* c, int s, int64_t n, double* dst, int book) {
     double Cb = 2.0 * hb / (2.0 * K->w[i] + Kr);
     double hin = 2.0 * K->w[i] * Cb - hb;
     dst[i] = hin;
+    if (rl) rl[i] = c->p.k_react * Cb;
     if (book) {
       /* reaction rate at the wall, Eq. reactO2: k C_b (= (1 - 1/(2 tau_c)) (hb - h_i)) */
       double r = c->p.k_react * Cb;
@@ -799,7 +823,8 @@ static void close_node(orc_ctx* c, int s, int64_t n, double* dst, int book) {
    (Eq. fluxCon with an adiabatic solid).  The coupled pair is solved by n_it fixed-point
    iterations from the zero-flux value T_b = gb / w; then
        h_C,i = 2 w C_b - hb,      h_T,i = gb + Q tau_T / (tau_T - 1/2). */
-static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book) {
+static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book,
+                               double* rl) {
   int Qc = c->lc.q;
   const lattice_t* K = &c->lc;
   const double* h0 = &c->h[0][n * Qc];
@@ -831,6 +856,7 @@ static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1
     const double Q = c->p.heat_release * k * Cb;
     dst0[i] = 2.0 * w * Cb - hb;
     dst1[i] = gb + Q * fT;
+    rl[i] = k * Cb;
     if (book) {
       const double r = k * Cb;
       c->acc[src] += r;
@@ -846,7 +872,8 @@ static void close_node_thermal(orc_ctx* c, int64_t n, double* dst0, double* dst1
    found together with C_b; before a link's first exchange k is taken at the heat-capacity-
    weighted mean of the two sides' temperatures.  The heat of the reaction was put into the
    temperature fields by that exchange, so the closure leaves the temperature unchanged. */
-static void close_node_conjugate(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book) {
+static void close_node_conjugate(orc_ctx* c, int64_t n, double* dst0, double* dst1, int book,
+                                 double* rl) {
   int Qc = c->lc.q;
   const lattice_t* K = &c->lc;
   const double* h0 = &c->h[0][n * Qc];
@@ -875,6 +902,7 @@ static void close_node_conjugate(orc_ctx* c, int64_t n, double* dst0, double* ds
     const double hb = h0[K->opp[i]];
     const double Cb = 2.0 * hb / (2.0 * w + k * fc);
     dst0[i] = 2.0 * w * Cb - hb;
+    rl[i] = k * Cb;
     if (book) {
       const double r = k * Cb;
       c->acc[src] += r;
@@ -884,20 +912,49 @@ static void close_node_conjugate(orc_ctx* c, int64_t n, double* dst0, double* ds
   }
 }
 
+/* The product of the surface reaction (Sec. 2.1.5, Eq. react, reactCO2): at each reactive link
+   the product enters the fluid at the rate the reaction takes scalar 0, r = k C_b of that link.
+   The same per-link wet-node ansatz as the species closure, with the sign of the flux reversed,
+   (1 - 1/(2 tau_p)) (h_P,i - h_P,opp(i)) = r, gives h_P,i = h_P,opp(i) + r tau_p / (tau_p - 1/2).
+   rl holds the link rates of scalar 0 from its closure at this node. */
+static void close_node_product(orc_ctx* c, int64_t n, double* dst, int book, const double* rl) {
+  int Qc = c->lc.q;
+  const lattice_t* K = &c->lc;
+  const double* hs = &c->h[c->p.n_scal][n * Qc];
+  for (int i = 0; i < Qc; ++i) dst[i] = hs[i];
+  if (c->flag[n] != 0) return;
+  const double fp = c->p.tau_p / (c->p.tau_p - 0.5);
+  int x, y, z;
+  coords(c, n, &x, &y, &z);
+  for (int i = 1; i < Qc; ++i) {
+    int64_t src = nbr(c, x, y, z, -K->c[i][0], -K->c[i][1], -K->c[i][2], c->per_c);
+    if (src < 0 || c->flag[src] != 2) continue;
+    dst[i] = hs[K->opp[i]] + rl[i] * fp;
+    if (book) c->mon[ORC_MON_PRODUCED] += dst[i] - hs[i];
+  }
+}
+
+/* Every scalar closure of node n, into dst[s] for each scalar lattice s. */
+static void close_node_all(orc_ctx* c, int64_t n, double* const* dst, int book) {
+  double rl[QMAX];
+  for (int i = 0; i < QMAX; ++i) rl[i] = 0.0;
+  if (c->p.conjugate) {
+    close_node_conjugate(c, n, dst[0], dst[1], book, rl);
+  } else if (c->p.arrhenius) {
+    close_node_thermal(c, n, dst[0], dst[1], book, rl);
+  } else {
+    for (int s = 0; s < c->p.n_scal; ++s) close_node(c, s, n, dst[s], book, s == 0 ? rl : NULL);
+  }
+  if (c->p.product) close_node_product(c, n, dst[c->p.n_scal], book, rl);
+}
+
 static void close_all(orc_ctx* c, int book) {
   int Qc = c->lc.q;
-  if (c->p.conjugate) {
-    for (int64_t n = 0; n < c->N; ++n)
-      close_node_conjugate(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
-    return;
+  for (int64_t n = 0; n < c->N; ++n) {
+    double* dst[3] = {NULL, NULL, NULL};
+    for (int s = 0; s < n_lat(c); ++s) dst[s] = &c->hc[s][n * Qc];
+    close_node_all(c, n, dst, book);
   }
-  if (c->p.arrhenius) {
-    for (int64_t n = 0; n < c->N; ++n)
-      close_node_thermal(c, n, &c->hc[0][n * Qc], &c->hc[1][n * Qc], book);
-    return;
-  }
-  for (int s = 0; s < c->p.n_scal; ++s)
-    for (int64_t n = 0; n < c->N; ++n) close_node(c, s, n, &c->hc[s][n * Qc], book);
 }
 
 /* ---------------------------------------------- step, part A and E */
@@ -948,13 +1005,14 @@ static void flips(orc_ctx* c) {
   if (c->p.geo_mode == 1) {
     /* dissolution: new fluid node at rest equilibrium with the mean density and
        concentration of its fluid neighbours (values after this step's streaming) */
-    double* mean = (double*)zalloc(sizeof(double) * (size_t)(cnt * 4 + 1));
+    /* per new node: the mean density of each component, then the mean of each scalar */
+    double* mean = (double*)zalloc(sizeof(double) * (size_t)(cnt * 5 + 1));
     int* ok = (int*)zalloc(sizeof(int) * (size_t)(cnt + 1));
     for (int64_t k = 0; k < cnt; ++k) {
       int64_t n = list[k];
       int x, y, z;
       coords(c, n, &x, &y, &z);
-      double sr[2] = {0.0, 0.0}, sc[2] = {0.0, 0.0};
+      double sr[2] = {0.0, 0.0}, sc[3] = {0.0, 0.0, 0.0};
       int m_count = 0;
       for (int i = 1; i < Qf; ++i) {
         int64_t m = nbr(c, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2], c->p.periodic);
@@ -966,37 +1024,30 @@ static void flips(orc_ctx* c) {
           sr[s] += r;
         }
         /* the neighbour's scalars after its closure (the same closure the step applies) */
-        double hm[2][QMAX];
-        if (c->p.conjugate) {
-          close_node_conjugate(c, m, hm[0], hm[1], 0);
-        } else if (c->p.arrhenius) {
-          close_node_thermal(c, m, hm[0], hm[1], 0);
-        } else {
-          for (int s = 0; s < c->p.n_scal; ++s) close_node(c, s, m, hm[s], 0);
-        }
-        for (int s = 0; s < c->p.n_scal; ++s) {
+        double hm[3][QMAX];
+        double* dst[3] = {hm[0], hm[1], hm[2]};
+        close_node_all(c, m, dst, 0);
+        for (int s = 0; s < n_lat(c); ++s) {
           double C = 0.0;
           for (int j = 0; j < Qc; ++j) C += hm[s][j];
           sc[s] += C;
         }
       }
       ok[k] = m_count > 0;
-      for (int s = 0; s < 2; ++s) {
-        mean[k * 4 + s] = m_count ? sr[s] / (double)m_count : 0.0;
-        mean[k * 4 + 2 + s] = m_count ? sc[s] / (double)m_count : 0.0;
-      }
+      for (int s = 0; s < 2; ++s) mean[k * 5 + s] = m_count ? sr[s] / (double)m_count : 0.0;
+      for (int s = 0; s < 3; ++s) mean[k * 5 + 2 + s] = m_count ? sc[s] / (double)m_count : 0.0;
     }
     double zero[3] = {0.0, 0.0, 0.0};
     for (int64_t k = 0; k < cnt; ++k) {
       if (!ok[k]) continue;
       int64_t n = list[k];
       for (int s = 0; s < c->p.n_comp; ++s) {
-        double r = mean[k * 4 + s];
+        double r = mean[k * 5 + s];
         for (int i = 0; i < Qf; ++i) c->f[s][n * Qf + i] = feq(L, i, r, zero);
         c->mon[ORC_MON_INJ_MASS + s] += r;
       }
-      for (int s = 0; s < c->p.n_scal; ++s) {
-        double C = mean[k * 4 + 2 + s];
+      for (int s = 0; s < n_lat(c); ++s) {
+        double C = mean[k * 5 + 2 + s];
         if (s == 1 && c->p.conjugate) {
           /* with conduction in the solid the node keeps its own temperature; its solid
              populations leave the solid lattice */
@@ -1008,7 +1059,7 @@ static void flips(orc_ctx* c) {
           c->mon[ORC_MON_SOLID_REM] += C;
         }
         for (int i = 0; i < Qc; ++i) c->h[s][n * Qc + i] = heq(&c->lc, i, C, zero);
-        c->mon[ORC_MON_INJ_SPEC + s] += C;
+        c->mon[mon_of(c, ORC_MON_INJ_SPEC, s)] += C;
       }
       c->flag[n] = 0;
     }
@@ -1026,13 +1077,13 @@ static void flips(orc_ctx* c) {
         }
         c->mon[ORC_MON_REM_MASS + s] += r;
       }
-      for (int s = 0; s < c->p.n_scal; ++s) {
+      for (int s = 0; s < n_lat(c); ++s) {
         double C = 0.0;
         for (int i = 0; i < Qc; ++i) {
           C += c->h[s][n * Qc + i];
           c->h[s][n * Qc + i] = 0.0;
         }
-        c->mon[ORC_MON_REM_SPEC + s] += C;
+        c->mon[mon_of(c, ORC_MON_REM_SPEC, s)] += C;
       }
       c->flag[n] = 1;
     }
@@ -1067,7 +1118,7 @@ int orc_get_fields(orc_ctx* c, double* rho, double* u, double* C, uint8_t* flags
       if (rho) rho[s * N + n] = c->rho[s][n];
     if (u)
       for (int a = 0; a < 3; ++a) u[a * N + n] = (c->flag[n] == 0) ? c->ub[n * 3 + a] : 0.0;
-    for (int s = 0; s < c->p.n_scal; ++s)
+    for (int s = 0; s < n_lat(c); ++s)
       if (C) C[s * N + n] = c->Cs[s][n];
     if (flags) flags[n] = c->flag[n];
     if (acc) acc[n] = c->acc[n];
@@ -1082,7 +1133,7 @@ int orc_get_pops(orc_ctx* c, double* f, double* h) {
     for (int i = 0; i < Qf; ++i)
       for (int64_t n = 0; n < N; ++n)
         if (f) f[((int64_t)s * Qf + i) * N + n] = c->f[s][n * Qf + i];
-  for (int s = 0; s < c->p.n_scal; ++s)
+  for (int s = 0; s < n_lat(c); ++s)
     for (int i = 0; i < Qc; ++i)
       for (int64_t n = 0; n < N; ++n)
         if (h) h[((int64_t)s * Qc + i) * N + n] = c->h[s][n * Qc + i];
@@ -1096,7 +1147,7 @@ int orc_set_pops(orc_ctx* c, const double* f, const double* h) {
     for (int i = 0; i < Qf; ++i)
       for (int64_t n = 0; n < N; ++n)
         if (f) c->f[s][n * Qf + i] = f[((int64_t)s * Qf + i) * N + n];
-  for (int s = 0; s < c->p.n_scal; ++s)
+  for (int s = 0; s < n_lat(c); ++s)
     for (int i = 0; i < Qc; ++i)
       for (int64_t n = 0; n < N; ++n)
         if (h) c->h[s][n * Qc + i] = h[((int64_t)s * Qc + i) * N + n];
@@ -1107,7 +1158,7 @@ int orc_get_monitors(orc_ctx* c, double* out) {
   int64_t N = c->N;
   int Qf = c->lf.q, Qc = c->lc.q;
   const lattice_t* L = &c->lf;
-  double mass[2] = {0.0, 0.0}, mom[3] = {0.0, 0.0, 0.0}, spec[2] = {0.0, 0.0};
+  double mass[2] = {0.0, 0.0}, mom[3] = {0.0, 0.0, 0.0}, spec[3] = {0.0, 0.0, 0.0};
   double nsolid = 0.0, nfluid = 0.0, nonfinite = 0.0;
   for (int64_t n = 0; n < N; ++n) {
     if (c->flag[n] != 0) {
@@ -1123,7 +1174,7 @@ int orc_get_monitors(orc_ctx* c, double* out) {
         for (int a = 0; a < 3; ++a) mom[a] += (double)L->c[i][a] * fi;
         if (!isfinite(fi)) bad = 1;
       }
-    for (int s = 0; s < c->p.n_scal; ++s)
+    for (int s = 0; s < n_lat(c); ++s)
       for (int i = 0; i < Qc; ++i) {
         double hi = c->h[s][n * Qc + i];
         spec[s] += hi;
@@ -1135,7 +1186,7 @@ int orc_get_monitors(orc_ctx* c, double* out) {
   out[ORC_MON_STEP] = (double)c->t;
   for (int s = 0; s < 2; ++s) out[ORC_MON_MASS + s] = mass[s];
   for (int a = 0; a < 3; ++a) out[ORC_MON_MOM + a] = mom[a];
-  for (int s = 0; s < 2; ++s) out[ORC_MON_SPECIES + s] = spec[s];
+  for (int s = 0; s < n_lat(c); ++s) out[mon_of(c, ORC_MON_SPECIES, s)] = spec[s];
   out[ORC_MON_NSOLID] = nsolid;
   out[ORC_MON_NFLUID] = nfluid;
   out[ORC_MON_NONFINITE] = nonfinite;

@@ -32,7 +32,8 @@ typedef struct orc_params {
   double g[3];                 /* body acceleration; F_body^sigma = rho^sigma g */
   int32_t collision;           /* 0: BGK; 1: MRT (Gram-Schmidt moment basis) */
   double s_e, s_eps, s_q, s_pi, s_m;   /* MRT rates of the non-hydrodynamic moment groups */
-  int32_t n_scal;              /* advection-diffusion lattices, 0..2; scalar 0 reacts */
+  int32_t n_scal;              /* advection-diffusion lattices, 0..2; scalar 0 reacts (the product
+                                  lattice, if any, comes after them) */
   double tau_c[2];             /* scalar relaxation times (Eq. therpop_species) */
   double J0;                   /* rest weight of D2Q5 / D3Q7 */
   double k_react;              /* first-order surface rate k of scalar 0 (Eq. reactO2, wetnode9) */
@@ -67,6 +68,11 @@ typedef struct orc_params {
                                   not with deposition */
   double tau_s;                /* relaxation time of the solid thermal lattice (tau_e,s) */
   double c_fs;                 /* heat-capacity ratio (rho c_p)_f / (rho c_p)_s */
+  int32_t product;             /* 1: one more scalar lattice after the n_scal ones, the product (CO2)
+                                  of the surface reaction: at each reactive link it gains what the
+                                  reaction takes from scalar 0 (Sec. 2.1.5, Eq. react, reactCO2) */
+  double tau_p;                /* relaxation time of the product lattice (tau_d,CO2) */
+  double C_in_p;               /* product value of the inlet ghost (with ade_open_x) */
 } orc_params;
 
 /* Monitor vector layout (doubles). */
@@ -94,7 +100,13 @@ enum {
   ORC_MON_HEAT_SRC = 29,   /* conjugate: cumulative reaction heat put into the link exchanges,
                               in units of the fluid's rho c_p */
   ORC_MON_SOLID_REM = 30,  /* conjugate: cumulative solid populations removed by dissolution */
-  ORC_MON_COUNT = 31
+  ORC_MON_SPECIES_P = 31,  /* product lattice: the entries that scalars 0 and 1 have above */
+  ORC_MON_INFLOW_P = 32,
+  ORC_MON_OUTFLOW_P = 33,
+  ORC_MON_INJ_SPEC_P = 34,
+  ORC_MON_REM_SPEC_P = 35,
+  ORC_MON_PRODUCED = 36,   /* cumulative product-population gain through reactive links */
+  ORC_MON_COUNT = 37
 };
 
 typedef struct orc_ctx orc_ctx;
@@ -102,12 +114,14 @@ typedef struct orc_ctx orc_ctx;
 orc_ctx* orc_create(const orc_params* p, int* status);
 void orc_destroy(orc_ctx* c);
 int orc_set_geometry(orc_ctx* c, const uint8_t* flags);
-/* rho: [n_comp][N], u: [3][N] (2D: uz ignored), C: [n_scal][N]; NULL C allowed if n_scal == 0 */
+/* rho: [n_comp][N], u: [3][N] (2D: uz ignored), C: [n_scal + product][N] (the product last);
+   NULL C allowed if there is no scalar lattice */
 int orc_set_fields(orc_ctx* c, const double* rho, const double* u, const double* C);
 int orc_step(orc_ctx* c, int64_t nsteps);
-/* rho [n_comp][N], u [3][N] physical velocity, C [n_scal][N], flags [N], acc [N]; any may be NULL */
+/* rho [n_comp][N], u [3][N] physical velocity, C [n_scal + product][N], flags [N], acc [N]; any
+   may be NULL */
 int orc_get_fields(orc_ctx* c, double* rho, double* u, double* C, uint8_t* flags, double* acc);
-/* pre-collision populations at the current time: f [n_comp][Qf][N], h [n_scal][Qc][N] */
+/* pre-collision populations at the current time: f [n_comp][Qf][N], h [n_scal + product][Qc][N] */
 int orc_get_pops(orc_ctx* c, double* f, double* h);
 int orc_set_pops(orc_ctx* c, const double* f, const double* h);
 int orc_get_monitors(orc_ctx* c, double* out /* ORC_MON_COUNT */);

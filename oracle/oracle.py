@@ -54,7 +54,8 @@ class OrcParams(C.Structure):
         ("N_geo", C.c_int32), ("u_wall_ymax", C.c_double * 3), ("flow_open_x", C.c_int32),
         ("u_in", C.c_double), ("arrhenius", C.c_int32), ("arr_A", C.c_double), ("arr_Ta", C.c_double),
         ("heat_release", C.c_double), ("n_it", C.c_int32), ("conjugate", C.c_int32),
-        ("tau_s", C.c_double), ("c_fs", C.c_double),
+        ("tau_s", C.c_double), ("c_fs", C.c_double), ("product", C.c_int32), ("tau_p", C.c_double),
+        ("C_in_p", C.c_double),
     ]
 
 
@@ -63,6 +64,7 @@ MON_NAMES = [
     "inflow0", "inflow1", "outflow0", "outflow1", "inj_mass0", "inj_mass1", "inj_spec0",
     "inj_spec1", "rem_mass0", "rem_mass1", "rem_spec0", "rem_spec1", "deposited", "nsolid",
     "nfluid", "nonfinite", "wallx", "heat", "tsolid", "heat_s", "heat_src", "solid_rem",
+    "species_p", "inflow_p", "outflow_p", "inj_spec_p", "rem_spec_p", "produced",
 ]
 
 _ENUMS = {
@@ -157,6 +159,9 @@ def make_params(cfg: dict) -> OrcParams:
     p.conjugate = int(bool(d.get("conjugate", False)))
     p.tau_s = float(d.get("tau_s", 1.0))
     p.c_fs = float(d.get("c_fs", 1.0))
+    p.product = int(bool(d.get("product", False)))
+    p.tau_p = float(d.get("tau_p", 1.0))
+    p.C_in_p = float(d.get("C_in_p", 0.0))
     return p
 
 
@@ -176,6 +181,7 @@ class Oracle:
         if not self.h:
             raise ValueError(f"oracle rejected the configuration (status {st.value})")
         self.dim = self.p.dim
+        self.n_lat = self.p.n_scal + self.p.product    # scalar lattices, the product last
         self.shape = (self.p.nz, self.p.ny, self.p.nx)
         self.N = self.p.nx * self.p.ny * self.p.nz
         self.qf = 19 if self.dim == 3 else 9
@@ -196,7 +202,7 @@ class Oracle:
             raise ValueError("bad flag value")
 
     def set_fields(self, rho, u, Cs=None):
-        nc, ns = self.p.n_comp, self.p.n_scal
+        nc, ns = self.p.n_comp, self.n_lat
         r = np.ascontiguousarray(rho, dtype=np.float64).reshape(nc, self.N)
         uu = np.ascontiguousarray(u, dtype=np.float64).reshape(3, self.N)
         cc = np.ascontiguousarray(Cs, dtype=np.float64).reshape(ns, self.N) if ns else None
@@ -206,7 +212,7 @@ class Oracle:
         self.lib.orc_step(self.h, int(n))
 
     def fields(self):
-        nc, ns, N = self.p.n_comp, self.p.n_scal, self.N
+        nc, ns, N = self.p.n_comp, self.n_lat, self.N
         rho = np.zeros((nc, N))
         u = np.zeros((3, N))
         Cs = np.zeros((max(ns, 1), N))
@@ -220,7 +226,7 @@ class Oracle:
                 "acc": acc.reshape(sh)}
 
     def pops(self):
-        nc, ns, N = self.p.n_comp, self.p.n_scal, self.N
+        nc, ns, N = self.p.n_comp, self.n_lat, self.N
         f = np.zeros((nc, self.qf, N))
         h = np.zeros((max(ns, 1), self.qc, N))
         self.lib.orc_get_pops(self.h, _dp(f), _dp(h))
@@ -228,7 +234,7 @@ class Oracle:
 
     def set_pops(self, f, h=None):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        hh = np.ascontiguousarray(h, dtype=np.float64) if h is not None and self.p.n_scal else None
+        hh = np.ascontiguousarray(h, dtype=np.float64) if h is not None and self.n_lat else None
         self.lib.orc_set_pops(self.h, _dp(f), _dp(hh))
 
     def monitors(self):

@@ -83,7 +83,17 @@ class NaiveLBM:
         self.dim = int(cfg["dim"])
         self.nx, self.ny, self.nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg.get("nz", 1))
         self.nc = int(cfg.get("n_comp", 1))
-        self.ns = int(cfg.get("n_scal", 0))
+        # scalar lattices: the n_scal given ones, then the reaction product if there is one
+        self.n_given = int(cfg.get("n_scal", 0))
+        self.prod = bool(cfg.get("product", False))
+        self.ns = self.n_given + int(self.prod)
+        tc = [float(t) for t in cfg.get("tau_c", [1.0, 1.0])]
+        ci = [float(v) for v in cfg.get("C_in", [0.0, 0.0])]
+        self.tau_s_list = [tc[s] if s < len(tc) else tc[0] for s in range(self.n_given)]
+        self.cin_list = [ci[s] if s < len(ci) else 0.0 for s in range(self.n_given)]
+        if self.prod:
+            self.tau_s_list.append(float(cfg["tau_p"]))
+            self.cin_list.append(float(cfg.get("C_in_p", 0.0)))
         self.J0 = float(cfg.get("J0", 0.25))
         self.cf, self.wf, self.cc, self.wc = velocity_sets(self.dim, self.J0)
         self.of, self.oc = opposite(self.cf), opposite(self.cc)
@@ -144,6 +154,7 @@ class NaiveLBM:
         tauc = [float(t) for t in cfg.get("tau_c", [1.0, 1.0])]
         closed = hstate[:, :, z, y, x].copy()
         reactions = []
+        link_rate = {}
         arr = bool(cfg.get("arrhenius", False))
         if arr:
             # temperature-dependent rate k(T) = A exp(-Ta / T) at the interface temperature, heat
@@ -173,11 +184,13 @@ class NaiveLBM:
                 cb = 2 * hb / (2 * w + kk * fc)
                 closed[0, j] = 2 * w * cb - hb
                 reactions.append((src, kk * cb))
+                link_rate[j] = kk * cb
                 continue
             if not arr:
                 Cb = 2 * hb / (2 * w + Kr)
                 closed[0, j] = 2 * w * Cb - hb
                 reactions.append((src, k * Cb))
+                link_rate[j] = k * Cb
                 continue
             gb = hstate[1, self.oc[j], z, y, x]
 
@@ -196,6 +209,13 @@ class NaiveLBM:
             closed[0, j] = 2 * w * cb - hb
             closed[1, j] = gb + hr * kk * cb * fT
             reactions.append((src, kk * cb))
+            link_rate[j] = kk * cb
+        if self.prod:
+            # the product enters through each reactive link at the rate the reaction takes scalar 0:
+            # (1 - 1/(2 tau_p)) (h_P,j - h_P,opp(j)) = r_j
+            P, tp = self.n_given, float(cfg["tau_p"])
+            for j, r in link_rate.items():
+                closed[P, j] = hstate[P, self.oc[j], z, y, x] + r * tp / (tp - 0.5)
         return closed, reactions
 
     def _flips(self):
@@ -403,7 +423,7 @@ class NaiveLBM:
                 C = float(hc[s, :, z, y, x].sum())
                 for j in range(Qc):
                     heq = self.wc[j] * C * (1 + float(np.dot(self.cc[j], u)) / cs2)
-                    hpost[s, j, z, y, x] = hc[s, j, z, y, x] - (hc[s, j, z, y, x] - heq) / tauc[s]
+                    hpost[s, j, z, y, x] = hc[s, j, z, y, x] - (hc[s, j, z, y, x] - heq) / self.tau_s_list[s]
 
         # push streaming with halfway bounce-back, inlet ghost and zero-gradient outlet
         cs2 = (1.0 - self.J0) / self.dim
@@ -449,7 +469,7 @@ class NaiveLBM:
                     if not cfg.get("ade_open_x", False) or self.cc[j][1] or self.cc[j][2]:
                         continue
                     if xs < 0:
-                        C_in = float(cfg.get("C_in", [0.0, 0.0])[s])
+                        C_in = self.cin_list[s]
                         hnew[s, j, z, y, x] = self.wc[j] * C_in * (1 + float(np.dot(self.cc[j], vel[n])) / cs2)
                     elif xs >= nx:
                         hnew[s, j, z, y, x] = hpost[s, j, z, y, x]

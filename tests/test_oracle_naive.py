@@ -60,6 +60,18 @@ CASES = {
                                          n_scal=2, tau_c=[0.6, 0.8], J0=0.25, arrhenius=True, arr_A=0.3,
                                          arr_Ta=0.8, heat_release=0.03, n_it=40, conjugate=True, tau_s=0.7,
                                          c_fs=0.6, geo_mode="dissolve", V_m=40.0, N_geo=2, periodic=[1, 1, 1]),
+    "2d_product_open": dict(dim=2, nx=8, ny=8, tau=[0.8], g=[2e-4, -1e-4, 0], n_scal=1, tau_c=[0.7], J0=0.4,
+                            k_react=0.05, product=True, tau_p=0.9, ade_open_x=True, C_in=[1.0], C_in_p=0.1,
+                            periodic=[1, 1, 1]),
+    "3d_mrt_arrhenius_product_dissolution": dict(dim=3, nx=8, ny=8, nz=8, tau=[1.0], collision="mrt",
+                                                 g=[1e-4, 0, 0], n_scal=2, tau_c=[0.6, 0.8], J0=0.25,
+                                                 arrhenius=True, arr_A=0.3, arr_Ta=0.8, heat_release=0.03,
+                                                 n_it=24, product=True, tau_p=0.75, geo_mode="dissolve",
+                                                 V_m=40.0, N_geo=2, periodic=[1, 1, 1]),
+    "2d_conjugate_product_walls": dict(dim=2, nx=8, ny=8, tau=[0.8], g=[2e-4, 0, 0], n_scal=2, tau_c=[0.7, 0.9],
+                                       J0=0.4, arrhenius=True, arr_A=0.4, arr_Ta=1.0, heat_release=0.05,
+                                       n_it=40, conjugate=True, tau_s=0.65, c_fs=2.5, product=True, tau_p=1.2,
+                                       periodic=[1, 0, 1]),
     "3d_mrt_velocity_inlet": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", flow_open_x=True,
                                   u_in=0.02, g=[0, 0, 1e-4], u_wall_ymax=[0.01, 0, 0], periodic=[0, 0, 1]),
 }
@@ -71,7 +83,7 @@ def test_oracle_matches_naive_formulation(name):
     dim = cfg["dim"]
     shape = (cfg.get("nz", 1), cfg["ny"], cfg["nx"])
     geom = inputs.random_solids(shape, 0.2, seed=zlib.crc32(name.encode()) % 1000)
-    nc, ns = cfg.get("n_comp", 1), cfg.get("n_scal", 0)
+    nc, ns = cfg.get("n_comp", 1), cfg.get("n_scal", 0) + int(cfg.get("product", False))
     rho, u, C = inputs.perturbed_fields(shape, nc, ns, seed=7, amp_rho=0.02, amp_u=0.02,
                                         rho0=[0.9, 0.4] if nc == 2 else 1.0)
     if dim == 2:
