@@ -157,6 +157,41 @@ def reactive_channel_2d(nx=128, ny=64, seed=0, precision="fp64"):
     return cfg, geom, (rho, u, C)
 
 
+def combustion_channel_2d(nx=420, ny=80, n_obstacles=4, radius=None, precision="fp64"):
+    """Stand-in for the reactive porous channel of Sec. 3.4 (Xu et al.'s set-up, whose exact
+    geometry is not in the text): a channel of nx x ny nodes with no-slip walls at y = -1/2 and
+    ny - 1/2, the parabolic velocity inlet at x = 0 and zero-gradient outlets for every field;
+    n_obstacles reactive carbon discs of radius ny/8 (default) on the centre line, evenly spaced
+    in the middle three fifths.  O2 (scalar 0) enters at 0.22, CO2 (the product) at 0, and the
+    fluid at the temperature 1; the solid starts at 1 too.  Lattice parameters: D2Q9 BGK
+    tau 0.8, D2Q5 J0 0.4; tau_O2 0.8, tau_T 0.9, tau_CO2 0.75, tau_s 0.7, c_fs 0.5; with L the
+    disc diameter, U the mean inlet velocity and D the O2 diffusivity, Pe = U L / D = 1e-2 and
+    Da = k(1) L / D = 3.525e-2 at the inlet temperature (Sec. 3.4), k(T) = A exp(-Ta / T) with
+    Ta = 8, and the heat release h_r = 2."""
+    r = int(radius if radius is not None else max(2, ny // 8))
+    g = np.zeros((1, ny, nx), dtype=np.uint8)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    cy = (ny - 1) / 2.0
+    for k in range(n_obstacles):
+        cx = nx * (0.2 + 0.6 * (k + 0.5) / n_obstacles)
+        g[0][(xx - cx) ** 2 + (yy - cy) ** 2 <= r * r] = REACTIVE
+    L = 2.0 * r
+    D = 0.3 * (0.8 - 0.5)
+    U = 1e-2 * D / L
+    k_in = 3.525e-2 * D / L
+    Ta = 8.0
+    cfg = dict(dim=2, nx=nx, ny=ny, nz=1, n_comp=1, tau=[0.8], g=[0.0, 0.0, 0.0], collision="bgk",
+               forcing="guo", flow_open_x=True, u_in=U, periodic=[0, 0, 1], n_scal=2,
+               tau_c=[0.8, 0.9], J0=0.4, ade_open_x=True, C_in=[0.22, 1.0], arrhenius=True,
+               arr_A=k_in * float(np.exp(Ta)), arr_Ta=Ta, heat_release=2.0, n_it=24,
+               conjugate=True, tau_s=0.7, c_fs=0.5, product=True, tau_p=0.75, C_in_p=0.0,
+               geo_mode="none", precision=precision)
+    rho, u, _ = uniform_fields((1, ny, nx), 1, 0)
+    C = np.zeros((3, 1, ny, nx))
+    C[1] = 1.0
+    return cfg, g, (rho, u, C)
+
+
 def droplet_3d(n=128, radius=16.0, precision="fp32", G=2.7):
     """3D two-component Shan-Chen static droplet: D3Q19 per component, psi = rho,
     cross-cohesion G (0.9 in the w_i/c_s^2 convention = 2.7 in Eq. 1.14's w_i

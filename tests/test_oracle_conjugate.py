@@ -199,3 +199,37 @@ def test_conduction_needs_the_temperature_rate_and_valid_media():
     for bad in (dict(arrhenius=False), dict(tau_s=0.5), dict(c_fs=0.0), dict(geo_mode="deposit")):
         with pytest.raises(Exception):
             Oracle(dict(ok, **bad))
+
+
+def test_reactive_channel_budgets():
+    """The reactive porous channel of Sec. 3.4 in small (84 x 16, four carbon discs): velocity
+    inlet, O2, temperature and CO2 entering at x = 0, the temperature-dependent rate, heat
+    release, conduction in the discs and the CO2 product, all at once. Each step the O2, the CO2
+    and the heat of both lattices change by exactly what the links and the open faces carry; the
+    fields stay within the bounds the inlet and the initial state set (O2 below its inlet value,
+    CO2 non-negative, the temperature not below its initial value under an exothermic
+    reaction)."""
+    cfg, geom, fields = inputs.combustion_channel_2d(nx=84, ny=16)
+    o = make(cfg, geom, fields)
+    c_fs = cfg["c_fs"]
+    for _ in range(600):
+        m0 = o.monitors()
+        o.step(1)
+        m1 = o.monitors()
+
+        def d(k):
+            return m1[k] - m0[k]
+
+        o2 = d("species0") - (d("inflow0") - d("outflow0") - d("wallx"))
+        co2 = d("species_p") - (d("produced") + d("inflow_p") - d("outflow_p"))
+        heat = (_energy(m1, c_fs) - _energy(m0, c_fs)) - (d("heat_src") + d("inflow1") - d("outflow1"))
+        assert abs(o2) < 1e-13 * max(m1["species0"], 1.0)
+        assert abs(co2) < 1e-13 * max(m1["species_p"], 1.0)
+        assert abs(heat) < 1e-13 * _energy(m1, c_fs)
+    f = o.fields()
+    assert m1["nonfinite"] == 0
+    assert m1["heat_src"] > 0 and m1["produced"] > 0
+    assert f["C"][0].max() <= cfg["C_in"][0]
+    assert f["C"][2].min() >= 0.0
+    assert f["C"][1].min() >= 1.0 - 1e-12
+    assert f["C"][1][geom == 2].max() > 1.0      # the discs heat up
