@@ -233,3 +233,46 @@ def test_reactive_channel_budgets():
     assert f["C"][2].min() >= 0.0
     assert f["C"][1].min() >= 1.0 - 1e-12
     assert f["C"][1][geom == 2].max() > 1.0      # the discs heat up
+
+
+def test_steady_front_fluxes_and_interface_temperature():
+    """1D burning front at steady state: O2 enters at x = 0 and reacts at the face of a carbon
+    slab whose far end is adiabatic; heat and CO2 flow back to the inlet. Then (Eq. reactO2,
+    reactCO2, fluxCon, tempCon):
+    - the O2 and CO2 profiles are linear with link fluxes D ΔC equal to the reaction per step,
+    - the fluid temperature is linear, with link flux D_T ΔT equal to the heat released per step,
+      which is h_r tau_T / (tau_T - 1/2) times the reaction,
+    - the slab is isothermal (no heat leaves through its far end), at the temperature the fluid
+      profile takes at the halfway face: temperature continuity."""
+    nx, nf = 16, 10
+    geom = np.zeros((1, 1, nx), np.uint8)
+    geom[0, 0, nf:] = 2
+    tau_O, tau_T, tau_P, hr = 0.8, 0.9, 0.75, 0.5
+    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=2, tau_c=[tau_O, tau_T], J0=0.4, ade_open_x=True,
+               C_in=[1.0, 1.0], arrhenius=True, arr_A=0.5, arr_Ta=1.0, heat_release=hr, n_it=40,
+               conjugate=True, tau_s=0.7, c_fs=0.5, product=True, tau_p=tau_P, C_in_p=0.0,
+               periodic=[1, 1, 1])
+    shape = (1, 1, nx)
+    C = np.zeros((3,) + shape)
+    C[1] = 1.0
+    o = make(cfg, geom, (np.ones((1,) + shape), np.zeros((3,) + shape), C))
+    o.step(40000)
+    m0 = o.monitors()
+    o.step(1)
+    m1 = o.monitors()
+    reaction = m1["reacted"] - m0["reacted"]
+    heat = m1["heat_src"] - m0["heat_src"]
+    f = o.fields()["C"][:, 0, 0]
+    O2, T, P = f[0, :nf], f[1, :nf], f[2, :nf]
+    D = {k: 0.3 * (t - 0.5) for k, t in (("O", tau_O), ("T", tau_T), ("P", tau_P))}
+    inner = slice(1, nf - 2)
+    for prof in (O2, T, P):
+        np.testing.assert_allclose(prof[:-2] - 2 * prof[1:-1] + prof[2:], 0, atol=1e-12)
+    np.testing.assert_allclose(D["O"] * (O2[:-1] - O2[1:])[inner], reaction, rtol=1e-9)
+    np.testing.assert_allclose(D["P"] * (P[1:] - P[:-1])[inner], reaction, rtol=1e-9)
+    np.testing.assert_allclose(D["T"] * (T[1:] - T[:-1])[inner], heat, rtol=1e-9)
+    np.testing.assert_allclose(heat, hr * tau_T / (tau_T - 0.5) * reaction, rtol=1e-9)
+    Ts = f[1, nf:]
+    assert np.ptp(Ts) < 1e-11
+    assert abs(T[-1] + 0.5 * (T[-1] - T[-2]) - Ts[0]) < 1e-11
+    assert reaction > 0 and Ts[0] > 1.5
