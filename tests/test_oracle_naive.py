@@ -72,6 +72,11 @@ CASES = {
                                        J0=0.4, arrhenius=True, arr_A=0.4, arr_Ta=1.0, heat_release=0.05,
                                        n_it=40, conjugate=True, tau_s=0.65, c_fs=2.5, product=True, tau_p=1.2,
                                        periodic=[1, 0, 1]),
+    "3d_conjugate_product_open": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], g=[1e-4, 0, 1e-4], n_scal=2,
+                                      tau_c=[0.7, 0.6], J0=0.25, arrhenius=True, arr_A=0.5, arr_Ta=0.7,
+                                      heat_release=0.08, n_it=40, conjugate=True, tau_s=0.9, c_fs=1.7,
+                                      product=True, tau_p=0.65, ade_open_x=True, C_in=[1.0, 1.1], C_in_p=0.05,
+                                      periodic=[1, 0, 1]),
     "3d_mrt_velocity_inlet": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", flow_open_x=True,
                                   u_in=0.02, g=[0, 0, 1e-4], u_wall_ymax=[0.01, 0, 0], periodic=[0, 0, 1]),
 }
