@@ -641,7 +641,7 @@ static void collide_solid(orc_ctx* c) {
    so that T_b = (c_fs ho + go + c_fs Qp / 2) / (w (c_fs + 1)).  With c_fs = 1, tau_s = tau_T
    and Qp = 0 this is plain streaming (h_T,i = go, g_s,opp(i) = ho).  At a reactive link
    Qp = h_r k(T_b) C_b tau_T / (tau_T - 1/2), the heat source scaled as the fluid's missing
-   populations carry it, with C_b = 2 hb / (2 w + k tau_c / (tau_c - 1/2)) the closure of the
+   populations carry it (the factor of the source in Eq. unknownpopTempS), with C_b = 2 hb / (2 w + k tau_c / (tau_c - 1/2)) the closure of the
    species population hb = h_C,opp(i)(n) that has just streamed in; T_b and C_b are solved
    together by n_it fixed-point iterations from the source-free T_b, and k is kept for the
    species closure of the next step, which then finds the same C_b. */
