@@ -457,8 +457,9 @@ def _two_comp(shape, G, rho):
     return make(cfg, None, (rho, np.zeros((3,) + shape), None))
 
 
-def _coexistence(G, steps=6000):
-    """Flat interfaces in a periodic slab: bulk densities of the two phases."""
+def _coexistence(G, steps=6000, tension=False):
+    """Flat interfaces in a periodic slab: bulk densities of the two phases and, if asked, the
+    surface tension of one interface by its mechanical definition (below)."""
     shape = (1, 2, 64)
     x = np.arange(64)
     inside = (x >= 16) & (x < 48)
@@ -468,7 +469,23 @@ def _coexistence(G, steps=6000):
     o = _two_comp(shape, G, rho)
     o.step(steps)
     r = o.fields()["rho"][:, 0, 0]
-    return r[0, 32], r[1, 32]
+    if not tension:
+        return r[0, 32], r[1, 32]
+    return r[0, 32], r[1, 32], _mechanical_tension(r[0], r[1], G)
+
+
+def _mechanical_tension(psi1, psi2, G):
+    """gamma = integral of (P_N - P_T) across a flat interface normal to x, for the pair force
+    F_1 = -psi_1 G sum_i w_i psi_2(x + c_i) c_i and its mirror (Eq. 1.14), with the node-centred
+    pressure tensor P_ab = c_s^2 (rho_1 + rho_2) delta_ab
+    + (G / 2) sum_i w_i [psi_1(x) psi_2(x + c_i) + psi_2(x) psi_1(x + c_i)] c_ia c_ib, whose
+    normal component is constant through the interface at equilibrium (mechanical balance).  On
+    D2Q9 only the axis links differ between P_xx and P_yy, and summation by parts leaves
+    -G w_1 sum_x (psi_1(x+1) - psi_1(x)) (psi_2(x+1) - psi_2(x)) for the whole periodic slab,
+    which holds two interfaces."""
+    d1 = np.roll(psi1, -1) - psi1
+    d2 = np.roll(psi2, -1) - psi2
+    return -G * (1.0 / 9.0) * float((d1 * d2).sum()) / 2.0
 
 
 def _droplet_dp(R, G, hi, lo, n=48, steps=2000):
@@ -495,9 +512,11 @@ def test_coexistence_and_laplace_law_2d():
     coexistence densities satisfy the symmetric-binary binodal ln(rho_h / rho_l) =
     G (rho_h - rho_l) of the EOS p = c_s^2 (rho_1 + rho_2 + G rho_1 rho_2), up to lattice
     corrections.  (2) Static droplets obey Delta p = gamma / R (2D Laplace law): Delta p is
-    linear in 1/R with a small intercept, and component masses are conserved exactly."""
+    linear in 1/R with a small intercept, and component masses are conserved exactly.  (3) That
+    gamma is the mechanical surface tension of the flat interface, the integral of
+    P_N - P_T across it, to 3 %: the absolute tension, not only its scaling."""
     G = 2.7
-    hi, lo = _coexistence(G)
+    hi, lo, gamma_mech = _coexistence(G, tension=True)
     assert abs(np.log(hi / lo) / (G * (hi - lo)) - 1) < 0.03
     Rs, dps = [], []
     for R in (7.0, 10.0, 13.0):
@@ -514,6 +533,8 @@ def test_coexistence_and_laplace_law_2d():
     r2 = 1 - ((dps - pred) ** 2).sum() / ((dps - dps.mean()) ** 2).sum()
     assert r2 > 0.99
     assert coef[0] > 0 and abs(coef[1]) < 0.2 * dps.min()
+    # (3) the Laplace slope is the surface tension of the flat interface at the same bulk state
+    assert abs(coef[0] / gamma_mech - 1) < 0.03, (coef[0], gamma_mech)
 
 
 def test_literal_weak_cohesion_dissolves_droplet():
