@@ -161,3 +161,45 @@ def test_deposition_budget_and_flips(conservative):
     else:
         np.testing.assert_allclose(m["species0"] + m["rem_spec0"], m0["species0"], rtol=1e-13)
     np.testing.assert_allclose(f["acc"].sum(), m["deposited"], rtol=1e-12)
+
+
+def _front_channel(xs, **geo):
+    """1D channel at rest: inlet C = 1 at x = 0, reactive solid from node xs to the end."""
+    nx = 24
+    shape = (1, 1, nx)
+    g = np.zeros(shape, np.uint8)
+    g[0, 0, xs:] = 2
+    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=1, tau_c=[0.8], J0=0.4, k_react=0.05,
+               ade_open_x=True, C_in=[1.0], periodic=[1, 1, 1], **geo)
+    return make(cfg, g, (np.ones((1,) + shape), np.zeros((3,) + shape), np.zeros((1,) + shape)))
+
+
+def test_dissolution_front_advances_at_the_quasi_steady_rate():
+    """A slowly dissolving slab (Sec. 2.1.5 solid consumption): each front node takes
+    m_s0 / V_m of reaction to dissolve, and while the front is slow the reaction at it is the
+    steady rate for the current front position (whose link flux the steady-diffusion pin ties
+    to k C_b). So the time between two flips is (m_s0 / V_m) / r(front), to 0.5 %: the
+    threshold, the booking of each link's reaction on its own solid node, and the closure of
+    the links the new fluid node opens all enter it."""
+    rates = {}
+    for xs in (11, 12, 13):
+        o = _front_channel(xs)
+        o.step(20000)
+        m0 = o.monitors()
+        o.step(1)
+        rates[xs] = o.monitors()["reacted"] - m0["reacted"]
+    thr = 300.0
+    o = _front_channel(10, geo_mode="dissolve", V_m=1.0 / thr, m_s0=1.0)
+    flips, step, n_solid = [], 0, o.monitors()["nsolid"]
+    while len(flips) < 4 and step < 400000:
+        o.step(20)
+        step += 20
+        ns = o.monitors()["nsolid"]
+        if ns < n_solid:
+            assert ns == n_solid - 1, "one node per flip"
+            flips.append(step)
+            n_solid = ns
+    assert len(flips) == 4
+    for k, xs in enumerate((11, 12, 13), start=1):
+        interval = flips[k] - flips[k - 1]
+        assert abs(interval / (thr / rates[xs]) - 1) < 5e-3, (xs, interval, thr / rates[xs])
