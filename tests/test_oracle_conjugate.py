@@ -243,7 +243,8 @@ def test_steady_front_fluxes_and_interface_temperature():
     - the fluid temperature is linear, with link flux D_T ΔT equal to the heat released per step,
       which is h_r tau_T / (tau_T - 1/2) times the reaction,
     - the slab is isothermal (no heat leaves through its far end), at the temperature the fluid
-      profile takes at the halfway face: temperature continuity."""
+      profile takes at the halfway face: temperature continuity,
+    - and all of it equals the closed-form steady state, up to one bracketed root for T_b."""
     nx, nf = 16, 10
     geom = np.zeros((1, 1, nx), np.uint8)
     geom[0, 0, nf:] = 2
@@ -276,3 +277,25 @@ def test_steady_front_fluxes_and_interface_temperature():
     assert np.ptp(Ts) < 1e-11
     assert abs(T[-1] + 0.5 * (T[-1] - T[-2]) - Ts[0]) < 1e-11
     assert reaction > 0 and Ts[0] > 1.5
+    # The same state in closed form. A linear profile phi(x) = phi_in + b (tau + x) carries the
+    # populations w (phi -/+ b tau), so each inlet ghost sets phi(0) = phi_in + b tau. At the slab
+    # face the species closure gives k C_b = -D_O b_O with C_b = O2(nf - 1); the product gains r
+    # there, D_P b_P = r; the fluid carries the whole heat to the inlet, D_T b_T = h_r f_T r; and
+    # the face temperature is the fluid profile at the halfway point, T_b = T(nf - 1/2). With
+    # k = A exp(-Ta / T_b) this leaves one equation in T_b, solved here by bracketing.
+    from scipy.optimize import brentq
+    A, Ta, fT = cfg["arr_A"], cfg["arr_Ta"], tau_T / (tau_T - 0.5)
+
+    def rate(Tb):
+        k = A * np.exp(-Ta / Tb)
+        return D["O"] * 1.0 * k / (k * (nf - 1 + tau_O) + D["O"])
+
+    Tb = brentq(lambda t: t - (1.0 + hr * fT * rate(t) / D["T"] * (tau_T + nf - 0.5)), 1.0, 10.0,
+                xtol=1e-15, rtol=1e-15)
+    r = rate(Tb)
+    x = np.arange(nf)
+    np.testing.assert_allclose(reaction, r, rtol=1e-10)
+    np.testing.assert_allclose(Ts, Tb, rtol=1e-11)
+    np.testing.assert_allclose(O2, 1.0 - r / D["O"] * (tau_O + x), atol=1e-11)
+    np.testing.assert_allclose(P, 0.0 + r / D["P"] * (tau_P + x), atol=1e-11)
+    np.testing.assert_allclose(T, 1.0 + hr * fT * r / D["T"] * (tau_T + x), atol=1e-11)
