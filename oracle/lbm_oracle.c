@@ -640,9 +640,11 @@ static void collide_solid(orc_ctx* c) {
        h_T,i = 2 w T_b - ho,   g_s,opp(i) = 2 w T_b - go,
    so that T_b = (c_fs ho + go + c_fs Qp / 2) / (w (c_fs + 1)).  With c_fs = 1, tau_s = tau_T
    and Qp = 0 this is plain streaming (h_T,i = go, g_s,opp(i) = ho).  At a reactive link
-   Qp = h_r k(T_b) C_b tau_T / (tau_T - 1/2), the heat source scaled as the fluid's missing
-   populations carry it (the factor of the source in Eq. unknownpopTempS), with C_b = 2 hb / (2 w + k tau_c / (tau_c - 1/2)) the closure of the
-   species population hb = h_C,opp(i)(n) that has just streamed in; T_b and C_b are solved
+   Qp = h_r k(T_b) C_b, the heat release of Eq. reacRate: ho and go are post-collision, so what
+   the link adds to the populations in one step is the heat that crosses it, the physical flux
+   that Eq. fluxCon balances (the factor tau / (tau - 1/2) of Eq. unknownpopTempS belongs to a
+   closure written on pre-collision populations).  C_b = 2 hb / (2 w + k tau_c / (tau_c - 1/2))
+   is the closure of the species population hb = h_C,opp(i)(n) that has just streamed in; T_b and C_b are solved
    together by n_it fixed-point iterations from the source-free T_b, and k is kept for the
    species closure of the next step, which then finds the same C_b. */
 static void exchange_solid(orc_ctx* c) {
@@ -651,7 +653,6 @@ static void exchange_solid(orc_ctx* c) {
   const lattice_t* K = &c->lc;
   const double cf = c->p.c_fs;
   const double fc = c->p.tau_c[0] / (c->p.tau_c[0] - 0.5);
-  const double fT = c->p.tau_c[1] / (c->p.tau_c[1] - 0.5);
   for (int64_t n = 0; n < c->N; ++n) {
     if (c->flag[n] != 0) continue;
     int x, y, z;
@@ -670,7 +671,7 @@ static void exchange_solid(orc_ctx* c) {
         for (int it = 0; it <= c->p.n_it; ++it) {
           k = c->p.arr_A * exp(-c->p.arr_Ta / Tb);
           const double Cb = 2.0 * hb / (2.0 * w + k * fc);
-          Qp = c->p.heat_release * k * Cb * fT;
+          Qp = c->p.heat_release * k * Cb;
           Tb = (cf * ho + go + 0.5 * cf * Qp) / (w * (cf + 1.0));
         }
         c->kb[n * Qc + i] = k;

@@ -268,7 +268,7 @@ class NaiveLBM:
         therpop_solid, tempCon, fluxCon, reacRate), pushed: a solid link carries ho out of the
         fluid node and go out of the solid node; both sides get back 2 w T_b minus what they
         sent, with T_b the root of
-            (h_in - ho) + (g_in - go) / c_fs = h_r k(T_b) C_b(T_b) tau_T / (tau_T - 1/2)
+            (h_in - ho) + (g_in - go) / c_fs = h_r k(T_b) C_b(T_b)
         found by bracketing; C_b closes the species population that has just streamed into the
         fluid node against the wall."""
         from scipy.optimize import brentq
@@ -278,7 +278,6 @@ class NaiveLBM:
         A, Ta, hr = float(cfg["arr_A"]), float(cfg["arr_Ta"]), float(cfg["heat_release"])
         tauc = [float(t) for t in cfg.get("tau_c", [1.0, 1.0])]
         fc = tauc[0] / (tauc[0] - 0.5)
-        fT = tauc[1] / (tauc[1] - 0.5)
         cells = [(x, y, z) for z in range(self.nz) for y in range(self.ny) for x in range(self.nx)]
         solid = [q for q in cells if self.flags[q[2], q[1], q[0]] != 0]
         gpost = np.zeros_like(self.g)
@@ -310,13 +309,13 @@ class NaiveLBM:
 
                     def source(T):
                         kk = A * np.exp(-Ta / T)
-                        return kk, hr * kk * (2 * hb / (2 * w + kk * fc)) * fT
+                        return kk, hr * kk * (2 * hb / (2 * w + kk * fc))
 
                     def balance(T):
                         return T - (cfs * ho + go + 0.5 * cfs * source(T)[1]) / (w * (cfs + 1))
 
                     if hr != 0.0:
-                        T1 = T0 + 0.5 * cfs * hr * A * (hb / w) * fT / (w * (cfs + 1)) + 1e-9
+                        T1 = T0 + 0.5 * cfs * hr * A * (hb / w) / (w * (cfs + 1)) + 1e-9
                         Tb = brentq(balance, T0, T1, xtol=1e-15, rtol=1e-15, maxiter=500)
                     self.kb[(x, y, z, self.oc[j])] = source(Tb)[0]
                 hnew[1, self.oc[j], z, y, x] = 2 * w * Tb - ho

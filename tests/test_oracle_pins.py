@@ -758,6 +758,49 @@ def test_heat_release_budget_per_step():
         assert abs((m1["species0"] - m0["species0"]) + (m1["wallx"] - m0["wallx"])) < 1e-12 * m0["species0"]
 
 
+def test_steady_burning_face_closed_form():
+    """The steady 1D state of the temperature-dependent closure (adiabatic solid): O2 and heat
+    enter at x = 0, the reactive face is past node xs - 1. Linear profiles
+    phi(x) = phi_in + b (tau + x) carry the populations w (phi -/+ b tau). The closure's two
+    conditions then give C_b = C(xs - 1) and T_b = T(xs - 1) (each pair sum is 2 w times the node
+    value), k(T_b) C_b = -D_O b_O, and a heat flux D_T b_T = h_r k(T_b) C_b carried back to the
+    inlet (Eq. reactO2, reacRate, fluxCon). One equation in T_b remains; its bracketed root
+    fixes the profiles, the rate and the heat monitor."""
+    from scipy.optimize import brentq
+    xs, tau_O, tau_T, hr, A, Ta = 10, 0.8, 0.9, 0.5, 0.5, 1.0
+    nx = xs + 3
+    shape = (1, 1, nx)
+    geom = np.zeros(shape, np.uint8)
+    geom[0, 0, xs:] = 2
+    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=2, tau_c=[tau_O, tau_T], J0=0.4, ade_open_x=True,
+               C_in=[1.0, 1.0], arrhenius=True, arr_A=A, arr_Ta=Ta, heat_release=hr, n_it=40,
+               periodic=[1, 1, 1])
+    C0 = np.zeros((2,) + shape)
+    C0[1] = 1.0
+    o = make(cfg, geom, (np.ones((1,) + shape), np.zeros((3,) + shape), C0))
+    o.step(40000)
+    m0 = o.monitors()
+    o.step(1)
+    m1 = o.monitors()
+    reaction = m1["reacted"] - m0["reacted"]
+    DO, DT = 0.3 * (tau_O - 0.5), 0.3 * (tau_T - 0.5)
+
+    def rate(Tb):
+        k = A * np.exp(-Ta / Tb)
+        return DO * k / (k * (xs - 1 + tau_O) + DO)
+
+    Tb = brentq(lambda t: t - (1.0 + hr * rate(t) / DT * (tau_T + xs - 1)), 1.0, 10.0,
+                xtol=1e-15, rtol=1e-15)
+    r = rate(Tb)
+    x = np.arange(xs)
+    f = o.fields()["C"][:, 0, 0, :xs]
+    np.testing.assert_allclose(reaction, r, rtol=1e-10)
+    np.testing.assert_allclose(f[0], 1.0 - r / DO * (tau_O + x), atol=1e-11)
+    np.testing.assert_allclose(f[1], 1.0 + hr * r / DT * (tau_T + x), atol=1e-11)
+    np.testing.assert_allclose(f[1][-1], Tb, rtol=1e-11)
+    assert Tb > 1.2
+
+
 def test_thermal_closure_needs_the_temperature_scalar():
     for bad in (dict(n_scal=1), dict(n_scal=2, arr_A=-1.0), dict(n_scal=2, n_it=65)):
         with pytest.raises(Exception):
