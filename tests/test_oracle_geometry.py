@@ -200,3 +200,42 @@ def test_dissolution_front_advances_at_the_quasi_steady_rate():
     for k, xs in enumerate((11, 12, 13), start=1):
         interval = flips[k] - flips[k - 1]
         assert abs(interval / (thr / rates[xs]) - 1) < 5e-3, (xs, interval, thr / rates[xs])
+
+
+@pytest.mark.parametrize("tau_c,DP,xs,J0,C_in,conservative", [(0.8, 0.01, 10, 0.4, 1.0, True),
+                                                               (1.2, 0.05, 7, 0.2, 0.6, True),
+                                                               (0.9, 0.02, 8, 0.4, 0.8, False)])
+def test_steady_deposition_channel_closed_form(tau_c, DP, xs, J0, C_in, conservative):
+    """Particles enter a 1D channel at x = 0 and deposit at the node next to an inert wall
+    (Sec. 3.3, Eq. surface_deposition), with the flips held off. The steady state follows from
+    the update itself. Before the last node the profile is linear, C(x) = C_in + b (tau + x),
+    with populations w (C -/+ b tau). At the last node n = xs - 1 every population is scaled by
+    s = 1 - DP (by 1 without removal), relaxed, and the +x one comes back by bounce-back. Three
+    linear equations in b, C(n) and the returning population give the whole state, and the
+    deposit per step is DP C(n)."""
+    nx = xs + 3
+    shape = (1, 1, nx)
+    geom = np.zeros(shape, np.uint8)
+    geom[0, 0, xs:] = 1
+    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=1, tau_c=[tau_c], J0=J0, ade_open_x=True,
+               C_in=[C_in], geo_mode="deposit", DP=DP, deposit_conservative=conservative,
+               N_geo=10 ** 9, periodic=[1, 1, 1])
+    o = make(cfg, geom, (np.ones((1,) + shape), np.zeros((3,) + shape), np.zeros((1,) + shape)))
+    o.step(60000)
+    m0 = o.monitors()
+    o.step(1)
+    dep = o.monitors()["deposited"] - m0["deposited"]
+    C = o.fields()["C"][0, 0, 0, :xs]
+    w, om, n = (1.0 - J0) / 4.0, 1.0 / tau_c, xs - 1
+    s = 1.0 - DP if conservative else 1.0
+    q = om * (J0 + 2 * w) * s / (1.0 - (1.0 - om) * s)      # rest + y populations over C(n)
+    # unknowns (b, C(n), m): the -x population m* leaving n is the linear profile's at n - 1;
+    # m at n is the bounced-back +x population; C(n) sums all populations of n
+    M = np.array([[-w * (2 * tau_c + n - 1), om * w * s, (1 - om) * s],
+                  [-(1 - om) * s * w * n, -om * w * s, 1.0],
+                  [-w * n, 1.0 - q, -1.0]])
+    rhs = np.array([w * C_in, (1 - om) * s * w * C_in, w * C_in])
+    b, Cn, _ = np.linalg.solve(M, rhs)
+    np.testing.assert_allclose(C[:n], C_in + b * (tau_c + np.arange(n)), atol=1e-12)
+    np.testing.assert_allclose(C[n], Cn, rtol=1e-11)
+    np.testing.assert_allclose(dep, DP * Cn, rtol=1e-10)
