@@ -298,3 +298,29 @@ def test_steady_front_fluxes_and_interface_temperature():
     np.testing.assert_allclose(O2, 1.0 - r / D["O"] * (tau_O + x), atol=1e-11)
     np.testing.assert_allclose(P, 0.0 + r / D["P"] * (tau_P + x), atol=1e-11)
     np.testing.assert_allclose(T, 1.0 + hr * r / D["T"] * (tau_T + x), atol=1e-11)
+
+
+def test_reactive_channel_recipe_uses_the_printed_values():
+    """The channel recipe takes the printed inlet values, Pe and Da of Sec. 3.4
+    (tests/golden/reactive_channel.json): Pe = U L / D and Da = k(T_in) L / D with L the disc
+    diameter, U the mean inlet velocity and D the O2 diffusivity of the scalar lattice; and the
+    inlet profile 6 U s (1 - s) has mean U and peak 1.5 U."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "reactive_channel.json")))
+    cfg, geom, _ = inputs.combustion_channel_2d()
+    assert (cfg["nx"], cfg["ny"]) == (gold["nx"], gold["ny"])
+    assert cfg["C_in"][0] == gold["C_O2_inlet"] and cfg["C_in_p"] == gold["C_CO2_inlet"]
+    # the disc diameter 2 (ny // 8), and the discs in the geometry are that wide
+    L = 2.0 * (cfg["ny"] // 8)
+    widths = [np.diff(np.nonzero(np.diff(np.r_[0, row != 0, 0]))[0])[::2].max()
+              for row in geom[0] if (row != 0).any()]
+    assert abs(max(widths) - L) <= 1
+    D = (1.0 - cfg["J0"]) / 2.0 * (cfg["tau_c"][0] - 0.5)
+    k_in = cfg["arr_A"] * np.exp(-cfg["arr_Ta"] / cfg["C_in"][1])
+    assert abs(cfg["u_in"] * L / D / gold["Pe"] - 1) < 1e-12
+    assert abs(k_in * L / D / gold["Da"] - 1) < 1e-12
+    s = (np.arange(cfg["ny"]) + 0.5) / cfg["ny"]
+    prof = 6.0 * s * (1.0 - s)
+    assert abs(prof.mean() - 1.0) < 1e-3
+    assert abs(prof.mean() / prof.max() - gold["inlet_profile_mean_over_peak"]) < 1e-3
