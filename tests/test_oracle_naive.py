@@ -77,6 +77,11 @@ CASES = {
                                       heat_release=0.08, n_it=40, conjugate=True, tau_s=0.9, c_fs=1.7,
                                       product=True, tau_p=0.65, ade_open_x=True, C_in=[1.0, 1.1], C_in_p=0.05,
                                       periodic=[1, 0, 1]),
+    "2d_burning_channel": dict(dim=2, nx=8, ny=8, tau=[0.8], flow_open_x=True, u_in=0.03, n_scal=2,
+                               tau_c=[0.8, 0.9], J0=0.4, ade_open_x=True, C_in=[0.22, 1.0], arrhenius=True,
+                               arr_A=2.0, arr_Ta=1.5, heat_release=0.5, n_it=40, conjugate=True, tau_s=0.7,
+                               c_fs=0.5, product=True, tau_p=0.75, C_in_p=0.0, geo_mode="dissolve", V_m=200.0,
+                               periodic=[0, 0, 1]),
     "3d_mrt_velocity_inlet": dict(dim=3, nx=8, ny=8, nz=8, tau=[0.9], collision="mrt", flow_open_x=True,
                                   u_in=0.02, g=[0, 0, 1e-4], u_wall_ymax=[0.01, 0, 0], periodic=[0, 0, 1]),
 }
