@@ -242,6 +242,31 @@ def test_poiseuille_halfway_wall_exact_at_magic_tau():
     np.testing.assert_allclose(ux, exact, rtol=1e-8)
 
 
+@pytest.mark.parametrize("tau,collision,s_q", [(0.6, "bgk", None), (0.8, "bgk", None), (1.5, "bgk", None),
+                                               (0.8, "mrt", 1.2), (1.1, "mrt", 1.6)])
+def test_poiseuille_equals_its_exact_discrete_solution(tau, collision, s_q):
+    """For any tau, the steady force-driven D2Q9 channel with halfway bounce-back is the exact
+    discrete solution u(y) = g/(2 nu) ((H/2)^2 - y^2) + (g/nu) (16 Lambda - 3)/24, y measured
+    from the channel centre, H the fluid width. Lambda = (1/s_nu - 1/2)(1/s_q - 1/2) is the
+    product of the relaxation parameters of the shear and the odd (energy-flux) moments, the
+    only odd non-conserved moments of D2Q9; for BGK it is (tau - 1/2)^2 (Ginzburg & d'Humieres
+    2003). The wall slip vanishes at Lambda = 3/16, the magic value of the test above."""
+    ny = 12
+    shape = (1, ny, 1)
+    g = 1e-6
+    cfg = dict(dim=2, nx=1, ny=ny, tau=[tau], g=[g, 0, 0], collision=collision, periodic=[1, 0, 1])
+    if s_q is not None:
+        cfg["mrt_rates"] = dict(s_q=s_q)
+    o = make(cfg, np.zeros(shape, np.uint8))
+    nu = (tau - 0.5) / 3
+    o.step(int(25 * ny * ny / nu))
+    ux = o.fields()["u"][0, 0, :, 0]
+    y = np.arange(ny) - (ny - 1) / 2
+    lam = (tau - 0.5) * ((1.0 / s_q if s_q else tau) - 0.5)
+    exact = g / (2 * nu) * ((ny / 2) ** 2 - y ** 2) + g / nu * (16 * lam - 3) / 24
+    np.testing.assert_allclose(ux, exact, rtol=1e-8)
+
+
 def test_poiseuille_slip_small_at_config_tau():
     """tau = 0.8 (config 1): u_max within 1e-3 relative of g H^2 / (8 nu) with H = ny - 2."""
     ux, g, nu = _poiseuille(0.8)
