@@ -9,6 +9,10 @@ differently on purpose:
   (D2Q9) polynomial matrix and its numerical inverse, where the oracle builds rows by
   Gram-Schmidt.
 - Every node and link is a plain Python loop.
+- The coupled interface values (T_b of the temperature-dependent closure and of the solid-link
+  exchange) are bracketed roots, where the oracle iterates a fixed point.
+- Heat conduction in the solid and its link exchange are pushed after the fluid streaming, and
+  the CO2 product is closed from the link rates of the species closure.
 
 The velocity sets come from the paper's printed tables (tests/golden/lattice_tables.json), with
 the same readings the project documents: D2Q9 axis weights 1/9, D3Q7 as the first seven D3Q19
