@@ -389,27 +389,29 @@ def test_steady_reactive_diffusion_flux(tau_c):
     np.testing.assert_allclose(reaction, per_step, rtol=1e-9)
 
 
-@pytest.mark.parametrize("tau_c,k,xs,J0,C_in", [(0.8, 0.05, 10, 0.4, 1.0), (1.3, 0.2, 7, 0.4, 0.7),
-                                                 (0.6, 0.01, 12, 0.2, 1.5)])
-def test_steady_reactive_channel_closed_form(tau_c, k, xs, J0, C_in):
+@pytest.mark.parametrize("dim,tau_c,k,xs,J0,C_in", [(2, 0.8, 0.05, 10, 0.4, 1.0), (2, 1.3, 0.2, 7, 0.4, 0.7),
+                                                     (2, 0.6, 0.01, 12, 0.2, 1.5), (3, 0.5667, 0.02, 9, 0.25, 1.0),
+                                                     (3, 1.1, 0.1, 6, 0.4, 0.5)])
+def test_steady_reactive_channel_closed_form(dim, tau_c, k, xs, J0, C_in):
     """The whole steady 1D solution in closed form, derived from the update itself: at rest,
     with a linear profile C(x) = C_in + b (tau + x), the +x and -x populations are
     w (C -/+ b tau) (w = (1 - J0)/4), so the inlet ghost w C_in entering node 0 fixes C(0) =
     C_in + b tau; at the last fluid node xs - 1 the wet-node closure (Eq. wetnode9, per link)
-    gives C_b = C(xs - 1) and k C_b = -D b with D = (1 - J0)/2 (tau - 1/2). Together:
-    b = -C_in / (xs - 1 + tau + D / k), and the reaction per step is -D b."""
+    gives C_b = C(xs - 1) and k C_b = -D b with D = (1 - J0)/dim (tau - 1/2) (D2Q5, and D3Q7
+    with w = (1 - J0)/6). Together: b = -C_in / (xs - 1 + tau + D / k), and the reaction per
+    step is -D b."""
     nx = xs + 3
     shape = (1, 1, nx)
     geom = np.zeros(shape, np.uint8)
     geom[0, 0, xs:] = 2
-    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=1, tau_c=[tau_c], J0=J0, k_react=k,
+    cfg = dict(dim=dim, nx=nx, ny=1, nz=1, tau=[1.0], n_scal=1, tau_c=[tau_c], J0=J0, k_react=k,
                ade_open_x=True, C_in=[C_in], periodic=[1, 1, 1])
     o = make(cfg, geom, (np.ones((1,) + shape), np.zeros((3,) + shape), np.zeros((1,) + shape)))
     o.step(100000)
     m0 = o.monitors()
     o.step(1)
     r = o.monitors()["reacted"] - m0["reacted"]
-    D = (1.0 - J0) / 2.0 * (tau_c - 0.5)
+    D = (1.0 - J0) / dim * (tau_c - 0.5)
     b = -C_in / (xs - 1 + tau_c + D / k)
     C = o.fields()["C"][0, 0, 0, :xs]
     np.testing.assert_allclose(C, C_in + b * (tau_c + np.arange(xs)), atol=1e-12)
