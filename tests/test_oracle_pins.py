@@ -242,21 +242,26 @@ def test_poiseuille_halfway_wall_exact_at_magic_tau():
     np.testing.assert_allclose(ux, exact, rtol=1e-8)
 
 
-@pytest.mark.parametrize("tau,collision,s_q", [(0.6, "bgk", None), (0.8, "bgk", None), (1.5, "bgk", None),
-                                               (0.8, "mrt", 1.2), (1.1, "mrt", 1.6)])
-def test_poiseuille_equals_its_exact_discrete_solution(tau, collision, s_q):
+@pytest.mark.parametrize("dim,tau,collision,s_q", [(2, 0.6, "bgk", None), (2, 0.8, "bgk", None),
+                                                   (2, 1.5, "bgk", None), (2, 0.8, "mrt", 1.2),
+                                                   (2, 1.1, "mrt", 1.6), (3, 0.8, "bgk", None),
+                                                   (3, 0.9, "mrt", 1.3)])
+def test_poiseuille_equals_its_exact_discrete_solution(dim, tau, collision, s_q):
     """For any tau, the steady force-driven D2Q9 channel with halfway bounce-back is the exact
     discrete solution u(y) = g/(2 nu) ((H/2)^2 - y^2) + (g/nu) (16 Lambda - 3)/24, y measured
     from the channel centre, H the fluid width. Lambda = (1/s_nu - 1/2)(1/s_q - 1/2) is the
     product of the relaxation parameters of the shear and the odd (energy-flux) moments, the
     only odd non-conserved moments of D2Q9; for BGK it is (tau - 1/2)^2 (Ginzburg & d'Humieres
-    2003). The wall slip vanishes at Lambda = 3/16, the magic value of the test above."""
+    2003). The wall slip vanishes at Lambda = 3/16, the magic value of the test above. D3Q19 has
+    two families of odd moments (q and m); with one rate for both, the same Lambda holds."""
     ny = 12
-    shape = (1, ny, 1)
+    nz = 1 if dim == 2 else 2
+    shape = (nz, ny, 1)
     g = 1e-6
-    cfg = dict(dim=2, nx=1, ny=ny, tau=[tau], g=[g, 0, 0], collision=collision, periodic=[1, 0, 1])
+    cfg = dict(dim=dim, nx=1, ny=ny, nz=nz, tau=[tau], g=[g, 0, 0], collision=collision,
+               periodic=[1, 0, 1])
     if s_q is not None:
-        cfg["mrt_rates"] = dict(s_q=s_q)
+        cfg["mrt_rates"] = dict(s_q=s_q, s_m=s_q)
     o = make(cfg, np.zeros(shape, np.uint8))
     nu = (tau - 0.5) / 3
     o.step(int(25 * ny * ny / nu))
