@@ -234,7 +234,8 @@ def test_reactive_channel_budgets():
     assert f["C"][1][geom == 2].max() > 1.0      # the discs heat up
 
 
-def test_steady_front_fluxes_and_interface_temperature():
+@pytest.mark.parametrize("dim,J0", [(2, 0.4), (3, 0.25)])
+def test_steady_front_fluxes_and_interface_temperature(dim, J0):
     """1D burning front at steady state: O2 enters at x = 0 and reacts at the face of a carbon
     slab whose far end is adiabatic; heat and CO2 flow back to the inlet. Then (Eq. reactO2,
     reactCO2, fluxCon, tempCon):
@@ -248,7 +249,7 @@ def test_steady_front_fluxes_and_interface_temperature():
     geom = np.zeros((1, 1, nx), np.uint8)
     geom[0, 0, nf:] = 2
     tau_O, tau_T, tau_P, hr = 0.8, 0.9, 0.75, 0.5
-    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=2, tau_c=[tau_O, tau_T], J0=0.4, ade_open_x=True,
+    cfg = dict(dim=dim, nx=nx, ny=1, nz=1, tau=[1.0], n_scal=2, tau_c=[tau_O, tau_T], J0=J0, ade_open_x=True,
                C_in=[1.0, 1.0], arrhenius=True, arr_A=0.5, arr_Ta=1.0, heat_release=hr, n_it=40,
                conjugate=True, tau_s=0.7, c_fs=0.5, product=True, tau_p=tau_P, C_in_p=0.0,
                periodic=[1, 1, 1])
@@ -256,7 +257,7 @@ def test_steady_front_fluxes_and_interface_temperature():
     C = np.zeros((3,) + shape)
     C[1] = 1.0
     o = make(cfg, geom, (np.ones((1,) + shape), np.zeros((3,) + shape), C))
-    o.step(40000)
+    o.step(80000)
     m0 = o.monitors()
     o.step(1)
     m1 = o.monitors()
@@ -264,7 +265,7 @@ def test_steady_front_fluxes_and_interface_temperature():
     heat = m1["heat_src"] - m0["heat_src"]
     f = o.fields()["C"][:, 0, 0]
     O2, T, P = f[0, :nf], f[1, :nf], f[2, :nf]
-    D = {k: 0.3 * (t - 0.5) for k, t in (("O", tau_O), ("T", tau_T), ("P", tau_P))}
+    D = {k: (1.0 - J0) / dim * (t - 0.5) for k, t in (("O", tau_O), ("T", tau_T), ("P", tau_P))}
     inner = slice(1, nf - 2)
     for prof in (O2, T, P):
         np.testing.assert_allclose(prof[:-2] - 2 * prof[1:-1] + prof[2:], 0, atol=1e-12)

@@ -790,7 +790,8 @@ def test_heat_release_budget_per_step():
         assert abs((m1["species0"] - m0["species0"]) + (m1["wallx"] - m0["wallx"])) < 1e-12 * m0["species0"]
 
 
-def test_steady_burning_face_closed_form():
+@pytest.mark.parametrize("dim,J0", [(2, 0.4), (3, 0.25)])
+def test_steady_burning_face_closed_form(dim, J0):
     """The steady 1D state of the temperature-dependent closure (adiabatic solid): O2 and heat
     enter at x = 0, the reactive face is past node xs - 1. Linear profiles
     phi(x) = phi_in + b (tau + x) carry the populations w (phi -/+ b tau). The closure's two
@@ -804,8 +805,8 @@ def test_steady_burning_face_closed_form():
     shape = (1, 1, nx)
     geom = np.zeros(shape, np.uint8)
     geom[0, 0, xs:] = 2
-    cfg = dict(dim=2, nx=nx, ny=1, tau=[1.0], n_scal=2, tau_c=[tau_O, tau_T], J0=0.4, ade_open_x=True,
-               C_in=[1.0, 1.0], arrhenius=True, arr_A=A, arr_Ta=Ta, heat_release=hr, n_it=40,
+    cfg = dict(dim=dim, nx=nx, ny=1, nz=1, tau=[1.0], n_scal=2, tau_c=[tau_O, tau_T], J0=J0,
+               ade_open_x=True, C_in=[1.0, 1.0], arrhenius=True, arr_A=A, arr_Ta=Ta, heat_release=hr, n_it=40,
                periodic=[1, 1, 1])
     C0 = np.zeros((2,) + shape)
     C0[1] = 1.0
@@ -815,7 +816,7 @@ def test_steady_burning_face_closed_form():
     o.step(1)
     m1 = o.monitors()
     reaction = m1["reacted"] - m0["reacted"]
-    DO, DT = 0.3 * (tau_O - 0.5), 0.3 * (tau_T - 0.5)
+    DO, DT = (1.0 - J0) / dim * (tau_O - 0.5), (1.0 - J0) / dim * (tau_T - 0.5)
 
     def rate(Tb):
         k = A * np.exp(-Ta / Tb)
