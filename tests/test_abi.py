@@ -135,3 +135,24 @@ def test_save_fields_round_trip(tmp_path):
     back = np.load(path)
     for k, v in fields.items():
         assert np.array_equal(back[k], v) and back[k].dtype == v.dtype
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the CUDA library there is no fallback: loading it, and so constructing a
+    Solver, raises."""
+    import subprocess
+    import sys
+    code = ("import sys\n"
+            "from paper_2502_12955_gb300 import lbm\n"
+            "try:\n"
+            "    lbm.Solver(dict(dim=2, nx=8, ny=8))\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(1)\n")
+    env = dict(os.environ, LBM_LIBRARY=str(tmp_path / "absent" / "liblbm.so"))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "not found" in r.stdout
