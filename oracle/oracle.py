@@ -5,6 +5,11 @@ cpu_baseline / reference leg of bench.py.  The product path never imports it.
 
 The oracle follows the paper's per-step update (CooLBM, arXiv 2502.12955,
 Sec. 2.1-2.1.5 and Sec. 3.3); see lbm_oracle.c for the equation map.
+
+Configuration keys are the fields of orc_params (lbm_oracle.h).  Scalar fields and
+populations come as [n_scal + product] rows: the given scalars, then the CO2 product
+lattice when `product` is set.  With `conjugate`, fields()["C"][1] holds the solid
+temperature on solid nodes.
 """
 from __future__ import annotations
 
