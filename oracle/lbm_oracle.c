@@ -997,10 +997,10 @@ static void flips(orc_ctx* c) {
   const lattice_t* L = &c->lf;
   int64_t* list = (int64_t*)zalloc(sizeof(int64_t) * (size_t)N);
   int64_t cnt = 0;
-  /* a reactive node has consumed its mass once V_m acc >= m_s0, i.e. acc >= m_s0 / V_m */
-  double thr = (c->p.V_m > 0.0) ? c->p.m_s0 / c->p.V_m : INFINITY;
+  /* a reactive node has consumed its solid mass once V_m acc >= m_s0: the remaining mass
+     m_s0 - V_m acc has reached zero (solid consumption, Sec. 2.1.5) */
   for (int64_t n = 0; n < N; ++n) {
-    if (c->p.geo_mode == 1 && c->flag[n] == 2 && c->acc[n] >= thr) list[cnt++] = n;
+    if (c->p.geo_mode == 1 && c->flag[n] == 2 && c->p.V_m * c->acc[n] >= c->p.m_s0) list[cnt++] = n;
     if (c->p.geo_mode == 2 && c->flag[n] == 0 && c->acc[n] > 1.0) list[cnt++] = n;
   }
   if (c->p.geo_mode == 1) {

@@ -180,7 +180,6 @@ struct Coef {
   T arrA, arrTa;    // temperature-dependent rate A exp(-Ta / T)
   T fc, fT;         // tau / (tau - 1/2) of scalar 0 and of the temperature (scalar 1)
   T hr;             // reaction heat per unit rate
-  double thr;       // dissolution threshold on acc: m_s0 / V_m (+inf if V_m == 0)
 };
 
 constexpr int NMON = 18;
@@ -398,6 +397,12 @@ __device__ __forceinline__ void push_flip(const Args& a, int n) {
   else
     atomicOr(a.err, ERR_CAPACITY);
 }
+
+// A reactive solid node has consumed its solid mass once V_m acc >= m_s0, i.e. its remaining
+// mass m_s0 - V_m acc has reached zero (solid consumption, Sec. 2.1.5).  The product is formed
+// in FP64 exactly as written; a node whose V_m acc lies within rounding of m_s0 may flip one
+// geometry update earlier or later than in a run that summed its links in another order.
+__device__ __forceinline__ bool consumed(const Args& a, double acc) { return a.V_m * acc >= a.m_s0; }
 
 // Exact float -> double widening by re-biasing the IEEE-754 fields with integer operations; the
 // conversion instruction itself runs on the FP64 unit, which is narrow on this GPU.  Zero keeps
@@ -1835,7 +1840,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
     const long long s = a.flip_list[e];
     bool ok;
     if (dissolve)
-      ok = a.flags[s] == FL_REACTIVE && a.acc[s] >= k.thr &&
+      ok = a.flags[s] == FL_REACTIVE && consumed(a, a.acc[s]) &&
            cas_flag(a.flags, s, FL_REACTIVE, FL_FLIPPING, a.err);
     else
       ok = a.flags[s] == FL_FLUID && a.acc[s] > 1.0 && cas_flag(a.flags, s, FL_FLUID, FL_FLIPPING, a.err);

@@ -80,7 +80,6 @@ Coef<T> make_coef(const Args& a, bool shifted) {
   k.kr = T(a.k_react);
   k.DP = T(a.DP);
   k.keep = T(1.0 - a.DP);
-  k.thr = a.V_m > 0.0 ? a.m_s0 / a.V_m : __builtin_huge_val();
   for (int c = 0; c < 3; ++c) k.uw6[c] = T(6.0 * a.u_wall[c]);
   k.arrA = T(a.arr_A);
   k.arrTa = T(a.arr_Ta);
@@ -325,7 +324,7 @@ const KernelSet& kernels_d3_bf16();
 // Storage-independent kernels (runtime.cu)
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,
                           int nonfin_slot, cudaStream_t st);
-cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st);
+cudaError_t launch_detect(const Args& a, cudaStream_t st);
 cudaError_t launch_permute(const void* src, void* dst, int elem, long long pitch, int planes,
                            const uint8_t* flags, long long N, const uint32_t* from, const uint32_t* to,
                            cudaStream_t st);

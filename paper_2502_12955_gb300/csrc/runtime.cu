@@ -6,6 +6,8 @@
 // back to host arithmetic: every step of the update runs in the kernels of kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -309,10 +311,6 @@ lbm_status rebuild_geometry(lbm_ctx* c, bool carry) {
   return relist(c, carry);
 }
 
-double dissolve_threshold(const lbm_params& p) {
-  return p.V_m > 0.0 ? p.m_s0 / p.V_m : HUGE_VAL;
-}
-
 lbm_status run_monitor(lbm_ctx* c) {
   long long nb = 0;
   LAUNCH(c->ks->monitor(c->a, parity_of(c->step), c->stream, &nb));
@@ -398,12 +396,12 @@ cudaError_t launch_reduce(const double* partials, long long nblocks, int K, doub
   return cudaGetLastError();
 }
 
-// Dissolution threshold test (acc >= m_s0 / V_m) over the interface list.
-__global__ void __launch_bounds__(256) k_detect(const Args a, const double thr) {
+// Dissolution test (V_m acc >= m_s0) over the interface list.
+__global__ void __launch_bounds__(256) k_detect(const Args a) {
   const unsigned int cnt = *a.iface_count;
   for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
     const long long n = a.iface_list[e];
-    if (a.acc[n] >= thr && a.flags[n] == FL_REACTIVE) push_flip(a, int(n));
+    if (a.flags[n] == FL_REACTIVE && consumed(a, a.acc[n])) push_flip(a, int(n));
   }
 }
 
@@ -451,11 +449,11 @@ cudaError_t launch_iota(uint32_t* v, long long N, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_detect(const Args& a, double thr, cudaStream_t st) {
+cudaError_t launch_detect(const Args& a, cudaStream_t st) {
   long long nb = (a.N / 8 + 255) / 256;
   if (nb < 1) nb = 1;
   if (nb > 152 * 16) nb = 152 * 16;
-  k_detect<<<(unsigned int)nb, 256, 0, st>>>(a, thr);
+  k_detect<<<(unsigned int)nb, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -659,8 +657,6 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
 
 namespace {
 
-double dissolve_thr(const lbm_ctx* c) { return dissolve_threshold(c->p); }
-
 bool geo_after(const lbm_ctx* c, long long step_done) {
   return c->p.geo_mode != LBM_GEO_NONE && (step_done % c->p.N_geo) == 0;
 }
@@ -687,7 +683,7 @@ lbm_status enqueue_step(lbm_ctx* c, long long step, cudaStream_t st, bool timed)
     c->ev_used.push_back({e0, e1});
   }
   if (geo_after(c, step + 1)) {
-    if (c->p.geo_mode == LBM_GEO_DISSOLVE) LAUNCH(launch_detect(c->a, dissolve_thr(c), st));
+    if (c->p.geo_mode == LBM_GEO_DISSOLVE) LAUNCH(launch_detect(c->a, st));
     LAUNCH(c->ks->flip(c->a, parity_of(step + 1), st));
   }
   return LBM_OK;
@@ -822,19 +818,20 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCR
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+// device address of g_noalloc_scratch, per device; racing first calls store the same value
+std::atomic<void*> g_noalloc_ptr[kMaxDevices] = {};
 
 // Looks up the scratch array's device address once per device (the device must be current).
 lbm_status noalloc_scratch(lbm_ctx* c, void** out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(c, LBM_ERR_INVALID_ARG, "device ordinal %d", dev);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
+  void* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
     CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = p;
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return LBM_OK;
 }
 }  // namespace
@@ -844,7 +841,7 @@ extern "C" {
 lbm_status lbm_get_pops_noalloc(lbm_ctx* c, double* f, double* h) {
   if (!c) return LBM_ERR_INVALID_ARG;
   const size_t N = (size_t)c->N;
-  const size_t nf = (size_t)c->p.n_comp * c->Qf * N;
+  const size_t nf = f ? (size_t)c->p.n_comp * c->Qf * N : 0;
   const size_t nh = (h && c->p.n_scal > 0) ? (size_t)c->p.n_scal * c->Qc * N : 0;
   const size_t need = (nf + nh) * sizeof(double);
   if (need > LBM_NOALLOC_SCRATCH_BYTES)
@@ -856,7 +853,7 @@ lbm_status lbm_get_pops_noalloc(lbm_ctx* c, double* f, double* h) {
   void* scratch = nullptr;
   lbm_status st = noalloc_scratch(c, &scratch);
   if (st == LBM_OK) {
-    double* df = f ? static_cast<double*>(scratch) : nullptr;
+    double* df = nf ? static_cast<double*>(scratch) : nullptr;
     double* dh = nh ? static_cast<double*>(scratch) + nf : nullptr;
     cudaError_t e = c->ks->pops_io(c->a, parity_of(c->step), 0, df, dh, c->stream);
     c->launches += 1;

@@ -239,10 +239,10 @@ class NaiveLBM:
                     self.h[:, :, z, y, x] = 0.0
             return
         V_m = float(cfg.get("V_m", 1.0))
-        thr = float(cfg.get("m_s0", 1.0)) / V_m if V_m > 0 else np.inf
+        m_s0 = float(cfg.get("m_s0", 1.0))
         new = []
         for (x, y, z) in cells:
-            if self.flags[z, y, x] != 2 or self.acc[z, y, x] < thr:
+            if self.flags[z, y, x] != 2 or not V_m * self.acc[z, y, x] >= m_s0:
                 continue
             rs, cs, cnt = np.zeros(self.nc), np.zeros(self.ns), 0
             for i in range(1, len(self.cf)):
