@@ -19,6 +19,8 @@
  *  - Work is enqueued on params.stream (a cudaStream_t, NULL for the legacy default stream).
  *    lbm_step returns after enqueueing.  Calls that return data synchronise that stream.
  *  - One context is used by one host thread at a time.
+ *  - The device named by params.device must be the current device of the calling thread for
+ *    every call on a context (lbm_get_pops_noalloc alone switches to it and back).
  */
 #ifndef LBM_H
 #define LBM_H
@@ -38,7 +40,9 @@ typedef enum lbm_status {
   LBM_ERR_NONFINITE = -4,    /* a monitor evaluation found non-finite populations */
   LBM_ERR_TIMEOUT = -5,      /* a bounded device wait ran out */
   LBM_ERR_STATE = -6,        /* call out of order (e.g. step before fields were set) */
-  LBM_ERR_CAPACITY = -7,     /* a device work list overflowed; results after it are invalid */
+  LBM_ERR_CAPACITY = -7,     /* a device work list overflowed; results after it are invalid.
+                                From lbm_get_pops_noalloc: the request exceeds its fixed
+                                scratch array; nothing ran and the context is unchanged */
   LBM_ERR_BOUNDS = -8        /* bounds-checked build only (-DLBM_BOUNDS_CHECK): a step kernel
                                 computed an index outside its buffer and used 0 instead */
 } lbm_status;
@@ -200,11 +204,14 @@ lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f, const double* h);
    must not trigger the implicit device-wide synchronisation of cudaMalloc / cudaFree.
    The populations are staged through a fixed device scratch array of
    LBM_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading this library holds until the
-   process exits.  Domains whose (n_comp*Qf + n_scal*Qc) * N * 8 bytes exceed it are rejected
-   with LBM_ERR_CAPACITY.  All calls share that array: calls on different contexts or streams
-   that overlap on the GPU race on it, so serialise them.  The first call on a device looks up
-   the array's device address (cudaGetSymbolAddress); make that first call before any stream
-   capture.  Outputs are host buffers as in lbm_get_pops; the call synchronises the stream. */
+   process exits.  A request of more than that many bytes, (n_comp*Qf [if f] + n_scal*Qc [if h])
+   * N * 8, is rejected with LBM_ERR_CAPACITY before anything runs.  All calls share that array:
+   calls on different contexts or streams that overlap on the GPU race on it, so serialise
+   them.  The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) and keeps it for the life of the process; make that first call before
+   any stream capture, and make no call after cudaDeviceReset, which would leave the kept
+   address stale.  Outputs are host buffers as in lbm_get_pops; the call synchronises the
+   stream. */
 #define LBM_NOALLOC_SCRATCH_BYTES (16u << 20)
 lbm_status lbm_get_pops_noalloc(lbm_ctx* ctx, double* f, double* h);
 

@@ -313,12 +313,14 @@ class Solver:
         self._ck(self.lib.lbm_get_pops(self.h, _dp(f), _dp(h) if self.n_scal else None))
         return f, h[: self.n_scal]
 
-    def pops_noalloc(self):
-        """pops() through lbm_get_pops_noalloc (no device allocation, bounded domain size)."""
-        f = np.zeros((self.n_comp, self.qf, self.N))
-        h = np.zeros((max(self.n_scal, 1), self.qc, self.N))
-        self._ck(self.lib.lbm_get_pops_noalloc(self.h, _dp(f), _dp(h) if self.n_scal else None))
-        return f, h[: self.n_scal]
+    def pops_noalloc(self, want_f=True, want_h=True):
+        """pops() through lbm_get_pops_noalloc (no device allocation, bounded domain size).
+        want_f / want_h = False pass NULL for that output, which then comes back as None."""
+        f = np.zeros((self.n_comp, self.qf, self.N)) if want_f else None
+        h = np.zeros((max(self.n_scal, 1), self.qc, self.N)) if want_h else None
+        self._ck(self.lib.lbm_get_pops_noalloc(self.h, _dp(f) if want_f else None,
+                                               _dp(h) if (want_h and self.n_scal) else None))
+        return f, (h[: self.n_scal] if want_h else None)
 
     def set_pops(self, f, h=None):
         f = np.ascontiguousarray(f, dtype=np.float64)
