@@ -1,4 +1,4 @@
-"""Build liblbm.so (the C ABI of include/lbm.h) for sm_103a with nvcc, in-tree.
+"""Build liblbm.so (the C ABIs of include/lbm.h and include/lbm_nn.h) for sm_103a with nvcc, in-tree.
 
 Translation units compile in parallel (one per lattice and storage type plus the runtime) and
 are linked into paper_2502_12955_gb300/_build/liblbm.so.  A rebuild happens only when a source
@@ -34,8 +34,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "lbm.h"),
-                                                                  __file__]
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+            + [__file__])
 
 
 def _stale(target, deps):
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
     if not force and not _stale(LIB, _deps()):
         return LIB
     nvcc = _nvcc()
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "lbm.h")]
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     objs, cmds = [], []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

@@ -1,0 +1,160 @@
+"""Warm start of the steady state by the learned encoder-decoder (surrogate.py), end to end.
+
+  generate()  solver-generated training data: seeded random-sphere packings (the dissolution
+              workload's recipe at the given size, seeds from 10^4), transport numbers Pe, Da
+              drawn log-uniform around 10 and 0.1, each run by the lattice Boltzmann step from
+              rest to its steady state (residual <= tol, geometry update frozen);
+  train()     Adam on the masked squared error of the fields, one sample per step;
+  compare()   on held-out geometries: steps and wall time to residual <= tol from rest and from
+              the network's prediction (inference time included), the same solver and stream.
+
+The residual is the step's own (relative L2 change of u and C over 100 steps, the larger of the
+two), so the network only moves the starting point: a wrong prediction costs steps, never
+accuracy, and plain LBM from rest is the fallback.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import inputs
+from . import surrogate as sg
+from .lbm import Solver
+
+L_CHAR = 9.0        # characteristic length: mean sphere radius of the packing
+U_DESIGN = 0.0185   # design speed the dissolution workload's transport numbers are built on
+CS2_D3Q7 = 0.25     # c_s^2 of the D3Q7 lattice at J0 = 1/4
+
+
+def transport(Pe, Da):
+    """tau_c and k of the dissolution workload for the given Peclet and Damkohler numbers
+    (D = U L / Pe, tau_c = D / c_s^2 + 1/2, k = Da D / L)."""
+    D = U_DESIGN * L_CHAR / Pe
+    return D / CS2_D3Q7 + 0.5, Da * D / L_CHAR
+
+
+def case(seed, n, Pe=sg.PE0, Da=sg.DA0, precision="fp32"):
+    cfg, geom, fields = inputs.dissolution_3d(n=n, seed=seed, precision=precision)
+    tau_c, k = transport(Pe, Da)
+    cfg = dict(cfg, tau_c=[tau_c], k_react=k, geo_mode="none", N_mon=100)
+    return cfg, geom, fields
+
+
+def run_to_steady(cfg, geom, fields, tol, max_steps, stream=None):
+    """Steps the solver from the given fields until the residual is <= tol; returns
+    (steps, seconds, converged, solver).  Seconds are CUDA-event time on the solver's stream,
+    including the host reads of the residual."""
+    import torch
+    s = Solver(cfg, stream=stream.cuda_stream if stream is not None else None)
+    s.set_geometry(geom)
+    rho, u, C = fields
+    s.set_fields(rho, u, C)
+    s.sync()
+    st = stream or torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    steps, r = 0, float("inf")
+    while steps < max_steps:
+        s.step(100)
+        steps += 100
+        r = s.monitors()["residual"]
+        if 0.0 <= r <= tol:
+            break
+    e1.record(st)
+    torch.cuda.synchronize()
+    return steps, e0.elapsed_time(e1) * 1e-3, bool(0.0 <= r <= tol), s
+
+
+class Sample:
+    """One training or test case held on the device: features, targets and fluid mask."""
+
+    def __init__(self, seed, n, Pe, Da, geom, u=None, Cf=None, device=0):
+        import torch
+        self.seed, self.n, self.Pe, self.Da, self.geom = seed, n, Pe, Da, geom
+        self.x = sg.features(geom, Pe, Da, device)
+        fl = (geom == 0).reshape(-1).astype(np.uint8)
+        self.fluid = torch.from_numpy(fl).to(torch.device("cuda", device))
+        self.n_fluid = int(fl.sum())
+        self.t = sg.targets(u, Cf, device) if u is not None else None
+
+
+def draw_transport(rng, spread=1.5):
+    """Pe and Da log-uniform in [x / spread, x spread] around 10 and 0.1."""
+    lo = math.log(1.0 / spread)
+    return sg.PE0 * math.exp(rng.uniform(lo, -lo)), sg.DA0 * math.exp(rng.uniform(lo, -lo))
+
+
+def generate(count, n=128, seed0=10_000, tol=1e-5, max_steps=400_000, device=0, log=None):
+    """count solver-generated samples; returns (samples, per-sample steps and seconds)."""
+    rng = np.random.default_rng(seed0)
+    out, stats = [], []
+    for i in range(count):
+        seed = seed0 + i
+        Pe, Da = draw_transport(rng)
+        cfg, geom, fields = case(seed, n, Pe, Da)
+        cfg = dict(cfg, device=device)
+        steps, sec, ok, s = run_to_steady(cfg, geom, fields, tol, max_steps)
+        f = s.fields()
+        s.close()
+        out.append(Sample(seed, n, Pe, Da, geom, f["u"], f["C"][0], device))
+        stats.append({"seed": seed, "Pe": Pe, "Da": Da, "steps": steps, "seconds": sec, "converged": ok})
+        if log:
+            log(f"sample {i}: seed {seed} Pe {Pe:.2f} Da {Da:.3f} steps {steps} {sec:.2f} s")
+    return out, stats
+
+
+def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, seed=0, log=None):
+    """Adam over the samples in a seeded random order each epoch, cosine-decayed learning rate;
+    returns the mean loss of each epoch."""
+    rng = np.random.default_rng(seed)
+    total = epochs * len(samples)
+    hist, it = [], 0
+    for ep in range(epochs):
+        acc = []
+        for j in rng.permutation(len(samples)):
+            s = samples[j]
+            a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * it / max(1, total - 1)))
+            loss = net.train_step(s.x, s.t, s.fluid, s.n_fluid, s.geom.shape, lr=a)
+            acc.append(loss)
+            it += 1
+        net.check()
+        m = float(sum(float(v.item()) for v in acc) / len(acc))
+        hist.append(m)
+        if log:
+            log(f"epoch {ep}: loss {m:.4e}")
+    return hist
+
+
+def compare(net, seeds, n=128, tol=1e-6, max_steps=400_000, device=0, rng_seed=99):
+    """Time to steady state from rest and from the network's prediction on held-out seeds."""
+    import torch
+    rng = np.random.default_rng(rng_seed)
+    rows = []
+    for seed in seeds:
+        Pe, Da = draw_transport(rng)
+        cfg, geom, fields = case(seed, n, Pe, Da)
+        cfg = dict(cfg, device=device)
+        steps0, sec0, ok0, s0 = run_to_steady(cfg, geom, fields, tol, max_steps)
+        f_ref = s0.fields()
+        s0.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        warm = sg.predict_fields(net, geom, Pe, Da)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        steps1, sec1, ok1, s1 = run_to_steady(cfg, geom, warm, tol, max_steps)
+        f_w = s1.fields()
+        s1.close()
+        fl = geom == 0
+        eC = float(np.linalg.norm((warm[2][0] - f_ref["C"][0])[fl]) / np.linalg.norm(f_ref["C"][0][fl]))
+        eu = float(np.linalg.norm((warm[1] - f_ref["u"])[:, fl]) / np.linalg.norm(f_ref["u"][:, fl]))
+        # both runs end at the same steady state (to the tolerance): the network changes the path only
+        dC = float(np.linalg.norm((f_w["C"][0] - f_ref["C"][0])[fl]) / np.linalg.norm(f_ref["C"][0][fl]))
+        rows.append({"seed": seed, "Pe": Pe, "Da": Da, "rest_steps": steps0, "rest_s": sec0,
+                     "warm_steps": steps1, "warm_s": sec1 + t_inf, "inference_s": t_inf,
+                     "converged": ok0 and ok1, "pred_err_C": eC, "pred_err_u": eu,
+                     "final_fields_rel_diff_C": dC,
+                     "speedup_steps": steps0 / max(1, steps1), "speedup_time": sec0 / (sec1 + t_inf)})
+    return rows

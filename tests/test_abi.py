@@ -21,6 +21,31 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
 
 
+NN_HDR = os.path.join(ROOT, "include", "lbm_nn.h")
+
+
+def declared_nn_functions():
+    text = open(NN_HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_nn_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_network_library_exports_every_declared_symbol():
+    """include/lbm_nn.h: every declared call is exported by liblbm.so and bound by the Python
+    binding under the same name."""
+    from paper_2502_12955_gb300 import surrogate
+
+    names = declared_nn_functions()
+    assert len(names) >= 18
+    lib = surrogate.nn_lib()
+    nm = subprocess.run(["nm", "-D", "--defined-only", lbm.library_path()], capture_output=True,
+                        text=True).stdout
+    for name in names:
+        assert hasattr(lib, name), name
+        assert hasattr(surrogate, name), f"{name} has no binding"
+        assert re.search(rf"\bT {name}$", nm, re.M), f"{name} not exported"
+
+
 def test_library_exports_every_declared_symbol():
     lib = lbm.load()
     names = declared_functions()
