@@ -196,6 +196,28 @@ def oracle_sample(name, precision, seconds=10.0, sample_n=64, steps=None, warmup
             "steps": n, "seconds": el}
 
 
+def oracle_full_size(name, size, steps=2, warmup=1):
+    """The single-thread FP64 oracle on the benchmark's own input at full size (a few steps)."""
+    from oracle.oracle import Oracle
+
+    cfg, geom, fields, label = workload(name, size, "fp64")
+    o = Oracle(dict(cfg, precision="fp64"))
+    o.set_geometry(geom)
+    rho, u, C = fields
+    o.set_fields(rho, u, C if o.p.n_scal else None)
+    o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": geom.size * steps / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{label} at full size ({geom.size} nodes), FP64 oracle, {steps} steps after "
+                      f"{warmup} warm-up, {el:.1f} s", "steps": steps, "seconds": el}
+
+
+def _oracle_full_worker(job):
+    return oracle_full_size(*job)
+
+
 def _oracle_worker(job):
     name, precision, seconds, sample_n, steps, warmup = job
     return oracle_sample(name, precision, seconds=seconds, sample_n=sample_n, steps=steps, warmup=warmup)
@@ -244,9 +266,17 @@ def parse():
     ap.add_argument("--l2-fetch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-full-cpu", action="store_true",
+                    help="skip the single-thread oracle steps on the full-size input")
     ap.add_argument("--to-steady", type=float, default=None,
                     help="instead of the timed steps: run from rest to residual <= this tolerance")
     ap.add_argument("--max-steps", type=int, default=2_000_000)
+    ap.add_argument("--warm-start", action="store_true",
+                    help="with --to-steady: train the encoder-decoder on solver steady states, then compare "
+                         "time to steady state from rest and from its prediction on held-out geometries")
+    ap.add_argument("--train-samples", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--test-samples", type=int, default=4)
     return ap.parse_args()
 
 
@@ -421,6 +451,55 @@ def run_to_steady(args, local):
     s.close()
 
 
+def run_warm_start(args, local):
+    """Learned warm start against plain LBM from rest (the dissolution workload's recipe at the
+    given size, default 128^3): generate solver steady states (r <= 1e-5) on seeded training
+    geometries with Pe and Da drawn log-uniform in [5, 10] and [0.05, 0.2], train the encoder-decoder, then on held-out
+    seeds run to r <= tol from rest and from the prediction.  value = mean warm time to steady
+    (network inference included); the rest time, step counts and the speed-up are beside it."""
+    import torch
+    from paper_2502_12955_gb300 import surrogate, warmstart
+
+    n = args.size or 128
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    samples, gen = warmstart.generate(args.train_samples, n=n, tol=1e-5, device=local)
+    t_gen = time.perf_counter() - t0
+    net = surrogate.WarmStartNet(device=local)
+    t0 = time.perf_counter()
+    hist = warmstart.train(net, samples, args.epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del samples
+    seeds = [20_000 + i for i in range(args.test_samples)]
+    rows = warmstart.compare(net, seeds, n=n, tol=args.to_steady, max_steps=args.max_steps, device=local)
+    # a warm run that failed (non-finite, or another end state) falls back to the rest run's cost
+    for r in rows:
+        if not r["converged_warm"]:
+            r["warm_s"] = r["rest_s"] + r["warm_s"]
+            r["warm_steps"] = r["rest_steps"] + r["warm_steps"]
+    rest_s = float(np.mean([r["rest_s"] for r in rows]))
+    warm_s = float(np.mean([r["warm_s"] for r in rows]))
+    rest_k = float(np.mean([r["rest_steps"] for r in rows]))
+    warm_k = float(np.mean([r["warm_steps"] for r in rows]))
+    speed = rest_s / warm_s
+    line = {"metric": "time_to_steady", "value": warm_s, "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "start": "learned warm start (encoder-decoder prediction)",
+            "rest_value": rest_s, "speedup_time": speed, "speedup_steps": rest_k / warm_k,
+            "warm_steps_mean": warm_k, "rest_steps_mean": rest_k, "tol": args.to_steady,
+            "target_speedup": 3.0, "target_met": bool(speed >= 3.0),
+            "all_converged": all(r["converged"] for r in rows),
+            "dtype": "f32 LBM; network bf16 weights and activations, f32 accumulate",
+            "data": "synthetic (seeded sphere packings, dissolution recipe), geometry update frozen",
+            "config": {"workload": f"dissolution3d_{n}^3_warm_start", "train_samples": args.train_samples,
+                       "epochs": args.epochs, "params": net.n_params, "held_out_seeds": seeds},
+            "train_loss_first_last": [hist[0], hist[-1]], "generate_s": t_gen, "train_s": t_train,
+            "train_steps_mean": float(np.mean([g["steps"] for g in gen if g["converged"]])),
+            "train_cases_skipped": [g for g in gen if not g["converged"]],
+            "cases": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -444,7 +523,7 @@ def main():
         return
     if args.to_steady is not None:
         if rank == 0:
-            run_to_steady(args, local)
+            (run_warm_start if args.warm_start else run_to_steady)(args, local)
         return
     precision = args.precision or ("fp64" if args.workload == "channel" else "fp32")
     cfg, geom, fields, label = workload(args.workload, args.size, precision)
@@ -504,9 +583,13 @@ def main():
     kavg_ms = kern_ms / max(1, kern_n)
     achieved = algo_bytes / (kavg_ms * 1e-3) / 1e9
     peak, peak_src = measured_peak()
+    # with Shan-Chen forces the timed population pass is the psi pass plus the fused step, and the
+    # bytes are the step's (one read and one write of every population of both components)
+    sc_on = any(v != 0 for row in cfg.get("G", [[0.0, 0.0], [0.0, 0.0]]) for v in row)
+    kernel = "k_psi + k_step" if sc_on else "k_step"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profile_traffic(label),
-                "peak_source": peak_src, "kernel": "k_step", "kernel_ms": kavg_ms,
+                "peak_source": peak_src, "kernel": kernel, "kernel_ms": kavg_ms,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "bytes_per_fluid_node": bpn}
 
@@ -540,6 +623,12 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = oracle_sample_all_cores(args.workload, precision, seconds=12.0)
+        if args.workload == "dissolution" and not args.no_full_cpu:
+            import multiprocessing as mp
+
+            with mp.get_context("spawn").Pool(1) as pool:
+                cpu["full_size_single_thread"] = pool.map(_oracle_full_worker,
+                                                          [(args.workload, args.size, 2, 1)])[0]
 
     q = 19 if cfg["dim"] == 3 else 9
     qc = 7 if cfg["dim"] == 3 else 5

@@ -229,9 +229,10 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r);
 lbm_status lbm_get_state(lbm_ctx* ctx, void* host, size_t* nbytes);
 lbm_status lbm_set_state(lbm_ctx* ctx, const void* host, size_t nbytes);
 
-/* Device time of the fused step kernel: when enabled, lbm_step brackets every launch of it
-   with CUDA events on the context's stream.  lbm_profile_read synchronises and returns the
-   summed milliseconds and the number of launches since the last read. */
+/* Device time of the population pass of each step: when enabled, lbm_step brackets the fused
+   step kernel, together with the psi pass that precedes it when Shan-Chen forces are on, with
+   CUDA events on the context's stream.  lbm_profile_read synchronises and returns the summed
+   milliseconds and the number of bracketed steps since the last read. */
 lbm_status lbm_profile_enable(lbm_ctx* ctx, int32_t on);
 lbm_status lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches);
 

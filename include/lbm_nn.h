@@ -50,6 +50,10 @@ lbm_status lbm_nn_status(void* stream);
 /* im2col of x [D*H*W][C] into col [V][Kp] (transposed = 0) or [Kp][V] (transposed = 1). */
 lbm_status lbm_nn_im2col(const void* x, void* col, int32_t D, int32_t H, int32_t W, int32_t C, int32_t Kp,
                          int32_t transposed, void* stream);
+/* The transposed im2col colT [Kp][V] from a channel-major copy xT [C][V] of the input (W % 8 == 0):
+   the same values as lbm_nn_im2col with transposed = 1, with coalesced reads and writes. */
+lbm_status lbm_nn_im2col_cv(const void* xT, void* colT, int32_t D, int32_t H, int32_t W, int32_t C, int32_t Kp,
+                            void* stream);
 /* y [Cc][R] = x [R][Cc] (BF16). */
 lbm_status lbm_nn_transpose(const void* x, void* y, int64_t R, int32_t Cc, void* stream);
 /* out[i] = sum_z part[z * stride + i], i < n (FP32). */
@@ -67,7 +71,7 @@ lbm_status lbm_nn_up2(const void* in, void* out, int32_t D, int32_t H, int32_t W
 /* out [V][Ca+Cb] = [a [V][Ca], b [V][Cb]]; backward = 1 splits out back into a and b. */
 lbm_status lbm_nn_concat(void* a, int32_t Ca, void* b, int32_t Cb, void* out, int64_t V, int32_t backward,
                          void* stream);
-/* out[c] = sum_v x[v][c] (bias gradient), FP32. */
+/* out[c] = sum_v x[v][c] (bias gradient), FP32, overwritten. */
 lbm_status lbm_nn_colsum(const void* x, float* out, int64_t V, int32_t C, void* stream);
 /* Head (1x1 convolution, FP32 weights w [Co][C], bias b [Co]): y [V][Co] FP32 from h [V][C]. */
 lbm_status lbm_nn_head_fwd(const void* h, const float* w, const float* b, float* y, int64_t V, int32_t C, int32_t Co,

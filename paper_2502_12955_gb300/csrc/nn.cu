@@ -277,6 +277,58 @@ __global__ void k_im2col(const bf16* __restrict__ x, bf16* __restrict__ col, int
   }
 }
 
+// Row layout for C % 8 == 0: one thread per 8 consecutive k of one row (16 bytes, always inside
+// one tap since C is a multiple of 8), copied with one 16-byte load and store.
+__global__ void k_im2col_vec(const bf16* __restrict__ x, bf16* __restrict__ col, int D, int H, int W, int C, int Kp) {
+  const long long V = (long long)D * H * W;
+  const int CH = Kp / 8;
+  const long long total = V * CH;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long v = i / CH;
+    const int k0 = (int)(i - v * CH) * 8;
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (k0 < 27 * C) {
+      const int tap = k0 / C, c = k0 - tap * C;
+      const int xx = (int)(v % W), yy = (int)((v / W) % H), zz = (int)(v / ((long long)W * H));
+      const int x2 = xx + tap % 3 - 1, y2 = yy + (tap / 3) % 3 - 1, z2 = zz + tap / 9 - 1;
+      if (x2 >= 0 && x2 < W && y2 >= 0 && y2 < H && z2 >= 0 && z2 < D)
+        val = *reinterpret_cast<const uint4*>(x + ((long long)(z2 * H + y2) * W + x2) * C + c);
+    }
+    *reinterpret_cast<uint4*>(col + v * Kp + k0) = val;
+  }
+}
+
+// Transposed layout from a channel-major copy xT [C][V] (W % 8 == 0): colT[k][v] = xT[c][v + tap],
+// one thread per 8 consecutive voxels of one row k (same y and z), one 16-byte store.
+__global__ void k_im2col_cv(const bf16* __restrict__ xT, bf16* __restrict__ colT, int D, int H, int W, int C,
+                            int Kp) {
+  const long long V = (long long)D * H * W;
+  const long long VC = V / 8;
+  const long long total = (long long)Kp * VC;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / VC);
+    const long long v0 = (i - (long long)k * VC) * 8;
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16_rn(0.f);
+    if (k < 27 * C) {
+      const int tap = k / C, c = k - tap * C;
+      const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+      const int x0 = (int)(v0 % W), yy = (int)((v0 / W) % H), zz = (int)(v0 / ((long long)W * H));
+      const int y2 = yy + dy, z2 = zz + dz;
+      if (y2 >= 0 && y2 < H && z2 >= 0 && z2 < D) {
+        const bf16* row = xT + (long long)c * V + (long long)(z2 * H + y2) * W;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int x2 = x0 + e + dx;
+          if (x2 >= 0 && x2 < W) o[e] = row[x2];
+        }
+      }
+    }
+    *reinterpret_cast<uint4*>(colT + (long long)k * V + v0) = *reinterpret_cast<const uint4*>(o);
+  }
+}
+
 // y[c][r] = x[r][c]
 __global__ void k_transpose(const bf16* __restrict__ x, bf16* __restrict__ y, long long R, int Cc) {
   __shared__ bf16 t[32][33];
@@ -370,19 +422,27 @@ __global__ void k_concat(bf16* __restrict__ a, int Ca, bf16* __restrict__ b, int
   }
 }
 
-// Column sums of a [V][C] BF16 array into FP32 (bias gradient), one block per column chunk.
-__global__ void k_colsum(const bf16* __restrict__ x, float* __restrict__ out, long long V, int C) {
-  const int c = blockIdx.x;
-  float s = 0.f;
-  for (long long v = threadIdx.x; v < V; v += blockDim.x) s += __bfloat162float(x[v * C + c]);
-  __shared__ float red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+// Column sums of a [V][C] BF16 array into FP32 (bias gradient; out zeroed first): per block a
+// chunk of voxels, warps over 32 consecutive columns (coalesced rows), a shared-memory reduction
+// over the block's 8 warps and one atomic per block and column.
+__global__ void k_colsum(const bf16* __restrict__ x, float* __restrict__ out, long long V, int C, long long chunk) {
+  __shared__ float red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long v0 = blockIdx.x * chunk, v1 = min(V, v0 + chunk);
+  for (int c0 = 0; c0 < C; c0 += 32) {
+    const int c = c0 + tx;
+    float sum = 0.f;
+    if (c < C)
+      for (long long v = v0 + ty; v < v1; v += 8) sum += __bfloat162float(x[v * C + c]);
+    red[ty][tx] = sum;
+    __syncthreads();
+    if (ty == 0) {
+      float t = 0.f;
+      for (int r = 0; r < 8; ++r) t += red[r][tx];
+      if (c < C) atomicAdd(&out[c], t);
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[c] = red[0];
 }
 
 // Head (1x1 convolution, C -> Co, FP32 output): y[v][o] = b[o] + sum_c w[o][c] h[v][c]
@@ -627,8 +687,22 @@ lbm_status lbm_nn_im2col(const void* x, void* col, int32_t D, int32_t H, int32_t
                          int32_t transposed, void* stream) {
   if (!x || !col || D <= 0 || H <= 0 || W <= 0 || C <= 0 || Kp < 27 * C) return LBM_ERR_INVALID_ARG;
   const long long n = (long long)D * H * W * Kp;
-  k_im2col<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(x), static_cast<bf16*>(col),
-                                                                       D, H, W, C, Kp, transposed);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!transposed && C % 8 == 0 && Kp % 8 == 0)
+    k_im2col_vec<<<grid_for(n / 8), 256, 0, st>>>(static_cast<const bf16*>(x), static_cast<bf16*>(col), D, H, W, C, Kp);
+  else
+    k_im2col<<<grid_for(n), 256, 0, st>>>(static_cast<const bf16*>(x), static_cast<bf16*>(col), D, H, W, C, Kp,
+                                          transposed);
+  NN_CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status lbm_nn_im2col_cv(const void* xT, void* colT, int32_t D, int32_t H, int32_t W, int32_t C, int32_t Kp,
+                            void* stream) {
+  if (!xT || !colT || D <= 0 || H <= 0 || W <= 0 || (W % 8) || C <= 0 || Kp < 27 * C) return LBM_ERR_INVALID_ARG;
+  const long long n = (long long)D * H * W * Kp / 8;
+  k_im2col_cv<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(xT),
+                                                                          static_cast<bf16*>(colT), D, H, W, C, Kp);
   NN_CK(cudaGetLastError());
   return LBM_OK;
 }
@@ -688,7 +762,12 @@ lbm_status lbm_nn_concat(void* a, int32_t Ca, void* b, int32_t Cb, void* out, in
 
 lbm_status lbm_nn_colsum(const void* x, float* out, int64_t V, int32_t C, void* stream) {
   if (!x || !out || V <= 0 || C <= 0) return LBM_ERR_INVALID_ARG;
-  k_colsum<<<C, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(x), out, V, C);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  NN_CK(cudaMemsetAsync(out, 0, sizeof(float) * C, st));
+  long long blocks = V / 2048 + 1;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const long long chunk = (V + blocks - 1) / blocks;
+  k_colsum<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const bf16*>(x), out, V, C, chunk);
   NN_CK(cudaGetLastError());
   return LBM_OK;
 }

@@ -665,7 +665,6 @@ bool geo_after(const lbm_ctx* c, long long step_done) {
 // on stream st; the step counter is not advanced.
 lbm_status enqueue_step(lbm_ctx* c, long long step, cudaStream_t st, bool timed) {
   const int par = parity_of(step);
-  if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, par, st));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (timed) {
     if (c->ev_free.size() < 2) {
@@ -677,6 +676,8 @@ lbm_status enqueue_step(lbm_ctx* c, long long step, cudaStream_t st, bool timed)
     }
     CK(cudaEventRecord(e0, st));
   }
+  // the psi pass (Shan-Chen forces) is part of the timed step: it reads every population too
+  if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, par, st));
   LAUNCH(c->ks->step(c->a, par, c->p.collision, st));
   if (timed) {
     CK(cudaEventRecord(e1, st));

@@ -47,6 +47,7 @@ def nn_lib():
         "lbm_nn_gemm_tn": [vp, vp, vp, i64, i32, i32, i32, i32, i32, vp, vp],
         "lbm_nn_status": [vp],
         "lbm_nn_im2col": [vp, vp, i32, i32, i32, i32, i32, i32, vp],
+        "lbm_nn_im2col_cv": [vp, vp, i32, i32, i32, i32, i32, vp],
         "lbm_nn_transpose": [vp, vp, i64, i32, vp],
         "lbm_nn_reduce_splits": [vp, vp, i64, i32, i64, vp],
         "lbm_nn_relu_grad": [vp, vp, vp, i64, vp],
@@ -107,6 +108,10 @@ def lbm_nn_status():
 
 def lbm_nn_im2col(x, col, D, H, W, Cc, Kp, transposed=0):
     _call("lbm_nn_im2col", _p(x), _p(col), D, H, W, Cc, Kp, transposed)
+
+
+def lbm_nn_im2col_cv(xT, colT, D, H, W, Cc, Kp):
+    _call("lbm_nn_im2col_cv", _p(xT), _p(colT), D, H, W, Cc, Kp)
 
 
 def lbm_nn_transpose(x, y, R, Cc):
@@ -314,8 +319,14 @@ class WarmStartNet:
         dpre = torch.empty_like(dy)
         lbm_nn_relu_grad(yout, dy, dpre, V * co)
         lbm_nn_colsum(dpre, self.g[name + ".b"], V, co)
-        # weight gradient: dW[k][o] = sum_v colT[k][v] dpreT[o][v], split over v
-        lbm_nn_im2col(xin, col, D, H, W, ci, kp, 1)
+        # weight gradient: dW[k][o] = sum_v colT[k][v] dpreT[o][v], split over v; colT is built
+        # from a channel-major copy of the input when the rows allow 8-voxel vectors
+        if W % 8 == 0:
+            xT = torch.empty((ci, V), dtype=torch.bfloat16, device=self.dev)
+            lbm_nn_transpose(xin, xT, V, ci)
+            lbm_nn_im2col_cv(xT, col, D, H, W, ci, kp)
+        else:
+            lbm_nn_im2col(xin, col, D, H, W, ci, kp, 1)
         dpreT = torch.empty((co, V), dtype=torch.bfloat16, device=self.dev)
         lbm_nn_transpose(dpre, dpreT, V, co)
         tiles = (kp // 128) * max(1, co // 128)

@@ -2,7 +2,7 @@
 
   generate()  solver-generated training data: seeded random-sphere packings (the dissolution
               workload's recipe at the given size, seeds from 10^4), transport numbers Pe, Da
-              drawn log-uniform around 10 and 0.1, each run by the lattice Boltzmann step from
+              drawn log-uniform in [5, 10] and [0.05, 0.2], each run by the lattice Boltzmann step from
               rest to its steady state (residual <= tol, geometry update frozen);
   train()     Adam on the masked squared error of the fields, one sample per step;
   compare()   on held-out geometries: steps and wall time to residual <= tol from rest and from
@@ -45,7 +45,8 @@ def case(seed, n, Pe=sg.PE0, Da=sg.DA0, precision="fp32"):
 def run_to_steady(cfg, geom, fields, tol, max_steps, stream=None):
     """Steps the solver from the given fields until the residual is <= tol; returns
     (steps, seconds, converged, solver).  Seconds are CUDA-event time on the solver's stream,
-    including the host reads of the residual."""
+    including the host reads of the residual.  A run whose populations turn non-finite stops
+    there and is not converged (its residual would read zero)."""
     import torch
     s = Solver(cfg, stream=stream.cuda_stream if stream is not None else None)
     s.set_geometry(geom)
@@ -56,15 +57,23 @@ def run_to_steady(cfg, geom, fields, tol, max_steps, stream=None):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     steps, r = 0, float("inf")
+    finite = True
     while steps < max_steps:
         s.step(100)
         steps += 100
-        r = s.monitors()["residual"]
+        m = s.monitors()
+        r = m["residual"]
+        # a diverging run: non-finite populations, a residual that grows past 5 % per 100 steps,
+        # or a species total beyond twice that of a domain filled at the inlet value
+        if (m["nonfinite"] != 0 or not math.isfinite(r) or (steps > 1000 and r > 0.05)
+                or abs(m["species0"]) > 2.0 * max(1.0, m["nfluid"])):
+            finite = False
+            break
         if 0.0 <= r <= tol:
             break
     e1.record(st)
     torch.cuda.synchronize()
-    return steps, e0.elapsed_time(e1) * 1e-3, bool(0.0 <= r <= tol), s
+    return steps, e0.elapsed_time(e1) * 1e-3, bool(finite and 0.0 <= r <= tol), s
 
 
 class Sample:
@@ -80,28 +89,37 @@ class Sample:
         self.t = sg.targets(u, Cf, device) if u is not None else None
 
 
-def draw_transport(rng, spread=1.5):
-    """Pe and Da log-uniform in [x / spread, x spread] around 10 and 0.1."""
-    lo = math.log(1.0 / spread)
-    return sg.PE0 * math.exp(rng.uniform(lo, -lo)), sg.DA0 * math.exp(rng.uniform(lo, -lo))
+PE_RANGE = (5.0, 10.0)   # the recipe's scalar lattice (tau_c = 1/2 + 0.67 / Pe) is stable below ~Pe 10
+DA_RANGE = (0.05, 0.2)
+
+
+def draw_transport(rng):
+    """Pe and Da log-uniform in PE_RANGE and DA_RANGE.  At Pe = 10 (tau_c = 0.567) the scalar
+    lattice of some packings grows an unstable concentration mode; below it the recipe is stable."""
+    lp = rng.uniform(math.log(PE_RANGE[0]), math.log(PE_RANGE[1]))
+    ld = rng.uniform(math.log(DA_RANGE[0]), math.log(DA_RANGE[1]))
+    return math.exp(lp), math.exp(ld)
 
 
 def generate(count, n=128, seed0=10_000, tol=1e-5, max_steps=400_000, device=0, log=None):
-    """count solver-generated samples; returns (samples, per-sample steps and seconds)."""
+    """count solver-generated samples (cases that do not converge are skipped and recorded, up to
+    count more draws); returns (samples, per-case steps, seconds and outcome)."""
     rng = np.random.default_rng(seed0)
     out, stats = [], []
-    for i in range(count):
-        seed = seed0 + i
+    seed = seed0
+    while len(out) < count and seed < seed0 + 2 * count:
         Pe, Da = draw_transport(rng)
         cfg, geom, fields = case(seed, n, Pe, Da)
         cfg = dict(cfg, device=device)
         steps, sec, ok, s = run_to_steady(cfg, geom, fields, tol, max_steps)
-        f = s.fields()
+        f = s.fields() if ok else None
         s.close()
-        out.append(Sample(seed, n, Pe, Da, geom, f["u"], f["C"][0], device))
+        if ok:
+            out.append(Sample(seed, n, Pe, Da, geom, f["u"], f["C"][0], device))
         stats.append({"seed": seed, "Pe": Pe, "Da": Da, "steps": steps, "seconds": sec, "converged": ok})
         if log:
-            log(f"sample {i}: seed {seed} Pe {Pe:.2f} Da {Da:.3f} steps {steps} {sec:.2f} s")
+            log(f"case seed {seed}: Pe {Pe:.2f} Da {Da:.3f} steps {steps} {sec:.2f} s converged {ok}")
+        seed += 1
     return out, stats
 
 
@@ -148,13 +166,18 @@ def compare(net, seeds, n=128, tol=1e-6, max_steps=400_000, device=0, rng_seed=9
         f_w = s1.fields()
         s1.close()
         fl = geom == 0
+        if not (np.all(np.isfinite(warm[1])) and np.all(np.isfinite(warm[2]))):
+            ok1 = False
         eC = float(np.linalg.norm((warm[2][0] - f_ref["C"][0])[fl]) / np.linalg.norm(f_ref["C"][0][fl]))
         eu = float(np.linalg.norm((warm[1] - f_ref["u"])[:, fl]) / np.linalg.norm(f_ref["u"][:, fl]))
         # both runs end at the same steady state (to the tolerance): the network changes the path only
         dC = float(np.linalg.norm((f_w["C"][0] - f_ref["C"][0])[fl]) / np.linalg.norm(f_ref["C"][0][fl]))
+        # the warm run counts only if it reached the rest run's steady state
+        ok1 = ok1 and math.isfinite(dC) and dC <= 1e-2
         rows.append({"seed": seed, "Pe": Pe, "Da": Da, "rest_steps": steps0, "rest_s": sec0,
                      "warm_steps": steps1, "warm_s": sec1 + t_inf, "inference_s": t_inf,
-                     "converged": ok0 and ok1, "pred_err_C": eC, "pred_err_u": eu,
+                     "converged_rest": ok0, "converged_warm": ok1, "converged": ok0 and ok1,
+                     "pred_err_C": eC, "pred_err_u": eu,
                      "final_fields_rel_diff_C": dC,
                      "speedup_steps": steps0 / max(1, steps1), "speedup_time": sec0 / (sec1 + t_inf)})
     return rows

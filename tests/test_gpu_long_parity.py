@@ -1,0 +1,170 @@
+"""GPU against the FP64 oracle at the workloads' own sizes and horizons.
+
+- The reactive dissolution workload on a 64^3 crop of its 256^3 packing, 500 steps with the
+  geometry update on: every field, population array and monitor within 1e-10, flags exact.
+- A flip exactly on the dissolution threshold (V_m acc == m_s0, Sec. 2.1.5): the rounding of the
+  consumed total decides the step, so the CUDA path may flip that node one step later than the
+  oracle; everything else agrees exactly.
+- The 16-bit storage modes over the workload's 20,000 steps against the oracle (stored by
+  tests/golden/make_precision_golden.py), errors stated per field on the deviations from the rest
+  state (rho - 1, C - 1) and on u.
+- The two-component droplet at 64^3, radii 8 / 12 / 16, 10,000 steps, against the oracle's run
+  (stored by tests/golden/make_droplet_golden.py) at the stored nodes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2502_12955_gb300 import inputs
+from paper_2502_12955_gb300.lbm import Solver
+from tests.gpu_common import FP64_TOL, compare, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _crop64(Pe=10.0, Da=0.1):
+    cfg, geom, _ = inputs.dissolution_3d(n=256)
+    geom = np.ascontiguousarray(geom[:64, :64, :64])
+    D = 0.0185 * 9.0 / Pe
+    cfg = dict(cfg, nx=64, ny=64, nz=64, tau_c=[D / 0.25 + 0.5], k_react=Da * D / 9.0)
+    return cfg, geom, inputs.uniform_fields((64, 64, 64), 1, 1, rho=1.0, C=1.0)
+
+
+def test_dissolution_crop64_500_steps_with_flips():
+    """64^3 crop of the 256^3 packing, the workload's MRT + D3Q7 + wet-node reaction, FP64, with
+    the solid consumed 25x faster (V_m = 25) so that interface nodes dissolve within the 500
+    steps; checked at 1, 250 and 500 steps."""
+    cfg, geom, fields = _crop64()
+    cfg = dict(cfg, V_m=25.0, precision="fp64")
+    o, g = make_pair(cfg, geom, fields)
+    done = 0
+    for target in (1, 250, 500):
+        o.step(target - done)
+        g.step(target - done)
+        done = target
+        compare(o, g, what=f"crop64 step {target}")
+    m = o.monitors()
+    assert m["inj_mass0"] > 0, "the case should dissolve solids"
+    assert m["nsolid"] < (geom != 0).sum()
+
+
+def test_flip_exactly_on_the_threshold():
+    """The node that consumes most by step t* gets m_s0 = V_m acc(t*), so V_m acc == m_s0 holds
+    exactly in the oracle at t* and it flips there.  The CUDA path sums the same link rates in
+    another order (FP64 atomics), so its acc(t*) may fall an ulp short: it flips that node at t* or
+    t* + 1, and every other flag agrees at every step."""
+    shape = (10, 12, 16)
+    cfg, geom, fields = inputs.dissolution_3d(shape=shape, g=5e-4, radius=(2.0, 4.0), precision="fp64")
+    cfg.update(k_react=0.05, V_m=25.0, m_s0=1e30)
+    probe = Oracle(cfg)
+    probe.set_geometry(geom)
+    probe.set_fields(*fields)
+    t_star = 9
+    accs = []
+    for _ in range(t_star):
+        probe.step(1)
+        accs.append(probe.fields()["acc"].reshape(-1).copy())
+    react = geom.reshape(-1) == 2
+    a_t = np.where(react, accs[-1], -np.inf)
+    node = int(np.argmax(a_t))
+    A = float(a_t[node])
+    others = np.delete(a_t[react], np.argmax(a_t[react]))
+    assert A > 1.001 * others.max() and accs[-2][node] < A, "the construction needs a unique leader"
+    m_s0 = 25.0 * A
+    cfg = dict(cfg, m_s0=m_s0)
+    o, g = make_pair(cfg, geom, fields)
+    flip_o = flip_g = None
+    for t in range(1, t_star + 3):
+        o.step(1)
+        g.step(1)
+        fo = o.fields()["flags"].reshape(-1)
+        fg = g.fields()["flags"].reshape(-1)
+        if flip_o is None and fo[node] == 0:
+            flip_o = t
+        if flip_g is None and fg[node] == 0:
+            flip_g = t
+        diff = np.flatnonzero(fo != fg)
+        assert set(diff.tolist()) <= {node}, f"step {t}: flags differ at {diff[:5]}"
+        if t == t_star - 1:
+            compare(o, g, what="before the tie")   # fields still equal at 1e-10
+    assert flip_o == t_star, "the oracle flips on the tie"
+    assert flip_g in (t_star, t_star + 1)
+
+
+def _precision_golden(Pe):
+    path = os.path.join(GOLDEN, f"precision64_pe{Pe}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{os.path.basename(path)} not generated")
+    return np.load(path)
+
+
+# Per-field relative L2 bounds over the workload's 20,000 steps (deviations from the rest state):
+# FP32 is held to FP32 round-off accumulated over the run; FP16 (11-bit significand on deviations
+# of order 1e-2) to the 1e-3 target; BF16 (8-bit significand) to the 1e-2 its rounding allows.
+PRECISION_BOUNDS = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
+
+
+@pytest.mark.parametrize("Pe", [7, 10])
+def test_storage_precision_against_oracle_at_workload_length(Pe):
+    gold = _precision_golden(Pe)
+    nodes = gold["nodes"]
+    cfg, geom, fields = _crop64(Pe=float(Pe))
+    cfg = dict(cfg, geo_mode="none")
+    table = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        s = Solver(dict(cfg, precision=prec))
+        s.set_geometry(geom)
+        s.set_fields(*fields)
+        done = 0
+        for t in (2000, 20000):
+            s.step(t - done)
+            done = t
+            f = s.fields()
+            drho = f["rho"][0].reshape(-1)[nodes] - 1.0
+            u = f["u"].reshape(3, -1)[:, nodes]
+            dC = f["C"][0].reshape(-1)[nodes] - 1.0
+            table[(prec, t)] = {"rho-1": rel_l2(gold[f"drho_{t}"], drho), "u": rel_l2(gold[f"u_{t}"], u),
+                                "C-1": rel_l2(gold[f"dC_{t}"], dC)}
+        s.close()
+    for (prec, t), errs in sorted(table.items()):
+        print(f"Pe {Pe} {prec} step {t}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for (prec, t), errs in table.items():
+        for k, v in errs.items():
+            assert v <= PRECISION_BOUNDS[prec], f"Pe {Pe} {prec} step {t} field {k}: {v:.3e}"
+
+
+@pytest.mark.parametrize("R", [8, 12, 16])
+def test_droplet64_against_oracle(R):
+    """Config-2 droplet at 64^3 (two D3Q19 components, psi = rho, G = 2.7, densities 1 / 0.05),
+    FP64, 10,000 steps: densities and velocity at the stored nodes within 1e-10 of the oracle's
+    run, masses exact, the pressure jump and the spurious-current peak equal."""
+    path = os.path.join(GOLDEN, f"droplet64_R{R}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{os.path.basename(path)} not generated")
+    gold = np.load(path)
+    nodes = gold["nodes"]
+    n = 64
+    cfg, geom, _ = inputs.droplet_3d(n=n, radius=float(R), precision="fp64", G=float(gold["G"]))
+    rho, u = inputs.droplet_fields((n, n, n), float(R))
+    s = Solver(cfg)
+    s.set_geometry(geom)
+    s.set_fields(rho, u, None)
+    done = 0
+    for t in (2000, 10000):
+        s.step(t - done)
+        done = t
+        f = s.fields()
+        r, uu = f["rho"], f["u"]
+        assert rel_l2(gold[f"rho_{t}"], r.reshape(2, -1)[:, nodes]) <= FP64_TOL
+        assert rel_l2(gold[f"u_{t}"], uu.reshape(3, -1)[:, nodes]) <= FP64_TOL
+        np.testing.assert_allclose(r.reshape(2, -1).sum(axis=1), gold[f"mass_{t}"], rtol=1e-12)
+        cs2, G, c = 1.0 / 3.0, float(gold["G"]), n // 2
+        p = cs2 * (r[0] + r[1]) + cs2 * G * r[0] * r[1]
+        assert abs((p[c, c, c] - p[0, 0, 0]) - float(gold[f"dp_{t}"])) <= 1e-10 * abs(float(gold[f"dp_{t}"]))
+        umax = float(np.sqrt((uu ** 2).sum(axis=0)).max())
+        assert abs(umax - float(gold[f"umax_{t}"])) <= 1e-8 * float(gold[f"umax_{t}"])
+        np.testing.assert_allclose((r.reshape(2, -1) ** 2).sum(axis=1), gold[f"rho2sum_{t}"], rtol=1e-10)
+    s.close()

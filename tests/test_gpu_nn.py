@@ -129,8 +129,30 @@ def test_conv3_gradients_against_oracle(ci, co):
         sg.lbm_nn_im2col(dyd, col, D, H, W, co, kpt, 0)
         dx = torch.empty((V, ci), dtype=torch.bfloat16, device="cuda")
         sg.lbm_nn_gemm_tn(col, wt, dx, ci, V, ci, kpt, 1, sg.OUT_BF16, None)
-    # weight gradient: transposed im2col, split over voxels
-    sg.lbm_nn_im2col(_chlast(x), col, D, H, W, ci, kp, 1)
+    # weight gradient: transposed im2col, split over voxels; the channel-major route builds the same
+    # transposed columns bit for bit
+    xd = _chlast(x)
+    xT = torch.empty((ci, V), dtype=torch.bfloat16, device="cuda")
+    sg.lbm_nn_transpose(xd, xT, V, ci)
+    col2 = torch.empty((kp * V,), dtype=torch.bfloat16, device="cuda")
+    sg.lbm_nn_im2col_cv(xT, col2, D, H, W, ci, kp)
+    sg.lbm_nn_im2col(xd, col, D, H, W, ci, kp, 1)
+    assert torch.equal(col[:kp * V], col2)
+    # and the row layout's vector route equals the generic one (C % 8 == 0)
+    if ci % 8 == 0:
+        r1 = torch.empty((V * kp,), dtype=torch.bfloat16, device="cuda")
+        sg.lbm_nn_im2col(xd, r1, D, H, W, ci, kp, 0)
+        r2 = torch.zeros((V, kp), dtype=torch.float32)
+        xh = np.moveaxis(x, 0, -1)
+        for tap in range(27):
+            dz, dy_, dx_ = tap // 9 - 1, (tap // 3) % 3 - 1, tap % 3 - 1
+            sh = np.zeros_like(xh)
+            zs = slice(max(0, -dz), D - max(0, dz)); zt = slice(max(0, dz), D - max(0, -dz))
+            ys = slice(max(0, -dy_), H - max(0, dy_)); yt = slice(max(0, dy_), H - max(0, -dy_))
+            xs = slice(max(0, -dx_), W - max(0, dx_)); xt = slice(max(0, dx_), W - max(0, -dx_))
+            sh[zs, ys, xs] = xh[zt, yt, xt]
+            r2[:, tap * ci:(tap + 1) * ci] = torch.tensor(sh.reshape(V, ci), dtype=torch.float32)
+        assert torch.equal(r1.view(V, kp).float().cpu(), r2)
     dyT = torch.empty((co, V), dtype=torch.bfloat16, device="cuda")
     sg.lbm_nn_transpose(dyd, dyT, V, co)
     ns = sg.lbm_nn_gemm_splits(V, 8)
