@@ -140,7 +140,9 @@ def test_storage_precision_against_oracle_at_workload_length(Pe):
 def test_droplet64_against_oracle(R):
     """Config-2 droplet at 64^3 (two D3Q19 components, psi = rho, G = 2.7, densities 1 / 0.05),
     FP64, 10,000 steps: densities and velocity at the stored nodes within 1e-10 of the oracle's
-    run, masses exact, the pressure jump and the spurious-current peak equal."""
+    run, masses exact, the pressure jump and the spurious-current peak equal.  Started sharp at
+    1 / 0.05, away from the coexistence densities (1.005 / 0.079), the R = 8 droplet dissolves
+    into its box within the 10,000 steps and R = 12 is dissolving; R = 16 persists."""
     path = os.path.join(GOLDEN, f"droplet64_R{R}.npz")
     if not os.path.exists(path):
         pytest.skip(f"{os.path.basename(path)} not generated")
@@ -163,8 +165,10 @@ def test_droplet64_against_oracle(R):
         np.testing.assert_allclose(r.reshape(2, -1).sum(axis=1), gold[f"mass_{t}"], rtol=1e-12)
         cs2, G, c = 1.0 / 3.0, float(gold["G"]), n // 2
         p = cs2 * (r[0] + r[1]) + cs2 * G * r[0] * r[1]
-        assert abs((p[c, c, c] - p[0, 0, 0]) - float(gold[f"dp_{t}"])) <= 1e-10 * abs(float(gold[f"dp_{t}"]))
+        # the pressure is of order 1: its jump is compared on that scale (the R = 8 droplet has
+        # dissolved by step 10,000, leaving a jump near zero)
+        assert abs((p[c, c, c] - p[0, 0, 0]) - float(gold[f"dp_{t}"])) <= 1e-10 * max(1.0, abs(float(gold[f"dp_{t}"])))
         umax = float(np.sqrt((uu ** 2).sum(axis=0)).max())
-        assert abs(umax - float(gold[f"umax_{t}"])) <= 1e-8 * float(gold[f"umax_{t}"])
+        assert abs(umax - float(gold[f"umax_{t}"])) <= 1e-8 * max(float(gold[f"umax_{t}"]), 1e-4)
         np.testing.assert_allclose((r.reshape(2, -1) ** 2).sum(axis=1), gold[f"rho2sum_{t}"], rtol=1e-10)
     s.close()
