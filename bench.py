@@ -257,7 +257,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="dissolution", choices=["dissolution", "droplet", "channel", "ensemble"])
+    ap.add_argument("--workload", default="dissolution",
+                    choices=["dissolution", "droplet", "channel", "ensemble", "nn"])
     ap.add_argument("--members", type=int, default=32,
                     help="ensemble workload: members, half 2D squares and half 3D cubes (512 = the full set)")
     ap.add_argument("--precision", default=None)
@@ -451,6 +452,75 @@ def run_to_steady(args, local):
     s.close()
 
 
+def measured_tensor_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_nn(args, local):
+    """The warm-start network's training step at 128^3 (forward, backward, Adam; BF16 tensor-core
+    GEMMs) on the seed-0 packing's features with synthetic targets, and the tcgen05 GEMM alone on
+    a square-ish BF16 problem against the measured BF16 tensor peak."""
+    import torch
+    from paper_2502_12955_gb300 import surrogate
+
+    torch.cuda.set_device(local)
+    n = args.size or 128
+    _, geom, _ = inputs.dissolution_3d(n=n)
+    net = surrogate.WarmStartNet(device=local)
+    x = surrogate.features(geom, device=local)
+    rng = np.random.default_rng(0)
+    t = torch.tensor(rng.standard_normal((geom.size, 4)).astype(np.float32), device=f"cuda:{local}")
+    fl = torch.tensor((geom == 0).reshape(-1).astype(np.uint8), device=f"cuda:{local}")
+    nf = int((geom == 0).sum())
+    for _ in range(max(3, args.warmup)):
+        net.train_step(x, t, fl, nf, geom.shape, lr=1e-4)
+    net.check()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        net.train_step(x, t, fl, nf, geom.shape, lr=1e-4)
+    e1.record(st)
+    torch.cuda.synchronize()
+    net.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the GEMM alone, a compute-bound shape: M x N x K = 38912 x 1024 x 4096 (128 x 256 tiles, four
+    # along N sharing each A tile in L2, 1216 tiles = 8 waves over 152 SMs), BF16 in, FP32
+    # accumulate, BF16 out
+    M, N, K = 38912, 1024, 4096
+    A = torch.randn((M, K), device=f"cuda:{local}").to(torch.bfloat16)
+    B = torch.randn((N, K), device=f"cuda:{local}").to(torch.bfloat16)
+    C = torch.empty((M, N), device=f"cuda:{local}", dtype=torch.bfloat16)
+    for _ in range(3):
+        surrogate.lbm_nn_gemm_tn(A, B, C, N, M, N, K, 1, surrogate.OUT_BF16, None)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        surrogate.lbm_nn_gemm_tn(A, B, C, N, M, N, K, 1, surrogate.OUT_BF16, None)
+    e1.record(st)
+    torch.cuda.synchronize()
+    net.check()
+    gms = e0.elapsed_time(e1) / reps
+    tflops = 2.0 * M * N * K / (gms * 1e-3) / 1e12
+    peak, src = measured_tensor_peak()
+    line = {"metric": "train_steps_per_s", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "bf16 weights and activations, f32 accumulate and master weights",
+            "data": "synthetic targets on the seed-0 packing's features",
+            "config": {"workload": f"warm_start_net_{n}^3_train_step", "params": net.n_params,
+                       "width": list(net.width)},
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "traffic": None, "peak_source": src,
+                         "kernel": "k_gemm_tn<256>", "shape": [M, N, K], "kernel_ms": gms}}
+    print(json.dumps(line), flush=True)
+
+
 def run_warm_start(args, local):
     """Learned warm start against plain LBM from rest (the dissolution workload's recipe at the
     given size, default 128^3): generate solver steady states (r <= 1e-5) on seeded training
@@ -520,6 +590,10 @@ def main():
 
     if args.workload == "ensemble":
         run_ensemble(args, dist, ws, rank, local)
+        return
+    if args.workload == "nn":
+        if rank == 0:
+            run_nn(args, local)
         return
     if args.to_steady is not None:
         if rank == 0:

@@ -34,7 +34,7 @@ enum { LBM_NN_OUT_F32 = 0, LBM_NN_OUT_BF16 = 1, LBM_NN_OUT_BF16_RELU = 2 };
 
 /* C = A B^T on the tensor cores (tcgen05.mma, FP32 accumulation in TMEM, TMA tile loads).
    A: BF16 [M][K], B: BF16 [N][K] (K contiguous, 16-byte aligned rows).  M % 128 == 0,
-   K % 64 == 0, N % 16 == 0, ldc % 8 == 0, ldc >= N.
+   M <= 65535 * 128, K % 64 == 0, N % 16 == 0, ldc % 8 == 0, ldc >= N.
    out_kind LBM_NN_OUT_F32: C is FP32 [splits][M][ldc]; the K blocks are divided among `splits`
    partial products (lbm_nn_gemm_splits gives the count actually used) to be summed with
    lbm_nn_reduce_splits.  LBM_NN_OUT_BF16 (_RELU): splits must be 1, C is BF16 [M][ldc] holding

@@ -439,7 +439,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 #define LBM_STEP_MIN_BLOCKS_ODD 3   // k_step's odd parity: the slot prefetch hides the lookups, registers pay
 #endif
 #ifndef LBM_TILES_MIN_BLOCKS_ODD
-#define LBM_TILES_MIN_BLOCKS_ODD 4  // k_step_tiles' odd parity waits on the lookups: more warps pay
+#define LBM_TILES_MIN_BLOCKS_ODD 3  // k_step_tiles: odd parity, slots prefetched a tile ahead (as k_step)
 #endif
 
 // Neighbour offsets of fluid node n from its coordinates (fast divisions by nx and ny).
@@ -1119,9 +1119,20 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
   // member's tiles together, so a chunk mostly stays within one member and its arguments are
   // staged again only when the chunk crosses into another; taking chunks in turn keeps a mix of
   // 2D and 3D members on every block
+  auto next_tile = [&](unsigned int t) {
+    return t + ((t % LBM_TILE_CHUNK == LBM_TILE_CHUNK - 1) ? (gridDim.x - 1) * LBM_TILE_CHUNK + 1 : 1);
+  };
+#if LBM_ODD_SLOT_CACHE
+  // odd parity: two slot buffers, the next tile's neighbour slots are copied in (cp.async)
+  // while this tile computes, as in k_step; the next tile's list entry and link mask are loaded
+  // one tile ahead at both parities whenever it belongs to the member already staged
+  uint32_t* cn = slot_smem + (blockDim.x + threadIdx.x) * L::Q;
+#endif
+  bool have_next = false;
+  int n_pf = 0;
+  uint32_t m_pf = 0u;
   unsigned int staged = 0xffffffffu;
-  for (unsigned int t = blockIdx.x * LBM_TILE_CHUNK; t < ntiles;
-       t += (t % LBM_TILE_CHUNK == LBM_TILE_CHUNK - 1) ? (gridDim.x - 1) * LBM_TILE_CHUNK + 1 : 1) {
+  for (unsigned int t = blockIdx.x * LBM_TILE_CHUNK; t < ntiles; t = next_tile(t)) {
     const Tile tile = tiles[t];
     if (tile.member != staged) {   // block-uniform
       __syncthreads();   // the previous member's tiles are done with sa / sk
@@ -1133,29 +1144,76 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       for (unsigned int i = threadIdx.x; i < sizeof(Coef<T>) / 4; i += blockDim.x) kdst[i] = ksrc[i];
       __syncthreads();
       staged = tile.member;
+      have_next = false;
     }
     const Args& a = sa;
     T wallx = T(0), heatx = T(0);
     const unsigned int e = tile.first + threadIdx.x;
-    if (e < a.fluid_count[0]) {
-      const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
-      const uint32_t m = a.mask[n];
-      if (m & 1u) {
-        const unsigned int base = a.fluid_count[1];
-        T f[NC][Q], h[NSD][QC];
-        const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+    const unsigned int count = a.fluid_count[0];
+    int n = 0;
+    uint32_t m = 0u;
+    if (have_next) {
+      n = n_pf;
+      m = m_pf;
+    } else if (e < count) {
+      n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
+      m = a.mask[n];
 #if LBM_ODD_SLOT_CACHE
-        if (parity) {
-          gather_entry_odd_cached<L, S, NC, NS, 1>(a, sn, n, m, cache, f, h);
-          collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1>(a, sk, n, m, sn, f, h, wallx, heatx, cache);
-        } else
+      if (parity) prefetch_slots<L, 1>(a, n, cache);
 #endif
-        {
-          gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
-          collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx, heatx);
+    }
+#if LBM_ODD_SLOT_CACHE
+    if (parity) cp_async_commit();
+#endif
+    // the next tile of this block, if it belongs to the staged member
+    have_next = false;
+    const unsigned int tn = next_tile(t);
+    if (tn < ntiles) {
+      const Tile tile2 = tiles[tn];
+      if (tile2.member == staged) {
+        const unsigned int e2 = tile2.first + threadIdx.x;
+        n_pf = 0;
+        m_pf = 0u;
+        if (e2 < count) {
+          n_pf = int(LBM_CHK(a.err, a.fluid_list[e2], a.N));
+          m_pf = a.mask[n_pf];
+#if LBM_ODD_SLOT_CACHE
+          if (parity) prefetch_slots<L, 1>(a, n_pf, cn);
+#endif
         }
+        have_next = true;
       }
     }
+#if LBM_ODD_SLOT_CACHE
+    if (parity) {
+      cp_async_commit();
+      cp_async_wait<1>();   // this tile's slots have arrived
+    }
+#endif
+    if (e < count && (m & 1u)) {
+      const unsigned int base = a.fluid_count[1];
+      T f[NC][Q], h[NSD][QC];
+      const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+#if LBM_ODD_SLOT_CACHE
+      if (parity) {
+        // the plain variant addresses every flow link through its cache entry (wall_offsets)
+        if (!BND) wall_offsets<L, 1>(a, sn, m, cache);
+        gather_entry_odd_cached<L, S, NC, NS, 1, true, !BND>(a, sn, n, m, cache, f, h);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1, !BND>(a, sk, n, m, sn, f, h, wallx, heatx, cache);
+      } else
+#endif
+      {
+        gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx, heatx);
+      }
+    }
+#if LBM_ODD_SLOT_CACHE
+    if (parity) {
+      uint32_t* tmp = cache;
+      cache = cn;
+      cn = tmp;
+    }
+#endif
     if (NS > 0) {
       const unsigned int any = __ballot_sync(0xffffffffu, wallx != T(0));
       if (any) {
@@ -1174,6 +1232,9 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       }
     }
   }
+#if LBM_ODD_SLOT_CACHE
+  if (parity) cp_async_wait<0>();
+#endif
 }
 
 // ================================================================ psi

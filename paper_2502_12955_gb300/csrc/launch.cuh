@@ -96,10 +96,11 @@ struct Launchers {
   static Coef<T> coef(const Args& a) { return make_coef<L, T>(a, kShifted); }
 
   // one resident wave of blocks; the kernel walks the fluid list with a grid-stride loop
-  // dynamic shared memory of the tile kernel's odd-step neighbour-slot cache: Q words per thread
+  // dynamic shared memory of the tile kernel's odd-step neighbour-slot caches: two buffers of Q
+  // words per thread (the current tile's and the next tile's)
   static size_t slot_smem_bytes(int parity, int threads) {
     if (!parity || !LBM_ODD_SLOT_CACHE) return 0;
-    return (size_t)threads * L::Q * sizeof(uint32_t);
+    return 2 * (size_t)threads * L::Q * sizeof(uint32_t);
   }
 
   template <int NC, int NS, int COLL, int PAR, bool BND>

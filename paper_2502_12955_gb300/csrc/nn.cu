@@ -11,7 +11,8 @@
 // tap = (dz + 1) 9 + (dy + 1) 3 + (dx + 1), zero outside the domain and for k >= 27 C (K is padded
 // to a multiple of 128).  The contraction runs on the 5th-generation tensor cores:
 //   - C[M][N] = A[M][K] B[N][K]^T, A and B BF16 with K contiguous ("TN"), FP32 accumulation;
-//   - one CTA of 4 warps per 128 x BN output tile; a TMA unit loads 128 x 64 and BN x 64 tiles
+//   - one CTA of 4 warps per 128 x BN output tile (BN = 16 .. 256, N tiles fastest across the grid
+//     so that CTAs resident together share A tiles in L2); a TMA unit loads 128 x 64 and BN x 64 tiles
 //     (128-byte swizzle) into a 4-stage shared-memory ring; one thread issues tcgen05.mma into
 //     a TMEM accumulator (128 lanes x BN columns); all four warps read it back with tcgen05.ld;
 //   - forward:       Y[v][o]  = col(X)[v][k]  W[o][k]            (bias, ReLU in the epilogue)
@@ -148,7 +149,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // N tiles vary fastest across the grid, so CTAs running at the same time share their A tiles in L2
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nkb_all = K / BK;
   const int kb0 = blockIdx.z * kb_per_split;
   const int kb1 = min(nkb_all, kb0 + kb_per_split);
@@ -612,7 +614,7 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(M / BM, N / BN, splits);
+  dim3 grid(N / BN, M / BM, splits);
   k_gemm_tn<BN><<<grid, 128, SM::bytes, st>>>(ta, tb, K, kbs, o, err_word());
   return cudaGetLastError();
 }
@@ -639,8 +641,9 @@ lbm_status lbm_nn_gemm_tn(const void* A, const void* B, void* C, int64_t ldc, in
   if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || (M % BM) || (K % BK) || (N % 16) || splits < 1)
     return LBM_ERR_INVALID_ARG;
   if (out_kind != LBM_NN_OUT_F32 && splits != 1) return LBM_ERR_INVALID_ARG;
+  if (M / BM > 65535 || splits > 65535) return LBM_ERR_INVALID_ARG;   // grid y and z limits
   if (out_kind < LBM_NN_OUT_F32 || out_kind > LBM_NN_OUT_BF16_RELU || ldc < N || (ldc % 8)) return LBM_ERR_INVALID_ARG;
-  const int BN = N % 128 == 0 ? 128 : (N % 64 == 0 ? 64 : (N % 32 == 0 ? 32 : 16));
+  const int BN = N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : (N % 64 == 0 ? 64 : (N % 32 == 0 ? 32 : 16)));
   const int nkb = K / BK;
   if (splits > nkb) splits = nkb;
   const int kbs = (nkb + splits - 1) / splits;
@@ -653,6 +656,7 @@ lbm_status lbm_nn_gemm_tn(const void* A, const void* B, void* C, int64_t ldc, in
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   switch (BN) {
+    case 256: e = launch_gemm<256>(ta, tb, M, N, K, splits, kbs, o, st); break;
     case 128: e = launch_gemm<128>(ta, tb, M, N, K, splits, kbs, o, st); break;
     case 64: e = launch_gemm<64>(ta, tb, M, N, K, splits, kbs, o, st); break;
     case 32: e = launch_gemm<32>(ta, tb, M, N, K, splits, kbs, o, st); break;

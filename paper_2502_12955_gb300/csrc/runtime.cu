@@ -1189,7 +1189,9 @@ lbm_status ens_launch(lbm_ensemble* e, int parity, cudaStream_t st) {
   if (e->ntiles == 0) return LBM_OK;
   const lbm_params& p = e->m[0]->p;
   int bnd = 0;   // the boundary-rule kernel variant when any member has a moving plate or an inlet
-  for (size_t k = 0; k < e->m.size(); ++k) bnd |= e->m[k]->a.moving_wall | e->m[k]->a.flow_open_x | e->m[k]->a.arrhenius;
+  // (or a domain too large for the plain variant's 32-bit wall offsets)
+  for (size_t k = 0; k < e->m.size(); ++k)
+    bnd |= e->m[k]->a.moving_wall | e->m[k]->a.flow_open_x | e->m[k]->a.arrhenius | !e->m[k]->a.voff_ok;
   const cudaError_t r = e->ks->step_tiles(e->d_args, e->d_coefs, e->d_tiles, e->ntiles, p.n_comp, p.n_scal,
                                           p.collision, parity, bnd, e->threads, st);
   e->launches += 1;

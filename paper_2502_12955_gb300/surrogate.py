@@ -14,8 +14,9 @@ used for device memory and the stream only.
 Network (the same plan as the FP64 reference of the test suite): encoder levels of two 3^3
 convolutions (ReLU) and 2x average pooling, a bottleneck of two 3^3 convolutions, decoder levels
 of 2x nearest upsampling, concatenation with the encoder output of that level and one 3^3
-convolution (ReLU), and a 1x1 head to 4 outputs.  Inputs (4 channels): solid indicator,
-x / (nx - 1), ln(Pe / 10), ln(Da / 0.1).  Outputs: u / 0.005 (3 channels) and 2 (C - 1/2), which
+convolution (ReLU), and a 1x1 head to 4 outputs.  Inputs (5 channels): solid indicator,
+x / (nx - 1), ln(Pe / 10), ln(Da / 0.1) and the distance to the nearest solid over the mean sphere
+radius (pore size, which sets how far a pore's concentration is depleted).  Outputs: u / 0.005 (3 channels) and 2 (C - 1/2), which
 weights the concentration, the field whose error sets the relaxation time, above the velocity.
 Training: masked mean squared error over fluid voxels, Adam.
 """
@@ -32,6 +33,8 @@ U_SCALE = 0.005      # velocity scale of the targets (of the order of the packin
 C_OFF, C_SCALE = 0.5, 2.0   # concentration target 2 (C - 1/2): order one, and weighted above u
 PE0, DA0 = 10.0, 0.1
 OUT_F32, OUT_BF16, OUT_BF16_RELU = 0, 1, 2
+PORE_SCALE = 9.0     # length scale of the pore-size channel (the packings' mean sphere radius)
+N_FEATURES = 5
 
 _NN = None
 
@@ -200,7 +203,7 @@ class WarmStartNet:
     """The encoder-decoder on one GPU: FP32 master weights with Adam, BF16 copies for the
     tensor-core GEMMs, channel-last BF16 activations."""
 
-    def __init__(self, width=(16, 32, 64, 160), c_in=4, c_out=4, seed=0, device=0):
+    def __init__(self, width=(16, 32, 64, 160), c_in=N_FEATURES, c_out=4, seed=0, device=0):
         import torch
         if width[0] != 16 or c_out != 4:
             raise ValueError("the head kernel takes 16 input and 4 output channels")
@@ -458,16 +461,29 @@ class WarmStartNet:
 
 # ------------------------------------------------------------------ data
 
+def pore_distance(geom, pad=16):
+    """Euclidean distance of every fluid node to the nearest solid node (0 on solids), with the
+    domain wrapped periodically in y and z and open in x (inlet and outlet faces)."""
+    from scipy.ndimage import distance_transform_edt
+    fl = geom == 0
+    p = min(pad, geom.shape[0], geom.shape[1])
+    big = np.pad(fl, ((p, p), (p, p), (0, 0)), mode="wrap")
+    d = distance_transform_edt(big)
+    return d[p:p + geom.shape[0], p:p + geom.shape[1], :]
+
+
 def features(geom, Pe=PE0, Da=DA0, device=0):
-    """Input channels (channel-last BF16 [V][4]) of a geometry [nz, ny, nx] of flags."""
+    """Input channels (channel-last BF16 [V][5]) of a geometry [nz, ny, nx] of flags: solid
+    indicator, x / (nx - 1), ln(Pe / 10), ln(Da / 0.1), distance to the nearest solid / 9."""
     import torch
     nz, ny, nx = geom.shape
-    f = np.empty((nz, ny, nx, 4), np.float32)
+    f = np.empty((nz, ny, nx, N_FEATURES), np.float32)
     f[..., 0] = (geom != 0)
     f[..., 1] = (np.arange(nx) / max(1, nx - 1))[None, None, :]
     f[..., 2] = math.log(Pe / PE0)
     f[..., 3] = math.log(Da / DA0)
-    return torch.from_numpy(f.reshape(-1, 4)).to(device=torch.device("cuda", device), dtype=torch.bfloat16)
+    f[..., 4] = pore_distance(geom) / PORE_SCALE
+    return torch.from_numpy(f.reshape(-1, N_FEATURES)).to(device=torch.device("cuda", device), dtype=torch.bfloat16)
 
 
 def targets(u, Cf, device=0):

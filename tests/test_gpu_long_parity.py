@@ -161,7 +161,11 @@ def test_droplet64_against_oracle(R):
         f = s.fields()
         r, uu = f["rho"], f["u"]
         assert rel_l2(gold[f"rho_{t}"], r.reshape(2, -1)[:, nodes]) <= FP64_TOL
-        assert rel_l2(gold[f"u_{t}"], uu.reshape(3, -1)[:, nodes]) <= FP64_TOL
+        # the static droplet's velocity is its spurious current (down to 1e-7): its round-off, a few
+        # ulps of the populations (~1e-16), is measured against an RMS floor of 1e-5
+        ug, uo = uu.reshape(3, -1)[:, nodes], gold[f"u_{t}"]
+        scale = max(np.linalg.norm(uo), 1e-5 * np.sqrt(uo.size))
+        assert np.linalg.norm(ug - uo) <= FP64_TOL * scale
         np.testing.assert_allclose(r.reshape(2, -1).sum(axis=1), gold[f"mass_{t}"], rtol=1e-12)
         cs2, G, c = 1.0 / 3.0, float(gold["G"]), n // 2
         p = cs2 * (r[0] + r[1]) + cs2 * G * r[0] * r[1]

@@ -37,7 +37,8 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 16, 64, 1), (256, 32, 192, 1), (384, 64, 576, 1),
                                           (512, 128, 1024, 1), (128, 48, 128, 1), (256, 16, 4096, 7),
-                                          (128, 128, 2048, 16)])
+                                          (128, 128, 2048, 16), (256, 256, 512, 1), (384, 768, 256, 1),
+                                          (256, 512, 1024, 3)])
 def test_gemm_fp32_against_fp64_product(M, N, K, splits):
     rng = np.random.default_rng(M + N + K)
     A, B = _bf(rng.standard_normal((M, K))), _bf(rng.standard_normal((N, K)))
@@ -236,7 +237,7 @@ def test_network_forward_and_gradients_against_oracle():
     for n, (mw, mb) in zip(order, calls):
         scale[n + ".w"], scale[n + ".b"] = np.linalg.norm(mw), np.linalg.norm(mb)
 
-    net = sg.WarmStartNet(width=width)
+    net = sg.WarmStartNet(width=width, c_in=4)
     net.set_params(params)
     y = net.forward(_chlast(x), shape)
     td = torch.tensor(np.moveaxis(t, 0, -1).reshape(-1, 4), dtype=torch.float32, device="cuda")
@@ -262,7 +263,7 @@ def test_training_steps_reduce_the_loss():
     tgt = np.stack([np.sin(np.linspace(0, 3, shape[2]))[None, None, :] * np.ones(shape)] * 4)
     td = torch.tensor(np.moveaxis(tgt, 0, -1).reshape(-1, 4), dtype=torch.float32, device="cuda")
     fl = torch.ones(int(np.prod(shape)), dtype=torch.uint8, device="cuda")
-    net = sg.WarmStartNet(width=width, seed=1)
+    net = sg.WarmStartNet(width=width, c_in=4, seed=1)
     losses = [float(net.train_step(x, td, fl, int(np.prod(shape)), shape, lr=3e-3).item()) for _ in range(30)]
     net.check()
     assert losses[-1] < 0.5 * losses[0], losses
