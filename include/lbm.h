@@ -128,6 +128,16 @@ typedef struct lbm_params {
   double arr_Ta;              /* activation temperature E / R_u (>= 0) */
   double heat_release;        /* h_r: heat flux per unit reaction rate */
   int32_t n_it;               /* iterations of the C_b - T_b coupling, 0..64 (default 16) */
+  int32_t product;            /* 1: one more scalar lattice after the n_scal given ones carries the
+                                 product of the surface reaction (CO2; Sec. 2.1.5, Eq. react,
+                                 reactCO2).  At each reactive link it gains what the reaction takes
+                                 from scalar 0 there, r = k C_b: the per-link wet-node ansatz with
+                                 the flux reversed gives h_P,i = h_P,opp(i) + r tau_p / (tau_p - 1/2).
+                                 Fields and populations then carry n_scal + 1 scalar rows, the
+                                 product last; its 16-bit storage reference is 0.  Needs n_scal >= 1,
+                                 no deposition, one component when n_scal == 2; not in ensembles. */
+  double tau_p;               /* relaxation time of the product lattice (> 0.5) */
+  double C_in_p;              /* product value of the inlet ghost (with ade_open_x) */
 } lbm_params;
 
 /* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */
@@ -151,6 +161,12 @@ typedef struct lbm_monitors {
   double residual;            /* last automatic residual (-1 if none yet) */
   double heat;                /* cumulative temperature-population gain through reactive links
                                  (arrhenius only) */
+  double species_p;           /* product lattice (product only): sum of its stored populations */
+  double inflow_p;            /* cumulative product entering through the inlet */
+  double outflow_p;           /* cumulative product leaving through the outlet */
+  double injected_species_p;  /* product added by dissolution flips */
+  double removed_species_p;   /* always 0 (the product is not combined with deposition) */
+  double produced;            /* cumulative product-population gain through reactive links */
 } lbm_monitors;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -173,8 +189,9 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz,
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, size_t n);
 
 /* Initialise populations at equilibrium (Eq. 6, Eq. therpopeq_species) from host FP64 fields:
-   rho [n_comp][N], u [3][N] (2D: the z row is ignored), C [n_scal][N] (NULL when n_scal == 0).
-   Solid nodes are ignored.  Resets the step counter and all monitors. */
+   rho [n_comp][N], u [3][N] (2D: the z row is ignored), C [n_scal + product][N] (NULL when
+   n_scal == 0; the product's row last).  Solid nodes are ignored.  Resets the step counter and
+   all monitors. */
 lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* C,
                           size_t n);
 
@@ -189,12 +206,13 @@ lbm_status lbm_sync(lbm_ctx* ctx);
 /* Copy macroscopic fields at the current time into caller buffers (any may be NULL):
    rho [n_comp][N]; u [3][N], the physical velocity sum_sigma (j^sigma + F^sigma/2) / rho
    (Eq. 1.19); C [n_scal][N] with the wet-node closure applied; flags [N]; acc [N], the
-   per-node consumed amount (reactive solids) or deposited fraction (deposition). */
+   per-node consumed amount (reactive solids) or deposited fraction (deposition).  With the
+   reaction product, C has n_scal + 1 rows (the product last), as in lbm_set_fields. */
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, double* C, uint8_t* flags,
                           double* acc);
 
-/* Pre-collision populations at the current time, FP64, [n_comp][Qf][N] and [n_scal][Qc][N]
-   (either may be NULL).  Reactive-link scalar slots hold the stored bounce-back value. */
+/* Pre-collision populations at the current time, FP64, [n_comp][Qf][N] and
+   [n_scal + product][Qc][N] (either may be NULL).  Reactive-link scalar slots hold the stored bounce-back value. */
 lbm_status lbm_get_pops(lbm_ctx* ctx, double* f, double* h);
 lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f, const double* h);
 

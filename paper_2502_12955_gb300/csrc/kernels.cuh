@@ -86,9 +86,9 @@ __host__ __device__ __forceinline__ unsigned int fast_div(unsigned int n, FastDi
 // Everything a kernel needs, in double; kernels convert to their compute type.
 struct Args {
   void* f[2];
-  void* h[2];
+  void* h[3];                // scalar lattices: the given scalars, then the reaction product (if any)
   void* fplane[2][19];       // base pointer of every population plane (host-computed)
-  void* hplane[2][7];
+  void* hplane[3][7];
   void* psi[2];              // compute-type psi per component (Shan-Chen only)
   uint8_t* flags;
   uint32_t* mask;
@@ -109,11 +109,11 @@ struct Args {
   uint32_t* flip_list;
   unsigned int* flip_count;
   unsigned int flip_cap;
-  double* flip_scratch;      // [flip_cap][4]
-  double* flip_mon;          // [8] inj_mass[2], inj_spec[2], rem_mass[2], rem_spec[2]
+  double* flip_scratch;      // [flip_cap][5]: new node's mean density (2) and scalars (3)
+  double* flip_mon;          // [10] inj_mass[2], inj_spec[3], rem_mass[2], rem_spec[3]
   int* err;
-  double* inflow_row;        // [2][rows]
-  double* outflow_row;       // [2][rows]
+  double* inflow_row;        // [3][rows]
+  double* outflow_row;       // [3][rows]
   double* partials;          // monitor partial sums [blocks][NMON]
   double* mon_out;           // [NMON]
   double* d_rho;             // FP64 staging [n_comp][N]
@@ -123,16 +123,17 @@ struct Args {
   long long pitch;           // elements per population plane (>= N, multiple of 32)
   long long N;
   int nx, ny, nz;
-  int n_comp, n_scal;
+  int n_comp, n_scal;        // n_scal: scalar lattices, the product included
+  int product;               // the last scalar lattice is the reaction product (Eq. reactCO2)
   int per[3];                // flow periodicity
   int open_x;                // scalar inlet / outlet on the x faces
   int sc_on, ads_on, shift_forcing, psi_identity;
   int geo_mode, deposit_conservative;
   double tau[2], G[2][2], G_ads[2], psi_wall, rho0, g[3];
   double s_grp[5];           // MRT rates: e, eps, q, pi, m
-  double tau_c[2], J0, k_react, C_in[2];
+  double tau_c[3], J0, k_react, C_in[3];
   double V_m, m_s0, DP;
-  double rho_ref[2], C_ref[2];
+  double rho_ref[2], C_ref[3];
   int bx, by;                // step-kernel block shape
   FastDiv div_x, div_y;      // node index / nx, (node index / nx) / ny
   double u_wall[3];          // velocity of the top plate beyond y = ny - 1
@@ -168,27 +169,33 @@ struct Coef {
   T tau[2];
   T G[2][2], G_ads[2], psi_wall, rho0, g[3];
   T mrt_g[10];      // (s_k - 1/tau) / |R_k|^2 of the MRT rows (one component)
-  T omc[2];         // 1 / tau_c
+  T omc[3];         // 1 / tau_c
   T wc0, wca;       // scalar weights: rest, axis
   T ics2c;          // 1 / c_s^2 of the scalar lattice
   T icb;            // 1 / (2 w_a + K), K = k tau_c / (tau_c - 1/2): wet-node closure
   T kr;             // k
-  T C_in[2];
+  T C_in[3];
   T DP, keep;       // deposition probability, 1 - DP
-  T rref[2], cref[2];   // storage references (0 in FP64 mode)
+  T rref[2], cref[3];   // storage references (0 in FP64 mode)
+  T fp;             // tau_P / (tau_P - 1/2) of the product lattice
   T uw6[3];         // 6 u_wall = 2 u_wall / c_s^2 of the moving top plate
   T arrA, arrTa;    // temperature-dependent rate A exp(-Ta / T)
   T fc, fT;         // tau / (tau - 1/2) of scalar 0 and of the temperature (scalar 1)
   T hr;             // reaction heat per unit rate
 };
 
-constexpr int NMON = 18;
+constexpr int NMON = 22;
 constexpr int WALLX_SLOTS = 4096;
 // partial-sum slots
 enum : int {
   M_MASS = 0, M_MOM = 2, M_SPEC = 5, M_REACT = 7, M_DEPO = 8, M_IN = 9, M_OUT = 11,
-  M_WALLX = 13, M_NSOLID = 14, M_NFLUID = 15, M_NONFIN = 16, M_HEAT = 17
+  M_WALLX = 13, M_NSOLID = 14, M_NFLUID = 15, M_NONFIN = 16, M_HEAT = 17,
+  M_SPEC2 = 18, M_IN2 = 19, M_OUT2 = 20, M_PROD = 21   // the third scalar lattice; product gained
 };
+// monitor slots of scalar lattice s (0 .. 2)
+__host__ __device__ constexpr int mon_spec(int s) { return s < 2 ? M_SPEC + s : M_SPEC2; }
+__host__ __device__ constexpr int mon_in(int s) { return s < 2 ? M_IN + s : M_IN2; }
+__host__ __device__ constexpr int mon_out(int s) { return s < 2 ? M_OUT + s : M_OUT2; }
 
 // ------------------------------------------------------------- indexing
 
@@ -357,6 +364,26 @@ __device__ __forceinline__ void close_thermal(T* h0, T* h1, uint32_t m, const Co
       h0[j] = hn0;
       h1[j] = hn1;
       on_link(j, kt * Cb, old0[j] - hn0, hn1 - old1[j]);
+    }
+  }
+}
+
+// The reaction product (Sec. 2.1.5, Eq. react, reactCO2): at each reactive link the product lattice
+// gains what the reaction takes from scalar 0 there, r = k C_b of that link's closure.  The per-link
+// wet-node ansatz of the species closure with the flux reversed, (1 - 1/(2 tau_P)) (h_P,j -
+// h_P,opp j) = r, gives h_P,j = h_P,opp j + r tau_P / (tau_P - 1/2).  All closures of a node use the
+// values before any closure; hp holds deviations from w C_ref,P on both sides of the link, so the
+// shift cancels.  gain accumulates what the closure adds to the populations.
+template <class L, class T>
+__device__ __forceinline__ void close_product(T* hp, uint32_t m, const Coef<T>& k, const T* rl, T& gain) {
+  T old[L::QC];
+#pragma unroll
+  for (int j = 0; j < L::QC; ++j) old[j] = hp[j];
+#pragma unroll
+  for (int j = 1; j < L::QC; ++j) {
+    if (MaskBits<L>::code(m, L::opp(j)) == 2u) {
+      hp[j] = old[L::opp(j)] + rl[j] * k.fp;
+      gain += hp[j] - old[j];
     }
   }
 }
@@ -684,14 +711,18 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
                                                 typename Store<S>::T (&f)[NC][L::Q],
                                                 typename Store<S>::T (&h)[NS > 0 ? NS : 1][L::QC],
                                                 typename Store<S>::T& wallx, typename Store<S>::T& heatx,
-                                                const uint32_t* cache = nullptr) {
+                                                typename Store<S>::T& prodx, const uint32_t* cache = nullptr) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC;
   const Nbr nb = nbr_of(a, n);
   // ---- wet-node closure of scalar 0 and reaction bookkeeping (Eq. wetnode9, reactO2)
   if (NS > 0) {
     // the consumed totals are reductions (no value returned): the threshold test runs in
-    // k_detect over the interface list before the geometry update
+    // k_detect over the interface list before the geometry update; rl keeps each link's rate
+    // for the product lattice's closure
+    T rl[QC];
+#pragma unroll
+    for (int j = 0; j < QC; ++j) rl[j] = T(0);
     if (BND && NS > 1 && a.arrhenius) {
       // temperature-dependent rate and reaction heat (the full kernel variant only)
       close_thermal<L, T>(h[0], h[NS > 1 ? 1 : 0], m, k, a.n_it, [&](int j, T r, T exch, T heat) {
@@ -699,14 +730,17 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
         atomicAdd(a.acc + src, widen(r));
         wallx += exch;
         heatx += heat;
+        rl[j] = r;
       });
     } else {
       close_scalar<L, T>(h[0], m, k, [&](int j, T Cb, T exch) {
         const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
         atomicAdd(a.acc + src, widen(k.kr * Cb));
         wallx += exch;
+        rl[j] = k.kr * Cb;
       });
     }
+    if (NS > 1 && a.product) close_product<L, T>(h[NS - 1], m, k, rl, prodx);
     // ---- deposition at near-substrate nodes (Eq. surface_deposition)
     if (a.geo_mode == GEO_DEPOSIT) {
       bool near = false;
@@ -958,11 +992,11 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
         if (L::cx(j) < 0) {
           const T cu = T(L::cx(jb)) * ux + T(L::cy(jb)) * uy + T(L::cz(jb)) * uz;
           b = k.wca * k.C_in[s] * (T(1) + cu * k.ics2c) - sh;
-          a.inflow_row[LBM_CHK(a.err, s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x)), 2ll * a.ny * a.nz)] +=
+          a.inflow_row[LBM_CHK(a.err, s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x)), 3ll * a.ny * a.nz)] +=
               widen(b) - widen(v);
         } else {
           b = h[s][jb];
-          a.outflow_row[LBM_CHK(a.err, s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x)), 2ll * a.ny * a.nz)] +=
+          a.outflow_row[LBM_CHK(a.err, s * (a.ny * a.nz) + int(fast_div(unsigned(n), a.div_x)), 3ll * a.ny * a.nz)] +=
               widen(v) - widen(b);
         }
         v = b;
@@ -989,7 +1023,7 @@ template <class L, class S, int NC, int NS, int COLL, int parity, bool BND>
 __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) == 4 ? (parity ? LBM_STEP_MIN_BLOCKS_ODD : LBM_STEP_MIN_BLOCKS) : 2)) k_step(const Args a, const Coef<typename Store<S>::T> k) {
   using T = typename Store<S>::T;
   constexpr int Q = L::Q, QC = L::QC, NSD = NS > 0 ? NS : 1;
-  T wallx = T(0), heatx = T(0);
+  T wallx = T(0), heatx = T(0), prodx = T(0);
   const unsigned int count = a.fluid_count[0];
   const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
   const unsigned int stride = gridDim.x * blockDim.x;
@@ -1026,7 +1060,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         if (!BND) wall_offsets<L, LBM_STEP_CACHE_STRIDE>(a, sn, m, cb);
         gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE, true, !BND>(a, sn, n, m, cb, f, h);
         collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE, !BND>(a, k, n, m, sn, f, h, wallx,
-                                                                                          heatx, cb);
+                                                                                          heatx, prodx, cb);
       }
       uint32_t* t = cb;
       cb = cn;
@@ -1056,13 +1090,14 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
     if (parity) {
       const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
       gather_entry_odd_cached<L, S, NC, NS, LBM_STEP_CACHE_STRIDE>(a, sn, n, m, cache, f, h);
-      collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, heatx, cache);
+      collide_scatter<L, S, NC, NS, COLL, parity, BND, true, LBM_STEP_CACHE_STRIDE>(a, k, n, m, sn, f, h, wallx, heatx,
+                                                                                    prodx, cache);
       continue;
     }
 #endif
     gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
     const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-    collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, k, n, m, sn, f, h, wallx, heatx);
+    collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, k, n, m, sn, f, h, wallx, heatx, prodx);
   }
   }
   // ---- wall-exchange monitor: one reduction per warp that saw a reactive link
@@ -1075,13 +1110,24 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
                   widen(w));
     }
   }
-  // ---- reaction heat monitor (second half of the slots)
+  // ---- reaction heat monitor (second bank of the slots)
   if (BND && NS > 1) {
     const unsigned int any = __ballot_sync(0xffffffffu, heatx != T(0));
     if (any) {
       const T w = warp_sum(heatx);
       if ((threadIdx.x & 31) == 0)
         atomicAdd(a.wallx_slot + WALLX_SLOTS +
+                      ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
+                  widen(w));
+    }
+  }
+  // ---- reaction product monitor (third bank)
+  if (NS > 1) {
+    const unsigned int any = __ballot_sync(0xffffffffu, prodx != T(0));
+    if (any) {
+      const T w = warp_sum(prodx);
+      if ((threadIdx.x & 31) == 0)
+        atomicAdd(a.wallx_slot + 2 * WALLX_SLOTS +
                       ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
                   widen(w));
     }
@@ -1147,7 +1193,7 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
       have_next = false;
     }
     const Args& a = sa;
-    T wallx = T(0), heatx = T(0);
+    T wallx = T(0), heatx = T(0), prodx = T(0);
     const unsigned int e = tile.first + threadIdx.x;
     const unsigned int count = a.fluid_count[0];
     int n = 0;
@@ -1199,12 +1245,13 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         // the plain variant addresses every flow link through its cache entry (wall_offsets)
         if (!BND) wall_offsets<L, 1>(a, sn, m, cache);
         gather_entry_odd_cached<L, S, NC, NS, 1, true, !BND>(a, sn, n, m, cache, f, h);
-        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1, !BND>(a, sk, n, m, sn, f, h, wallx, heatx, cache);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND, true, 1, !BND>(a, sk, n, m, sn, f, h, wallx, heatx, prodx,
+                                                                         cache);
       } else
 #endif
       {
         gather_entry<L, S, NC, NS, parity>(a, e, base, n, m, f, h);
-        collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx, heatx);
+        collide_scatter<L, S, NC, NS, COLL, parity, BND>(a, sk, n, m, sn, f, h, wallx, heatx, prodx);
       }
     }
 #if LBM_ODD_SLOT_CACHE
@@ -1228,6 +1275,15 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
         const T w = warp_sum(heatx);
         if ((threadIdx.x & 31) == 0)
           atomicAdd(a.wallx_slot + WALLX_SLOTS + ((t * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
+                    widen(w));
+      }
+    }
+    if (NS > 1) {
+      const unsigned int any = __ballot_sync(0xffffffffu, prodx != T(0));
+      if (any) {
+        const T w = warp_sum(prodx);
+        if ((threadIdx.x & 31) == 0)
+          atomicAdd(a.wallx_slot + 2 * WALLX_SLOTS + ((t * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS),
                     widen(w));
       }
     }
@@ -1346,7 +1402,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
   for (int q = 0; q < NMON; ++q) v[q] = 0.0;
   for (int s = 0; s < NC; ++s) v[M_MASS + s] = double(dm[s]) + double(k.rref[s]) * double(nfluid);
   for (int c = 0; c < 3; ++c) v[M_MOM + c] = double(mom[c]);
-  for (int s = 0; s < NS; ++s) v[M_SPEC + s] = double(dsp[s]) + double(k.cref[s]) * double(nfluid);
+  for (int s = 0; s < NS; ++s) v[mon_spec(s)] = double(dsp[s]) + double(k.cref[s]) * double(nfluid);
   v[M_NFLUID] = double(nfluid);
   v[M_NONFIN] = double(nonfin);
   // bookkeeping over every node
@@ -1366,12 +1422,13 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
   const int rows = a.ny * a.nz;
   for (int r = tid; r < rows; r += nthr)
     for (int s = 0; s < NS; ++s) {
-      v[M_IN + s] += a.inflow_row[s * rows + r];
-      v[M_OUT + s] += a.outflow_row[s * rows + r];
+      v[mon_in(s)] += a.inflow_row[s * rows + r];
+      v[mon_out(s)] += a.outflow_row[s * rows + r];
     }
   for (int q = tid; q < WALLX_SLOTS; q += nthr) {
     v[M_WALLX] += a.wallx_slot[q];
     v[M_HEAT] += a.wallx_slot[WALLX_SLOTS + q];
+    v[M_PROD] += a.wallx_slot[2 * WALLX_SLOTS + q];
   }
   block_reduce_store<NMON>(v, a.partials + (long long)blockIdx.x * NMON);
 }
@@ -1451,10 +1508,14 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
 #pragma unroll
   for (int s = 0; s < NS; ++s)
     gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, hh[s], a.err, a.N, a.pitch);
+  T rl[QC], gain = T(0);
+#pragma unroll
+  for (int j = 0; j < QC; ++j) rl[j] = T(0);
   if (NS > 1 && a.arrhenius)
-    close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], m, k, a.n_it, [](int, T, T, T) {});
+    close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], m, k, a.n_it, [&](int j, T r, T, T) { rl[j] = r; });
   else if (NS > 0)
-    close_scalar<L, T>(hh[0], m, k, [](int, T, T) {});
+    close_scalar<L, T>(hh[0], m, k, [&](int j, T Cb, T) { rl[j] = k.kr * Cb; });
+  if (NS > 1 && a.product) close_product<L, T>(hh[NS - 1], m, k, rl, gain);
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T C = k.cref[s];
@@ -1894,8 +1955,10 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
   const int percs[3] = {a.open_x ? 0 : a.per[0], a.per[1], a.per[2]};
   const long long P = a.pitch;
   const bool dissolve = a.geo_mode == GEO_DISSOLVE;
-  __shared__ double sred[8];
-  if (threadIdx.x < 8) sred[threadIdx.x] = 0.0;
+  // flip monitors: injected mass [0, 2), injected scalars [2, 5), removed mass [5, 7), removed
+  // scalars [7, 10)
+  __shared__ double sred[10];
+  if (threadIdx.x < 10) sred[threadIdx.x] = 0.0;
   // ---- phase 0: claim
   for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const long long s = a.flip_list[e];
@@ -1915,7 +1978,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
     int x, y, z;
     coords_of(a, s, &x, &y, &z);
     if (dissolve) {
-      double sr[2] = {0.0, 0.0}, sc[2] = {0.0, 0.0};
+      double sr[2] = {0.0, 0.0}, sc[3] = {0.0, 0.0, 0.0};
       int count = 0;
       int ax;
       for (int i = 1; i < Q; ++i) {
@@ -1936,26 +1999,27 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         T hh[NS > 0 ? NS : 1][QC];
         for (int c = 0; c < NS; ++c)
           gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, hh[c]);
+        T rl[QC], gain = T(0);
+        for (int j = 0; j < QC; ++j) rl[j] = T(0);
         if (NS > 1 && a.arrhenius)
-          close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], mq, k, a.n_it, [](int, T, T, T) {});
+          close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], mq, k, a.n_it, [&](int j, T r, T, T) { rl[j] = r; });
         else if (NS > 0)
-          close_scalar<L, T>(hh[0], mq, k, [](int, T, T) {});
+          close_scalar<L, T>(hh[0], mq, k, [&](int j, T Cb, T) { rl[j] = k.kr * Cb; });
+        if (NS > 1 && a.product) close_product<L, T>(hh[NS - 1], mq, k, rl, gain);
         for (int c = 0; c < NS; ++c) {
           double C = double(k.cref[c]);
           for (int j = 0; j < QC; ++j) C += double(hh[c][j]);
           sc[c] += C;
         }
       }
-      double* sc4 = a.flip_scratch + 4ll * e;
+      double* sc4 = a.flip_scratch + 5ll * e;
       if (count == 0) {
         leave_flipping(a.flags, s, FL_REACTIVE);   // nothing to average: stays solid
         a.flip_list[e] = 0xffffffffu;
         continue;
       }
-      for (int c = 0; c < 2; ++c) {
-        sc4[c] = sr[c] / count;
-        sc4[2 + c] = sc[c] / count;
-      }
+      for (int c = 0; c < 2; ++c) sc4[c] = sr[c] / count;
+      for (int c = 0; c < 3; ++c) sc4[2 + c] = sc[c] / count;
     } else {
       const Nbr ns = make_nbr(a, x, y, z);
       const uint32_t ms = a.mask[s];
@@ -1964,14 +2028,14 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         gather_flow<L, S>(reinterpret_cast<const S*>(a.f[c]), P, a.slot[s], a.slot, ms, ns, parity_next, f);
         double r = double(k.rref[c]);
         for (int j = 0; j < Q; ++j) r += double(f[j]);
-        atomicAdd(&sred[4 + c], r);
+        atomicAdd(&sred[5 + c], r);
       }
       for (int c = 0; c < NS; ++c) {
         T h[QC];
         gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[s], a.slot, ms, ns, parity_next, h);
         double C = double(k.cref[c]);
         for (int j = 0; j < QC; ++j) C += double(h[j]);
-        atomicAdd(&sred[6 + c], C);
+        atomicAdd(&sred[7 + c], C);
       }
     }
   }
@@ -1985,7 +2049,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
     coords_of(a, s, &x, &y, &z);
     int ax;
     if (dissolve) {
-      const double* sc4 = a.flip_scratch + 4ll * e;
+      const double* sc4 = a.flip_scratch + 5ll * e;
       for (int c = 0; c < NC; ++c) {
         S* fs = reinterpret_cast<S*>(a.f[c]);
         const double r = sc4[c];
@@ -2090,7 +2154,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
     }
   }
   __syncthreads();
-  if (threadIdx.x < 8 && sred[threadIdx.x] != 0.0) atomicAdd(a.flip_mon + threadIdx.x, sred[threadIdx.x]);
+  if (threadIdx.x < 10 && sred[threadIdx.x] != 0.0) atomicAdd(a.flip_mon + threadIdx.x, sred[threadIdx.x]);
   if (threadIdx.x == 0) *a.flip_count = 0u;
 }
 

@@ -63,10 +63,17 @@ Coef<T> make_coef(const Args& a, bool shifted) {
     k.tau[s] = T(a.tau[s]);
     k.G_ads[s] = T(a.G_ads[s]);
     for (int t = 0; t < 2; ++t) k.G[s][t] = T(a.G[s][t]);
+    k.rref[s] = shifted ? T(a.rho_ref[s]) : T(0);
+  }
+  for (int s = 0; s < 3; ++s) {
     k.omc[s] = T(1.0 / a.tau_c[s]);
     k.C_in[s] = T(a.C_in[s]);
-    k.rref[s] = shifted ? T(a.rho_ref[s]) : T(0);
     k.cref[s] = shifted ? T(a.C_ref[s]) : T(0);
+  }
+  // the product lattice is the last one (tau_c[n_scal - 1] when a.product)
+  {
+    const double tp = a.product && a.n_scal > 0 ? a.tau_c[a.n_scal - 1] : 1.0;
+    k.fp = T(tp / (tp - 0.5));
   }
   k.psi_wall = T(a.psi_wall);
   k.rho0 = T(a.rho0);
@@ -142,7 +149,11 @@ struct Launchers {
     switch (a.n_scal) {
       case 0: return step_c<NC, 0>(a, parity, coll, st);
       case 1: return step_c<NC, 1>(a, parity, coll, st);
-      default: return step_c<NC, 2>(a, parity, coll, st);
+      case 2: return step_c<NC, 2>(a, parity, coll, st);
+      default:
+        // three scalar lattices (two scalars and the reaction product): one component only
+        if constexpr (NC == 1) return step_c<1, 3>(a, parity, coll, st);
+        else return cudaErrorInvalidValue;
     }
   }
   static cudaError_t step(const Args& a, int parity, int coll, cudaStream_t st) {
@@ -162,7 +173,8 @@ struct Launchers {
     if (a.n_comp == 1) {
       if (a.n_scal == 0) fn(std::integral_constant<int, 1>(), std::integral_constant<int, 0>());
       else if (a.n_scal == 1) fn(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
-      else fn(std::integral_constant<int, 1>(), std::integral_constant<int, 2>());
+      else if (a.n_scal == 2) fn(std::integral_constant<int, 1>(), std::integral_constant<int, 2>());
+      else fn(std::integral_constant<int, 1>(), std::integral_constant<int, 3>());
     } else {
       if (a.n_scal == 0) fn(std::integral_constant<int, 2>(), std::integral_constant<int, 0>());
       else if (a.n_scal == 1) fn(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());

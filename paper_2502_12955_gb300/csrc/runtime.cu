@@ -41,9 +41,10 @@ struct lbm_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
   std::string err;
   std::vector<void*> allocs;
-  double* mon_host = nullptr;      // pinned [NMON + 8]
+  double* mon_host = nullptr;      // pinned [NMON + 12]: monitors, then the 10 flip monitors
   void* f_alt[2] = {nullptr, nullptr};   // second population buffers: targets of re-slotting
-  void* h_alt[2] = {nullptr, nullptr};
+  void* h_alt[3] = {nullptr, nullptr, nullptr};
+  int nlat = 0;                    // scalar lattices: the given scalars, then the product if any
   // CUDA graphs of one even + odd step pair, keyed by which of the two steps end with a
   // geometry update; rebuilt whenever the kernel arguments change (re-slotting)
   cudaStream_t cap_stream = nullptr;
@@ -167,6 +168,13 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
     if (p->n_comp != 1 || p->G[0][0] != 0.0 || p->G_ads[0] != 0.0 || p->rho_solid != 0.0)
       return fail(c, LBM_ERR_INVALID_ARG, "a velocity inlet needs one component without Shan-Chen forces");
   }
+  if (p->product != 0 && p->product != 1) return fail(c, LBM_ERR_INVALID_ARG, "product must be 0 or 1");
+  if (p->product) {
+    if (p->n_scal < 1) return fail(c, LBM_ERR_INVALID_ARG, "the reaction product needs the reacting scalar (n_scal >= 1)");
+    if (!(p->tau_p > 0.5)) return fail(c, LBM_ERR_INVALID_ARG, "tau_p = %g must exceed 0.5", p->tau_p);
+    if (p->geo_mode == LBM_GEO_DEPOSIT) return fail(c, LBM_ERR_INVALID_ARG, "the reaction product is not combined with deposition");
+    if (p->n_scal == 2 && p->n_comp != 1) return fail(c, LBM_ERR_INVALID_ARG, "three scalar lattices need one component");
+  }
   return LBM_OK;
 }
 
@@ -198,7 +206,9 @@ void fill_args(lbm_ctx* c) {
   a.voff_ok = 3ll * c->pitch < (1ll << 31) ? 1 : 0;
   a.N = c->N;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
-  a.n_comp = p.n_comp; a.n_scal = p.n_scal;
+  a.n_comp = p.n_comp;
+  a.n_scal = c->nlat;                 // scalar lattices, the product (if any) last
+  a.product = p.product ? 1 : 0;
   for (int k = 0; k < 3; ++k) a.per[k] = p.periodic[k] ? 1 : 0;
   a.open_x = p.ade_open_x ? 1 : 0;
   bool sc = false;
@@ -219,10 +229,21 @@ void fill_args(lbm_ctx* c) {
   a.rho0 = p.rho0;
   for (int s = 0; s < 2; ++s) {
     a.tau[s] = p.tau[s] > 0.5 ? p.tau[s] : 1.0;
+    a.rho_ref[s] = p.rho_ref[s];
+  }
+  for (int s = 0; s < 3; ++s) {
+    a.tau_c[s] = 1.0;
+    a.C_in[s] = 0.0;
+    a.C_ref[s] = 0.0;
+  }
+  for (int s = 0; s < p.n_scal; ++s) {
     a.tau_c[s] = p.tau_c[s] > 0.5 ? p.tau_c[s] : 1.0;
     a.C_in[s] = p.C_in[s];
-    a.rho_ref[s] = p.rho_ref[s];
     a.C_ref[s] = p.C_ref[s];
+  }
+  if (p.product) {   // the product lattice: its own relaxation time and inlet value, shift 0
+    a.tau_c[p.n_scal] = p.tau_p > 0.5 ? p.tau_p : 1.0;
+    a.C_in[p.n_scal] = p.C_in_p;
   }
   for (int k = 0; k < 3; ++k) a.g[k] = (k < 2 || c->lattice == LBM_D3Q19_D3Q7) ? p.g[k] : 0.0;
   a.s_grp[0] = p.s_e; a.s_grp[1] = p.s_eps; a.s_grp[2] = p.s_q; a.s_grp[3] = p.s_pi; a.s_grp[4] = p.s_m;
@@ -258,7 +279,7 @@ void set_planes(lbm_ctx* c) {
   for (int s = 0; s < c->p.n_comp; ++s)
     for (int i = 0; i < c->Qf; ++i)
       c->a.fplane[s][i] = static_cast<char*>(c->a.f[s]) + (size_t)i * c->pitch * c->elem;
-  for (int s = 0; s < c->p.n_scal; ++s)
+  for (int s = 0; s < c->nlat; ++s)
     for (int j = 0; j < c->Qc; ++j)
       c->a.hplane[s][j] = static_cast<char*>(c->a.h[s]) + (size_t)j * c->pitch * c->elem;
 }
@@ -270,7 +291,7 @@ lbm_status move_pops(lbm_ctx* c, void* const* src_f, void* const* dst_f, void* c
   for (int s = 0; s < c->p.n_comp; ++s)
     LAUNCH(launch_permute(src_f[s], dst_f[s], (int)c->elem, c->pitch, c->Qf, c->a.flags, c->N, from, to,
                           c->stream));
-  for (int s = 0; s < c->p.n_scal; ++s)
+  for (int s = 0; s < c->nlat; ++s)
     LAUNCH(launch_permute(src_h[s], dst_h[s], (int)c->elem, c->pitch, c->Qc, c->a.flags, c->N, from, to,
                           c->stream));
   return LBM_OK;
@@ -502,6 +523,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   c->N = (long long)nx * ny * nz;
   c->pitch = (c->N + 31) / 32 * 32;
   c->p = *params;
+  c->nlat = params->n_scal + (params->product ? 1 : 0);
   c->Qf = lattice == LBM_D3Q19_D3Q7 ? 19 : 9;
   c->Qc = lattice == LBM_D3Q19_D3Q7 ? 7 : 5;
   c->stream = reinterpret_cast<cudaStream_t>(params->stream);
@@ -532,9 +554,9 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     ptr = reinterpret_cast<decltype(ptr)>(v);               \
   } while (0)
   for (int s = 0; s < params->n_comp; ++s) DA(a.f[s], P * c->Qf * c->elem);
-  for (int s = 0; s < params->n_scal; ++s) DA(a.h[s], P * c->Qc * c->elem);
+  for (int s = 0; s < c->nlat; ++s) DA(a.h[s], P * c->Qc * c->elem);
   for (int s = 0; s < params->n_comp; ++s) DA(c->f_alt[s], P * c->Qf * c->elem);
-  for (int s = 0; s < params->n_scal; ++s) DA(c->h_alt[s], P * c->Qc * c->elem);
+  for (int s = 0; s < c->nlat; ++s) DA(c->h_alt[s], P * c->Qc * c->elem);
   set_planes(c);
   DA(a.slot, N * 4);
   DA(a.slot_new, N * 4);
@@ -556,27 +578,27 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     DA(a.block_counts, ((pos + 1023) / 1024 + 1) * 4);
     DA(a.block_counts_v, ((pos + 1023) / 1024 + 1) * 4);
   }
-  DA(a.wallx_slot, 2 * WALLX_SLOTS * 8);
+  DA(a.wallx_slot, 3 * WALLX_SLOTS * 8);
   DA(a.u_in_row, ny * 8);
   DA(a.iface_list, N * 4);
   DA(a.iface_count, 16);
   DA(a.listed, (N + 3) / 4 * 4);
   DA(a.flip_list, (size_t)cap * 4);
   DA(a.flip_count, 16);
-  DA(a.flip_scratch, (size_t)cap * 4 * 8);
-  DA(a.flip_mon, 8 * 8);
+  DA(a.flip_scratch, (size_t)cap * 5 * 8);
+  DA(a.flip_mon, 10 * 8);
   DA(a.err, 16);
-  DA(a.inflow_row, 2 * rows * 8);
-  DA(a.outflow_row, 2 * rows * 8);
+  DA(a.inflow_row, 3 * rows * 8);
+  DA(a.outflow_row, 3 * rows * 8);
   // monitor partials: the monitor grid uses 128-thread blocks over x; the residual 256 over N
   DA(a.partials, (long long)wave_blocks() * NMON * 8);
   DA(a.mon_out, (NMON + 8) * 8);
   DA(a.d_rho, 2 * N * 8);
   DA(a.d_u, 3 * N * 8);
-  DA(a.d_C, std::max<long long>(1, params->n_scal) * N * 8);
+  DA(a.d_C, std::max<long long>(1, c->nlat) * N * 8);
   DA(a.snap, 4 * P * c->ks->psi_bytes);
 #undef DA
-  e = cudaMallocHost(reinterpret_cast<void**>(&c->mon_host), (NMON + 8) * sizeof(double));
+  e = cudaMallocHost(reinterpret_cast<void**>(&c->mon_host), (NMON + 12) * sizeof(double));
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
   // zero everything the kernels accumulate into
   e = cudaMemsetAsync(a.flags, 0, (N + 3) / 4 * 4, c->stream);
@@ -585,15 +607,15 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.iface_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.listed, 0, (N + 3) / 4 * 4, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 64, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 80, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 16, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, 2 * WALLX_SLOTS * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, 3 * WALLX_SLOTS * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.fluid_count, 0, 16, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.inflow_row, 0, 2 * rows * 8, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 2 * rows * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.inflow_row, 0, 3 * rows * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 3 * rows * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.mon_out, 0, (NMON + 8) * 8, c->stream);
   for (int s = 0; s < params->n_comp && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.f[s], 0, P * c->Qf * c->elem, c->stream);
-  for (int s = 0; s < params->n_scal && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem, c->stream);
+  for (int s = 0; s < c->nlat && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem, c->stream);
   if (e == cudaSuccess) e = launch_iota(a.slot, N, c->stream);   // node order until a geometry is set
   if (e == cudaSuccess) {
     // inlet profile u_x(y) = 6 U s (1 - s), s = (y + 1/2) / ny (zero without a velocity inlet)
@@ -628,21 +650,21 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* flags, size_t n) {
 lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const double* C, size_t n) {
   if (!c || !rho || !u) return LBM_ERR_INVALID_ARG;
   if ((long long)n != c->N) return fail(c, LBM_ERR_INVALID_ARG, "fields have %zu nodes, domain %lld", n, c->N);
-  if (c->p.n_scal > 0 && !C) return fail(c, LBM_ERR_INVALID_ARG, "C is NULL with n_scal > 0");
+  if (c->nlat > 0 && !C) return fail(c, LBM_ERR_INVALID_ARG, "C is NULL with n_scal > 0");
   const size_t N = (size_t)c->N;
   CK(cudaMemcpyAsync(c->a.d_rho, rho, c->p.n_comp * N * 8, cudaMemcpyHostToDevice, c->stream));
   const int ud = c->lattice == LBM_D3Q19_D3Q7 ? 3 : 2;
   CK(cudaMemcpyAsync(c->a.d_u, u, ud * N * 8, cudaMemcpyHostToDevice, c->stream));
   if (ud == 2) CK(cudaMemsetAsync(c->a.d_u + 2 * N, 0, N * 8, c->stream));
-  if (c->p.n_scal > 0) CK(cudaMemcpyAsync(c->a.d_C, C, c->p.n_scal * N * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->nlat > 0) CK(cudaMemcpyAsync(c->a.d_C, C, c->nlat * N * 8, cudaMemcpyHostToDevice, c->stream));
   LAUNCH(c->ks->init(c->a, c->stream));
   const long long rows = (long long)c->ny * c->nz;
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
-  CK(cudaMemsetAsync(c->a.flip_mon, 0, 64, c->stream));
+  CK(cudaMemsetAsync(c->a.flip_mon, 0, 80, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
-  CK(cudaMemsetAsync(c->a.wallx_slot, 0, 2 * WALLX_SLOTS * 8, c->stream));
-  CK(cudaMemsetAsync(c->a.inflow_row, 0, 2 * rows * 8, c->stream));
-  CK(cudaMemsetAsync(c->a.outflow_row, 0, 2 * rows * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.wallx_slot, 0, 3 * WALLX_SLOTS * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.inflow_row, 0, 3 * rows * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.outflow_row, 0, 3 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
   CK(cudaMemsetAsync(c->a.snap, 0, 4 * c->pitch * c->ks->psi_bytes, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -786,7 +808,7 @@ lbm_status lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* C, uint8_t
   const size_t N = (size_t)c->N;
   if (rho) CK(cudaMemcpyAsync(rho, c->a.d_rho, c->p.n_comp * N * 8, cudaMemcpyDeviceToHost, c->stream));
   if (u) CK(cudaMemcpyAsync(u, c->a.d_u, 3 * N * 8, cudaMemcpyDeviceToHost, c->stream));
-  if (C && c->p.n_scal > 0) CK(cudaMemcpyAsync(C, c->a.d_C, c->p.n_scal * N * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (C && c->nlat > 0) CK(cudaMemcpyAsync(C, c->a.d_C, c->nlat * N * 8, cudaMemcpyDeviceToHost, c->stream));
   if (flags) CK(cudaMemcpyAsync(flags, c->a.flags, N, cudaMemcpyDeviceToHost, c->stream));
   if (acc) CK(cudaMemcpyAsync(acc, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -799,11 +821,11 @@ lbm_status lbm_get_pops(lbm_ctx* c, double* f, double* h) {
   double* df = nullptr;
   double* dh = nullptr;
   if (f) CK(cudaMalloc(&df, c->p.n_comp * c->Qf * N * 8));
-  if (h && c->p.n_scal > 0) CK(cudaMalloc(&dh, c->p.n_scal * c->Qc * N * 8));
+  if (h && c->nlat > 0) CK(cudaMalloc(&dh, c->nlat * c->Qc * N * 8));
   cudaError_t e = c->ks->pops_io(c->a, parity_of(c->step), 0, df, dh, c->stream);
   c->launches += 1;
   if (e == cudaSuccess && df) e = cudaMemcpyAsync(f, df, c->p.n_comp * c->Qf * N * 8, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess && dh) e = cudaMemcpyAsync(h, dh, c->p.n_scal * c->Qc * N * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && dh) e = cudaMemcpyAsync(h, dh, c->nlat * c->Qc * N * 8, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(df);
   cudaFree(dh);
@@ -843,7 +865,7 @@ lbm_status lbm_get_pops_noalloc(lbm_ctx* c, double* f, double* h) {
   if (!c) return LBM_ERR_INVALID_ARG;
   const size_t N = (size_t)c->N;
   const size_t nf = f ? (size_t)c->p.n_comp * c->Qf * N : 0;
-  const size_t nh = (h && c->p.n_scal > 0) ? (size_t)c->p.n_scal * c->Qc * N : 0;
+  const size_t nh = (h && c->nlat > 0) ? (size_t)c->nlat * c->Qc * N : 0;
   const size_t need = (nf + nh) * sizeof(double);
   if (need > LBM_NOALLOC_SCRATCH_BYTES)
     return fail(c, LBM_ERR_CAPACITY, "lbm_get_pops_noalloc needs %zu bytes of scratch, the fixed array holds %u",
@@ -874,9 +896,9 @@ lbm_status lbm_set_pops(lbm_ctx* c, const double* f, const double* h) {
   double* dh = nullptr;
   cudaError_t e = cudaSuccess;
   if (f) e = cudaMalloc(&df, c->p.n_comp * c->Qf * N * 8);
-  if (e == cudaSuccess && h && c->p.n_scal > 0) e = cudaMalloc(&dh, c->p.n_scal * c->Qc * N * 8);
+  if (e == cudaSuccess && h && c->nlat > 0) e = cudaMalloc(&dh, c->nlat * c->Qc * N * 8);
   if (e == cudaSuccess && df) e = cudaMemcpyAsync(df, f, c->p.n_comp * c->Qf * N * 8, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess && dh) e = cudaMemcpyAsync(dh, h, c->p.n_scal * c->Qc * N * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && dh) e = cudaMemcpyAsync(dh, h, c->nlat * c->Qc * N * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
     e = c->ks->pops_io(c->a, parity_of(c->step), 1, df, dh, c->stream);
     c->launches += 1;
@@ -896,22 +918,44 @@ lbm_status lbm_get_monitors(lbm_ctx* c, lbm_monitors* out) {
   if (st != LBM_OK) return st;
   double* hm = c->mon_host;
   CK(cudaMemcpyAsync(hm, c->a.mon_out, NMON * 8, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(hm + NMON, c->a.flip_mon, 8 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hm + NMON, c->a.flip_mon, 10 * 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   std::memset(out, 0, sizeof(*out));
   out->step = double(c->step);
   out->mass[0] = hm[M_MASS]; out->mass[1] = hm[M_MASS + 1];
   for (int k = 0; k < 3; ++k) out->momentum[k] = hm[M_MOM + k];
-  out->species[0] = hm[M_SPEC]; out->species[1] = hm[M_SPEC + 1];
   out->reacted = hm[M_REACT];
   out->deposited = hm[M_DEPO];
+  // flip monitors: injected mass [0, 2), injected scalars [2, 5), removed mass [5, 7), removed
+  // scalars [7, 10); the product lattice, when there is one, is scalar lattice n_scal
+  double sp[3], in[3], outf[3], inj[3], rem[3];
+  for (int s = 0; s < 3; ++s) {
+    sp[s] = hm[mon_spec(s)];
+    in[s] = hm[mon_in(s)];
+    outf[s] = hm[mon_out(s)];
+    inj[s] = hm[NMON + 2 + s];
+    rem[s] = hm[NMON + 7 + s];
+  }
   for (int s = 0; s < 2; ++s) {
-    out->inflow[s] = hm[M_IN + s];
-    out->outflow[s] = hm[M_OUT + s];
     out->injected_mass[s] = hm[NMON + s];
-    out->injected_species[s] = hm[NMON + 2 + s];
-    out->removed_mass[s] = hm[NMON + 4 + s];
-    out->removed_species[s] = hm[NMON + 6 + s];
+    out->removed_mass[s] = hm[NMON + 5 + s];
+  }
+  const int ns = c->p.n_scal;
+  for (int s = 0; s < 2; ++s) {
+    const bool given = s < ns;
+    out->species[s] = given ? sp[s] : 0.0;
+    out->inflow[s] = given ? in[s] : 0.0;
+    out->outflow[s] = given ? outf[s] : 0.0;
+    out->injected_species[s] = given ? inj[s] : 0.0;
+    out->removed_species[s] = given ? rem[s] : 0.0;
+  }
+  if (c->p.product) {
+    out->species_p = sp[ns];
+    out->inflow_p = in[ns];
+    out->outflow_p = outf[ns];
+    out->injected_species_p = inj[ns];
+    out->removed_species_p = rem[ns];
+    out->produced = hm[M_PROD];
   }
   out->wall_exchange = hm[M_WALLX];
   out->heat = hm[M_HEAT];
@@ -953,8 +997,8 @@ struct StateHeader {
 };
 size_t state_bytes(const lbm_ctx* c) {
   const size_t N = (size_t)c->N, P = (size_t)c->pitch, rows = (size_t)c->ny * c->nz;
-  return sizeof(StateHeader) + (c->p.n_comp * c->Qf + c->p.n_scal * c->Qc) * P * c->elem +
-         (N + 3) / 4 * 4 + N * 8 + 2 * WALLX_SLOTS * 8 + 4 * rows * 8 + 8 * 8;
+  return sizeof(StateHeader) + (c->p.n_comp * c->Qf + c->nlat * c->Qc) * P * c->elem +
+         (N + 3) / 4 * 4 + N * 8 + 3 * WALLX_SLOTS * 8 + 6 * rows * 8 + 10 * 8;
 }
 }  // namespace
 
@@ -968,32 +1012,32 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   if (*nbytes < need) return fail(c, LBM_ERR_INVALID_ARG, "state buffer %zu < %zu bytes", *nbytes, need);
   uint8_t* o = static_cast<uint8_t*>(host);
   StateHeader hd{};
-  std::memcpy(hd.magic, "LBMSTAT1", 8);
-  hd.version = 1; hd.lattice = c->lattice; hd.precision = c->p.precision;
-  hd.n_comp = c->p.n_comp; hd.n_scal = c->p.n_scal; hd.nx = c->nx; hd.ny = c->ny; hd.nz = c->nz;
+  std::memcpy(hd.magic, "LBMSTAT2", 8);   // format 2: three scalar lattices' worth of bookkeeping
+  hd.version = 2; hd.lattice = c->lattice; hd.precision = c->p.precision;
+  hd.n_comp = c->p.n_comp; hd.n_scal = c->nlat; hd.nx = c->nx; hd.ny = c->ny; hd.nz = c->nz;
   hd.step = c->step;
   std::memcpy(o, &hd, sizeof hd);
   o += sizeof hd;
   const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
   // populations in node order (solid nodes 0), staged in the second population buffers
   for (int s = 0; s < c->p.n_comp; ++s) CK(cudaMemsetAsync(c->f_alt[s], 0, c->Qf * P * c->elem, c->stream));
-  for (int s = 0; s < c->p.n_scal; ++s) CK(cudaMemsetAsync(c->h_alt[s], 0, c->Qc * P * c->elem, c->stream));
+  for (int s = 0; s < c->nlat; ++s) CK(cudaMemsetAsync(c->h_alt[s], 0, c->Qc * P * c->elem, c->stream));
   lbm_status st = move_pops(c, c->a.f, c->f_alt, c->a.h, c->h_alt, c->a.slot, nullptr);
   if (st != LBM_OK) return st;
   for (int s = 0; s < c->p.n_comp; ++s) {
     CK(cudaMemcpyAsync(o, c->f_alt[s], c->Qf * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
     o += c->Qf * P * c->elem;
   }
-  for (int s = 0; s < c->p.n_scal; ++s) {
+  for (int s = 0; s < c->nlat; ++s) {
     CK(cudaMemcpyAsync(o, c->h_alt[s], c->Qc * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
     o += c->Qc * P * c->elem;
   }
   CK(cudaMemcpyAsync(o, c->a.flags, (N + 3) / 4 * 4, cudaMemcpyDeviceToHost, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(o, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream)); o += N * 8;
-  CK(cudaMemcpyAsync(o, c->a.wallx_slot, 2 * WALLX_SLOTS * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * WALLX_SLOTS * 8;
-  CK(cudaMemcpyAsync(o, c->a.inflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
-  CK(cudaMemcpyAsync(o, c->a.outflow_row, 2 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 2 * rows * 8;
-  CK(cudaMemcpyAsync(o, c->a.flip_mon, 64, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(o, c->a.wallx_slot, 3 * WALLX_SLOTS * 8, cudaMemcpyDeviceToHost, c->stream)); o += 3 * WALLX_SLOTS * 8;
+  CK(cudaMemcpyAsync(o, c->a.inflow_row, 3 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 3 * rows * 8;
+  CK(cudaMemcpyAsync(o, c->a.outflow_row, 3 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 3 * rows * 8;
+  CK(cudaMemcpyAsync(o, c->a.flip_mon, 80, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *nbytes = need;
   return LBM_OK;
@@ -1006,8 +1050,8 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   const uint8_t* o = static_cast<const uint8_t*>(host);
   StateHeader hd;
   std::memcpy(&hd, o, sizeof hd);
-  if (std::memcmp(hd.magic, "LBMSTAT1", 8) != 0 || hd.lattice != c->lattice || hd.precision != c->p.precision ||
-      hd.n_comp != c->p.n_comp || hd.n_scal != c->p.n_scal || hd.nx != c->nx || hd.ny != c->ny || hd.nz != c->nz)
+  if (std::memcmp(hd.magic, "LBMSTAT2", 8) != 0 || hd.lattice != c->lattice || hd.precision != c->p.precision ||
+      hd.n_comp != c->p.n_comp || hd.n_scal != c->nlat || hd.nx != c->nx || hd.ny != c->ny || hd.nz != c->nz)
     return fail(c, LBM_ERR_INVALID_ARG, "checkpoint does not match this context");
   o += sizeof hd;
   const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
@@ -1017,16 +1061,16 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
     CK(cudaMemcpyAsync(c->f_alt[s], o, c->Qf * P * c->elem, cudaMemcpyHostToDevice, c->stream));
     o += c->Qf * P * c->elem;
   }
-  for (int s = 0; s < c->p.n_scal; ++s) {
+  for (int s = 0; s < c->nlat; ++s) {
     CK(cudaMemcpyAsync(c->h_alt[s], o, c->Qc * P * c->elem, cudaMemcpyHostToDevice, c->stream));
     o += c->Qc * P * c->elem;
   }
   CK(cudaMemcpyAsync(c->a.flags, o, (N + 3) / 4 * 4, cudaMemcpyHostToDevice, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(c->a.acc, o, N * 8, cudaMemcpyHostToDevice, c->stream)); o += N * 8;
-  CK(cudaMemcpyAsync(c->a.wallx_slot, o, 2 * WALLX_SLOTS * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * WALLX_SLOTS * 8;
-  CK(cudaMemcpyAsync(c->a.inflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
-  CK(cudaMemcpyAsync(c->a.outflow_row, o, 2 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 2 * rows * 8;
-  CK(cudaMemcpyAsync(c->a.flip_mon, o, 64, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->a.wallx_slot, o, 3 * WALLX_SLOTS * 8, cudaMemcpyHostToDevice, c->stream)); o += 3 * WALLX_SLOTS * 8;
+  CK(cudaMemcpyAsync(c->a.inflow_row, o, 3 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 3 * rows * 8;
+  CK(cudaMemcpyAsync(c->a.outflow_row, o, 3 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 3 * rows * 8;
+  CK(cudaMemcpyAsync(c->a.flip_mon, o, 80, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
   lbm_status st = rebuild_geometry(c, false);
@@ -1250,6 +1294,7 @@ lbm_status lbm_ensemble_create(lbm_lattice lattice, int32_t n, const int32_t* di
     const char* why = nullptr;
     if (p.precision != p0.precision) why = "precision differs from member 0";
     else if (p.n_comp != p0.n_comp || p.n_scal != p0.n_scal) why = "n_comp / n_scal differ from member 0";
+    else if (p.product) why = "the reaction product lattice is not supported in ensembles";
     else if (p.collision != p0.collision) why = "collision differs from member 0";
     else if (p.device != p0.device || p.stream != p0.stream) why = "device / stream differ from member 0";
     else if (p.geo_mode != LBM_GEO_NONE) why = "ensemble members keep their geometry (geo_mode none)";

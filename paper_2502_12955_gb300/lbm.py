@@ -54,6 +54,7 @@ class LbmParams(C.Structure):
         ("device", C.c_int32), ("l2_fetch_bytes", C.c_int32), ("u_wall_ymax", C.c_double * 3),
         ("flow_open_x", C.c_int32), ("u_in", C.c_double), ("arrhenius", C.c_int32),
         ("arr_A", C.c_double), ("arr_Ta", C.c_double), ("heat_release", C.c_double), ("n_it", C.c_int32),
+        ("product", C.c_int32), ("tau_p", C.c_double), ("C_in_p", C.c_double),
     ]
 
 
@@ -65,7 +66,9 @@ class LbmMonitors(C.Structure):
         ("injected_species", C.c_double * 2), ("removed_mass", C.c_double * 2),
         ("removed_species", C.c_double * 2), ("deposited", C.c_double), ("n_solid", C.c_double),
         ("n_fluid", C.c_double), ("nonfinite", C.c_double), ("wall_exchange", C.c_double),
-        ("residual", C.c_double), ("heat", C.c_double),
+        ("residual", C.c_double), ("heat", C.c_double), ("species_p", C.c_double),
+        ("inflow_p", C.c_double), ("outflow_p", C.c_double), ("injected_species_p", C.c_double),
+        ("removed_species_p", C.c_double), ("produced", C.c_double),
     ]
 
 
@@ -204,6 +207,9 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     p.arr_Ta = float(d.get("arr_Ta", 0.0))
     p.heat_release = float(d.get("heat_release", 0.0))
     p.n_it = int(d.get("n_it", 16))
+    p.product = int(bool(d.get("product", False)))
+    p.tau_p = float(d.get("tau_p", 1.0))
+    p.C_in_p = float(d.get("C_in_p", 0.0))
     return p
 
 
@@ -214,7 +220,8 @@ def _dp(a):
 MON_KEYS = ["step", "mass0", "mass1", "momx", "momy", "momz", "species0", "species1", "reacted",
             "inflow0", "inflow1", "outflow0", "outflow1", "inj_mass0", "inj_mass1", "inj_spec0",
             "inj_spec1", "rem_mass0", "rem_mass1", "rem_spec0", "rem_spec1", "deposited", "nsolid",
-            "nfluid", "nonfinite", "wallx", "residual", "heat"]
+            "nfluid", "nonfinite", "wallx", "residual", "heat", "species_p", "inflow_p", "outflow_p",
+            "inj_spec_p", "rem_spec_p", "produced"]
 
 
 def save_fields(fields, path):
@@ -242,7 +249,8 @@ class Solver:
         self.p = make_params(cfg, self.lib)
         if stream is not None:
             self.p.stream = C.c_void_p(int(stream))
-        self.n_comp, self.n_scal = self.p.n_comp, self.p.n_scal
+        # scalar lattices: the given scalars, then the reaction product (if any)
+        self.n_comp, self.n_scal = self.p.n_comp, self.p.n_scal + self.p.product
         self._owner = _handle is None
         if _handle is not None:   # a member context owned by an Ensemble
             self.h = _handle
@@ -334,7 +342,8 @@ class Solver:
                 m.inflow[0], m.inflow[1], m.outflow[0], m.outflow[1], m.injected_mass[0],
                 m.injected_mass[1], m.injected_species[0], m.injected_species[1],
                 m.removed_mass[0], m.removed_mass[1], m.removed_species[0], m.removed_species[1],
-                m.deposited, m.n_solid, m.n_fluid, m.nonfinite, m.wall_exchange, m.residual, m.heat]
+                m.deposited, m.n_solid, m.n_fluid, m.nonfinite, m.wall_exchange, m.residual, m.heat,
+                m.species_p, m.inflow_p, m.outflow_p, m.injected_species_p, m.removed_species_p, m.produced]
         return dict(zip(MON_KEYS, vals))
 
     def residual(self):

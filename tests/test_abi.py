@@ -65,11 +65,12 @@ def _c_layout(tmp_path):
 #include <stddef.h>
 #include "lbm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, l2_fetch_bytes),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, l2_fetch_bytes),
          offsetof(lbm_params, u_wall_ymax), offsetof(lbm_params, u_in),
          offsetof(lbm_params, stream),
          offsetof(lbm_params, N_mon), offsetof(lbm_params, C_ref), sizeof(lbm_monitors),
-         offsetof(lbm_monitors, wall_exchange), offsetof(lbm_monitors, residual));
+         offsetof(lbm_monitors, wall_exchange), offsetof(lbm_monitors, residual),
+         offsetof(lbm_params, product), offsetof(lbm_params, C_in_p), offsetof(lbm_monitors, produced));
   return 0;
 }
 ''')
@@ -82,7 +83,7 @@ def test_ctypes_layout_matches_c(tmp_path):
     c = _c_layout(tmp_path)
     P, M = lbm.LbmParams, lbm.LbmMonitors
     assert c == [C.sizeof(P), P.l2_fetch_bytes.offset, P.u_wall_ymax.offset, P.u_in.offset, P.stream.offset, P.N_mon.offset, P.C_ref.offset, C.sizeof(M),
-                 M.wall_exchange.offset, M.residual.offset]
+                 M.wall_exchange.offset, M.residual.offset, P.product.offset, P.C_in_p.offset, M.produced.offset]
 
 
 def test_params_default():
@@ -98,6 +99,8 @@ def test_params_default():
     dict(tau=[0.5]), dict(n_comp=3), dict(n_scal=3), dict(collision="mrt", n_comp=2, tau=[1, 1]),
     dict(collision="mrt", forcing="sc_shift"), dict(N_geo=0), dict(block_x=48),
     dict(n_scal=1, tau_c=[0.4]), dict(geo_mode="dissolve", n_scal=0), dict(J0=1.0, n_scal=1),
+    dict(product=True, n_scal=0), dict(product=True, n_scal=1, tau_p=0.5),
+    dict(product=True, n_scal=1, geo_mode="deposit", DP=0.1),
     dict(l2_fetch_bytes=48), dict(u_wall_ymax=[0.01, 0, 0]), dict(u_wall_ymax=[0, 0.01, 0], periodic=[1, 0, 1]),
     dict(flow_open_x=True, u_in=0.01), dict(flow_open_x=True, periodic=[0, 1, 1]),
     dict(flow_open_x=True, periodic=[0, 0, 1], n_comp=2, tau=[1, 1]),
