@@ -138,6 +138,19 @@ typedef struct lbm_params {
                                  no deposition, one component when n_scal == 2; not in ensembles. */
   double tau_p;               /* relaxation time of the product lattice (> 0.5) */
   double C_in_p;              /* product value of the inlet ghost (with ade_open_x) */
+  int32_t conjugate;          /* 1 (with arrhenius): heat conduction in the solid on its own D3Q7 /
+                                 D2Q5 lattice, g_s,eq = w T_s (Sec. 2.1.5, Eq. therpop_solid,
+                                 macroreacb_solid), exchanged with the fluid temperature link by
+                                 link after each step (Eq. tempCon, fluxCon, reacRate): at a fluid-
+                                 solid link the two post-collision populations meet at
+                                 T_b = (c_fs ho + go + c_fs Qp / 2) / (w (c_fs + 1)) and each side
+                                 receives 2 w T_b minus what it sent; Qp = heat_release k(T_b) C_b
+                                 at a reactive link, whose k the next step's species closure uses.
+                                 Faces that are not periodic for the scalars reflect.  Row 1 of the
+                                 fields (set and get) is the solid temperature at solid nodes.  Not
+                                 with deposition, in ensembles or in checkpoints. */
+  double tau_s;               /* relaxation time of the solid thermal lattice (> 0.5) */
+  double c_fs;                /* heat-capacity ratio (rho c_p)_fluid / (rho c_p)_solid (> 0) */
 } lbm_params;
 
 /* Monitors, all FP64.  Cumulative entries count from the last lbm_set_fields. */
@@ -160,13 +173,18 @@ typedef struct lbm_monitors {
   double wall_exchange;       /* cumulative scalar-0 population loss through reactive links */
   double residual;            /* last automatic residual (-1 if none yet) */
   double heat;                /* cumulative temperature-population gain through reactive links
-                                 (arrhenius only) */
+                                 (arrhenius only; with conjugate, through every fluid-solid link) */
   double species_p;           /* product lattice (product only): sum of its stored populations */
   double inflow_p;            /* cumulative product entering through the inlet */
   double outflow_p;           /* cumulative product leaving through the outlet */
   double injected_species_p;  /* product added by dissolution flips */
   double removed_species_p;   /* always 0 (the product is not combined with deposition) */
   double produced;            /* cumulative product-population gain through reactive links */
+  double t_solid;             /* conjugate only: sum of the solid lattice's populations */
+  double heat_solid;          /* cumulative solid-population gain through fluid-solid links
+                                 (conjugate; heat holds the fluid side's gain there) */
+  double heat_source;         /* cumulative reaction heat put into the link exchanges (conjugate) */
+  double solid_removed;       /* cumulative solid populations taken by dissolution (conjugate) */
 } lbm_monitors;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -190,8 +208,9 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* flags, size_t n);
 
 /* Initialise populations at equilibrium (Eq. 6, Eq. therpopeq_species) from host FP64 fields:
    rho [n_comp][N], u [3][N] (2D: the z row is ignored), C [n_scal + product][N] (NULL when
-   n_scal == 0; the product's row last).  Solid nodes are ignored.  Resets the step counter and
-   all monitors. */
+   n_scal == 0; the product's row last).  Solid nodes are ignored, except with conjugate, where
+   row 1 at a solid node is its initial temperature (the solid lattice starts at rest
+   equilibrium).  Resets the step counter and all monitors. */
 lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* C,
                           size_t n);
 
@@ -207,7 +226,8 @@ lbm_status lbm_sync(lbm_ctx* ctx);
    rho [n_comp][N]; u [3][N], the physical velocity sum_sigma (j^sigma + F^sigma/2) / rho
    (Eq. 1.19); C [n_scal][N] with the wet-node closure applied; flags [N]; acc [N], the
    per-node consumed amount (reactive solids) or deposited fraction (deposition).  With the
-   reaction product, C has n_scal + 1 rows (the product last), as in lbm_set_fields. */
+   reaction product, C has n_scal + 1 rows (the product last), as in lbm_set_fields.  With
+   conjugate, row 1 at a solid node holds the solid temperature (Eq. macroreacb_solid). */
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, double* C, uint8_t* flags,
                           double* acc);
 

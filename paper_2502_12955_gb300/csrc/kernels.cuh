@@ -102,7 +102,7 @@ struct Args {
   uint32_t* slot_new;         // rebuild scratch
   unsigned int* block_counts; // ordered-compaction scratch [chunks + 1]
   unsigned int* block_counts_v;   // the same for the in-domain positions of the fluid-list order
-  double* wallx_slot;        // [WALLX_SLOTS] wall-exchange accumulators
+  double* wallx_slot;        // [NBANKS][WALLX_SLOTS] wall-exchange accumulators
   uint32_t* iface_list;       // reactive solids with a fluid scalar-lattice neighbour
   unsigned int* iface_count;
   uint8_t* listed;           // 1 once a node is in iface_list
@@ -110,7 +110,7 @@ struct Args {
   unsigned int* flip_count;
   unsigned int flip_cap;
   double* flip_scratch;      // [flip_cap][5]: new node's mean density (2) and scalars (3)
-  double* flip_mon;          // [10] inj_mass[2], inj_spec[3], rem_mass[2], rem_spec[3]
+  double* flip_mon;          // [11] inj_mass[2], inj_spec[3], rem_mass[2], rem_spec[3], solid_rem
   int* err;
   double* inflow_row;        // [3][rows]
   double* outflow_row;       // [3][rows]
@@ -144,6 +144,13 @@ struct Args {
   int arrhenius;             // scalar 1 is the temperature: rate k(T_b), reaction heat into T
   int n_it;                  // fixed-point iterations of the C_b - T_b coupling per link
   double arr_A, arr_Ta, heat_release;
+  // conduction in the solid (with arrhenius): the solid thermal lattice in two compute-type
+  // buffers [QC][N] by node (full values); step t reads gs[t & 1] and writes gs[(t + 1) & 1]
+  int conjugate;
+  double tau_s, c_fs;
+  void* gs[2];
+  void* kb;                  // compute-type [QC - 1][N]: k(T_b) of the link arriving in
+                             // direction j at node n from the last exchange; NaN before one
 };
 
 // Index guard of the bounds-checked build (-DLBM_BOUNDS_CHECK): an index outside [0, bound)
@@ -182,16 +189,21 @@ struct Coef {
   T arrA, arrTa;    // temperature-dependent rate A exp(-Ta / T)
   T fc, fT;         // tau / (tau - 1/2) of scalar 0 and of the temperature (scalar 1)
   T hr;             // reaction heat per unit rate
+  T oms;            // 1 / tau_s of the solid thermal lattice
+  T cfs;            // heat-capacity ratio (rho c_p)_f / (rho c_p)_s
 };
 
-constexpr int NMON = 22;
+constexpr int NMON = 25;
 constexpr int WALLX_SLOTS = 4096;
 // partial-sum slots
 enum : int {
   M_MASS = 0, M_MOM = 2, M_SPEC = 5, M_REACT = 7, M_DEPO = 8, M_IN = 9, M_OUT = 11,
   M_WALLX = 13, M_NSOLID = 14, M_NFLUID = 15, M_NONFIN = 16, M_HEAT = 17,
-  M_SPEC2 = 18, M_IN2 = 19, M_OUT2 = 20, M_PROD = 21   // the third scalar lattice; product gained
+  M_SPEC2 = 18, M_IN2 = 19, M_OUT2 = 20, M_PROD = 21,  // the third scalar lattice; product gained
+  M_TSOLID = 22, M_HEAT_S = 23, M_HEAT_SRC = 24         // conduction in the solid
 };
+// banks of the wall-exchange accumulators (WALLX_SLOTS doubles each)
+enum : int { BANK_WALLX = 0, BANK_HEAT = 1, BANK_PROD = 2, BANK_HEAT_S = 3, BANK_HEAT_SRC = 4, NBANKS = 5 };
 // monitor slots of scalar lattice s (0 .. 2)
 __host__ __device__ constexpr int mon_spec(int s) { return s < 2 ? M_SPEC + s : M_SPEC2; }
 __host__ __device__ constexpr int mon_in(int s) { return s < 2 ? M_IN + s : M_IN2; }
@@ -364,6 +376,45 @@ __device__ __forceinline__ void close_thermal(T* h0, T* h1, uint32_t m, const Co
       h0[j] = hn0;
       h1[j] = hn1;
       on_link(j, kt * Cb, old0[j] - hn0, hn1 - old1[j]);
+    }
+  }
+}
+
+// Species closure with conduction in the solid (Sec. 2.1.5, Eq. reactO2, reacRate): the wet-node
+// closure at each reactive link with the rate constant k(T_b) that the link's last exchange
+// (k_exchange) found together with C_b, kept in kb[(j - 1) N + n] for the link arriving in direction
+// j.  Before a link's first exchange (NaN entry) k is taken at the heat-capacity-weighted mean
+// c_fs T_f + T_s over c_fs + 1 of the node's own temperature T_f and the solid's T_s.  The
+// reaction heat entered the temperature through that exchange, so the temperature is not closed
+// here.  h0 and h1 hold deviations from w cref; gsrc is the solid lattice the step reads.
+template <class L, class T, class OnLink>
+__device__ __forceinline__ void close_conjugate(T* h0, const T* h1, uint32_t m, const Coef<T>& k, const Args& a,
+                                                const Nbr& nb, const T* gsrc, OnLink on_link) {
+  T old[L::QC];
+#pragma unroll
+  for (int j = 0; j < L::QC; ++j) old[j] = h0[j];
+  const T sh0 = k.wca * k.cref[0];
+  const T w2 = T(2) * k.wca;
+  const T* kb = reinterpret_cast<const T*>(a.kb);
+#pragma unroll
+  for (int j = 1; j < L::QC; ++j) {
+    if (MaskBits<L>::code(m, L::opp(j)) == 2u) {
+      T kt = kb[(long long)(j - 1) * a.N + nb.n];
+      if (!(kt >= T(0))) {
+        const int src = nb.at(-L::cx(j), -L::cy(j), -L::cz(j));
+        T Tf = k.cref[1], Ts = T(0);
+#pragma unroll
+        for (int q = 0; q < L::QC; ++q) {
+          Tf += h1[q];
+          Ts += gsrc[(long long)q * a.N + src];
+        }
+        kt = k.arrA * exp(-k.arrTa / ((k.cfs * Tf + Ts) / (k.cfs + T(1))));
+      }
+      const T hb = old[L::opp(j)] + sh0;
+      const T Cb = T(2) * hb / (w2 + kt * k.fc);
+      const T hn = w2 * Cb - hb - sh0;
+      h0[j] = hn;
+      on_link(j, kt * Cb, old[j] - hn);
     }
   }
 }
@@ -723,7 +774,16 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
     T rl[QC];
 #pragma unroll
     for (int j = 0; j < QC; ++j) rl[j] = T(0);
-    if (BND && NS > 1 && a.arrhenius) {
+    if (BND && NS > 1 && a.conjugate) {
+      // conduction in the solid: the rate constant of the link's last exchange
+      close_conjugate<L, T>(h[0], h[NS > 1 ? 1 : 0], m, k, a, nb,
+                            reinterpret_cast<const T*>(a.gs[parity]), [&](int j, T r, T exch) {
+        const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
+        atomicAdd(a.acc + src, widen(r));
+        wallx += exch;
+        rl[j] = r;
+      });
+    } else if (BND && NS > 1 && a.arrhenius) {
       // temperature-dependent rate and reaction heat (the full kernel variant only)
       close_thermal<L, T>(h[0], h[NS > 1 ? 1 : 0], m, k, a.n_it, [&](int j, T r, T exch, T heat) {
         const int src = LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N);
@@ -1295,29 +1355,43 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 
 // ================================================================ psi
 
-template <class L, class S, int NC>
-__global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename Store<S>::T> k,
-                                             const int parity) {
+template <class L, class S, int NC, int parity>
+__global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename Store<S>::T> k) {
+  // Walks the fluid list in slot order, as k_step does: at parity 0 every population of the
+  // node sits in its own cell (coalesced); at parity 1 population i sits in cell (n - c_i, opp i),
+  // whose slot is looked up once for all components.  Sums in population order 0 .. Q-1 from
+  // rho_ref, the order the gather of the step uses.
   using T = typename Store<S>::T;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= a.nx || y >= a.ny) return;
-  const int n = x + a.nx * (y + a.ny * z);
-  const uint32_t m = a.mask[n];
-  if (!(m & 1u)) return;
-  const Nbr nb = make_nbr(a, x, y, z);
+  const unsigned int count = a.fluid_count[0];
+  const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride) {
+    const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
+    const uint32_t m = a.mask[n];
+    if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
+    const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+    long long cell[L::Q];   // slot of the cell holding population i
+    const Nbr nb = parity ? nbr_of(a, n) : Nbr{};
 #pragma unroll
-  for (int s = 0; s < NC; ++s) {
-    T f[L::Q];
-    gather_flow<L, S>(reinterpret_cast<const S*>(a.f[s]), a.pitch, a.slot[n], a.slot, m, nb, parity, f);
-    T r = k.rref[s];
+    for (int i = 0; i < L::Q; ++i)
+      cell[i] = (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
+                    ? sn
+                    : (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(i), -L::cy(i), -L::cz(i)), a.N));
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) r += f[i];
-    T p;
-    if (a.psi_identity) p = r;
-    else p = k.rho0 * (T(1) - exp(-r / k.rho0));   // Eq. 1.11
-    reinterpret_cast<T*>(a.psi[s])[n] = p;
+    for (int s = 0; s < NC; ++s) {
+      T r = k.rref[s];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        // the own cell in plane i, a neighbour's in plane opp(i)
+        const bool own = parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i));
+        const S* p = reinterpret_cast<const S*>(own ? a.fplane[s][i] : a.fplane[s][L::opp(i)]);
+        r += Store<S>::ld(p + LBM_CHK(a.err, cell[i], a.pitch));
+      }
+      T p;
+      if (a.psi_identity) p = r;
+      else p = k.rho0 * (T(1) - exp(-r / k.rho0));   // Eq. 1.11
+      reinterpret_cast<T*>(a.psi[s])[n] = p;
+    }
   }
 }
 
@@ -1407,7 +1481,8 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
   v[M_NONFIN] = double(nonfin);
   // bookkeeping over every node
   const bool dep = a.geo_mode == GEO_DEPOSIT;
-  double react = 0.0, depo = 0.0, nsolid = 0.0;
+  double react = 0.0, depo = 0.0, nsolid = 0.0, tsolid = 0.0;
+  const T* gcur = a.conjugate ? reinterpret_cast<const T*>(a.gs[parity]) : nullptr;
   for (long long n = tid; n < a.N; n += nthr) {
     const uint8_t fl = a.flags[n];
     nsolid += fl != FL_FLUID ? 1.0 : 0.0;
@@ -1415,10 +1490,17 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
     if (acc != 0.0) {
       if (dep && fl != FL_REACTIVE) depo += acc; else react += acc;
     }
+    if (gcur && fl != FL_FLUID) {
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < QC; ++q) t += gcur[(long long)q * a.N + n];
+      tsolid += double(t);
+    }
   }
   v[M_REACT] = react;
   v[M_DEPO] = depo;
   v[M_NSOLID] = nsolid;
+  v[M_TSOLID] = tsolid;
   const int rows = a.ny * a.nz;
   for (int r = tid; r < rows; r += nthr)
     for (int s = 0; s < NS; ++s) {
@@ -1426,9 +1508,11 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
       v[mon_out(s)] += a.outflow_row[s * rows + r];
     }
   for (int q = tid; q < WALLX_SLOTS; q += nthr) {
-    v[M_WALLX] += a.wallx_slot[q];
-    v[M_HEAT] += a.wallx_slot[WALLX_SLOTS + q];
-    v[M_PROD] += a.wallx_slot[2 * WALLX_SLOTS + q];
+    v[M_WALLX] += a.wallx_slot[BANK_WALLX * WALLX_SLOTS + q];
+    v[M_HEAT] += a.wallx_slot[BANK_HEAT * WALLX_SLOTS + q];
+    v[M_PROD] += a.wallx_slot[BANK_PROD * WALLX_SLOTS + q];
+    v[M_HEAT_S] += a.wallx_slot[BANK_HEAT_S * WALLX_SLOTS + q];
+    v[M_HEAT_SRC] += a.wallx_slot[BANK_HEAT_SRC * WALLX_SLOTS + q];
   }
   block_reduce_store<NMON>(v, a.partials + (long long)blockIdx.x * NMON);
 }
@@ -1511,7 +1595,10 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
   T rl[QC], gain = T(0);
 #pragma unroll
   for (int j = 0; j < QC; ++j) rl[j] = T(0);
-  if (NS > 1 && a.arrhenius)
+  if (NS > 1 && a.conjugate)
+    close_conjugate<L, T>(hh[0], hh[NS > 1 ? 1 : 0], m, k, a, nb, reinterpret_cast<const T*>(a.gs[parity]),
+                          [&](int j, T r, T) { rl[j] = r; });
+  else if (NS > 1 && a.arrhenius)
     close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], m, k, a.n_it, [&](int j, T r, T, T) { rl[j] = r; });
   else if (NS > 0)
     close_scalar<L, T>(hh[0], m, k, [&](int j, T Cb, T) { rl[j] = k.kr * Cb; });
@@ -1541,6 +1628,14 @@ __global__ void __launch_bounds__(256) k_moments(const Args a, const Coef<typena
     for (int s = 0; s < NC; ++s) rho[s] = T(0);
     u[0] = u[1] = u[2] = T(0);
     for (int s = 0; s < NS; ++s) C[s] = T(0);
+    if (NS > 1 && a.conjugate) {
+      // the solid temperature (Eq. macroreacb_solid)
+      const T* g = reinterpret_cast<const T*>(a.gs[parity]);
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < L::QC; ++q) t += g[(long long)q * N + n];
+      C[NS > 1 ? 1 : 0] = t;
+    }
   }
   for (int s = 0; s < NC; ++s) a.d_rho[s * N + n] = double(rho[s]);
   for (int c = 0; c < 3; ++c) a.d_u[c * N + n] = double(u[c]);
@@ -1956,9 +2051,9 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
   const long long P = a.pitch;
   const bool dissolve = a.geo_mode == GEO_DISSOLVE;
   // flip monitors: injected mass [0, 2), injected scalars [2, 5), removed mass [5, 7), removed
-  // scalars [7, 10)
-  __shared__ double sred[10];
-  if (threadIdx.x < 10) sred[threadIdx.x] = 0.0;
+  // scalars [7, 10), solid temperature taken from the solid lattice [10]
+  __shared__ double sred[11];
+  if (threadIdx.x < 11) sred[threadIdx.x] = 0.0;
   // ---- phase 0: claim
   for (unsigned int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const long long s = a.flip_list[e];
@@ -2001,7 +2096,10 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
           gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, hh[c]);
         T rl[QC], gain = T(0);
         for (int j = 0; j < QC; ++j) rl[j] = T(0);
-        if (NS > 1 && a.arrhenius)
+        if (NS > 1 && a.conjugate)
+          close_conjugate<L, T>(hh[0], hh[NS > 1 ? 1 : 0], mq, k, a, nq,
+                                reinterpret_cast<const T*>(a.gs[parity_next]), [&](int j, T r, T) { rl[j] = r; });
+        else if (NS > 1 && a.arrhenius)
           close_thermal<L, T>(hh[0], hh[NS > 1 ? 1 : 0], mq, k, a.n_it, [&](int j, T r, T, T) { rl[j] = r; });
         else if (NS > 0)
           close_scalar<L, T>(hh[0], mq, k, [&](int j, T Cb, T) { rl[j] = k.kr * Cb; });
@@ -2075,7 +2173,18 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
       }
       for (int c = 0; c < NS; ++c) {
         S* hs = reinterpret_cast<S*>(a.h[c]);
-        const double C = sc4[2 + c];
+        double C = sc4[2 + c];
+        if (c == 1 && a.conjugate) {
+          // with conduction in the solid the new fluid node keeps its own temperature: its solid
+          // populations leave the solid lattice
+          T* g = reinterpret_cast<T*>(a.gs[parity_next]);
+          C = 0.0;
+          for (int q = 0; q < QC; ++q) {
+            C += double(g[(long long)q * a.N + s]);
+            g[(long long)q * a.N + s] = T(0);
+          }
+          atomicAdd(&sred[10], C);
+        }
         atomicAdd(&sred[2 + c], C);
         for (int j = 0; j < QC; ++j) {
           const double wj = double(scal_w<T>(j, k));
@@ -2154,8 +2263,166 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
     }
   }
   __syncthreads();
-  if (threadIdx.x < 10 && sred[threadIdx.x] != 0.0) atomicAdd(a.flip_mon + threadIdx.x, sred[threadIdx.x]);
+  if (threadIdx.x < 11 && sred[threadIdx.x] != 0.0) atomicAdd(a.flip_mon + threadIdx.x, sred[threadIdx.x]);
   if (threadIdx.x == 0) *a.flip_count = 0u;
+}
+
+// ================================================================ conduction in the solid
+
+// Solid thermal lattice (Sec. 2.1.5, Eq. therpop_solid with g_s^eq = w T_s, Eq. macroreacb_solid):
+// collision and streaming of every solid node, from gs[parity] into gs[parity ^ 1] (node-indexed
+// planes, full values).  A population leaving toward another solid node streams there; one
+// leaving toward a fluid node or through a face that is not periodic for the scalars is kept at
+// the node as the arriving population of the opposite direction: at a closed face that is the
+// reflection, at a fluid neighbour it is the solid side of the link that k_exchange replaces.
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_solid(const Args a, const Coef<typename Store<S>::T> k,
+                                               const int parity) {
+  using T = typename Store<S>::T;
+  constexpr int QC = L::QC;
+  const T* gin = reinterpret_cast<const T*>(a.gs[parity]);
+  T* gout = reinterpret_cast<T*>(a.gs[parity ^ 1]);
+  const int perc[3] = {a.open_x ? 0 : a.per[0], a.per[1], a.per[2]};
+  const long long N = a.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    if (a.flags[n] == FL_FLUID) continue;
+    T g[QC];
+    T Ts = T(0);
+#pragma unroll
+    for (int q = 0; q < QC; ++q) {
+      g[q] = gin[(long long)q * N + n];
+      Ts += g[q];
+    }
+    int x, y, z, ax;
+    coords_of(a, n, &x, &y, &z);
+#pragma unroll
+    for (int q = 0; q < QC; ++q) {
+      const T v = g[q] - (g[q] - scal_w<T>(q, k) * Ts) * k.oms;
+      if (q == 0) {
+        gout[n] = v;
+        continue;
+      }
+      const long long d = nbr_checked(a, x, y, z, L::cx(q), L::cy(q), L::cz(q), perc, &ax);
+      if (d >= 0 && a.flags[d] != FL_FLUID) gout[(long long)q * N + d] = v;
+      else gout[(long long)L::opp(q) * N + n] = v;
+    }
+  }
+}
+
+// The exchange across every solid link of the temperature (Sec. 2.1.5, Eq. tempCon, fluxCon,
+// reacRate), after the fluid step and the solid lattice's streaming.  For fluid node n and a
+// direction j toward a solid node s = n + c_j (arriving direction i = opp(j)): the fluid
+// population ho = h*_T,j that left n toward s (kept at n by the bounce-back of the step, in plane
+// i) and the solid population go = g*_s,i that left s toward n (kept at s in plane j by k_solid)
+// meet at one interface temperature T_b.  Each side receives 2 w T_b minus what it sent, and the
+// link's energy in units of the fluid's rho c_p grows by the reaction heat Qp:
+//     T_b = (c_fs ho + go + c_fs Qp / 2) / (w (c_fs + 1)).
+// Qp = h_r k(T_b) C_b at a reactive link, where C_b = 2 hb / (2 w + k tau_c / (tau_c - 1/2)) closes
+// the species population hb = h_C,j that has just streamed into n (read as the next step's
+// gather reads it); T_b and C_b come from n_it + 1 fixed-point updates starting at the value
+// without reaction, and k is kept for the next step's species closure.  Monitors: heat gained by
+// the fluid side (bank HEAT), by the solid side (HEAT_S), reaction heat (HEAT_SRC).
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_exchange(const Args a, const Coef<typename Store<S>::T> k,
+                                                  const int parity_next) {
+  using T = typename Store<S>::T;
+  constexpr int QC = L::QC;
+  T* g = reinterpret_cast<T*>(a.gs[parity_next]);
+  T* kb = reinterpret_cast<T*>(a.kb);
+  const int perc[3] = {a.open_x ? 0 : a.per[0], a.per[1], a.per[2]};
+  const T sh0 = k.wca * k.cref[0], sh1 = k.wca * k.cref[1];
+  const T w = k.wca, cf = k.cfs;
+  const T den = w * (cf + T(1));
+  T heat = T(0), heat_s = T(0), src_q = T(0);
+  const unsigned int count = a.fluid_count[0], base = a.fluid_count[1];
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
+    const uint32_t m = a.mask[n];
+    if (!(m & 1u)) continue;
+    bool any = false;
+#pragma unroll
+    for (int j = 1; j < QC; ++j) {
+      const uint32_t c = MaskBits<L>::code(m, j);
+      any |= (c == 1u || c == 2u);
+    }
+    if (!any) continue;
+    const long long sn = e < base ? (long long)e : (long long)a.slot[n];
+    int x, y, z, ax;
+    coords_of(a, n, &x, &y, &z);
+    const Nbr nb = make_nbr(a, x, y, z);
+#pragma unroll
+    for (int j = 1; j < QC; ++j) {
+      const uint32_t c = MaskBits<L>::code(m, j);
+      if (c != 1u && c != 2u) continue;
+      const long long s = nbr_checked(a, x, y, z, L::cx(j), L::cy(j), L::cz(j), perc, &ax);
+      if (s < 0) continue;   // a closed face: plain bounce-back
+      const int i = L::opp(j);
+      S* hp = reinterpret_cast<S*>(a.hplane[1][i]) + LBM_CHK(a.err, sn, a.pitch);
+      T* gp = g + (long long)j * a.N + s;
+      const T ho = Store<S>::ld(hp) + sh1;
+      const T go = *gp;
+      T Tb = (cf * ho + go) / den;
+      T Qp = T(0);
+      if (c == 2u) {
+        // the species population moving toward the wall, where the next step gathers it
+        const S* bp;
+        if (parity_next == 0 || MaskBits<L>::code(m, i) != 0u)
+          bp = reinterpret_cast<const S*>(a.hplane[0][j]) + LBM_CHK(a.err, sn, a.pitch);
+        else
+          bp = reinterpret_cast<const S*>(a.hplane[0][i]) +
+               LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N)),
+                       a.pitch);
+        const T hb = Store<S>::ld(bp) + sh0;
+        T kt = T(0);
+        for (int it = 0; it <= a.n_it; ++it) {
+          kt = k.arrA * exp(-k.arrTa / Tb);
+          const T Cb = T(2) * hb / (T(2) * w + kt * k.fc);
+          Qp = k.hr * kt * Cb;
+          Tb = (cf * ho + go + T(0.5) * cf * Qp) / den;
+        }
+        kb[(long long)(i - 1) * a.N + n] = kt;
+      }
+      const T hn = T(2) * w * Tb - ho;
+      const T gn = T(2) * w * Tb - go;
+      Store<S>::st(hp, hn - sh1);
+      *gp = gn;
+      heat += hn - ho;
+      heat_s += gn - go;
+      src_q += Qp;
+    }
+  }
+  const int lane_slot = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % WALLX_SLOTS;
+  const T vals[3] = {heat, heat_s, src_q};
+  const int banks[3] = {BANK_HEAT, BANK_HEAT_S, BANK_HEAT_SRC};
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (__ballot_sync(0xffffffffu, vals[b] != T(0))) {
+      const T v = warp_sum(vals[b]);
+      if ((threadIdx.x & 31) == 0) atomicAdd(a.wallx_slot + banks[b] * WALLX_SLOTS + lane_slot, widen(v));
+    }
+  }
+}
+
+// The solid thermal lattice at rest equilibrium with the temperature given for each solid node
+// (row 1 of the staged scalar fields): g_q = w_q T into gs[0]; gs[1] and the exchange's rate
+// constants cleared (NaN: no exchange yet).
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_solid_init(const Args a, const Coef<typename Store<S>::T> k) {
+  using T = typename Store<S>::T;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  T* g0 = reinterpret_cast<T*>(a.gs[0]);
+  T* g1 = reinterpret_cast<T*>(a.gs[1]);
+  T* kb = reinterpret_cast<T*>(a.kb);
+  const bool solid = a.flags[n] != FL_FLUID;
+  const double Tn = a.d_C[a.N + n];
+#pragma unroll
+  for (int q = 0; q < L::QC; ++q) {
+    g0[(long long)q * a.N + n] = solid ? T(double(scal_w<T>(q, k)) * Tn) : T(0);
+    g1[(long long)q * a.N + n] = T(0);
+    if (q > 0) kb[(long long)(q - 1) * a.N + n] = T(NAN);
+  }
 }
 
 }  // namespace lbm

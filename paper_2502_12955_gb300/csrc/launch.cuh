@@ -20,6 +20,11 @@ struct KernelSet {
   cudaError_t (*masks)(const Args&, cudaStream_t);
   cudaError_t (*lists)(const Args&, int which, cudaStream_t);   // which: 1 fluid, 2 interface, 3 both
   cudaError_t (*resid)(const Args&, int parity, cudaStream_t, long long* nblocks);
+  // conduction in the solid: the solid lattice's step, the link exchange after the fluid step
+  // (parity of the next step), and the solid's initial state from the staged fields
+  cudaError_t (*solid)(const Args&, int parity, cudaStream_t);
+  cudaError_t (*exchange)(const Args&, int parity_next, cudaStream_t);
+  cudaError_t (*solid_init)(const Args&, cudaStream_t);
   // ensembles: compute-type constants of n members into host memory (coef_bytes each), and one
   // step of every tile
   void (*coefs)(const Args* a, int n, void* out);
@@ -91,6 +96,8 @@ Coef<T> make_coef(const Args& a, bool shifted) {
   k.arrA = T(a.arr_A);
   k.arrTa = T(a.arr_Ta);
   k.hr = T(a.heat_release);
+  k.oms = T(a.conjugate ? 1.0 / a.tau_s : 1.0);
+  k.cfs = T(a.c_fs);
   k.fc = T(a.tau_c[0] / (a.tau_c[0] - 0.5));
   k.fT = T(a.tau_c[1] / (a.tau_c[1] - 0.5));
   return k;
@@ -160,11 +167,25 @@ struct Launchers {
     return a.n_comp == 1 ? step_s<1>(a, parity, coll, st) : step_s<2>(a, parity, coll, st);
   }
 
-  static cudaError_t psi(const Args& a, int parity, cudaStream_t st) {
-    const dim3 blk(128, 1, 1);
-    if (a.n_comp == 1) k_psi<L, S, 1><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
-    else k_psi<L, S, 2><<<node_grid(a, blk), blk, 0, st>>>(a, coef(a), parity);
+  // psi pass: resident waves of 256-thread blocks over the fluid list (grid-stride)
+  template <int NC, int PAR>
+  static cudaError_t psi_p(const Args& a, cudaStream_t st) {
+    static int cached_blocks = 0;
+    if (!cached_blocks) {
+      int dev = 0, sms = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_psi<L, S, NC, PAR>, 256, 0);
+      cached_blocks = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
+    }
+    const long long need = (a.N + 255) / 256;
+    const unsigned int blocks = (unsigned int)(need < cached_blocks ? need : cached_blocks);
+    k_psi<L, S, NC, PAR><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(a, coef(a));
     return cudaGetLastError();
+  }
+  static cudaError_t psi(const Args& a, int parity, cudaStream_t st) {
+    if (a.n_comp == 1) return parity ? psi_p<1, 1>(a, st) : psi_p<1, 0>(a, st);
+    return parity ? psi_p<2, 1>(a, st) : psi_p<2, 0>(a, st);
   }
 
   template <class F>
@@ -229,6 +250,20 @@ struct Launchers {
     by_nc_ns(a, [&](auto nc, auto ns) {
       k_flip<L, S, decltype(nc)::value, decltype(ns)::value><<<1, 1024, 0, st>>>(a, coef(a), parity_next);
     });
+    return cudaGetLastError();
+  }
+
+  static cudaError_t solid(const Args& a, int parity, cudaStream_t st) {
+    k_solid<L, S><<<wave_blocks() * 2, 256, 0, st>>>(a, coef(a), parity);
+    return cudaGetLastError();
+  }
+  static cudaError_t exchange(const Args& a, int parity_next, cudaStream_t st) {
+    k_exchange<L, S><<<wave_blocks() * 2, 256, 0, st>>>(a, coef(a), parity_next);
+    return cudaGetLastError();
+  }
+  static cudaError_t solid_init(const Args& a, cudaStream_t st) {
+    const unsigned int nb = (unsigned int)((a.N + 255) / 256);
+    k_solid_init<L, S><<<nb, 256, 0, st>>>(a, coef(a));
     return cudaGetLastError();
   }
 
@@ -319,6 +354,9 @@ struct Launchers {
     k.masks = &masks;
     k.lists = &lists;
     k.resid = &resid;
+    k.solid = &solid;
+    k.exchange = &exchange;
+    k.solid_init = &solid_init;
     k.psi_bytes = (int)sizeof(typename Store<S>::T);
     return k;
   }

@@ -41,7 +41,7 @@ struct lbm_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
   std::string err;
   std::vector<void*> allocs;
-  double* mon_host = nullptr;      // pinned [NMON + 12]: monitors, then the 10 flip monitors
+  double* mon_host = nullptr;      // pinned [NMON + 12]: monitors, then the 11 flip monitors
   void* f_alt[2] = {nullptr, nullptr};   // second population buffers: targets of re-slotting
   void* h_alt[3] = {nullptr, nullptr, nullptr};
   int nlat = 0;                    // scalar lattices: the given scalars, then the product if any
@@ -168,6 +168,14 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
     if (p->n_comp != 1 || p->G[0][0] != 0.0 || p->G_ads[0] != 0.0 || p->rho_solid != 0.0)
       return fail(c, LBM_ERR_INVALID_ARG, "a velocity inlet needs one component without Shan-Chen forces");
   }
+  if (p->conjugate != 0 && p->conjugate != 1) return fail(c, LBM_ERR_INVALID_ARG, "conjugate must be 0 or 1");
+  if (p->conjugate) {
+    if (!p->arrhenius)
+      return fail(c, LBM_ERR_INVALID_ARG, "conduction in the solid couples to the temperature of the temperature-dependent rate (arrhenius)");
+    if (!(p->tau_s > 0.5)) return fail(c, LBM_ERR_INVALID_ARG, "tau_s = %g must exceed 0.5", p->tau_s);
+    if (!(p->c_fs > 0.0)) return fail(c, LBM_ERR_INVALID_ARG, "c_fs = %g must be positive", p->c_fs);
+    if (p->geo_mode == LBM_GEO_DEPOSIT) return fail(c, LBM_ERR_INVALID_ARG, "conduction in the solid is not combined with deposition");
+  }
   if (p->product != 0 && p->product != 1) return fail(c, LBM_ERR_INVALID_ARG, "product must be 0 or 1");
   if (p->product) {
     if (p->n_scal < 1) return fail(c, LBM_ERR_INVALID_ARG, "the reaction product needs the reacting scalar (n_scal >= 1)");
@@ -266,6 +274,9 @@ void fill_args(lbm_ctx* c) {
   a.arr_A = p.arr_A;
   a.arr_Ta = p.arr_Ta;
   a.heat_release = p.heat_release;
+  a.conjugate = p.conjugate ? 1 : 0;
+  a.tau_s = p.tau_s;
+  a.c_fs = p.c_fs;
 }
 
 int parity_of(long long step) { return int(step & 1); }
@@ -503,6 +514,9 @@ lbm_status lbm_params_default(lbm_params* p) {
   p->rho_ref[0] = p->rho_ref[1] = 1.0;
   p->l2_fetch_bytes = 0;
   p->n_it = 16;
+  p->tau_p = 1.0;
+  p->tau_s = 1.0;
+  p->c_fs = 1.0;
   return LBM_OK;
 }
 
@@ -578,7 +592,12 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     DA(a.block_counts, ((pos + 1023) / 1024 + 1) * 4);
     DA(a.block_counts_v, ((pos + 1023) / 1024 + 1) * 4);
   }
-  DA(a.wallx_slot, 3 * WALLX_SLOTS * 8);
+  DA(a.wallx_slot, NBANKS * WALLX_SLOTS * 8);
+  if (params->conjugate) {
+    // the solid thermal lattice (two node-indexed copies) and the exchange's rate constants
+    for (int b = 0; b < 2; ++b) DA(a.gs[b], N * c->Qc * c->ks->psi_bytes);
+    DA(a.kb, N * (c->Qc - 1) * c->ks->psi_bytes);
+  }
   DA(a.u_in_row, ny * 8);
   DA(a.iface_list, N * 4);
   DA(a.iface_count, 16);
@@ -586,7 +605,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   DA(a.flip_list, (size_t)cap * 4);
   DA(a.flip_count, 16);
   DA(a.flip_scratch, (size_t)cap * 5 * 8);
-  DA(a.flip_mon, 10 * 8);
+  DA(a.flip_mon, 11 * 8);
   DA(a.err, 16);
   DA(a.inflow_row, 3 * rows * 8);
   DA(a.outflow_row, 3 * rows * 8);
@@ -607,9 +626,9 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.iface_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.listed, 0, (N + 3) / 4 * 4, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 80, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.flip_mon, 0, 88, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 16, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, 3 * WALLX_SLOTS * 8, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.wallx_slot, 0, NBANKS * WALLX_SLOTS * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.fluid_count, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.inflow_row, 0, 3 * rows * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 3 * rows * 8, c->stream);
@@ -658,11 +677,12 @@ lbm_status lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, const 
   if (ud == 2) CK(cudaMemsetAsync(c->a.d_u + 2 * N, 0, N * 8, c->stream));
   if (c->nlat > 0) CK(cudaMemcpyAsync(c->a.d_C, C, c->nlat * N * 8, cudaMemcpyHostToDevice, c->stream));
   LAUNCH(c->ks->init(c->a, c->stream));
+  if (c->p.conjugate) LAUNCH(c->ks->solid_init(c->a, c->stream));
   const long long rows = (long long)c->ny * c->nz;
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
-  CK(cudaMemsetAsync(c->a.flip_mon, 0, 80, c->stream));
+  CK(cudaMemsetAsync(c->a.flip_mon, 0, 88, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
-  CK(cudaMemsetAsync(c->a.wallx_slot, 0, 3 * WALLX_SLOTS * 8, c->stream));
+  CK(cudaMemsetAsync(c->a.wallx_slot, 0, NBANKS * WALLX_SLOTS * 8, c->stream));
   CK(cudaMemsetAsync(c->a.inflow_row, 0, 3 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.outflow_row, 0, 3 * rows * 8, c->stream));
   CK(cudaMemsetAsync(c->a.acc, 0, c->N * 8, c->stream));
@@ -701,6 +721,11 @@ lbm_status enqueue_step(lbm_ctx* c, long long step, cudaStream_t st, bool timed)
   // the psi pass (Shan-Chen forces) is part of the timed step: it reads every population too
   if (c->a.sc_on) LAUNCH(c->ks->psi(c->a, par, st));
   LAUNCH(c->ks->step(c->a, par, c->p.collision, st));
+  if (c->p.conjugate) {
+    // conduction in the solid: the solid lattice's step, then the exchange across its links
+    LAUNCH(c->ks->solid(c->a, par, st));
+    LAUNCH(c->ks->exchange(c->a, par ^ 1, st));
+  }
   if (timed) {
     CK(cudaEventRecord(e1, st));
     c->ev_used.push_back({e0, e1});
@@ -918,7 +943,7 @@ lbm_status lbm_get_monitors(lbm_ctx* c, lbm_monitors* out) {
   if (st != LBM_OK) return st;
   double* hm = c->mon_host;
   CK(cudaMemcpyAsync(hm, c->a.mon_out, NMON * 8, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(hm + NMON, c->a.flip_mon, 10 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hm + NMON, c->a.flip_mon, 11 * 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   std::memset(out, 0, sizeof(*out));
   out->step = double(c->step);
@@ -959,6 +984,12 @@ lbm_status lbm_get_monitors(lbm_ctx* c, lbm_monitors* out) {
   }
   out->wall_exchange = hm[M_WALLX];
   out->heat = hm[M_HEAT];
+  if (c->p.conjugate) {
+    out->t_solid = hm[M_TSOLID];
+    out->heat_solid = hm[M_HEAT_S];
+    out->heat_source = hm[M_HEAT_SRC];
+    out->solid_removed = hm[NMON + 10];
+  }
   out->n_solid = hm[M_NSOLID];
   out->n_fluid = hm[M_NFLUID];
   out->nonfinite = hm[M_NONFIN];
@@ -1004,6 +1035,7 @@ size_t state_bytes(const lbm_ctx* c) {
 
 lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   if (!c || !nbytes) return LBM_ERR_INVALID_ARG;
+  if (c->p.conjugate) return fail(c, LBM_ERR_INVALID_ARG, "checkpoints do not hold the solid thermal lattice (conjugate)");
   const size_t need = state_bytes(c);
   if (!host) {
     *nbytes = need;
@@ -1045,6 +1077,7 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
 
 lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   if (!c || !host) return LBM_ERR_INVALID_ARG;
+  if (c->p.conjugate) return fail(c, LBM_ERR_INVALID_ARG, "checkpoints do not hold the solid thermal lattice (conjugate)");
   const size_t need = state_bytes(c);
   if (nbytes != need) return fail(c, LBM_ERR_INVALID_ARG, "state has %zu bytes, expected %zu", nbytes, need);
   const uint8_t* o = static_cast<const uint8_t*>(host);
@@ -1295,6 +1328,7 @@ lbm_status lbm_ensemble_create(lbm_lattice lattice, int32_t n, const int32_t* di
     if (p.precision != p0.precision) why = "precision differs from member 0";
     else if (p.n_comp != p0.n_comp || p.n_scal != p0.n_scal) why = "n_comp / n_scal differ from member 0";
     else if (p.product) why = "the reaction product lattice is not supported in ensembles";
+    else if (p.conjugate) why = "conduction in the solid is not supported in ensembles";
     else if (p.collision != p0.collision) why = "collision differs from member 0";
     else if (p.device != p0.device || p.stream != p0.stream) why = "device / stream differ from member 0";
     else if (p.geo_mode != LBM_GEO_NONE) why = "ensemble members keep their geometry (geo_mode none)";

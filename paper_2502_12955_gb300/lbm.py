@@ -55,6 +55,7 @@ class LbmParams(C.Structure):
         ("flow_open_x", C.c_int32), ("u_in", C.c_double), ("arrhenius", C.c_int32),
         ("arr_A", C.c_double), ("arr_Ta", C.c_double), ("heat_release", C.c_double), ("n_it", C.c_int32),
         ("product", C.c_int32), ("tau_p", C.c_double), ("C_in_p", C.c_double),
+        ("conjugate", C.c_int32), ("tau_s", C.c_double), ("c_fs", C.c_double),
     ]
 
 
@@ -69,6 +70,8 @@ class LbmMonitors(C.Structure):
         ("residual", C.c_double), ("heat", C.c_double), ("species_p", C.c_double),
         ("inflow_p", C.c_double), ("outflow_p", C.c_double), ("injected_species_p", C.c_double),
         ("removed_species_p", C.c_double), ("produced", C.c_double),
+        ("t_solid", C.c_double), ("heat_solid", C.c_double), ("heat_source", C.c_double),
+        ("solid_removed", C.c_double),
     ]
 
 
@@ -210,6 +213,9 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     p.product = int(bool(d.get("product", False)))
     p.tau_p = float(d.get("tau_p", 1.0))
     p.C_in_p = float(d.get("C_in_p", 0.0))
+    p.conjugate = int(bool(d.get("conjugate", False)))
+    p.tau_s = float(d.get("tau_s", 1.0))
+    p.c_fs = float(d.get("c_fs", 1.0))
     return p
 
 
@@ -221,7 +227,7 @@ MON_KEYS = ["step", "mass0", "mass1", "momx", "momy", "momz", "species0", "speci
             "inflow0", "inflow1", "outflow0", "outflow1", "inj_mass0", "inj_mass1", "inj_spec0",
             "inj_spec1", "rem_mass0", "rem_mass1", "rem_spec0", "rem_spec1", "deposited", "nsolid",
             "nfluid", "nonfinite", "wallx", "residual", "heat", "species_p", "inflow_p", "outflow_p",
-            "inj_spec_p", "rem_spec_p", "produced"]
+            "inj_spec_p", "rem_spec_p", "produced", "tsolid", "heat_s", "heat_src", "solid_rem"]
 
 
 def save_fields(fields, path):
@@ -343,7 +349,8 @@ class Solver:
                 m.injected_mass[1], m.injected_species[0], m.injected_species[1],
                 m.removed_mass[0], m.removed_mass[1], m.removed_species[0], m.removed_species[1],
                 m.deposited, m.n_solid, m.n_fluid, m.nonfinite, m.wall_exchange, m.residual, m.heat,
-                m.species_p, m.inflow_p, m.outflow_p, m.injected_species_p, m.removed_species_p, m.produced]
+                m.species_p, m.inflow_p, m.outflow_p, m.injected_species_p, m.removed_species_p, m.produced,
+                m.t_solid, m.heat_solid, m.heat_source, m.solid_removed]
         return dict(zip(MON_KEYS, vals))
 
     def residual(self):

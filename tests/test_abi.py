@@ -65,12 +65,14 @@ def _c_layout(tmp_path):
 #include <stddef.h>
 #include "lbm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, l2_fetch_bytes),
-         offsetof(lbm_params, u_wall_ymax), offsetof(lbm_params, u_in),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params),
+         offsetof(lbm_params, l2_fetch_bytes), offsetof(lbm_params, u_wall_ymax), offsetof(lbm_params, u_in),
          offsetof(lbm_params, stream),
          offsetof(lbm_params, N_mon), offsetof(lbm_params, C_ref), sizeof(lbm_monitors),
          offsetof(lbm_monitors, wall_exchange), offsetof(lbm_monitors, residual),
-         offsetof(lbm_params, product), offsetof(lbm_params, C_in_p), offsetof(lbm_monitors, produced));
+         offsetof(lbm_params, product), offsetof(lbm_params, C_in_p), offsetof(lbm_monitors, produced),
+         offsetof(lbm_params, conjugate), offsetof(lbm_params, c_fs), offsetof(lbm_monitors, t_solid),
+         offsetof(lbm_monitors, solid_removed));
   return 0;
 }
 ''')
@@ -83,7 +85,8 @@ def test_ctypes_layout_matches_c(tmp_path):
     c = _c_layout(tmp_path)
     P, M = lbm.LbmParams, lbm.LbmMonitors
     assert c == [C.sizeof(P), P.l2_fetch_bytes.offset, P.u_wall_ymax.offset, P.u_in.offset, P.stream.offset, P.N_mon.offset, P.C_ref.offset, C.sizeof(M),
-                 M.wall_exchange.offset, M.residual.offset, P.product.offset, P.C_in_p.offset, M.produced.offset]
+                 M.wall_exchange.offset, M.residual.offset, P.product.offset, P.C_in_p.offset, M.produced.offset,
+                 P.conjugate.offset, P.c_fs.offset, M.t_solid.offset, M.solid_removed.offset]
 
 
 def test_params_default():
@@ -93,6 +96,7 @@ def test_params_default():
     assert p.precision == 1 and p.n_comp == 1 and p.tau[0] == 1.0 and p.N_geo == 1
     assert list(p.periodic) == [1, 1, 1] and p.deposit_conservative == 1
     assert p.n_it == 16 and p.arrhenius == 0
+    assert p.conjugate == 0 and p.tau_s == 1.0 and p.c_fs == 1.0 and p.tau_p == 1.0
 
 
 @pytest.mark.parametrize("bad", [
@@ -108,6 +112,9 @@ def test_params_default():
     dict(flow_open_x=True, periodic=[0, 0, 1], G_ads=[0.1, 0]),
     dict(arrhenius=True, n_scal=1, arr_A=0.1), dict(arrhenius=True, n_scal=2, arr_A=-0.1),
     dict(arrhenius=True, n_scal=2, arr_A=0.1, n_it=65),
+    dict(conjugate=True, n_scal=2, tau_s=0.8), dict(conjugate=True, n_scal=2, arrhenius=True, tau_s=0.5),
+    dict(conjugate=True, n_scal=2, arrhenius=True, c_fs=0.0),
+    dict(conjugate=True, n_scal=2, arrhenius=True, geo_mode="deposit", DP=0.1),
 ])
 def test_create_rejects_invalid_parameters(bad):
     lib = lbm.load()
@@ -139,6 +146,7 @@ def test_null_context_calls_fail_cleanly():
 
 
 @pytest.mark.parametrize("bad", [dict(precision="fp16"), dict(geo_mode="dissolve", n_scal=1),
+                                 dict(n_scal=2, arrhenius=True, conjugate=True),
                                  dict(G=[[-5.0, 0], [0, 0]]), dict(forcing="sc_shift"), dict(collision="mrt")])
 def test_ensemble_create_rejects_mixed_or_unsupported_members(bad):
     lib = lbm.load()
