@@ -1358,39 +1358,62 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 template <class L, class S, int NC, int parity>
 __global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename Store<S>::T> k) {
   // Walks the fluid list in slot order, as k_step does: at parity 0 every population of the
-  // node sits in its own cell (coalesced); at parity 1 population i sits in cell (n - c_i, opp i),
-  // whose slot is looked up once for all components.  Sums in population order 0 .. Q-1 from
-  // rho_ref, the order the gather of the step uses.
+  // node sits in its own cell (coalesced); at parity 1 population i sits in cell (n - c_i, opp i).
+  // At parity 1 the neighbour slots of the next list entry are copied into shared memory
+  // (cp.async) while this entry sums, as in the step kernel.  Sums in population order 0 .. Q-1
+  // from rho_ref, the order the gather of the step uses.
   using T = typename Store<S>::T;
   const unsigned int count = a.fluid_count[0];
   const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
   const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride) {
-    const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
-    const uint32_t m = a.mask[n];
-    if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
-    const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-    long long cell[L::Q];   // slot of the cell holding population i
-    const Nbr nb = parity ? nbr_of(a, n) : Nbr{};
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-      cell[i] = (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
-                    ? sn
-                    : (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(i), -L::cy(i), -L::cz(i)), a.N));
+  unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
+  auto finish = [&](int n, long long sn, uint32_t m, const uint32_t* cache) {
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T r = k.rref[s];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        // the own cell in plane i, a neighbour's in plane opp(i)
+        // the own cell in plane i, a neighbour's (slot cached for n + c_opp(i)) in plane opp(i)
         const bool own = parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i));
+        const long long cell = own ? sn : (long long)cache[(L::opp(i) - 1) * LBM_STEP_CACHE_STRIDE];
         const S* p = reinterpret_cast<const S*>(own ? a.fplane[s][i] : a.fplane[s][L::opp(i)]);
-        r += Store<S>::ld(p + LBM_CHK(a.err, cell[i], a.pitch));
+        r += Store<S>::ld(p + LBM_CHK(a.err, cell, a.pitch));
       }
       T p;
       if (a.psi_identity) p = r;
       else p = k.rho0 * (T(1) - exp(-r / k.rho0));   // Eq. 1.11
       reinterpret_cast<T*>(a.psi[s])[n] = p;
+    }
+  };
+  if constexpr (parity == 1) {
+    __shared__ uint32_t slot_buf[2 * (L::Q - 1) * LBM_STEP_CACHE_STRIDE];
+    uint32_t* cb = slot_buf + threadIdx.x;
+    uint32_t* cn = slot_buf + (L::Q - 1) * LBM_STEP_CACHE_STRIDE + threadIdx.x;
+    int n_cur = e < count ? int(LBM_CHK(a.err, a.fluid_list[e], a.N)) : 0;
+    if (e < count) prefetch_slots<L, LBM_STEP_CACHE_STRIDE>(a, n_cur, cb);
+    cp_async_commit();
+    for (; e < count; e += stride) {
+      const int n = n_cur;
+      const uint32_t m = a.mask[n];
+      if (e + stride < count) {
+        n_cur = int(LBM_CHK(a.err, a.fluid_list[e + stride], a.N));
+        prefetch_slots<L, LBM_STEP_CACHE_STRIDE>(a, n_cur, cn);
+      }
+      cp_async_commit();
+      const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+      cp_async_wait<1>();   // this entry's slots have arrived
+      if (m & 1u) finish(n, sn, m, cb);   // skips a node removed by deposition since the rebuild
+      uint32_t* t = cb;
+      cb = cn;
+      cn = t;
+    }
+    cp_async_wait<0>();
+  } else {
+    for (; e < count; e += stride) {
+      const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
+      const uint32_t m = a.mask[n];
+      if (!(m & 1u)) continue;
+      finish(n, e < base ? (long long)e : (long long)__ldg(a.slot + n), m, nullptr);
     }
   }
 }

@@ -72,6 +72,33 @@ def test_contact_angle_of_sessile_droplet():
         assert 0.5 < ratio < 3.0, ratio
 
 
+@pytest.mark.parametrize("g", [-0.15, 0.0, 0.15])
+def test_contact_angle_against_oracle(g):
+    """The same sessile droplet in FP64 against the FP64 oracle's run of 60,000 steps (stored by
+    tests/golden/make_contact_angle_golden.py): both components' densities within 1e-10 and the
+    measured angle equal.  The angle, and so its distance from Huang's closed form, is the
+    method's own, not a rounding or kernel effect."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"sessile200_g{g:+.2f}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{os.path.basename(path)} not generated")
+    gold = np.load(path)
+    cfg, geom, fields = inputs.sessile_droplet_2d(g_ads=g, precision="fp64")
+    s = Solver(cfg)
+    s.set_geometry(geom)
+    s.set_fields(*fields)
+    s.step(int(gold["steps"]))
+    rho = s.fields()["rho"]
+    s.close()
+    r_o = gold["rho"]
+    err = float(np.linalg.norm(rho - r_o) / np.linalg.norm(r_o))
+    assert err <= 1e-10, err
+    t_g = contact_angle(rho[0, 0])[0]
+    t_o = contact_angle(r_o[0, 0])[0]
+    print(f"G_ads = ({g}, {-g}): theta GPU {t_g:.6f} deg, oracle {t_o:.6f} deg, rel L2 {err:.2e}")
+    assert abs(t_g - t_o) < 1e-6
+
+
 def _coexistence_3d(G, steps=6000):
     """Bulk densities of the two phases across flat interfaces in a periodic 3D slab."""
     nx = 64
