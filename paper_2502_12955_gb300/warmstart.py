@@ -123,9 +123,37 @@ def generate(count, n=128, seed0=10_000, tol=1e-5, max_steps=400_000, device=0, 
     return out, stats
 
 
-def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, seed=0, log=None):
+def symmetric_copy(s, k):
+    """Sample s under symmetry k (0..7) of the y-z plane: bit 0 mirrors y, bit 1 mirrors z, bit 2
+    exchanges y and z (cubic cross-sections only).  The flow is driven along x and y, z are
+    periodic, so the D3Q19 / D3Q7 step commutes with these maps: the mapped steady state is the
+    steady state of the mapped packing, with u_y, u_z mirrored or exchanged alike.  Returns
+    (features, targets, fluid mask) as device tensors in the layout of Sample."""
+    nz, ny, nx = s.geom.shape
+    if k == 0:
+        return s.x, s.t, s.fluid
+    x = s.x.view(nz, ny, nx, -1)
+    t = s.t.view(nz, ny, nx, 4)
+    f = s.fluid.view(nz, ny, nx)
+    sign = [1.0, 1.0, 1.0, 1.0]
+    if k & 1:
+        x, t, f = x.flip(1), t.flip(1), f.flip(1)
+        sign[1] = -1.0
+    if k & 2:
+        x, t, f = x.flip(0), t.flip(0), f.flip(0)
+        sign[2] = -1.0
+    if (k & 4) and ny == nz:
+        x, t, f = x.transpose(0, 1), t.transpose(0, 1), f.transpose(0, 1)
+        t = t[..., [0, 2, 1, 3]]
+        sign[1], sign[2] = sign[2], sign[1]
+    t = t * t.new_tensor(sign)
+    return x.contiguous().view(-1, x.shape[-1]), t.contiguous().view(-1, 4), f.contiguous().view(-1)
+
+
+def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, seed=0, log=None, augment=True):
     """Adam over the samples in a seeded random order each epoch, cosine-decayed learning rate;
-    returns the mean loss of each epoch."""
+    with augment, each visit takes one of the eight y-z symmetric copies of the sample (drawn
+    from the same seeded generator).  Returns the mean loss of each epoch."""
     rng = np.random.default_rng(seed)
     total = epochs * len(samples)
     hist, it = [], 0
@@ -134,7 +162,8 @@ def train(net, samples, epochs, lr=1e-3, lr_final=1e-4, seed=0, log=None):
         for j in rng.permutation(len(samples)):
             s = samples[j]
             a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * it / max(1, total - 1)))
-            loss = net.train_step(s.x, s.t, s.fluid, s.n_fluid, s.geom.shape, lr=a)
+            x, t, fl = symmetric_copy(s, int(rng.integers(8))) if augment else (s.x, s.t, s.fluid)
+            loss = net.train_step(x, t, fl, s.n_fluid, s.geom.shape, lr=a)
             acc.append(loss)
             it += 1
         net.check()
