@@ -58,13 +58,20 @@ def workload(name, size, precision):
     return cfg, geom, fields, label
 
 
+# bytes per stored (flow, scalar) population of each storage mode; the *s32 modes keep the
+# scalar lattices in FP32
+ELEM = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 2), "bf16": (2, 2), "fp16s32": (2, 4), "bf16s32": (2, 4)}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math", "bf16": "bf16 storage, f32 math",
+         "fp16s32": "f16 flow / f32 scalar storage, f32 math", "bf16s32": "bf16 flow / f32 scalar storage, f32 math"}
+
+
 def bytes_per_fluid_node(cfg):
     """Algorithmic HBM bytes per fluid node and step: one read and one write of every
     population of every lattice."""
     q = 19 if cfg["dim"] == 3 else 9
     qc = 7 if cfg["dim"] == 3 else 5
-    elem = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[cfg["precision"]]
-    return 2 * elem * (q * cfg.get("n_comp", 1) + qc * cfg.get("n_scal", 0))
+    ef, es = ELEM[cfg["precision"]]
+    return 2 * (ef * q * cfg.get("n_comp", 1) + es * qc * cfg.get("n_scal", 0))
 
 
 def source_hash():
@@ -342,7 +349,7 @@ def run_ensemble(args, dist, ws, rank, local):
     sets = inputs.ensemble_members(n2d, n3d, seed0=1000 * local, precision=precision)
     stream = torch.cuda.Stream(device=local)
     ens, nodes, fluid, bpn = [], 0, 0, 0.0
-    elem = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
+    ef, es = ELEM[precision]
     for members in sets:
         if not members:
             continue
@@ -354,7 +361,7 @@ def run_ensemble(args, dist, ws, rank, local):
             nodes += geom.size
             fluid += nf
             q, qc = (19, 7) if cfg["dim"] == 3 else (9, 5)
-            bpn += nf * 2 * elem * (q + qc)
+            bpn += nf * 2 * (ef * q + es * qc)
         ens.append(e)
     tiles = [e.autotune(steps=4) for e in ens]
     for e in ens:
@@ -387,8 +394,7 @@ def run_ensemble(args, dist, ws, rank, local):
             "metric": "MLUPS", "value": nodes_all / sec / 1e6, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math",
-                      "bf16": "bf16 storage, f32 math"}[precision],
+            "dtype": DTYPE[precision],
             "data": "synthetic (seeded porous geometries, inputs.ensemble_members)",
             "config": {"workload": f"ensemble_{args.members}_members_{n2d}x2d_{n3d}x3d_{precision}",
                        "nodes": nodes, "fluid_nodes": fluid, "tile_threads": tiles,
@@ -445,8 +451,7 @@ def run_to_steady(args, local):
     line = {"metric": "time_to_steady", "value": sec, "unit": "s", "n_gpus": 1, "steps": steps,
             "higher_is_better": False, "converged": bool(0.0 <= r <= args.to_steady),
             "residual": r, "tol": args.to_steady, "start": "rest (uniform density, zero velocity)",
-            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math",
-                      "bf16": "bf16 storage, f32 math"}[precision],
+            "dtype": DTYPE[precision],
             "data": "synthetic (seeded geometry, inputs/ recipe), geometry update frozen",
             "config": {"workload": label, "nodes": int(geom.size), "fluid_nodes": int((geom == 0).sum())},
             "mlups": geom.size * steps / sec / 1e6, "clocks": clk}
@@ -709,14 +714,13 @@ def main():
 
     q = 19 if cfg["dim"] == 3 else 9
     qc = 7 if cfg["dim"] == 3 else 5
-    state_gb = N * (q * cfg.get("n_comp", 1) + qc * cfg.get("n_scal", 0)) * (bpn // (2 * (q * cfg.get("n_comp", 1) + qc * cfg.get("n_scal", 0)))) / 1e9
+    state_gb = N * bpn / 2 / 1e9   # one stored copy of every population of every node
     if rank == 0:
         line = {
             "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math",
-                      "bf16": "bf16 storage, f32 math"}[precision],
+            "dtype": DTYPE[precision],
             "data": "synthetic (seeded geometry, inputs/ recipe)",
             "config": {"workload": label, "nodes": N, "fluid_nodes": Nf,
                        "parallelism": "replicas" if ws > 1 else "single GPU",

@@ -56,7 +56,11 @@ typedef enum lbm_precision {
   LBM_FP64 = 0,          /* populations and arithmetic in FP64 */
   LBM_FP32 = 1,          /* populations and arithmetic in FP32 */
   LBM_FP16_SHIFTED = 2,  /* stored as FP16 deviation from w_i * reference, FP32 arithmetic */
-  LBM_BF16_SHIFTED = 3   /* stored as BF16 deviation from w_i * reference, FP32 arithmetic */
+  LBM_BF16_SHIFTED = 3,  /* stored as BF16 deviation from w_i * reference, FP32 arithmetic */
+  LBM_FP16_SHIFTED_S32 = 4,  /* flow populations as in LBM_FP16_SHIFTED, scalar populations in FP32
+                                (deviations from w_j * C_ref): scalars that vary by O(1) across the
+                                domain keep FP32 rounding */
+  LBM_BF16_SHIFTED_S32 = 5   /* flow populations as in LBM_BF16_SHIFTED, scalars in FP32 */
 } lbm_precision;
 
 enum { LBM_FORCING_GUO = 0, LBM_FORCING_SC_SHIFT = 1 };

@@ -65,6 +65,42 @@ struct Store<__nv_bfloat16> {
   __device__ static void st(__nv_bfloat16* p, T v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Mixed storage: 16-bit flow populations with the scalar lattices in FP32.  The tag types are
+// the flow's storage element (2 bytes, loaded and stored like the plain 16-bit types); the scalar
+// lattices of every storage type S are stored as ScalarOf<S>.
+struct half_s32 {
+  __half v;
+};
+struct bf16_s32 {
+  __nv_bfloat16 v;
+};
+template <>
+struct Store<half_s32> {
+  using T = float;
+  __device__ static T ld(const half_s32* p) { return __half2float(__ldg(&p->v)); }
+  __device__ static T ldv(const half_s32* p) { return __half2float(p->v); }
+  __device__ static void st(half_s32* p, T v) { p->v = __float2half_rn(v); }
+};
+template <>
+struct Store<bf16_s32> {
+  using T = float;
+  __device__ static T ld(const bf16_s32* p) { return __bfloat162float(__ldg(&p->v)); }
+  __device__ static T ldv(const bf16_s32* p) { return __bfloat162float(p->v); }
+  __device__ static void st(bf16_s32* p, T v) { p->v = __float2bfloat16_rn(v); }
+};
+template <class S>
+struct ScalarOf {
+  using type = S;
+};
+template <>
+struct ScalarOf<half_s32> {
+  using type = float;
+};
+template <>
+struct ScalarOf<bf16_s32> {
+  using type = float;
+};
+
 // ------------------------------------------------------------- arguments
 
 enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_CAS = 4, ERR_BOUNDS = 8 };
@@ -537,7 +573,8 @@ __device__ __forceinline__ void gather_entry(const Args& a, unsigned int e, unsi
 #pragma unroll
   for (int s = 0; s < NC; ++s) gather_flow_pl<L, S>(a.fplane[s], sn, a.slot, m, nb, parity, f[s], a.err, a.N, a.pitch);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h[s], a.err, a.N, a.pitch);
+  for (int s = 0; s < NS; ++s)
+    gather_scal_pl<L, typename ScalarOf<S>::type>(a.hplane[s], sn, a.slot, m, nb, parity, h[s], a.err, a.N, a.pitch);
 }
 
 // Neighbour-slot cache of the odd step.  An odd step reads cell (n - c_i, opp i) and writes
@@ -629,12 +666,13 @@ __device__ __forceinline__ void gather_entry_odd_cached(const Args& a, long long
   for (int s = 0; s < NS; ++s) {
 #pragma unroll
     for (int j = 0; j < L::QC; ++j) {
-      const S* p;
+      using SC = typename ScalarOf<S>::type;
+      const SC* p;
       if (j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0)
-        p = reinterpret_cast<const S*>(a.hplane[s][j]) + LBM_CHK(a.err, sn, a.pitch);
+        p = reinterpret_cast<const SC*>(a.hplane[s][j]) + LBM_CHK(a.err, sn, a.pitch);
       else
-        p = reinterpret_cast<const S*>(a.hplane[s][L::opp(j)]) + cache[(L::opp(j) - 1) * CS];
-      h[s][j] = Store<S>::ld(p);
+        p = reinterpret_cast<const SC*>(a.hplane[s][L::opp(j)]) + cache[(L::opp(j) - 1) * CS];
+      h[s][j] = Store<SC>::ld(p);
     }
   }
 }
@@ -1041,9 +1079,10 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
   for (int s = 0; s < NS; ++s) {
 #pragma unroll
     for (int j = 0; j < QC; ++j) {
+      using SC = typename ScalarOf<S>::type;
       const uint32_t code = j == 0 ? 0u : MaskBits<L>::code(m, j);
       T v = h[s][j];
-      S* p;
+      SC* p;
       if (code == 3u) {
         // open face: the population arriving from outside replaces the one leaving
         const int jb = L::opp(j);
@@ -1060,17 +1099,17 @@ __device__ __forceinline__ void collide_scatter(const Args& a, const Coef<typena
               widen(v) - widen(b);
         }
         v = b;
-        p = reinterpret_cast<S*>(a.hplane[s][jb]) + LBM_CHK(a.err, sn, a.pitch);
+        p = reinterpret_cast<SC*>(a.hplane[s][jb]) + LBM_CHK(a.err, sn, a.pitch);
       } else if (parity == 0 || j == 0 || code != 0u) {
-        p = reinterpret_cast<S*>(a.hplane[s][L::opp(j)]) + LBM_CHK(a.err, sn, a.pitch);
+        p = reinterpret_cast<SC*>(a.hplane[s][L::opp(j)]) + LBM_CHK(a.err, sn, a.pitch);
       } else {
         if (CACHE)
-          p = reinterpret_cast<S*>(a.hplane[s][j]) + cache[(j - 1) * CS];
+          p = reinterpret_cast<SC*>(a.hplane[s][j]) + cache[(j - 1) * CS];
         else
-          p = reinterpret_cast<S*>(a.hplane[s][j]) +
+          p = reinterpret_cast<SC*>(a.hplane[s][j]) +
               LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(L::cx(j), L::cy(j), L::cz(j)), a.N)), a.pitch);
       }
-      Store<S>::st(p, v);
+      Store<SC>::st(p, v);
     }
   }
 }
@@ -1358,62 +1397,39 @@ __global__ void __launch_bounds__(256, (NC == 1 && sizeof(typename Store<S>::T) 
 template <class L, class S, int NC, int parity>
 __global__ void __launch_bounds__(256) k_psi(const Args a, const Coef<typename Store<S>::T> k) {
   // Walks the fluid list in slot order, as k_step does: at parity 0 every population of the
-  // node sits in its own cell (coalesced); at parity 1 population i sits in cell (n - c_i, opp i).
-  // At parity 1 the neighbour slots of the next list entry are copied into shared memory
-  // (cp.async) while this entry sums, as in the step kernel.  Sums in population order 0 .. Q-1
-  // from rho_ref, the order the gather of the step uses.
+  // node sits in its own cell (coalesced); at parity 1 population i sits in cell (n - c_i, opp i),
+  // whose slot is looked up once for all components.  Sums in population order 0 .. Q-1 from
+  // rho_ref, the order the gather of the step uses.
   using T = typename Store<S>::T;
   const unsigned int count = a.fluid_count[0];
   const unsigned int base = a.fluid_count[1];   // entries below it have slot == entry
   const unsigned int stride = gridDim.x * blockDim.x;
-  unsigned int e = blockIdx.x * blockDim.x + threadIdx.x;
-  auto finish = [&](int n, long long sn, uint32_t m, const uint32_t* cache) {
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride) {
+    const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
+    const uint32_t m = a.mask[n];
+    if (!(m & 1u)) continue;   // a node removed by deposition since the last list rebuild
+    const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
+    long long cell[L::Q];   // slot of the cell holding population i
+    const Nbr nb = parity ? nbr_of(a, n) : Nbr{};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      cell[i] = (parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i)))
+                    ? sn
+                    : (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(i), -L::cy(i), -L::cz(i)), a.N));
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T r = k.rref[s];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        // the own cell in plane i, a neighbour's (slot cached for n + c_opp(i)) in plane opp(i)
+        // the own cell in plane i, a neighbour's in plane opp(i)
         const bool own = parity == 0 || i == 0 || flow_wall<L>(m, L::opp(i));
-        const long long cell = own ? sn : (long long)cache[(L::opp(i) - 1) * LBM_STEP_CACHE_STRIDE];
         const S* p = reinterpret_cast<const S*>(own ? a.fplane[s][i] : a.fplane[s][L::opp(i)]);
-        r += Store<S>::ld(p + LBM_CHK(a.err, cell, a.pitch));
+        r += Store<S>::ld(p + LBM_CHK(a.err, cell[i], a.pitch));
       }
       T p;
       if (a.psi_identity) p = r;
       else p = k.rho0 * (T(1) - exp(-r / k.rho0));   // Eq. 1.11
       reinterpret_cast<T*>(a.psi[s])[n] = p;
-    }
-  };
-  if constexpr (parity == 1) {
-    __shared__ uint32_t slot_buf[2 * (L::Q - 1) * LBM_STEP_CACHE_STRIDE];
-    uint32_t* cb = slot_buf + threadIdx.x;
-    uint32_t* cn = slot_buf + (L::Q - 1) * LBM_STEP_CACHE_STRIDE + threadIdx.x;
-    int n_cur = e < count ? int(LBM_CHK(a.err, a.fluid_list[e], a.N)) : 0;
-    if (e < count) prefetch_slots<L, LBM_STEP_CACHE_STRIDE>(a, n_cur, cb);
-    cp_async_commit();
-    for (; e < count; e += stride) {
-      const int n = n_cur;
-      const uint32_t m = a.mask[n];
-      if (e + stride < count) {
-        n_cur = int(LBM_CHK(a.err, a.fluid_list[e + stride], a.N));
-        prefetch_slots<L, LBM_STEP_CACHE_STRIDE>(a, n_cur, cn);
-      }
-      cp_async_commit();
-      const long long sn = e < base ? (long long)e : (long long)__ldg(a.slot + n);
-      cp_async_wait<1>();   // this entry's slots have arrived
-      if (m & 1u) finish(n, sn, m, cb);   // skips a node removed by deposition since the rebuild
-      uint32_t* t = cb;
-      cb = cn;
-      cn = t;
-    }
-    cp_async_wait<0>();
-  } else {
-    for (; e < count; e += stride) {
-      const int n = int(LBM_CHK(a.err, a.fluid_list[e], a.N));
-      const uint32_t m = a.mask[n];
-      if (!(m & 1u)) continue;
-      finish(n, e < base ? (long long)e : (long long)__ldg(a.slot + n), m, nullptr);
     }
   }
 }
@@ -1485,7 +1501,7 @@ __global__ void __launch_bounds__(256) k_monitor(const Args a, const Coef<typena
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       T h[QC];
-      gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, h, a.err, a.N, a.pitch);
+      gather_scal_pl<L, typename ScalarOf<S>::type>(a.hplane[s], sn, a.slot, m, nb, parity, h, a.err, a.N, a.pitch);
       T c = T(0);
 #pragma unroll
       for (int j = 0; j < QC; ++j) c += h[j];
@@ -1614,7 +1630,7 @@ __device__ __forceinline__ void node_macros(const Args& a, const Coef<typename S
   T hh[NS > 0 ? NS : 1][QC];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
-    gather_scal_pl<L, S>(a.hplane[s], sn, a.slot, m, nb, parity, hh[s], a.err, a.N, a.pitch);
+    gather_scal_pl<L, typename ScalarOf<S>::type>(a.hplane[s], sn, a.slot, m, nb, parity, hh[s], a.err, a.N, a.pitch);
   T rl[QC], gain = T(0);
 #pragma unroll
   for (int j = 0; j < QC; ++j) rl[j] = T(0);
@@ -1723,7 +1739,8 @@ __global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename 
     }
   }
   for (int s = 0; s < NS; ++s) {
-    S* hs = reinterpret_cast<S*>(a.h[s]);
+    using SC = typename ScalarOf<S>::type;
+    SC* hs = reinterpret_cast<SC*>(a.h[s]);
     const T C = T(a.d_C[s * a.N + n]);
     const T dC = T(a.d_C[s * a.N + n] - double(k.cref[s]));
 #pragma unroll
@@ -1731,7 +1748,7 @@ __global__ void __launch_bounds__(256) k_init(const Args a, const Coef<typename 
       const T cu = T(L::cx(j)) * ux + T(L::cy(j)) * uy + T(L::cz(j)) * uz;
       const T wj = scal_w<T>(j, k);
       const T v = fluid ? wj * (dC + C * cu * k.ics2c) : T(0);
-      Store<S>::st(hs + (long long)j * a.pitch + sn, v);
+      Store<SC>::st(hs + (long long)j * a.pitch + sn, v);
     }
   }
 }
@@ -1776,8 +1793,9 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const Coef<typena
     }
   }
   if (hio) {
+    using SC = typename ScalarOf<S>::type;
     for (int s = 0; s < NS; ++s) {
-      S* hs = reinterpret_cast<S*>(a.h[s]);
+      SC* hs = reinterpret_cast<SC*>(a.h[s]);
 #pragma unroll
       for (int j = 0; j < L::QC; ++j) {
         double* io = hio + ((long long)s * L::QC + j) * N + n;
@@ -1785,14 +1803,14 @@ __global__ void __launch_bounds__(256) k_pops_io(const Args a, const Coef<typena
           if (dir == 0) *io = 0.0;
           continue;
         }
-        S* p;
+        SC* p;
         if (parity == 0 || j == 0 || MaskBits<L>::code(m, L::opp(j)) != 0u)
           p = hs + (long long)j * P + sn;
         else
           p = hs + (long long)L::opp(j) * P + a.slot[nb.at(-L::cx(j), -L::cy(j), -L::cz(j))];
         const double sh = double(scal_w<T>(j, k)) * double(k.cref[s]);
-        if (dir == 0) *io = double(Store<S>::ldv(p)) + sh;
-        else Store<S>::st(p, T(*io - sh));
+        if (dir == 0) *io = double(Store<SC>::ldv(p)) + sh;
+        else Store<SC>::st(p, T(*io - sh));
       }
     }
   }
@@ -2065,6 +2083,7 @@ template <class L, class S, int NC, int NS>
 __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename Store<S>::T> k,
                                                const int parity_next) {
   using T = typename Store<S>::T;
+  using SC = typename ScalarOf<S>::type;   // scalar lattices' storage
   constexpr int Q = L::Q, QC = L::QC;
   const unsigned int cnt_raw = *a.flip_count;
   const unsigned int cnt = cnt_raw < a.flip_cap ? cnt_raw : a.flip_cap;
@@ -2116,7 +2135,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         }
         T hh[NS > 0 ? NS : 1][QC];
         for (int c = 0; c < NS; ++c)
-          gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, hh[c]);
+          gather_scal<L, SC>(reinterpret_cast<const SC*>(a.h[c]), P, a.slot[q], a.slot, mq, nq, parity_next, hh[c]);
         T rl[QC], gain = T(0);
         for (int j = 0; j < QC; ++j) rl[j] = T(0);
         if (NS > 1 && a.conjugate)
@@ -2153,7 +2172,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
       }
       for (int c = 0; c < NS; ++c) {
         T h[QC];
-        gather_scal<L, S>(reinterpret_cast<const S*>(a.h[c]), P, a.slot[s], a.slot, ms, ns, parity_next, h);
+        gather_scal<L, SC>(reinterpret_cast<const SC*>(a.h[c]), P, a.slot[s], a.slot, ms, ns, parity_next, h);
         double C = double(k.cref[c]);
         for (int j = 0; j < QC; ++j) C += double(h[j]);
         atomicAdd(&sred[7 + c], C);
@@ -2195,7 +2214,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         }
       }
       for (int c = 0; c < NS; ++c) {
-        S* hs = reinterpret_cast<S*>(a.h[c]);
+        SC* hs = reinterpret_cast<SC*>(a.h[c]);
         double C = sc4[2 + c];
         if (c == 1 && a.conjugate) {
           // with conduction in the solid the new fluid node keeps its own temperature: its solid
@@ -2213,19 +2232,19 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
           const double wj = double(scal_w<T>(j, k));
           const T tv = T(wj * (C - double(k.cref[c])));       // h_eq(C_bar, u = 0) - w cref
           if (parity_next == 0 || j == 0) {
-            Store<S>::st(hs + (long long)j * P + ss, tv);
+            Store<SC>::st(hs + (long long)j * P + ss, tv);
             continue;
           }
           const long long src = nbr_checked(a, x, y, z, -L::cx(j), -L::cy(j), -L::cz(j), percs, &ax);
           const uint8_t fl = src < 0 ? FL_SOLID : a.flags[src];
           if (fl == FL_FLUID) {
-            S* from = hs + (long long)L::opp(j) * P + a.slot[src];
+            SC* from = hs + (long long)L::opp(j) * P + a.slot[src];
             *(hs + (long long)j * P + ss) = *from;
-            Store<S>::st(from, tv);
+            Store<SC>::st(from, tv);
           } else if (fl == FL_FLIPPING) {
-            Store<S>::st(hs + (long long)L::opp(j) * P + a.slot[src], tv);
+            Store<SC>::st(hs + (long long)L::opp(j) * P + a.slot[src], tv);
           } else {
-            Store<S>::st(hs + (long long)j * P + ss, tv);
+            Store<SC>::st(hs + (long long)j * P + ss, tv);
           }
         }
       }
@@ -2241,7 +2260,7 @@ __global__ void __launch_bounds__(1024) k_flip(const Args a, const Coef<typename
         }
       }
       for (int c = 0; c < NS; ++c) {
-        S* hs = reinterpret_cast<S*>(a.h[c]);
+        SC* hs = reinterpret_cast<SC*>(a.h[c]);
         for (int d = 1; d < QC; ++d) {
           const long long yn = nbr_checked(a, x, y, z, L::cx(d), L::cy(d), L::cz(d), percs, &ax);
           if (yn < 0 || a.flags[yn] != FL_FLUID) continue;
@@ -2350,6 +2369,7 @@ template <class L, class S>
 __global__ void __launch_bounds__(256) k_exchange(const Args a, const Coef<typename Store<S>::T> k,
                                                   const int parity_next) {
   using T = typename Store<S>::T;
+  using SC = typename ScalarOf<S>::type;
   constexpr int QC = L::QC;
   T* g = reinterpret_cast<T*>(a.gs[parity_next]);
   T* kb = reinterpret_cast<T*>(a.kb);
@@ -2381,22 +2401,22 @@ __global__ void __launch_bounds__(256) k_exchange(const Args a, const Coef<typen
       const long long s = nbr_checked(a, x, y, z, L::cx(j), L::cy(j), L::cz(j), perc, &ax);
       if (s < 0) continue;   // a closed face: plain bounce-back
       const int i = L::opp(j);
-      S* hp = reinterpret_cast<S*>(a.hplane[1][i]) + LBM_CHK(a.err, sn, a.pitch);
+      SC* hp = reinterpret_cast<SC*>(a.hplane[1][i]) + LBM_CHK(a.err, sn, a.pitch);
       T* gp = g + (long long)j * a.N + s;
-      const T ho = Store<S>::ld(hp) + sh1;
+      const T ho = Store<SC>::ld(hp) + sh1;
       const T go = *gp;
       T Tb = (cf * ho + go) / den;
       T Qp = T(0);
       if (c == 2u) {
         // the species population moving toward the wall, where the next step gathers it
-        const S* bp;
+        const SC* bp;
         if (parity_next == 0 || MaskBits<L>::code(m, i) != 0u)
-          bp = reinterpret_cast<const S*>(a.hplane[0][j]) + LBM_CHK(a.err, sn, a.pitch);
+          bp = reinterpret_cast<const SC*>(a.hplane[0][j]) + LBM_CHK(a.err, sn, a.pitch);
         else
-          bp = reinterpret_cast<const S*>(a.hplane[0][i]) +
+          bp = reinterpret_cast<const SC*>(a.hplane[0][i]) +
                LBM_CHK(a.err, (long long)__ldg(a.slot + LBM_CHK(a.err, nb.at(-L::cx(j), -L::cy(j), -L::cz(j)), a.N)),
                        a.pitch);
-        const T hb = Store<S>::ld(bp) + sh0;
+        const T hb = Store<SC>::ld(bp) + sh0;
         T kt = T(0);
         for (int it = 0; it <= a.n_it; ++it) {
           kt = k.arrA * exp(-k.arrTa / Tb);
@@ -2408,7 +2428,7 @@ __global__ void __launch_bounds__(256) k_exchange(const Args a, const Coef<typen
       }
       const T hn = T(2) * w * Tb - ho;
       const T gn = T(2) * w * Tb - go;
-      Store<S>::st(hp, hn - sh1);
+      Store<SC>::st(hp, hn - sh1);
       *gp = gn;
       heat += hn - ho;
       heat_s += gn - go;

@@ -371,6 +371,10 @@ const KernelSet& kernels_d3_f64();
 const KernelSet& kernels_d3_f32();
 const KernelSet& kernels_d3_f16();
 const KernelSet& kernels_d3_bf16();
+const KernelSet& kernels_d2_f16s32();
+const KernelSet& kernels_d2_bf16s32();
+const KernelSet& kernels_d3_f16s32();
+const KernelSet& kernels_d3_bf16s32();
 
 // Storage-independent kernels (runtime.cu)
 cudaError_t launch_reduce(const double* partials, long long nblocks, int K, double* out, int* err,

@@ -29,7 +29,8 @@ struct lbm_ctx {
   lbm_params p{};
   cudaStream_t stream = nullptr;
   const KernelSet* ks = nullptr;
-  size_t elem = 0;                 // bytes per stored population
+  size_t elem = 0;                 // bytes per stored flow population
+  size_t elem_h = 0;               // bytes per stored scalar population
   Args a{};
   long long step = 0;
   bool fields_set = false;
@@ -106,6 +107,8 @@ const KernelSet* pick(int lattice, int precision) {
       case LBM_FP32: return &kernels_d2_f32();
       case LBM_FP16_SHIFTED: return &kernels_d2_f16();
       case LBM_BF16_SHIFTED: return &kernels_d2_bf16();
+      case LBM_FP16_SHIFTED_S32: return &kernels_d2_f16s32();
+      case LBM_BF16_SHIFTED_S32: return &kernels_d2_bf16s32();
     }
   } else {
     switch (precision) {
@@ -113,6 +116,8 @@ const KernelSet* pick(int lattice, int precision) {
       case LBM_FP32: return &kernels_d3_f32();
       case LBM_FP16_SHIFTED: return &kernels_d3_f16();
       case LBM_BF16_SHIFTED: return &kernels_d3_bf16();
+      case LBM_FP16_SHIFTED_S32: return &kernels_d3_f16s32();
+      case LBM_BF16_SHIFTED_S32: return &kernels_d3_bf16s32();
     }
   }
   return nullptr;
@@ -129,7 +134,7 @@ lbm_status validate(lbm_ctx* c, int lattice, int nx, int ny, int nz, const lbm_p
   if (lattice == LBM_D2Q9_D2Q5 && nz != 1) return fail(c, LBM_ERR_INVALID_ARG, "2D lattice needs nz == 1");
   if ((long long)nx * ny * nz >= (1ll << 31)) return fail(c, LBM_ERR_INVALID_ARG, "more than 2^31 nodes");
   if (ny > 65535 || nz > 65535) return fail(c, LBM_ERR_INVALID_ARG, "ny and nz must not exceed 65535");
-  if (p->precision < 0 || p->precision > 3) return fail(c, LBM_ERR_INVALID_ARG, "precision %d", p->precision);
+  if (p->precision < 0 || p->precision > 5) return fail(c, LBM_ERR_INVALID_ARG, "precision %d", p->precision);
   if (p->n_comp < 1 || p->n_comp > 2) return fail(c, LBM_ERR_INVALID_ARG, "n_comp %d", p->n_comp);
   for (int s = 0; s < p->n_comp; ++s)
     if (!(p->tau[s] > 0.5)) return fail(c, LBM_ERR_INVALID_ARG, "tau[%d] = %g must exceed 0.5", s, p->tau[s]);
@@ -292,7 +297,7 @@ void set_planes(lbm_ctx* c) {
       c->a.fplane[s][i] = static_cast<char*>(c->a.f[s]) + (size_t)i * c->pitch * c->elem;
   for (int s = 0; s < c->nlat; ++s)
     for (int j = 0; j < c->Qc; ++j)
-      c->a.hplane[s][j] = static_cast<char*>(c->a.h[s]) + (size_t)j * c->pitch * c->elem;
+      c->a.hplane[s][j] = static_cast<char*>(c->a.h[s]) + (size_t)j * c->pitch * c->elem_h;
 }
 
 // Copies the populations of every fluid node between two population buffers.  A NULL map
@@ -303,7 +308,7 @@ lbm_status move_pops(lbm_ctx* c, void* const* src_f, void* const* dst_f, void* c
     LAUNCH(launch_permute(src_f[s], dst_f[s], (int)c->elem, c->pitch, c->Qf, c->a.flags, c->N, from, to,
                           c->stream));
   for (int s = 0; s < c->nlat; ++s)
-    LAUNCH(launch_permute(src_h[s], dst_h[s], (int)c->elem, c->pitch, c->Qc, c->a.flags, c->N, from, to,
+    LAUNCH(launch_permute(src_h[s], dst_h[s], (int)c->elem_h, c->pitch, c->Qc, c->a.flags, c->N, from, to,
                           c->stream));
   return LBM_OK;
 }
@@ -543,6 +548,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   c->stream = reinterpret_cast<cudaStream_t>(params->stream);
   c->ks = pick(lattice, params->precision);
   c->elem = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32 ? 4 : 2);
+  c->elem_h = (params->precision == LBM_FP16_SHIFTED_S32 || params->precision == LBM_BF16_SHIFTED_S32) ? 4 : c->elem;
   auto bail = [&](lbm_status s) {
     g_create_err = c->err;    // reachable through lbm_last_error(NULL)
     lbm_destroy(c);
@@ -568,9 +574,9 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
     ptr = reinterpret_cast<decltype(ptr)>(v);               \
   } while (0)
   for (int s = 0; s < params->n_comp; ++s) DA(a.f[s], P * c->Qf * c->elem);
-  for (int s = 0; s < c->nlat; ++s) DA(a.h[s], P * c->Qc * c->elem);
+  for (int s = 0; s < c->nlat; ++s) DA(a.h[s], P * c->Qc * c->elem_h);
   for (int s = 0; s < params->n_comp; ++s) DA(c->f_alt[s], P * c->Qf * c->elem);
-  for (int s = 0; s < c->nlat; ++s) DA(c->h_alt[s], P * c->Qc * c->elem);
+  for (int s = 0; s < c->nlat; ++s) DA(c->h_alt[s], P * c->Qc * c->elem_h);
   set_planes(c);
   DA(a.slot, N * 4);
   DA(a.slot_new, N * 4);
@@ -634,7 +640,7 @@ lbm_status lbm_create(lbm_lattice lattice, int32_t nx, int32_t ny, int32_t nz, c
   if (e == cudaSuccess) e = cudaMemsetAsync(a.outflow_row, 0, 3 * rows * 8, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.mon_out, 0, (NMON + 8) * 8, c->stream);
   for (int s = 0; s < params->n_comp && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.f[s], 0, P * c->Qf * c->elem, c->stream);
-  for (int s = 0; s < c->nlat && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem, c->stream);
+  for (int s = 0; s < c->nlat && e == cudaSuccess; ++s) e = cudaMemsetAsync(a.h[s], 0, P * c->Qc * c->elem_h, c->stream);
   if (e == cudaSuccess) e = launch_iota(a.slot, N, c->stream);   // node order until a geometry is set
   if (e == cudaSuccess) {
     // inlet profile u_x(y) = 6 U s (1 - s), s = (y + 1/2) / ny (zero without a velocity inlet)
@@ -1028,7 +1034,7 @@ struct StateHeader {
 };
 size_t state_bytes(const lbm_ctx* c) {
   const size_t N = (size_t)c->N, P = (size_t)c->pitch, rows = (size_t)c->ny * c->nz;
-  return sizeof(StateHeader) + (c->p.n_comp * c->Qf + c->nlat * c->Qc) * P * c->elem +
+  return sizeof(StateHeader) + (c->p.n_comp * c->Qf * c->elem + c->nlat * c->Qc * c->elem_h) * P +
          (N + 3) / 4 * 4 + N * 8 + 3 * WALLX_SLOTS * 8 + 6 * rows * 8 + 10 * 8;
 }
 }  // namespace
@@ -1053,7 +1059,7 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   const size_t P = (size_t)c->pitch, N = (size_t)c->N, rows = (size_t)c->ny * c->nz;
   // populations in node order (solid nodes 0), staged in the second population buffers
   for (int s = 0; s < c->p.n_comp; ++s) CK(cudaMemsetAsync(c->f_alt[s], 0, c->Qf * P * c->elem, c->stream));
-  for (int s = 0; s < c->nlat; ++s) CK(cudaMemsetAsync(c->h_alt[s], 0, c->Qc * P * c->elem, c->stream));
+  for (int s = 0; s < c->nlat; ++s) CK(cudaMemsetAsync(c->h_alt[s], 0, c->Qc * P * c->elem_h, c->stream));
   lbm_status st = move_pops(c, c->a.f, c->f_alt, c->a.h, c->h_alt, c->a.slot, nullptr);
   if (st != LBM_OK) return st;
   for (int s = 0; s < c->p.n_comp; ++s) {
@@ -1061,8 +1067,8 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
     o += c->Qf * P * c->elem;
   }
   for (int s = 0; s < c->nlat; ++s) {
-    CK(cudaMemcpyAsync(o, c->h_alt[s], c->Qc * P * c->elem, cudaMemcpyDeviceToHost, c->stream));
-    o += c->Qc * P * c->elem;
+    CK(cudaMemcpyAsync(o, c->h_alt[s], c->Qc * P * c->elem_h, cudaMemcpyDeviceToHost, c->stream));
+    o += c->Qc * P * c->elem_h;
   }
   CK(cudaMemcpyAsync(o, c->a.flags, (N + 3) / 4 * 4, cudaMemcpyDeviceToHost, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(o, c->a.acc, N * 8, cudaMemcpyDeviceToHost, c->stream)); o += N * 8;
@@ -1095,8 +1101,8 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
     o += c->Qf * P * c->elem;
   }
   for (int s = 0; s < c->nlat; ++s) {
-    CK(cudaMemcpyAsync(c->h_alt[s], o, c->Qc * P * c->elem, cudaMemcpyHostToDevice, c->stream));
-    o += c->Qc * P * c->elem;
+    CK(cudaMemcpyAsync(c->h_alt[s], o, c->Qc * P * c->elem_h, cudaMemcpyHostToDevice, c->stream));
+    o += c->Qc * P * c->elem_h;
   }
   CK(cudaMemcpyAsync(c->a.flags, o, (N + 3) / 4 * 4, cudaMemcpyHostToDevice, c->stream)); o += (N + 3) / 4 * 4;
   CK(cudaMemcpyAsync(c->a.acc, o, N * 8, cudaMemcpyHostToDevice, c->stream)); o += N * 8;

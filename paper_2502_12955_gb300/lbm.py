@@ -19,7 +19,7 @@ _lib = None
 
 LBM_D2Q9_D2Q5 = 2
 LBM_D3Q19_D3Q7 = 3
-PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "fp16s32": 4, "bf16s32": 5}   # *s32: FP32 scalars
 FORCING = {"guo": 0, "sc_shift": 1}
 COLLISION = {"bgk": 0, "mrt": 1}
 PSI = {"exp": 0, "identity": 1}

@@ -26,7 +26,7 @@ def _load(s, geom, fields):
     s.set_fields(rho, u, C if s.n_scal else None)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64", "fp16s32"])
 def test_ensemble_matches_single_domains_bitwise(precision):
     mem = _members_3d(precision)
     ens = Ensemble([c for c, _, _ in mem])

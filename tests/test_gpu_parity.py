@@ -183,9 +183,13 @@ def test_checkpoint_resume_is_bitwise():
 REDUCED_TOL = {"fp32": {"rho": 1e-6, "u": 1e-4, "C": 1e-5},
                "fp16": {"rho": 1e-4, "u": 1e-2, "C": 2e-3},
                "bf16": {"rho": 1e-3, "u": 5e-2, "C": 1e-2}}
+# the mixed modes store the flow as the 16-bit modes do and the scalars in FP32: flow bounds
+# of the 16-bit mode, scalar bound of FP32 arithmetic carried by a 16-bit flow
+REDUCED_TOL["fp16s32"] = dict(REDUCED_TOL["fp16"])
+REDUCED_TOL["bf16s32"] = dict(REDUCED_TOL["bf16"])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp16s32", "bf16s32"])
 def test_reduced_precision_against_fp64_oracle(precision):
     cfg, geom, fields = inputs.dissolution_3d(shape=(16, 18, 24), radius=(2.0, 4.0), g=2e-3)
     cfg.update(geo_mode="none")

@@ -17,6 +17,9 @@ pytestmark = pytest.mark.gpu
 BOUND = {"fp32": {"rho": 1e-7, "u": 2e-6, "C": 3e-7},
          "fp16": {"rho": 1e-5, "u": 1e-3, "C": 3e-4},
          "bf16": {"rho": 6e-5, "u": 1e-2, "C": 3e-3}}
+# mixed storage (16-bit flow, FP32 scalars): no worse than the pure 16-bit mode on any field
+BOUND["fp16s32"] = dict(BOUND["fp16"])
+BOUND["bf16s32"] = dict(BOUND["bf16"])
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +35,7 @@ def fp64_reference():
     return cfg, geom, fields, ref
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp16s32", "bf16s32"])
 def test_storage_precision_errors_per_field(fp64_reference, precision):
     cfg, geom, fields, ref = fp64_reference
     s = Solver(dict(cfg, precision=precision))

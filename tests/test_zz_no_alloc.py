@@ -57,7 +57,7 @@ def _same_as_allocating_read(s):
     np.testing.assert_array_equal(h_only, h_ref)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16", "fp16s32"])
 def test_noalloc_matches_allocating_read_on_consecutive_calls(precision):
     s = _solver((10, 12, 16), precision)
     for steps in (3, 8):                      # odd then even layout parity
