@@ -438,7 +438,8 @@ __global__ void __launch_bounds__(256) k_detect(const Args a) {
   const unsigned int cnt = *a.iface_count;
   for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
     const long long n = a.iface_list[e];
-    if (a.flags[n] == FL_REACTIVE && consumed(a, a.acc[n])) push_flip(a, int(n));
+    // the flag is read only for the few nodes past the threshold (most of them flipped already)
+    if (consumed(a, a.acc[n]) && a.flags[n] == FL_REACTIVE) push_flip(a, int(n));
   }
 }
 
