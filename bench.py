@@ -683,6 +683,15 @@ def main():
         rho_h = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory().numpy()
         u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()
         C_h = torch.from_numpy(np.ascontiguousarray(C)).pin_memory().numpy() if s.n_scal else None
+        # the read-back lands in preallocated pinned buffers (Solver.fields(out=...))
+        sh = tuple(s.shape)
+
+        def pinned(shape, dt):
+            return torch.empty(shape, dtype=dt).pin_memory().numpy()
+
+        out_h = {"rho": pinned((s.n_comp,) + sh, torch.float64), "u": pinned((3,) + sh, torch.float64),
+                 "C": pinned((s.n_scal,) + sh, torch.float64), "flags": pinned(sh, torch.uint8),
+                 "acc": pinned(sh, torch.float64)}
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -691,7 +700,7 @@ def main():
         for _ in range(ke):
             s.step(1)
             s.sync()          # per-step read of the device status word (4 bytes)
-        out = s.fields()
+        out = s.fields(out=out_h)
         torch.cuda.synchronize()
         barrier()
         el, e2e_nodes = reduce_over_ranks(dist, dev, time.perf_counter() - t0, N * ke)
@@ -700,7 +709,7 @@ def main():
         e2e = {"value": e2e_nodes / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / ke,
                "d2h_bytes_per_step": d2h / ke, "steps": ke,
                "includes": "set_geometry + set_fields from pinned host memory, per-step lbm_step + "
-                           "lbm_sync (4-byte status read), final lbm_get_fields to host"}
+                           "lbm_sync (4-byte status read), final lbm_get_fields into pinned host memory"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

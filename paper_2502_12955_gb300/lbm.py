@@ -303,18 +303,24 @@ class Solver:
     def sync(self):
         self._ck(self.lib.lbm_sync(self.h))
 
-    def fields(self):
+    def fields(self, out=None):
+        """Macroscopic fields as a dict of arrays (rho, u, C, flags, acc; x fastest).  out may be
+        such a dict of preallocated C-contiguous arrays (float64; flags uint8) of the same shapes,
+        for example in pinned host memory, which are filled in place and returned."""
         nc, ns, N = self.n_comp, self.n_scal, self.N
-        rho = np.zeros((nc, N))
-        u = np.zeros((3, N))
-        Cs = np.zeros((max(ns, 1), N))
-        flags = np.zeros(N, dtype=np.uint8)
-        acc = np.zeros(N)
-        self._ck(self.lib.lbm_get_fields(self.h, _dp(rho), _dp(u), _dp(Cs),
-                                         flags.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(acc)))
         sh = self.shape
-        return {"rho": rho.reshape((nc,) + sh), "u": u.reshape((3,) + sh),
-                "C": Cs[:ns].reshape((ns,) + sh), "flags": flags.reshape(sh), "acc": acc.reshape(sh)}
+        if out is None:
+            out = {"rho": np.zeros((nc,) + sh), "u": np.zeros((3,) + sh), "C": np.zeros((ns,) + sh),
+                   "flags": np.zeros(sh, dtype=np.uint8), "acc": np.zeros(sh)}
+        want = {"rho": ((nc,) + sh, np.float64), "u": ((3,) + sh, np.float64), "C": ((ns,) + sh, np.float64),
+                "flags": (sh, np.uint8), "acc": (sh, np.float64)}
+        for k, (shape, dt) in want.items():
+            a = out[k]
+            if a.shape != shape or a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"fields(out): {k} must be a C-contiguous {np.dtype(dt).name} array of shape {shape}")
+        self._ck(self.lib.lbm_get_fields(self.h, _dp(out["rho"]), _dp(out["u"]), _dp(out["C"]) if ns else None,
+                                         out["flags"].ctypes.data_as(C.POINTER(C.c_uint8)), _dp(out["acc"])))
+        return out
 
     def save_fields(self, path):
         """Write the macroscopic fields (rho, u, C, flags, acc; x fastest) to an .npz file for
