@@ -235,6 +235,16 @@ lbm_status lbm_sync(lbm_ctx* ctx);
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u, double* C, uint8_t* flags,
                           double* acc);
 
+/* The same fields left on the device: computes them into the context's FP64 staging arrays and
+   returns device pointers (any output may be NULL): rho [n_comp][N], u [3][N], C [n_scal +
+   product][N] (NULL without scalars), flags [N] (uint8), acc [N], in the layouts of
+   lbm_get_fields.  The context owns the memory.  The arrays hold this call's values until the
+   next lbm_get_fields, lbm_get_fields_device or lbm_set_fields (which stage through them), the
+   flags and acc until the next step or geometry call.  The context's stream is synchronised
+   before return, so readers on any stream see complete values.  No host copy is made. */
+lbm_status lbm_get_fields_device(lbm_ctx* ctx, const double** rho, const double** u, const double** C,
+                                 const uint8_t** flags, const double** acc);
+
 /* Pre-collision populations at the current time, FP64, [n_comp][Qf][N] and
    [n_scal + product][Qc][N] (either may be NULL).  Reactive-link scalar slots hold the stored bounce-back value. */
 lbm_status lbm_get_pops(lbm_ctx* ctx, double* f, double* h);

@@ -852,6 +852,21 @@ lbm_status lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* C, uint8_t
   return LBM_OK;
 }
 
+lbm_status lbm_get_fields_device(lbm_ctx* c, const double** rho, const double** u, const double** C,
+                                 const uint8_t** flags, const double** acc) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (!c->fields_set) return fail(c, LBM_ERR_STATE, "fields were never set");
+  lbm_status st = run_moments(c);
+  if (st != LBM_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  if (rho) *rho = c->a.d_rho;
+  if (u) *u = c->a.d_u;
+  if (C) *C = c->nlat > 0 ? c->a.d_C : nullptr;
+  if (flags) *flags = c->a.flags;
+  if (acc) *acc = c->a.acc;
+  return LBM_OK;
+}
+
 lbm_status lbm_get_pops(lbm_ctx* c, double* f, double* h) {
   if (!c) return LBM_ERR_INVALID_ARG;
   const size_t N = (size_t)c->N;

@@ -30,7 +30,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ER
 
 # Names of every entry point declared in include/lbm.h.
 EXPORTS = ["lbm_params_default", "lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step",
-           "lbm_sync", "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_get_monitors",
+           "lbm_sync", "lbm_get_fields", "lbm_get_fields_device", "lbm_get_pops", "lbm_set_pops", "lbm_get_monitors",
            "lbm_residual", "lbm_get_state", "lbm_set_state", "lbm_profile_enable",
            "lbm_profile_read", "lbm_launch_count", "lbm_last_error", "lbm_destroy",
            "lbm_get_pops_noalloc", "lbm_ensemble_create", "lbm_ensemble_member", "lbm_ensemble_step",
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         lib.lbm_step.argtypes = [vp, C.c_int64]
         lib.lbm_sync.argtypes = [vp]
         lib.lbm_get_fields.argtypes = [vp, dp, dp, dp, P(C.c_uint8), dp]
+        lib.lbm_get_fields_device.argtypes = [vp, P(vp), P(vp), P(vp), P(vp), P(vp)]
         lib.lbm_get_pops.argtypes = [vp, dp, dp]
         lib.lbm_set_pops.argtypes = [vp, dp, dp]
         lib.lbm_get_pops_noalloc.argtypes = [vp, dp, dp]
@@ -219,6 +220,19 @@ def make_params(cfg: dict, lib=None) -> LbmParams:
     return p
 
 
+class DeviceArray:
+    """A device array owned by a Solver, exposed through the CUDA array interface (version 3).
+    Keeps its solver alive; the data stream is synchronised before it is handed out."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.ptr, self.shape, self.typestr, self._owner = int(ptr), tuple(shape), typestr, owner
+
+    @property
+    def __cuda_array_interface__(self):
+        return {"shape": self.shape, "typestr": self.typestr, "data": (self.ptr, False), "version": 3,
+                "strides": None, "stream": None}
+
+
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
 
@@ -320,6 +334,23 @@ class Solver:
                 raise ValueError(f"fields(out): {k} must be a C-contiguous {np.dtype(dt).name} array of shape {shape}")
         self._ck(self.lib.lbm_get_fields(self.h, _dp(out["rho"]), _dp(out["u"]), _dp(out["C"]) if ns else None,
                                          out["flags"].ctypes.data_as(C.POINTER(C.c_uint8)), _dp(out["acc"])))
+        return out
+
+    def fields_device(self):
+        """The fields left on the device (lbm_get_fields_device): a dict of objects exposing the
+        CUDA array interface (no copy; read them with torch.as_tensor(v, device="cuda") or any
+        consumer of that interface), in the layouts of fields().  They stay valid until the next
+        fields(), fields_device() or set_fields() (flags and acc: until the next step)."""
+        ptr = [C.c_void_p() for _ in range(5)]
+        self._ck(self.lib.lbm_get_fields_device(self.h, *[C.byref(p) for p in ptr]))
+        nc, ns, sh = self.n_comp, self.n_scal, self.shape
+        spec = {"rho": ((nc,) + sh, "<f8"), "u": ((3,) + sh, "<f8"), "C": ((ns,) + sh, "<f8"),
+                "flags": (sh, "|u1"), "acc": (sh, "<f8")}
+        out = {}
+        for (k, (shape, typestr)), p in zip(spec.items(), ptr):
+            if p.value is None:
+                continue
+            out[k] = DeviceArray(p.value, shape, typestr, self)
         return out
 
     def save_fields(self, path):
