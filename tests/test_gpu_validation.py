@@ -99,6 +99,73 @@ def test_contact_angle_against_oracle(g):
     assert abs(t_g - t_o) < 1e-6
 
 
+def _interface_heights(phi):
+    """Height of the interface (phi = rho_0 - rho_1 through its mid value) in every column: the
+    crossing nearest the box centre, linearly interpolated."""
+    ny, nx = phi.shape
+    mid = 0.5 * (phi.max() + phi.min())
+    sg = np.sign(phi - mid)
+    h = np.full(nx, np.nan)
+    for x in range(nx):
+        c = np.flatnonzero(sg[1:, x] != sg[:-1, x])
+        if c.size:
+            y0 = c[np.argmin(np.abs(c - ny / 2))]
+            p0, p1 = phi[y0, x] - mid, phi[y0 + 1, x] - mid
+            h[x] = y0 + p0 / (p0 - p1)
+    return h
+
+
+def _rti(heavy_top, nx, ny=512, g=1e-4, steps=20000, every=2000, amp=4.0):
+    """Two-component Rayleigh-Taylor case (reading of Sec. 3.2's RTI with a density contrast):
+    component 0 is made heavier by a self-cohesion G_00 = -0.3 (psi = rho), the cross coupling
+    G_01 = 2.7 separates the components, gravity g acts on both (F = rho g), walls at y = -1/2 and
+    ny - 1/2, periodic x.  A single-mode interface y = ny/2 + amp cos(2 pi x / nx).  Returns
+    (t, amplitude of that mode, total density in the heavy and light bulk) every `every` steps."""
+    cfg = dict(dim=2, nx=nx, ny=ny, nz=1, n_comp=2, tau=[1.0, 1.0], G=[[-0.3, 2.7], [2.7, 0.0]],
+               psi_kind="identity", g=[0.0, -g, 0.0], periodic=[1, 0, 1], precision="fp32")
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    top = yy >= ny / 2 + amp * np.cos(2 * np.pi * (xx + 0.5) / nx)
+    heavy = top if heavy_top else ~top
+    rho = np.stack([np.where(heavy, 1.3, 0.03), np.where(heavy, 0.03, 1.0)])[:, None]
+    s = Solver(cfg)
+    s.set_geometry(np.zeros((1, ny, nx), np.uint8))
+    s.set_fields(rho, np.zeros((3, 1, ny, nx)), None)
+    out = []
+    for t in range(every, steps + 1, every):
+        s.step(every)
+        r = s.fields()["rho"][:, 0]
+        h = _interface_heights(r[0] - r[1])
+        a1 = 2.0 * abs(np.fft.rfft(np.nan_to_num(h - np.nanmean(h)))[1]) / nx
+        tot = r[0] + r[1]
+        hi, lo = (tot[3 * ny // 4].mean(), tot[ny // 4].mean()) if heavy_top else (tot[ny // 4].mean(), tot[3 * ny // 4].mean())
+        out.append((t, float(a1), float(hi), float(lo)))
+    s.close()
+    return out
+
+
+def test_rayleigh_taylor_instability():
+    """Heavy fluid on top with a wavelength above the capillary cutoff: the mode grows
+    exponentially, at a rate below the inviscid, tension-free sqrt(A g k) (viscosity and surface
+    tension only slow it) and above half of it, and the spike of heavy fluid then reaches the
+    bottom.  The same mode with the heavy fluid below does not grow, and with heavy fluid on top
+    a wavelength below the cutoff (128 against about 270) decays: surface tension stabilises it."""
+    g, nx = 1e-4, 512
+    a = _rti(True, nx, g=g)
+    amp = {t: a1 for t, a1, _, _ in a}
+    assert amp[20000] > 10.0 * amp[4000], amp
+    rate = np.log(amp[16000] / amp[8000]) / 8000.0
+    _, _, hi, lo = a[1]                       # bulk densities at step 4000
+    A = (hi - lo) / (hi + lo)
+    inviscid = np.sqrt(A * g * 2.0 * np.pi / nx)
+    print(f"RTI: Atwood {A:.3f}, growth rate {rate:.3e} per step, sqrt(A g k) {inviscid:.3e}, "
+          f"amplitudes {[round(v, 2) for v in amp.values()]}")
+    assert 0.5 * inviscid < rate < inviscid, (rate, inviscid)
+    b = _rti(False, nx, g=g)
+    assert max(a1 for _, a1, _, _ in b) <= 4.0, b
+    c = _rti(True, 128, g=g)
+    assert c[-1][1] < 0.1, c
+
+
 def _coexistence_3d(G, steps=6000):
     """Bulk densities of the two phases across flat interfaces in a periodic 3D slab."""
     nx = 64
