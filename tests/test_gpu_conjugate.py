@@ -166,3 +166,22 @@ def test_conjugate_state_is_not_checkpointed():
     with pytest.raises(LbmError):
         s.get_state()
     s.close()
+
+
+def test_conjugate_sphere_packing_400_steps():
+    """A 32^3 sphere packing of the dissolution recipe with the temperature-dependent rate, heat
+    release and conduction in the solid, MRT, dissolving (V_m = 1: 40 % of the solid nodes turn
+    fluid within the 400 steps): every field, population and monitor at steps 200 and 400."""
+    cfg, geom, (rho, u, C) = inputs.dissolution_3d(shape=(32, 32, 32), g=2e-4, radius=(3.0, 6.0), precision="fp64")
+    cfg.update(n_scal=2, tau_c=[0.6, 0.8], C_in=[1.0, 1.0], C_ref=[1.0, 1.0], arrhenius=True, arr_A=0.3,
+               arr_Ta=0.8, heat_release=0.03, n_it=24, conjugate=True, tau_s=0.7, c_fs=0.6, V_m=1.0)
+    T = np.ones_like(C) + 0.1 * (geom[None] != 0)
+    o, g = make_pair(cfg, geom, (rho, u, np.concatenate([C, T])))
+    done = 0
+    for target in (200, 400):
+        o.step(target - done)
+        g.step(target - done)
+        done = target
+        compare(o, g, what=f"conjugate packing step {target}")
+    m = o.monitors()
+    assert m["heat_src"] > 0 and m["tsolid"] > 0
