@@ -7,7 +7,7 @@ A "step" is one time step of the whole path (fused collide-stream, interface det
 flips, monitors every N_mon steps).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload dissolution|droplet|channel] [--precision fp32|fp16|bf16|fp64]
+                  [--workload dissolution|droplet|channel|combustion] [--precision fp32|fp16|bf16|fp64|fp16s32|bf16s32]
                   [--size S] [--no-e2e] [--no-cpu]
   python bench.py --workload dissolution --size 128 --to-steady 1e-6
                   (time to steady state from rest, geometry frozen; its own JSON line)
@@ -52,6 +52,11 @@ def workload(name, size, precision):
     elif name == "channel":
         cfg, geom, fields = inputs.reactive_channel_2d(precision=precision)
         label = f"channel2d_128x64_d2q9_d2q5_{precision}"
+    elif name == "combustion":
+        # the paper's reactive porous channel (Sec. 3.4) at its 420 x 80: velocity inlet, O2,
+        # temperature and CO2 lattices, temperature-dependent rate, conduction in the solid
+        cfg, geom, fields = inputs.combustion_channel_2d(precision=precision)
+        label = f"combustion2d_420x80_d2q9_3xd2q5_conjugate_{precision}"
     else:
         raise SystemExit(f"unknown workload {name}")
     cfg = dict(cfg, precision=precision, N_mon=100)
@@ -66,12 +71,14 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage, f32 math", "bf16": 
 
 
 def bytes_per_fluid_node(cfg):
-    """Algorithmic HBM bytes per fluid node and step: one read and one write of every
-    population of every lattice."""
+    """Algorithmic HBM bytes per fluid node and step of the step kernel: one read and one write of
+    every population of every fluid lattice (the reaction product's included).  The solid
+    thermal lattice of conduction in the solid lives at solid nodes and has its own kernel."""
     q = 19 if cfg["dim"] == 3 else 9
     qc = 7 if cfg["dim"] == 3 else 5
     ef, es = ELEM[cfg["precision"]]
-    return 2 * (ef * q * cfg.get("n_comp", 1) + es * qc * cfg.get("n_scal", 0))
+    n_lat = cfg.get("n_scal", 0) + (1 if cfg.get("product") else 0)
+    return 2 * (ef * q * cfg.get("n_comp", 1) + es * qc * n_lat)
 
 
 def source_hash():
@@ -179,6 +186,9 @@ def oracle_sample(name, precision, seconds=10.0, sample_n=64, steps=None, warmup
     elif name == "droplet":
         cfg, geom, fields = inputs.droplet_3d(n=sample_n, radius=sample_n / 8.0, precision="fp64")
         sample = f"droplet 3D {sample_n}^3, two components, FP64 oracle"
+    elif name == "combustion":
+        cfg, geom, fields = inputs.combustion_channel_2d(precision="fp64")
+        sample = "combustion channel 2D 420x80 (the same input), FP64 oracle"
     else:
         cfg, geom, fields = inputs.reactive_channel_2d(precision="fp64")
         sample = "channel 2D 128x64, FP64 oracle"
@@ -265,7 +275,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="dissolution",
-                    choices=["dissolution", "droplet", "channel", "ensemble", "nn"])
+                    choices=["dissolution", "droplet", "channel", "combustion", "ensemble", "nn"])
     ap.add_argument("--members", type=int, default=32,
                     help="ensemble workload: members, half 2D squares and half 3D cubes (512 = the full set)")
     ap.add_argument("--precision", default=None)
