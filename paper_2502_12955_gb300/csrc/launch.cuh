@@ -253,12 +253,18 @@ struct Launchers {
     return cudaGetLastError();
   }
 
+  // grid-stride kernels over the box (k_solid) and the fluid list (k_exchange): two waves of
+  // blocks, fewer on a small domain
+  static unsigned int box_blocks(const Args& a) {
+    const long long need = (a.N + 255) / 256, cap = 2ll * wave_blocks();
+    return (unsigned int)(need < cap ? (need > 0 ? need : 1) : cap);
+  }
   static cudaError_t solid(const Args& a, int parity, cudaStream_t st) {
-    k_solid<L, S><<<wave_blocks() * 2, 256, 0, st>>>(a, coef(a), parity);
+    k_solid<L, S><<<box_blocks(a), 256, 0, st>>>(a, coef(a), parity);
     return cudaGetLastError();
   }
   static cudaError_t exchange(const Args& a, int parity_next, cudaStream_t st) {
-    k_exchange<L, S><<<wave_blocks() * 2, 256, 0, st>>>(a, coef(a), parity_next);
+    k_exchange<L, S><<<box_blocks(a), 256, 0, st>>>(a, coef(a), parity_next);
     return cudaGetLastError();
   }
   static cudaError_t solid_init(const Args& a, cudaStream_t st) {
