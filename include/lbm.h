@@ -152,7 +152,7 @@ typedef struct lbm_params {
                                  at a reactive link, whose k the next step's species closure uses.
                                  Faces that are not periodic for the scalars reflect.  Row 1 of the
                                  fields (set and get) is the solid temperature at solid nodes.  Not
-                                 with deposition, in ensembles or in checkpoints. */
+                                 with deposition or in ensembles; checkpoints carry the solid lattice. */
   double tau_s;               /* relaxation time of the solid thermal lattice (> 0.5) */
   double c_fs;                /* heat-capacity ratio (rho c_p)_fluid / (rho c_p)_solid (> 0) */
 } lbm_params;

@@ -1053,16 +1053,22 @@ struct StateHeader {
   int32_t version, lattice, precision, n_comp, n_scal, nx, ny, nz;
   int64_t step;
 };
+// bytes of the solid thermal lattice's state (conduction in the solid): both node-indexed copies,
+// the exchange's rate constants, the two heat banks and the removed-solid monitor
+size_t solid_state_bytes(const lbm_ctx* c) {
+  if (!c->p.conjugate) return 0;
+  const size_t N = (size_t)c->N, e = (size_t)c->ks->psi_bytes;
+  return (2 * c->Qc + (c->Qc - 1)) * N * e + 2 * WALLX_SLOTS * 8 + 8;
+}
 size_t state_bytes(const lbm_ctx* c) {
   const size_t N = (size_t)c->N, P = (size_t)c->pitch, rows = (size_t)c->ny * c->nz;
   return sizeof(StateHeader) + (c->p.n_comp * c->Qf * c->elem + c->nlat * c->Qc * c->elem_h) * P +
-         (N + 3) / 4 * 4 + N * 8 + 3 * WALLX_SLOTS * 8 + 6 * rows * 8 + 10 * 8;
+         (N + 3) / 4 * 4 + N * 8 + 3 * WALLX_SLOTS * 8 + 6 * rows * 8 + 10 * 8 + solid_state_bytes(c);
 }
 }  // namespace
 
 lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   if (!c || !nbytes) return LBM_ERR_INVALID_ARG;
-  if (c->p.conjugate) return fail(c, LBM_ERR_INVALID_ARG, "checkpoints do not hold the solid thermal lattice (conjugate)");
   const size_t need = state_bytes(c);
   if (!host) {
     *nbytes = need;
@@ -1096,7 +1102,17 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
   CK(cudaMemcpyAsync(o, c->a.wallx_slot, 3 * WALLX_SLOTS * 8, cudaMemcpyDeviceToHost, c->stream)); o += 3 * WALLX_SLOTS * 8;
   CK(cudaMemcpyAsync(o, c->a.inflow_row, 3 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 3 * rows * 8;
   CK(cudaMemcpyAsync(o, c->a.outflow_row, 3 * rows * 8, cudaMemcpyDeviceToHost, c->stream)); o += 3 * rows * 8;
-  CK(cudaMemcpyAsync(o, c->a.flip_mon, 80, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(o, c->a.flip_mon, 80, cudaMemcpyDeviceToHost, c->stream)); o += 80;
+  if (c->p.conjugate) {
+    const size_t gsb = (size_t)c->Qc * N * c->ks->psi_bytes, kbb = (size_t)(c->Qc - 1) * N * c->ks->psi_bytes;
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaMemcpyAsync(o, c->a.gs[b], gsb, cudaMemcpyDeviceToHost, c->stream)); o += gsb;
+    }
+    CK(cudaMemcpyAsync(o, c->a.kb, kbb, cudaMemcpyDeviceToHost, c->stream)); o += kbb;
+    CK(cudaMemcpyAsync(o, c->a.wallx_slot + BANK_HEAT_S * WALLX_SLOTS, 2 * WALLX_SLOTS * 8, cudaMemcpyDeviceToHost,
+                       c->stream)); o += 2 * WALLX_SLOTS * 8;
+    CK(cudaMemcpyAsync(o, c->a.flip_mon + 10, 8, cudaMemcpyDeviceToHost, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   *nbytes = need;
   return LBM_OK;
@@ -1104,7 +1120,6 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host, size_t* nbytes) {
 
 lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   if (!c || !host) return LBM_ERR_INVALID_ARG;
-  if (c->p.conjugate) return fail(c, LBM_ERR_INVALID_ARG, "checkpoints do not hold the solid thermal lattice (conjugate)");
   const size_t need = state_bytes(c);
   if (nbytes != need) return fail(c, LBM_ERR_INVALID_ARG, "state has %zu bytes, expected %zu", nbytes, need);
   const uint8_t* o = static_cast<const uint8_t*>(host);
@@ -1130,7 +1145,17 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host, size_t nbytes) {
   CK(cudaMemcpyAsync(c->a.wallx_slot, o, 3 * WALLX_SLOTS * 8, cudaMemcpyHostToDevice, c->stream)); o += 3 * WALLX_SLOTS * 8;
   CK(cudaMemcpyAsync(c->a.inflow_row, o, 3 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 3 * rows * 8;
   CK(cudaMemcpyAsync(c->a.outflow_row, o, 3 * rows * 8, cudaMemcpyHostToDevice, c->stream)); o += 3 * rows * 8;
-  CK(cudaMemcpyAsync(c->a.flip_mon, o, 80, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->a.flip_mon, o, 80, cudaMemcpyHostToDevice, c->stream)); o += 80;
+  if (c->p.conjugate) {
+    const size_t gsb = (size_t)c->Qc * N * c->ks->psi_bytes, kbb = (size_t)(c->Qc - 1) * N * c->ks->psi_bytes;
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaMemcpyAsync(c->a.gs[b], o, gsb, cudaMemcpyHostToDevice, c->stream)); o += gsb;
+    }
+    CK(cudaMemcpyAsync(c->a.kb, o, kbb, cudaMemcpyHostToDevice, c->stream)); o += kbb;
+    CK(cudaMemcpyAsync(c->a.wallx_slot + BANK_HEAT_S * WALLX_SLOTS, o, 2 * WALLX_SLOTS * 8, cudaMemcpyHostToDevice,
+                       c->stream)); o += 2 * WALLX_SLOTS * 8;
+    CK(cudaMemcpyAsync(c->a.flip_mon + 10, o, 8, cudaMemcpyHostToDevice, c->stream));
+  }
   CK(cudaMemsetAsync(c->a.flip_count, 0, 16, c->stream));
   CK(cudaMemsetAsync(c->a.err, 0, 16, c->stream));
   lbm_status st = rebuild_geometry(c, false);

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2502_12955_gb300 import inputs
-from paper_2502_12955_gb300.lbm import LbmError, Solver
+from paper_2502_12955_gb300.lbm import Solver
 from tests.gpu_common import compare, make_pair, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -157,14 +157,27 @@ def test_conjugate_fp32_tracks_fp64():
     assert abs(g.monitors()["tsolid"] - o.monitors()["tsolid"]) <= 1e-5 * abs(o.monitors()["tsolid"])
 
 
-def test_conjugate_state_is_not_checkpointed():
+def test_conjugate_checkpoint_resume_is_bitwise():
+    """The checkpoint carries the solid thermal lattice (both copies), the exchange's rate
+    constants and the heat monitors: resuming reproduces the uninterrupted run bit for bit, at
+    both layout parities."""
     shape = (1, 14, 18)
     geom = inputs.random_solids(shape, 0.22, seed=80, reactive_fraction=0.6)
-    s = Solver(dict(WALLS_2D, precision="fp64"))
+    s = Solver(dict(WALLS_2D, precision="fp32", product=True, tau_p=1.2))
     s.set_geometry(geom)
-    s.set_fields(*_fields(shape, 2, 81, T_solid=1.3))
-    with pytest.raises(LbmError):
-        s.get_state()
+    s.set_fields(*_fields(shape, 3, 81, T_solid=1.3))
+    for first in (30, 2):   # checkpoints at steps 30 and 53
+        s.step(first)
+        blob = s.get_state()
+        s.step(21)
+        fa, ma = s.fields(), s.monitors()
+        s.set_state(blob)
+        s.step(21)
+        fb, mb = s.fields(), s.monitors()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), (first, k)
+        for k in ("tsolid", "heat", "heat_s", "heat_src", "produced", "wallx"):
+            assert ma[k] == mb[k], (first, k)
     s.close()
 
 
