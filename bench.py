@@ -615,6 +615,8 @@ def main():
         if rank == 0:
             run_nn(args, local)
         return
+    if args.warm_start and args.to_steady is None:
+        args.to_steady = 1e-6   # the warm start is judged by the time to r <= 1e-6
     if args.to_steady is not None:
         if rank == 0:
             (run_warm_start if args.warm_start else run_to_steady)(args, local)
