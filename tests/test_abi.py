@@ -146,7 +146,6 @@ def test_null_context_calls_fail_cleanly():
 
 
 @pytest.mark.parametrize("bad", [dict(precision="fp16"), dict(geo_mode="dissolve", n_scal=1),
-                                 dict(n_scal=2, arrhenius=True, conjugate=True),
                                  dict(G=[[-5.0, 0], [0, 0]]), dict(forcing="sc_shift"), dict(collision="mrt")])
 def test_ensemble_create_rejects_mixed_or_unsupported_members(bad):
     lib = lbm.load()
@@ -192,3 +191,17 @@ def test_missing_library_fails_loudly(tmp_path):
                        timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "not found" in r.stdout
+
+
+@pytest.mark.parametrize("extra", [dict(conjugate=True), dict(product=True)])
+def test_ensemble_rejects_conduction_in_the_solid_and_the_product(extra):
+    lib = lbm.load()
+    base = dict(dim=2, nx=8, ny=8, precision="fp32", n_scal=2, tau_c=[0.7, 0.8], arrhenius=True, arr_A=0.1)
+    ps = (lbm.LbmParams * 2)()
+    ps[0] = lbm.make_params(base, lib)
+    ps[1] = lbm.make_params(dict(base, **extra), lib)
+    dims = (C.c_int32 * 6)(8, 8, 1, 8, 8, 1)
+    h = C.c_void_p()
+    assert lib.lbm_ensemble_create(lbm.LBM_D2Q9_D2Q5, 2, dims, ps, C.byref(h)) == -1 and not h.value
+    msg = lib.lbm_ensemble_last_error(None)
+    assert b"member 1" in msg and (b"solid" in msg or b"product" in msg), msg
