@@ -297,6 +297,8 @@ def parse():
     ap.add_argument("--train-samples", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--test-samples", type=int, default=4)
+    ap.add_argument("--net-width", default="",
+                    help="warm start: channel widths of the encoder levels and the bottleneck, e.g. 16,32,64,160")
     ap.add_argument("--no-augment", action="store_true",
                     help="warm start: train on the samples only, without their y-z symmetric copies")
     return ap.parse_args()
@@ -554,7 +556,8 @@ def run_warm_start(args, local):
     t0 = time.perf_counter()
     samples, gen = warmstart.generate(args.train_samples, n=n, tol=1e-5, device=local)
     t_gen = time.perf_counter() - t0
-    net = surrogate.WarmStartNet(device=local)
+    width = tuple(int(v) for v in args.net_width.split(",")) if args.net_width else (16, 32, 64, 160)
+    net = surrogate.WarmStartNet(width=width, device=local)
     t0 = time.perf_counter()
     hist = warmstart.train(net, samples, args.epochs, augment=not args.no_augment)
     torch.cuda.synchronize()
@@ -581,7 +584,7 @@ def run_warm_start(args, local):
             "dtype": "f32 LBM; network bf16 weights and activations, f32 accumulate",
             "data": "synthetic (seeded sphere packings, dissolution recipe), geometry update frozen",
             "config": {"workload": f"dissolution3d_{n}^3_warm_start", "train_samples": args.train_samples,
-                       "epochs": args.epochs, "params": net.n_params, "held_out_seeds": seeds,
+                       "epochs": args.epochs, "params": net.n_params, "held_out_seeds": seeds, "width": list(width),
                        "augment_yz_symmetries": not args.no_augment},
             "train_loss_first_last": [hist[0], hist[-1]], "generate_s": t_gen, "train_s": t_train,
             "train_steps_mean": float(np.mean([g["steps"] for g in gen if g["converged"]])),
