@@ -340,7 +340,8 @@ class Solver:
         """The fields left on the device (lbm_get_fields_device): a dict of objects exposing the
         CUDA array interface (no copy; read them with torch.as_tensor(v, device="cuda") or any
         consumer of that interface), in the layouts of fields().  They stay valid until the next
-        fields(), fields_device() or set_fields() (flags and acc: until the next step)."""
+        fields(), fields_device() or set_fields() (flags and acc: until the next step), and never
+        after close()."""
         ptr = [C.c_void_p() for _ in range(5)]
         self._ck(self.lib.lbm_get_fields_device(self.h, *[C.byref(p) for p in ptr]))
         nc, ns, sh = self.n_comp, self.n_scal, self.shape
