@@ -96,13 +96,15 @@ def droplet_fields(shape, radius: float, rho_in: float = 1.0, rho_out: float = 0
     return rho, u
 
 
-def sessile_droplet_2d(nx=200, ny=80, radius=30.0, G=2.7, g_ads=0.0, precision="fp32"):
+def sessile_droplet_2d(nx=200, ny=80, radius=30.0, G=2.7, g_ads=0.0, precision="fp32", rho_solid=0.0):
     """Two-component Shan-Chen sessile droplet for the contact angle (Sec. 3.2, contact angle):
     a half disc of component 0 (density 1.0, 0.05 of component 1) centred on the bottom wall
     (the halfway face y = -1/2 of a closed y axis), component 1 elsewhere; psi = rho, cross
-    cohesion G, adhesion G_ads = (g, -g), periodic x, tau 1."""
+    cohesion G, adhesion G_ads = (g, -g), periodic x, tau 1.  Solid nodes carry
+    psi(rho_solid) in the cohesion sums (0: the wall interacts through G_ads alone)."""
     cfg = dict(dim=2, nx=nx, ny=ny, nz=1, n_comp=2, tau=[1.0, 1.0], G=[[0.0, G], [G, 0.0]],
-               psi_kind="identity", G_ads=[g_ads, -g_ads], periodic=[1, 0, 1], precision=precision)
+               psi_kind="identity", G_ads=[g_ads, -g_ads], periodic=[1, 0, 1], precision=precision,
+               rho_solid=rho_solid)
     yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
     inside = (xx - nx / 2.0) ** 2 + (yy + 0.5) ** 2 < radius * radius
     rho = np.empty((2, 1, ny, nx))
