@@ -4,7 +4,7 @@ concentration of the reactive porous-media workload from its geometry and transp
 The lattice Boltzmann step (lbm.py) then starts from the prediction instead of from rest and
 relaxes it to its own steady state; its residual, not the network, decides convergence, so a
 poor prediction costs steps but never accuracy.  Plain LBM from rest stays the fallback and the
-judge of the network's error.
+arbiter of the network's error.
 
 Binding: the `lbm_nn_*` functions below carry the C ABI's names (include/lbm_nn.h) and only
 marshal torch tensors into device pointers; every operation runs in liblbm.so's sm_103a kernels
